@@ -1,0 +1,323 @@
+"""Benchmark of the CGKS-5 S2O4 step on GB300 (one JSON line on rank 0).
+
+Metric: cell-updates/s per S2O4 step (cells x steps / time) on the 3-D
+Taylor-Green vortex (Ma 0.1, Re 1600, Pr 0.72, gamma 1.4) on a periodic
+uniform [0, 2 pi]^3 mesh, 128^3 by default, plain FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv128|tgv256|vortex64]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+A step is one full S2O4 step (time-step reduction, two stages of
+reconstruction + interface flux + update) over the whole mesh.  The state
+(1.3 GB at 128^3) is larger than the 129 MB L2, so no flush is needed between
+steps.  For N > 1 (torchrun) every rank advances an independent replica
+(the path needs no exchange on one GPU per replica): weak scaling.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "tgv128": dict(dim=3, n=(128, 128, 128), desc="3-D Taylor-Green vortex 128^3, Ma 0.1, Re 1600, Pr 0.72, FP64"),
+    "tgv256": dict(dim=3, n=(256, 256, 256), desc="3-D Taylor-Green vortex 256^3, Ma 0.1, Re 1600, Pr 0.72, FP64"),
+    "vortex64": dict(dim=2, n=(64, 64), desc="2-D isentropic vortex 64^2 over [0,10]^2, eps 5"),
+}
+
+# FP64 work per unit of the dominant kernels, counted from the executed FP64
+# instructions (ncu, sass op counters) on a small case of the same kernels:
+# flops = 2 x DFMA + DADD + DMUL (+ the multi-instruction sequences of
+# division, sqrt and the special functions counted as executed).
+FLOPS_PER_UNIT = {
+    ("recon", 3): None,  # per cell
+    ("flux", 3): None,   # per face Gauss point
+}
+
+
+# kernels launched per S2O4 step: time-step reduction (reset, rate, final),
+# two stages x (reconstruction, interface flux, update), time advance
+KERNELS_PER_STEP = 3 + 2 * 3 + 1
+
+
+def mesh_kwargs(wl):
+    if wl.startswith("tgv"):
+        return dict(lo=(0.0, 0.0, 0.0), hi=(2 * math.pi,) * 3, mu=1.0 / 1600.0, prandtl=0.72, tau_mode=2, cfl=0.5)
+    return dict(lo=(0.0, 0.0), hi=(10.0, 10.0), tau_mode=0, cfl=0.5)
+
+
+def field_fn(wl):
+    import synth
+    if wl.startswith("tgv"):
+        return lambda x, y, z: synth.taylor_green_3d(x, y, z, mach=0.1)
+    return lambda x, y: synth.isentropic_vortex_2d(x, y)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.rows.append([x.strip() for x in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._th.join(timeout=10)
+
+    def summary(self):
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for i, nme in enumerate(names):
+                    if r[5 + i].lower() == "active":
+                        reasons.add(nme)
+            except (ValueError, IndexError):
+                continue
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp64_alu_peak_tflops(sm_count=152, sm_mhz=2070.0):
+    """FP64 FMA pipe peak from unit counts and clock: 2 FP64 FMA per clock per SM
+    on GB300 (the probe of this project measured 1.19-1.20 TFLOP/s, 95% of it)."""
+    return sm_count * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def cpu_baseline(wl, sample_cells=None):
+    """Time the CPU oracle, as it stands, on a bounded sample of the workload:
+    the same analytic field and physics on a smaller periodic mesh (same
+    per-cell work), whole S2O4 steps."""
+    import oracle.oracle as o
+    spec = WORKLOADS[wl]
+    dim = spec["dim"]
+    kw = mesh_kwargs(wl)
+    if dim == 3:
+        m = sample_cells or 24
+        n = (m, m, m)
+    else:
+        n = (64, 64)
+    orc = o.Oracle(dim, n, **kw)
+    orc.init(field_fn(wl))
+    orc.step(1)  # warm-up (builds tables, touches memory)
+    steps = 2 if dim == 3 else 20
+    t0 = time.perf_counter()
+    orc.step(steps)
+    el = time.perf_counter() - t0
+    ncell = int(math.prod(n))
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": ncell * steps / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+            "sample": "%s on %s (%d cells, same per-cell work), %d S2O4 steps, %.1f s" % (
+                spec["desc"].split(",")[0], "x".join(map(str, n)), ncell, steps, el)}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle timed on the host cores."""
+    if rank != 0:
+        return 0
+    wl = args.workload
+    spec = WORKLOADS[wl]
+    import oracle.oracle as o
+    dim = spec["dim"]
+    kw = mesh_kwargs(wl)
+    n = (20, 20, 20) if dim == 3 else (64, 64)
+    orc = o.Oracle(dim, n, **kw)
+    orc.init(field_fn(wl))
+    for _ in range(args.warmup):
+        orc.step(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.step(1)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    ncell = int(math.prod(n))
+    val = ncell * args.steps / tot
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": "cell-updates/s per S2O4 step", "value": val, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl, "description": spec["desc"], "sample_mesh": "x".join(map(str, n)),
+                   "note": "CPU oracle (plain FP64 C, OpenMP) on a bounded sample of the workload"},
+        "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": "%s cells, %d steps" % ("x".join(map(str, n)), args.steps)},
+        "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tgv128", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2508_08965_gb300 import Mesh
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = args.workload
+    spec = WORKLOADS[wl]
+    stream = torch.cuda.Stream()
+    mesh = Mesh(spec["dim"], spec["n"], stream=stream, **mesh_kwargs(wl))
+    mesh.init(field_fn(wl))
+    ncell = mesh.ncell
+    for _ in range(args.warmup):
+        mesh.step(1)
+    # timed region: K whole steps on the context stream, profiled per kernel
+    mesh.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        mesh.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = world * ncell * args.steps / (ms / 1e3)
+
+    # end to end through the C-ABI with host buffers: every step copies the
+    # state in from pinned host memory, steps, and copies the new state out
+    shape = mesh.state_shape
+    h_in = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+    h_out = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+    mesh.get_state(h_in.numpy())
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        mesh.set_state(h_in.numpy(), 0.0)
+        mesh.step(1)
+        mesh.get_state(h_out.numpy())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_s = float(e2e_t.item())
+    state_bytes = int(np.prod(shape)) * 8
+
+    peaks = measured_peaks()
+    sm_mhz = clk.summary()["sm_max_mhz"] or 2070.0
+    # dominant kernel and its FP64 roofline
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, tot_ms) = dom
+    avg_ms = tot_ms / max(launches, 1)
+    fpu = FLOPS_PER_UNIT.get((name, spec["dim"]))
+    units = ncell if name in ("recon", "update", "dt") else ncell * spec["dim"] * (4 if spec["dim"] == 3 else 2)
+    peak = fp64_alu_peak_tflops(sm_mhz=2070.0)
+    if fpu:
+        achieved = fpu * units / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz (derived; probe 1.19-1.20)"}
+    else:
+        roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "note": "flops per unit not yet counted"}
+    kernels = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)}
+               for k, v in prof.items()}
+
+    line = {
+        "metric": "cell-updates/s per S2O4 step", "value": value, "unit": "cell-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl, "description": spec["desc"], "cells": ncell,
+                   "l2": "state (%.2f GB) larger than L2; no flush" % (state_bytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": world * ncell * args.e2e_steps / e2e_s, "unit": "cell-updates/s",
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": args.steps * KERNELS_PER_STEP,
+        "kernels": kernels,
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        except Exception as e:  # the oracle is a reported baseline only
+            line["cpu_baseline"] = {"error": str(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    mesh.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,136 @@
+/*
+ * cgks.h -- C-ABI of the GB300 CGKS-5 library: the per-stage sweep of the
+ * fifth-order compact gas-kinetic scheme of arXiv 2508.08965 on one GPU.
+ *
+ * One S2O4 step (temporal discretisation section) runs two stages; each stage
+ *   (a) reconstructs, on the standard reference cell (Sec. 4), the quartic
+ *       compact polynomial of Eq. (compact-big-ref) from cell averages,
+ *       cell-averaged gradients and line-averaged derivatives, blended with
+ *       the six linear sub-stencil polynomials by the GENO path function
+ *       (Eq. weno-new and the path function of Sec. 3.3);
+ *   (b) evaluates the gas-kinetic time-dependent interface solution
+ *       (Eq. flux) at the 2x2 (3-D) or 2 (2-D) Gauss points of every face and
+ *       takes its moments (Eqs. deri-t-f, deri-t-q);
+ *   (c) updates cell averages by S2O4 and cell/line-averaged derivatives from
+ *       the evolved interface values (Eqs. derivative, derivative-l).
+ *
+ * Problem statement: conservative variables Q = (rho, rho U, rho V[, rho W],
+ * rho E) of an ideal gas (Sec. 2), E = |U|^2/2 + p/((gamma-1) rho);
+ * Navier-Stokes through the collision time tau = mu/p (Sec. 6).
+ *
+ * State layout (host and device buffers alike): structure of arrays of
+ * doubles, state[(f * nv + v) * ncell + cell], cell = i + n0*(j + n1*k),
+ * nv = dim + 2 variables and nf = 1 + dim + L fields per variable:
+ *   f = 0          cell average,
+ *   f = 1..dim     cell-averaged gradient (physical coordinates),
+ *   f = 1+dim+s    line-averaged derivative s = axis*gpf + k (gpf = 4 in 3-D,
+ *                  2 in 2-D): difference of the values at the paired Gauss
+ *                  points k of the cell's two faces normal to `axis`, divided
+ *                  by their physical distance (Eq. derivative-l).
+ * Gauss point k of a face: tangential axes (a, b) in increasing order,
+ * coordinate along a is 1/2 - g for even k and 1/2 + g for odd k, along b
+ * 1/2 - g for k < 2 and 1/2 + g otherwise, g = 1/(2 sqrt 3).
+ *
+ * Conventions: every call returns a cgks_status; on error the message is kept
+ * for cgks_last_error.  The caller owns every buffer it passes; the library
+ * copies from/to them and owns all device memory it allocates.  Calls on one
+ * context are not thread-safe.  All work is queued on the context's stream.
+ */
+#ifndef CGKS_H
+#define CGKS_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CGKS_OK = 0,
+  CGKS_EINVAL = -1,      /* invalid argument */
+  CGKS_ENOMEM = -2,      /* device allocation failed */
+  CGKS_ECUDA = -3,       /* a CUDA runtime call failed */
+  CGKS_ENONPHYS = -4,    /* non-positive density/pressure that even chi = 0 cannot cure */
+  CGKS_ETIMEOUT = -5,    /* reserved: a bounded device wait gave up */
+  CGKS_ESTATE = -6,      /* call made in the wrong state */
+  CGKS_EUNSUPPORTED = -7 /* option not available in this build */
+} cgks_status;
+
+enum { CGKS_BC_PERIODIC = 0 };
+
+/* Mesh and physics description.  Uniform box when nodes == NULL. */
+typedef struct {
+  int dim;              /* 2 or 3 */
+  int n[3];             /* cells per axis (n[2] ignored in 2-D) */
+  const double* nodes;  /* host, (n0+1)(n1+1)[(n2+1)] x dim node coordinates, i fastest,
+                           or NULL for the box [lo, hi]; copied */
+  double lo[3], hi[3];
+  int bc[6];            /* boundary kinds per face (-x,+x,-y,+y,-z,+z); periodic only */
+  double gamma;         /* specific heat ratio */
+  double mu;            /* dynamic viscosity; 0 = inviscid */
+  double prandtl;       /* Prandtl number for the heat-flux correction (used when mu > 0) */
+  int tau_mode;         /* collision time (Sec. 6): 0 tau = 0; 1 inviscid shock
+                           capturing 0.05 dt + 5 |dp|/(sum p) dt; 2 viscous mu/p + 5 |dp|/(sum p) dt */
+  double cfl;           /* CFL number (0.5 in the paper) */
+  double dt_fixed;      /* > 0: constant time step instead of the CFL rule */
+  int linear;           /* 1: linear CGKS-5 (chi = 1) */
+  double c_chi;         /* GENO path-function constant C (<= 0: default 100) */
+  int precision;        /* 0: FP64 throughout */
+  void* stream;         /* cudaStream_t to queue work on; NULL = default stream */
+} cgks_mesh_desc;
+
+typedef struct cgks_ctx cgks_ctx;
+
+/* Allocate the device state and metrics of a mesh; metrics are computed once
+   (standard-cell Jacobian J0 of Sec. 4, volumes by the trilinear map of the
+   Appendix, face area vectors at the Gauss points, line lengths).  *out is set
+   only on success. */
+cgks_status cgks_create_mesh(const cgks_mesh_desc* desc, cgks_ctx** out);
+void cgks_destroy(cgks_ctx* ctx);
+
+int cgks_num_vars(const cgks_ctx* ctx);    /* nv */
+int cgks_num_fields(const cgks_ctx* ctx);  /* nf */
+long cgks_num_cells(const cgks_ctx* ctx);
+
+/* Copy a full state in (layout above), from host (is_device = 0) or device
+   memory, and set the time. */
+cgks_status cgks_set_state(cgks_ctx* ctx, const double* src, int is_device, double t);
+/* Copy the state out; *t (may be NULL) receives the time.  Synchronises. */
+cgks_status cgks_get_state(cgks_ctx* ctx, double* dst, int is_device, double* t);
+
+/* Advance nsteps S2O4 steps.  t_end > 0 shortens the last step so that the
+   time does not pass t_end (and stops there).  t_out / dt_last may be NULL.
+   Returns CGKS_ENONPHYS if a state became non-physical (the state is then
+   undefined; restore it with cgks_set_state). Synchronises once. */
+cgks_status cgks_step(cgks_ctx* ctx, int nsteps, double t_end, double* t_out, double* dt_last);
+
+/* The CFL time step of the current state (dt = CFL / max over cells of
+   sum_d (|U.n_d| + c)/h_d, capped by CFL h^2/(3 nu)). */
+cgks_status cgks_compute_dt(cgks_ctx* ctx, double* dt);
+
+/* Initial data from point values.  For cells [cell0, cell0+ncells) the
+   library lists the points it needs (per cell: the 5^dim Gauss points of the
+   cell, then its face Gauss points in the order gp = (2*axis+side)*gpf + k)
+   into dev_pts (device, ncells*npc*dim doubles); the caller evaluates the
+   primitive variables (rho, U, V[, W], p) there and passes them back in
+   dev_prims (device, ncells*npc*nv doubles).  Averages come from the Gauss
+   rule, gradients and line derivatives from the discrete definitions
+   (Eqs. derivative, derivative-l) applied to the point values. */
+int cgks_init_points_per_cell(const cgks_ctx* ctx);
+cgks_status cgks_init_points(cgks_ctx* ctx, long cell0, long ncells, double* dev_pts);
+cgks_status cgks_init_from_prims(cgks_ctx* ctx, long cell0, long ncells, const double* dev_prims);
+
+/* The GENO weight chi of the first stage of the last step, [v][cell]. */
+cgks_status cgks_get_chi(cgks_ctx* ctx, double* dst, int is_device);
+
+/* Per-kernel timing with CUDA events on the context stream: enable/disable
+   (resets the counters), then read kernel names, launch counts and total
+   milliseconds.  names receives up to cap entries; returns the count. */
+cgks_status cgks_profile_enable(cgks_ctx* ctx, int on);
+int cgks_profile_read(cgks_ctx* ctx, const char** names, long* launches, double* total_ms, int cap);
+
+/* Copy the last error message (NUL-terminated, truncated to cap). */
+cgks_status cgks_last_error(const cgks_ctx* ctx, char* msg, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

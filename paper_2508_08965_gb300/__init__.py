@@ -1,0 +1,7 @@
+"""GB300-native CGKS-5: the per-stage sweep of the fifth-order compact
+gas-kinetic scheme (arXiv 2508.08965) as hand-written sm_103a CUDA behind a
+C-ABI (include/cgks.h).  This package holds the ctypes binding (argument
+marshalling only) and the in-tree build; there is no CPU fallback."""
+from .binding import (  # noqa: F401
+    CgksError, Mesh, lib, STATUS_NAMES,
+)

@@ -1,0 +1,209 @@
+"""ctypes binding of libcgks.so with the C-ABI's names; marshalling only.
+
+Every step of the scheme runs in the library's kernels.  Loading fails
+loudly if the library is missing or was not built for this machine; there is
+no CPU path.  PyTorch is used only for device buffers and the CUDA stream.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+STATUS_NAMES = {0: "CGKS_OK", -1: "CGKS_EINVAL", -2: "CGKS_ENOMEM", -3: "CGKS_ECUDA", -4: "CGKS_ENONPHYS",
+                -5: "CGKS_ETIMEOUT", -6: "CGKS_ESTATE", -7: "CGKS_EUNSUPPORTED"}
+
+
+class CgksError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__("%s (%d)%s" % (STATUS_NAMES.get(status, "?"), status, (": " + msg) if msg else ""))
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("nodes", C.POINTER(C.c_double)),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("bc", C.c_int * 6),
+                ("gamma", C.c_double), ("mu", C.c_double), ("prandtl", C.c_double),
+                ("tau_mode", C.c_int), ("cfl", C.c_double), ("dt_fixed", C.c_double),
+                ("linear", C.c_int), ("c_chi", C.c_double), ("precision", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+EXPORTS = ["cgks_create_mesh", "cgks_destroy", "cgks_num_vars", "cgks_num_fields", "cgks_num_cells",
+           "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_compute_dt", "cgks_init_points_per_cell",
+           "cgks_init_points", "cgks_init_from_prims", "cgks_get_chi", "cgks_profile_enable",
+           "cgks_profile_read", "cgks_last_error"]
+
+_lib = None
+
+
+def lib(build_if_missing=True):
+    """Load libcgks.so (building it in-tree first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libcgks.so is missing: build it with paper_2508_08965_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, dp, lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_long)
+    L.cgks_create_mesh.argtypes = [C.POINTER(MeshDesc), C.POINTER(vp)]
+    L.cgks_destroy.argtypes = [vp]
+    L.cgks_destroy.restype = None
+    L.cgks_num_vars.argtypes = [vp]
+    L.cgks_num_fields.argtypes = [vp]
+    L.cgks_num_cells.argtypes = [vp]
+    L.cgks_num_cells.restype = C.c_long
+    L.cgks_set_state.argtypes = [vp, vp, C.c_int, C.c_double]
+    L.cgks_get_state.argtypes = [vp, vp, C.c_int, dp]
+    L.cgks_step.argtypes = [vp, C.c_int, C.c_double, dp, dp]
+    L.cgks_compute_dt.argtypes = [vp, dp]
+    L.cgks_init_points_per_cell.argtypes = [vp]
+    L.cgks_init_points.argtypes = [vp, C.c_long, C.c_long, vp]
+    L.cgks_init_from_prims.argtypes = [vp, C.c_long, C.c_long, vp]
+    L.cgks_get_chi.argtypes = [vp, vp, C.c_int]
+    L.cgks_profile_enable.argtypes = [vp, C.c_int]
+    L.cgks_profile_read.argtypes = [vp, C.POINTER(C.c_char_p), lp, dp, C.c_int]
+    L.cgks_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
+    _lib = L
+    return L
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Mesh:
+    """One library context: a mesh, its device state and metrics.
+
+    Arguments follow cgks_mesh_desc.  ``stream`` is a torch.cuda.Stream (or
+    None for torch's current stream at construction time).
+    """
+
+    def __init__(self, dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=1.4, mu=0.0,
+                 prandtl=1.0, tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=0.0, stream=None):
+        torch = _torch()
+        L = lib()
+        d = MeshDesc()
+        d.dim = dim
+        nn = list(n) + [1] * (3 - len(n))
+        for a in range(3):
+            d.n[a] = int(nn[a])
+            d.lo[a] = float(lo[a]) if a < len(lo) else 0.0
+            d.hi[a] = float(hi[a]) if a < len(hi) else 1.0
+        self._nodes = None
+        if nodes is not None:
+            self._nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+            d.nodes = self._nodes.ctypes.data_as(C.POINTER(C.c_double))
+        d.gamma, d.mu, d.prandtl, d.tau_mode = gamma, mu, prandtl, tau_mode
+        d.cfl, d.dt_fixed, d.linear, d.c_chi = cfl, dt_fixed, int(linear), c_chi
+        d.precision = 0
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d.stream = C.c_void_p(self.stream.cuda_stream)
+        h = C.c_void_p()
+        self._h = None
+        self._check(L.cgks_create_mesh(C.byref(d), C.byref(h)))
+        self._h = h
+        self.dim = dim
+        self.n = tuple(int(x) for x in nn[:dim])
+        self.nv = L.cgks_num_vars(h)
+        self.nf = L.cgks_num_fields(h)
+        self.ncell = L.cgks_num_cells(h)
+        self.lo, self.hi = tuple(lo[:dim]), tuple(hi[:dim])
+
+    def _check(self, st):
+        if st != 0:
+            msg = ""
+            if self._h:
+                buf = C.create_string_buffer(512)
+                lib().cgks_last_error(self._h, buf, 512)
+                msg = buf.value.decode()
+            raise CgksError(st, msg)
+
+    def close(self):
+        if self._h:
+            lib().cgks_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def state_shape(self):
+        return (self.nf, self.nv) + tuple(reversed(self.n))
+
+    def set_state(self, s, t=0.0):
+        """s: numpy array (host) or torch CUDA tensor of state_shape, float64."""
+        torch = _torch()
+        if isinstance(s, torch.Tensor) and s.is_cuda:
+            s = s.contiguous()
+            assert s.dtype == torch.float64 and s.numel() == self.nf * self.nv * self.ncell
+            self._check(lib().cgks_set_state(self._h, C.c_void_p(s.data_ptr()), 1, float(t)))
+            self._keep = s
+        else:
+            a = np.ascontiguousarray(s, dtype=np.float64)
+            assert a.size == self.nf * self.nv * self.ncell
+            self._check(lib().cgks_set_state(self._h, a.ctypes.data_as(C.c_void_p), 0, float(t)))
+
+    def get_state(self, out=None):
+        """Host numpy copy (or into a torch CUDA tensor `out`); returns (state, t)."""
+        torch = _torch()
+        t = C.c_double(0)
+        if out is not None and isinstance(out, torch.Tensor) and out.is_cuda:
+            self._check(lib().cgks_get_state(self._h, C.c_void_p(out.data_ptr()), 1, C.byref(t)))
+            return out, t.value
+        a = np.empty(self.state_shape) if out is None else out
+        self._check(lib().cgks_get_state(self._h, a.ctypes.data_as(C.c_void_p), 0, C.byref(t)))
+        return a, t.value
+
+    def step(self, nsteps=1, t_end=0.0):
+        t, dt = C.c_double(0), C.c_double(0)
+        self._check(lib().cgks_step(self._h, int(nsteps), float(t_end), C.byref(t), C.byref(dt)))
+        return t.value, dt.value
+
+    def advance_to(self, t_end, max_steps=10 ** 7):
+        t, _ = self.step(max_steps, t_end)
+        return t
+
+    def compute_dt(self):
+        dt = C.c_double(0)
+        self._check(lib().cgks_compute_dt(self._h, C.byref(dt)))
+        return dt.value
+
+    def chi(self):
+        a = np.empty((self.nv,) + tuple(reversed(self.n)))
+        self._check(lib().cgks_get_chi(self._h, a.ctypes.data_as(C.c_void_p), 0))
+        return a
+
+    def init(self, field_fn, chunk_cells=1 << 18):
+        """Initial data from a point function field_fn(*coords) -> [rho, U, V[, W], p]
+        evaluated on the device (torch tensors), chunk by chunk."""
+        torch = _torch()
+        L = lib()
+        npc = L.cgks_init_points_per_cell(self._h)
+        with torch.cuda.stream(self.stream):
+            for c0 in range(0, self.ncell, chunk_cells):
+                nc = min(chunk_cells, self.ncell - c0)
+                pts = torch.empty((nc * npc, self.dim), dtype=torch.float64, device="cuda")
+                self._check(L.cgks_init_points(self._h, c0, nc, C.c_void_p(pts.data_ptr())))
+                prims = torch.stack([torch.as_tensor(p, dtype=torch.float64, device="cuda").expand(nc * npc)
+                                     for p in field_fn(*[pts[:, a] for a in range(self.dim)])], dim=-1).contiguous()
+                self.stream.synchronize()
+                self._check(L.cgks_init_from_prims(self._h, c0, nc, C.c_void_p(prims.data_ptr())))
+
+    def profile(self, on=True):
+        self._check(lib().cgks_profile_enable(self._h, int(on)))
+
+    def profile_read(self):
+        names = (C.c_char_p * 16)()
+        launches = (C.c_long * 16)()
+        ms = (C.c_double * 16)()
+        n = lib().cgks_profile_read(self._h, names, launches, ms, 16)
+        return {names[i].decode(): (launches[i], ms[i]) for i in range(n)}

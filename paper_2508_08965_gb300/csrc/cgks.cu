@@ -1,0 +1,426 @@
+/*
+ * Host side of the CGKS-5 C-ABI (include/cgks.h): context, device memory,
+ * step orchestration and per-kernel event timing.  All arithmetic of the
+ * scheme runs in the kernels of cgks_kernels.cuh.
+ */
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cgks.h"
+#include "cgks_kernels.cuh"
+
+using namespace cgks;
+
+namespace {
+
+enum KernelId { KID_RECON, KID_FLUX, KID_UPDATE, KID_DT, KID_N };
+const char* kKernelNames[KID_N] = {"recon", "flux", "update", "dt"};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, int>> rec;  /* (kernel id, event index of start) */
+  long launches[KID_N] = {0};
+  double ms[KID_N] = {0};
+};
+
+}  // namespace
+
+struct cgks_ctx {
+  int dim, nv, nf;
+  int n[3];
+  long ncell;
+  cgks_mesh_desc desc;
+  cudaStream_t stream;
+  DevGeo geo;
+  Phys ph;
+  double* d_nodes = nullptr;
+  double* d_met = nullptr;
+  double* d_lo = nullptr;
+  double* U = nullptr;      /* current state */
+  double* Us = nullptr;     /* intermediate state */
+  double* stash = nullptr;  /* stage-1 stash */
+  double* gpL = nullptr;
+  double* gpR = nullptr;
+  double* flux = nullptr;
+  double* chi = nullptr;
+  DtState* dts = nullptr;
+  int* st = nullptr;
+  double t = 0.0;
+  std::string err;
+  Prof prof;
+};
+
+static cgks_status fail(cgks_ctx* c, cgks_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(ctx, CGKS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static long cdiv(long a, long b) { return (a + b - 1) / b; }
+
+/* ---- profiling: CUDA events around each launch on the context stream ---- */
+static void prof_begin(cgks_ctx* ctx, int kid) {
+  if (!ctx->prof.on) return;
+  Prof& p = ctx->prof;
+  size_t need = p.rec.size() * 2 + 2;
+  while (p.pool.size() < need) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    p.pool.push_back(e);
+  }
+  int idx = (int)p.rec.size() * 2;
+  p.rec.push_back({kid, idx});
+  cudaEventRecord(p.pool[idx], ctx->stream);
+}
+static void prof_end(cgks_ctx* ctx) {
+  if (!ctx->prof.on) return;
+  Prof& p = ctx->prof;
+  cudaEventRecord(p.pool[p.rec.back().second + 1], ctx->stream);
+}
+static void prof_fold(cgks_ctx* ctx) {
+  Prof& p = ctx->prof;
+  if (p.rec.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& r : p.rec) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.pool[r.second], p.pool[r.second + 1]);
+    p.ms[r.first] += ms;
+    p.launches[r.first] += 1;
+  }
+  p.rec.clear();
+}
+
+template <int DIM>
+static cgks_status run_stage(cgks_ctx* ctx, const double* Uin, int stage, double* Uout) {
+  const long N = ctx->ncell;
+  const int B = 128;
+  prof_begin(ctx, KID_RECON);
+  k_recon<DIM><<<cdiv(N, B), B, 0, ctx->stream>>>(Uin, ctx->geo, ctx->ph, ctx->gpL, ctx->gpR, ctx->chi,
+                                                  stage == 1 ? 1 : 0, ctx->st);
+  prof_end(ctx);
+  long nf = (long)DIM * Sz<DIM>::GPF * N;
+  prof_begin(ctx, KID_FLUX);
+  k_flux<DIM><<<cdiv(nf, B), B, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, ctx->gpL, ctx->gpR, ctx->flux,
+                                                  ctx->st);
+  prof_end(ctx);
+  prof_begin(ctx, KID_UPDATE);
+  k_update<DIM><<<cdiv(N, B), B, 0, ctx->stream>>>(ctx->geo, ctx->dts, stage, Uin, ctx->flux, ctx->stash, Uout);
+  prof_end(ctx);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+template <int DIM>
+static cgks_status run_dt(cgks_ctx* ctx, const double* U) {
+  prof_begin(ctx, KID_DT);
+  k_dt_reset<<<1, 1, 0, ctx->stream>>>(ctx->dts);
+  k_dt_rate<DIM><<<cdiv(ctx->ncell, 256), 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, U, ctx->dts);
+  k_dt_final<<<1, 1, 0, ctx->stream>>>(ctx->ph, ctx->dts, ctx->st);
+  prof_end(ctx);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+template <int DIM>
+static cgks_status run_step(cgks_ctx* ctx) {
+  cgks_status s;
+  if ((s = run_dt<DIM>(ctx, ctx->U)) != CGKS_OK) return s;
+  if ((s = run_stage<DIM>(ctx, ctx->U, 1, ctx->Us)) != CGKS_OK) return s;
+  if ((s = run_stage<DIM>(ctx, ctx->Us, 2, ctx->U)) != CGKS_OK) return s;
+  k_time_advance<<<1, 1, 0, ctx->stream>>>(ctx->dts);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+extern "C" {
+
+cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
+  cgks_ctx* ctx = nullptr;
+  if (!d || !out) return CGKS_EINVAL;
+  if (d->dim != 2 && d->dim != 3) return CGKS_EINVAL;
+  for (int a = 0; a < d->dim; ++a)
+    if (d->n[a] < 3) return CGKS_EINVAL;
+  if (d->precision != 0) return CGKS_EUNSUPPORTED;
+  for (int f = 0; f < 2 * d->dim; ++f)
+    if (d->bc[f] != CGKS_BC_PERIODIC) return CGKS_EUNSUPPORTED;
+  if (!(d->gamma > 1.0) || d->mu < 0.0 || !(d->cfl > 0.0) || d->tau_mode < 0 || d->tau_mode > 2)
+    return CGKS_EINVAL;
+  ctx = new cgks_ctx();
+  ctx->desc = *d;
+  ctx->desc.nodes = nullptr;
+  ctx->dim = d->dim;
+  ctx->nv = d->dim + 2;
+  ctx->nf = d->dim == 3 ? Sz<3>::NF : Sz<2>::NF;
+  ctx->n[0] = d->n[0];
+  ctx->n[1] = d->n[1];
+  ctx->n[2] = d->dim == 3 ? d->n[2] : 1;
+  ctx->ncell = (long)ctx->n[0] * ctx->n[1] * ctx->n[2];
+  ctx->stream = (cudaStream_t)d->stream;
+  ctx->ph.gamma = d->gamma;
+  ctx->ph.mu = d->mu;
+  ctx->ph.prandtl = d->prandtl > 0.0 ? d->prandtl : 1.0;
+  ctx->ph.cfl = d->cfl;
+  ctx->ph.c_chi = d->c_chi > 0.0 ? d->c_chi : 100.0;
+  ctx->ph.tau_mode = d->tau_mode;
+  ctx->ph.linear = d->linear;
+  DevGeo& g = ctx->geo;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = ctx->n[a];
+    g.h[a] = a < d->dim ? (d->hi[a] - d->lo[a]) / d->n[a] : 1.0;
+  }
+  g.ncell = ctx->ncell;
+  g.curvi = d->nodes ? 1 : 0;
+  g.met = nullptr;
+  const long N = ctx->ncell;
+  const int dim = ctx->dim, nv = ctx->nv, nf = ctx->nf;
+  const int gpf = dim == 3 ? 4 : 2;
+  size_t st_sz = sizeof(double) * (size_t)nf * nv * N;
+  size_t gp_sz = sizeof(double) * (size_t)dim * gpf * nv * (1 + dim) * N;
+  size_t fx_sz = sizeof(double) * (size_t)dim * gpf * 6 * nv * N;
+#define ALLOC(p, sz)                                                                         \
+  do {                                                                                       \
+    if (cudaMalloc((void**)&(p), (sz)) != cudaSuccess) {                                     \
+      cudaGetLastError();                                                                    \
+      cgks_destroy(ctx);                                                                     \
+      return CGKS_ENOMEM;                                                                    \
+    }                                                                                        \
+  } while (0)
+  ALLOC(ctx->U, st_sz);
+  ALLOC(ctx->Us, st_sz);
+  ALLOC(ctx->stash, st_sz);
+  ALLOC(ctx->gpL, gp_sz);
+  ALLOC(ctx->gpR, gp_sz);
+  ALLOC(ctx->flux, fx_sz);
+  ALLOC(ctx->chi, sizeof(double) * (size_t)nv * N);
+  ALLOC(ctx->dts, sizeof(DtState));
+  ALLOC(ctx->st, sizeof(int) * ST_N);
+  ALLOC(ctx->d_lo, sizeof(double) * 3);
+  CK(cudaMemsetAsync(ctx->st, 0, sizeof(int) * ST_N, ctx->stream));
+  CK(cudaMemsetAsync(ctx->U, 0, st_sz, ctx->stream));
+  CK(cudaMemsetAsync(ctx->chi, 0, sizeof(double) * (size_t)nv * N, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_lo, d->lo, sizeof(double) * 3, cudaMemcpyHostToDevice, ctx->stream));
+  if (d->nodes) {
+    long nn = (long)(ctx->n[0] + 1) * (ctx->n[1] + 1) * (dim == 3 ? ctx->n[2] + 1 : 1);
+    int nmet = dim == 3 ? Met<3>::N : Met<2>::N;
+    ALLOC(ctx->d_nodes, sizeof(double) * nn * dim);
+    ALLOC(ctx->d_met, sizeof(double) * (size_t)nmet * N);
+    CK(cudaMemcpyAsync(ctx->d_nodes, d->nodes, sizeof(double) * nn * dim, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (dim == 3) k_metrics<3><<<cdiv(N, 128), 128, 0, ctx->stream>>>(ctx->d_nodes, g, ctx->d_met);
+    else k_metrics<2><<<cdiv(N, 128), 128, 0, ctx->stream>>>(ctx->d_nodes, g, ctx->d_met);
+    CK(cudaGetLastError());
+    g.met = ctx->d_met;
+  }
+#undef ALLOC
+  DtState init{};
+  init.t = 0.0;
+  init.dt_fixed = d->dt_fixed;
+  CK(cudaMemcpyAsync(ctx->dts, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *out = ctx;
+  return CGKS_OK;
+}
+
+void cgks_destroy(cgks_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  cudaFree(ctx->U);
+  cudaFree(ctx->Us);
+  cudaFree(ctx->stash);
+  cudaFree(ctx->gpL);
+  cudaFree(ctx->gpR);
+  cudaFree(ctx->flux);
+  cudaFree(ctx->chi);
+  cudaFree(ctx->dts);
+  cudaFree(ctx->st);
+  cudaFree(ctx->d_lo);
+  cudaFree(ctx->d_nodes);
+  cudaFree(ctx->d_met);
+  for (auto e : ctx->prof.pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+int cgks_num_vars(const cgks_ctx* ctx) { return ctx ? ctx->nv : -1; }
+int cgks_num_fields(const cgks_ctx* ctx) { return ctx ? ctx->nf : -1; }
+long cgks_num_cells(const cgks_ctx* ctx) { return ctx ? ctx->ncell : -1; }
+
+cgks_status cgks_set_state(cgks_ctx* ctx, const double* src, int is_device, double t) {
+  if (!ctx || !src) return CGKS_EINVAL;
+  size_t sz = sizeof(double) * (size_t)ctx->nf * ctx->nv * ctx->ncell;
+  CK(cudaMemcpyAsync(ctx->U, src, sz, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  ctx->t = t;
+  DtState init{};
+  init.t = t;
+  init.dt_fixed = ctx->desc.dt_fixed;
+  CK(cudaMemcpyAsync(ctx->dts, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+  if (!is_device) CK(cudaStreamSynchronize(ctx->stream));
+  return CGKS_OK;
+}
+
+cgks_status cgks_get_state(cgks_ctx* ctx, double* dst, int is_device, double* t) {
+  if (!ctx || !dst) return CGKS_EINVAL;
+  size_t sz = sizeof(double) * (size_t)ctx->nf * ctx->nv * ctx->ncell;
+  CK(cudaMemcpyAsync(dst, ctx->U, sz, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  DtState h;
+  CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->t = h.t;
+  if (t) *t = h.t;
+  return CGKS_OK;
+}
+
+static cgks_status check_status(cgks_ctx* ctx) {
+  int st[ST_N];
+  CK(cudaMemcpyAsync(st, ctx->st, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st[ST_NONPHYS] || st[ST_FLUX] || st[ST_DT]) {
+    int z[ST_N] = {0, st[ST_FALLBACK], 0, 0};
+    CK(cudaMemcpyAsync(ctx->st, z, sizeof z, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return fail(ctx, CGKS_ENONPHYS, "non-physical state (recon %d, interface %d, cell %d)", st[ST_NONPHYS],
+                st[ST_FLUX], st[ST_DT]);
+  }
+  return CGKS_OK;
+}
+
+cgks_status cgks_step(cgks_ctx* ctx, int nsteps, double t_end, double* t_out, double* dt_last) {
+  if (!ctx || nsteps < 0) return CGKS_EINVAL;
+  DtState h;
+  CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  h.t_end = t_end > 0.0 ? t_end : 0.0;
+  CK(cudaMemcpyAsync(ctx->dts, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+  for (int s = 0; s < nsteps; ++s) {
+    if (t_end > 0.0) {
+      CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (h.t >= t_end * (1.0 - 1e-14)) break;
+    }
+    cgks_status r = ctx->dim == 3 ? run_step<3>(ctx) : run_step<2>(ctx);
+    if (r != CGKS_OK) return r;
+  }
+  if (ctx->prof.on) prof_fold(ctx);
+  cgks_status r = check_status(ctx);
+  CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->t = h.t;
+  if (t_out) *t_out = h.t;
+  if (dt_last) *dt_last = h.dt;
+  return r;
+}
+
+cgks_status cgks_compute_dt(cgks_ctx* ctx, double* dt) {
+  if (!ctx || !dt) return CGKS_EINVAL;
+  DtState h;
+  CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double keep_end = h.t_end;
+  h.t_end = 0.0;
+  CK(cudaMemcpyAsync(ctx->dts, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+  cgks_status r = ctx->dim == 3 ? run_dt<3>(ctx, ctx->U) : run_dt<2>(ctx, ctx->U);
+  if (r != CGKS_OK) return r;
+  CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *dt = h.dt;
+  h.t_end = keep_end;
+  CK(cudaMemcpyAsync(ctx->dts, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
+}
+
+int cgks_init_points_per_cell(const cgks_ctx* ctx) {
+  if (!ctx) return -1;
+  return ctx->dim == 3 ? npts_cell<3>() : npts_cell<2>();
+}
+
+cgks_status cgks_init_points(cgks_ctx* ctx, long cell0, long ncells, double* dev_pts) {
+  if (!ctx || !dev_pts || cell0 < 0 || ncells < 0 || cell0 + ncells > ctx->ncell) return CGKS_EINVAL;
+  long tot = ncells * cgks_init_points_per_cell(ctx);
+  if (tot == 0) return CGKS_OK;
+  if (ctx->dim == 3)
+    k_init_points<3><<<cdiv(tot, 128), 128, 0, ctx->stream>>>(ctx->d_nodes, ctx->geo, ctx->d_lo, cell0, ncells,
+                                                              dev_pts);
+  else
+    k_init_points<2><<<cdiv(tot, 128), 128, 0, ctx->stream>>>(ctx->d_nodes, ctx->geo, ctx->d_lo, cell0, ncells,
+                                                              dev_pts);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CGKS_OK;
+}
+
+cgks_status cgks_init_from_prims(cgks_ctx* ctx, long cell0, long ncells, const double* dev_prims) {
+  if (!ctx || !dev_prims || cell0 < 0 || ncells < 0 || cell0 + ncells > ctx->ncell) return CGKS_EINVAL;
+  if (ncells == 0) return CGKS_OK;
+  if (ctx->dim == 3)
+    k_init_from_prims<3><<<cdiv(ncells, 128), 128, 0, ctx->stream>>>(ctx->d_nodes, ctx->geo, ctx->ph, ctx->d_lo,
+                                                                     cell0, ncells, dev_prims, ctx->U);
+  else
+    k_init_from_prims<2><<<cdiv(ncells, 128), 128, 0, ctx->stream>>>(ctx->d_nodes, ctx->geo, ctx->ph, ctx->d_lo,
+                                                                     cell0, ncells, dev_prims, ctx->U);
+  CK(cudaGetLastError());
+  DtState init{};
+  init.t = 0.0;
+  init.dt_fixed = ctx->desc.dt_fixed;
+  CK(cudaMemcpyAsync(ctx->dts, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->t = 0.0;
+  return CGKS_OK;
+}
+
+cgks_status cgks_get_chi(cgks_ctx* ctx, double* dst, int is_device) {
+  if (!ctx || !dst) return CGKS_EINVAL;
+  CK(cudaMemcpyAsync(dst, ctx->chi, sizeof(double) * (size_t)ctx->nv * ctx->ncell,
+                     is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CGKS_OK;
+}
+
+cgks_status cgks_profile_enable(cgks_ctx* ctx, int on) {
+  if (!ctx) return CGKS_EINVAL;
+  prof_fold(ctx);
+  ctx->prof.on = on != 0;
+  for (int k = 0; k < KID_N; ++k) {
+    ctx->prof.launches[k] = 0;
+    ctx->prof.ms[k] = 0.0;
+  }
+  return CGKS_OK;
+}
+
+int cgks_profile_read(cgks_ctx* ctx, const char** names, long* launches, double* total_ms, int cap) {
+  if (!ctx) return -1;
+  prof_fold(ctx);
+  int n = 0;
+  for (int k = 0; k < KID_N && n < cap; ++k, ++n) {
+    if (names) names[n] = kKernelNames[k];
+    if (launches) launches[n] = ctx->prof.launches[k];
+    if (total_ms) total_ms[n] = ctx->prof.ms[k];
+  }
+  return n;
+}
+
+cgks_status cgks_last_error(const cgks_ctx* ctx, char* msg, size_t cap) {
+  if (!ctx || !msg || cap == 0) return CGKS_EINVAL;
+  snprintf(msg, cap, "%s", ctx->err.c_str());
+  return CGKS_OK;
+}
+
+}  // extern "C"

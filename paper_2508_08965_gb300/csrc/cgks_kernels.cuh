@@ -1,0 +1,397 @@
+/*
+ * Kernels of the CGKS-5 library: thin thread mappings onto the routines of
+ * cgks_device.cuh, plus the metric precompute (Sec. 4 and Appendix), the
+ * initial-data kernels and the time-step reduction.
+ */
+#pragma once
+#include "cgks_device.cuh"
+
+namespace cgks {
+
+/* device status words: [0] non-physical state that chi = 0 cannot cure,
+   [1] positivity fallbacks, [2] non-physical interface state,
+   [3] non-physical cell in the time-step reduction */
+enum { ST_NONPHYS = 0, ST_FALLBACK = 1, ST_FLUX = 2, ST_DT = 3, ST_N = 4 };
+
+/* time-step bookkeeping on the device: [0] rate bits (max), [1] dt, [2] t, [3] t_end */
+struct DtState {
+  unsigned long long rate_bits;
+  double dt, t, t_end, dt_fixed;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_recon(const double* __restrict__ U, DevGeo g, Phys ph,
+                                               double* __restrict__ gpL, double* __restrict__ gpR,
+                                               double* __restrict__ chi, int record_chi, int* __restrict__ st) {
+  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  int i, j, k;
+  cell_ijk(g, c, i, j, k);
+  const int NV = Sz<DIM>::NV;
+  double force = ph.linear ? 1.0 : -1.0;
+  double cs[NV];
+#pragma unroll 1
+  for (int v = 0; v < NV; ++v) cs[v] = recon_var<DIM>(U, g, ph, c, i, j, k, v, force, gpL, gpR);
+  if (!cell_states_physical<DIM>(g, ph, c, i, j, k, gpL, gpR)) {
+    atomicAdd(&st[ST_FALLBACK], 1);
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) cs[v] = recon_var<DIM>(U, g, ph, c, i, j, k, v, 0.0, gpL, gpR);
+    if (!cell_states_physical<DIM>(g, ph, c, i, j, k, gpL, gpR)) atomicOr(&st[ST_NONPHYS], 1);
+  }
+  if (record_chi)
+    for (int v = 0; v < NV; ++v) chi[(long)v * g.ncell + c] = cs[v];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
+                                              const double* __restrict__ gpL, const double* __restrict__ gpR,
+                                              double* __restrict__ flux, int* __restrict__ st) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long N = g.ncell;
+  if (t >= (long)DIM * Sz<DIM>::GPF * N) return;
+  long c = t % N;
+  int r = (int)(t / N);
+  int k = r % Sz<DIM>::GPF, ax = r / Sz<DIM>::GPF;
+  double dt = dts->dt;
+  if (!(dt > 0.0)) return;
+  if (!flux_point<DIM>(g, ph, dt, ax, k, c, gpL, gpR, flux)) atomicOr(&st[ST_FLUX], 1);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_update(DevGeo g, const DtState* __restrict__ dts, int stage,
+                                                const double* __restrict__ Uin, const double* __restrict__ flux,
+                                                double* __restrict__ stash, double* __restrict__ Uout) {
+  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  double dt = dts->dt;
+  if (!(dt > 0.0)) return;
+  int i, j, k;
+  cell_ijk(g, c, i, j, k);
+  update_cell<DIM>(g, dt, stage, c, i, j, k, Uin, flux, stash, Uout);
+}
+
+/* max over cells of the rate; positive doubles order like their bit patterns */
+template <int DIM>
+__global__ void __launch_bounds__(256) k_dt_rate(DevGeo g, Phys ph, const double* __restrict__ U,
+                                                 DtState* __restrict__ dts) {
+  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  double r = 0.0;
+  if (c < g.ncell) r = cell_rate<DIM>(g, ph, U, c);
+  unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
+  }
+  __shared__ unsigned long long wmax[8];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wmax[wid] = bits;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
+    atomicMax(&dts->rate_bits, m);
+  }
+}
+
+__global__ void k_dt_reset(DtState* dts) { dts->rate_bits = 0ull; }
+
+/* dt = CFL / max rate, or the fixed step; shortened to reach t_end */
+__global__ void k_dt_final(Phys ph, DtState* dts, int* st) {
+  double rate = __longlong_as_double((long long)dts->rate_bits);
+  double dt;
+  if (dts->dt_fixed > 0.0) dt = dts->dt_fixed;
+  else dt = (rate > 0.0 && rate < 1e299) ? ph.cfl / rate : 0.0;
+  if (rate >= 1e299) atomicOr(&st[ST_DT], 1);
+  if (dts->t_end > 0.0) {
+    double rem = dts->t_end - dts->t;
+    if (rem < dt) dt = rem > 0.0 ? rem : 0.0;
+  }
+  dts->dt = dt;
+}
+
+__global__ void k_time_advance(DtState* dts) { dts->t += dts->dt; }
+
+/* ------------------------------------------------------------------ */
+/* metrics from node coordinates (Sec. 4 J0, Appendix volume)           */
+/* ------------------------------------------------------------------ */
+template <int DIM>
+CGKS_HD void node_xyz(const double* nodes, const int* n, int i, int j, int k, double* x) {
+  long nx = n[0] + 1, ny = n[1] + 1;
+  long id = i + nx * (j + ny * (long)k);
+  for (int d = 0; d < DIM; ++d) x[d] = nodes[id * DIM + d];
+}
+
+/* trilinear (bilinear) map of cell (i,j,k) and its Jacobian at xi in [0,1]^DIM */
+template <int DIM>
+CGKS_HD void cell_map(const double* nodes, const int* n, int i, int j, int k, const double* xi, double* x,
+                      double J[3][3]) {
+  for (int a = 0; a < 3; ++a) {
+    x[a] = 0.0;
+    for (int b = 0; b < 3; ++b) J[a][b] = 0.0;
+  }
+  const int nvtx = DIM == 3 ? 8 : 4;
+  for (int vtx = 0; vtx < nvtx; ++vtx) {
+    int o[3] = {vtx & 1, (vtx >> 1) & 1, (vtx >> 2) & 1};
+    double X[3];
+    node_xyz<DIM>(nodes, n, i + o[0], j + o[1], k + o[2], X);
+    double w[3], dw[3];
+    for (int a = 0; a < DIM; ++a) {
+      w[a] = o[a] ? xi[a] : 1.0 - xi[a];
+      dw[a] = o[a] ? 1.0 : -1.0;
+    }
+    double wt = 1.0;
+    for (int a = 0; a < DIM; ++a) wt *= w[a];
+    for (int a = 0; a < DIM; ++a) {
+      x[a] += wt * X[a];
+      for (int b = 0; b < DIM; ++b) {
+        double d = dw[b];
+        for (int e = 0; e < DIM; ++e)
+          if (e != b) d *= w[e];
+        J[a][b] += d * X[a];
+      }
+    }
+  }
+}
+
+template <int DIM> CGKS_HD double det_dim(const double J[3][3]) {
+  if (DIM == 2) return J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+template <int DIM>
+CGKS_HD void metrics_cell(const double* __restrict__ nodes, const DevGeo& g, long c, double* __restrict__ met) {
+  typedef Sz<DIM> S;
+  typedef Met<DIM> MT;
+  const long N = g.ncell;
+  int i, j, k;
+  cell_ijk(g, c, i, j, k);
+  double N1[3], Nk[3];
+  node_xyz<DIM>(nodes, g.n, i, j, k, N1);
+  double J0[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 1}};
+  for (int a = 0; a < DIM; ++a) {
+    int o[3] = {0, 0, 0};
+    o[a] = 1;
+    node_xyz<DIM>(nodes, g.n, i + o[0], j + o[1], k + o[2], Nk);
+    for (int r = 0; r < DIM; ++r) J0[r][a] = Nk[r] - N1[r];
+  }
+  double det = det_dim<3>(J0);
+  double inv[3][3];
+  inv[0][0] = (J0[1][1] * J0[2][2] - J0[1][2] * J0[2][1]) / det;
+  inv[0][1] = (J0[0][2] * J0[2][1] - J0[0][1] * J0[2][2]) / det;
+  inv[0][2] = (J0[0][1] * J0[1][2] - J0[0][2] * J0[1][1]) / det;
+  inv[1][0] = (J0[1][2] * J0[2][0] - J0[1][0] * J0[2][2]) / det;
+  inv[1][1] = (J0[0][0] * J0[2][2] - J0[0][2] * J0[2][0]) / det;
+  inv[1][2] = (J0[0][2] * J0[1][0] - J0[0][0] * J0[1][2]) / det;
+  inv[2][0] = (J0[1][0] * J0[2][1] - J0[1][1] * J0[2][0]) / det;
+  inv[2][1] = (J0[0][1] * J0[2][0] - J0[0][0] * J0[2][1]) / det;
+  inv[2][2] = (J0[0][0] * J0[1][1] - J0[0][1] * J0[1][0]) / det;
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) {
+      met[(long)(MT::J0 + r * 3 + q) * N + c] = (r < DIM && q < DIM) ? J0[r][q] : 0.0;
+      met[(long)(MT::JIT + r * 3 + q) * N + c] = (r < DIM && q < DIM) ? inv[q][r] : 0.0;
+    }
+  /* volume: 3-point Gauss per axis of det(dX/dxi) */
+  const double gx[3] = {-0.77459666924148337704, 0.0, 0.77459666924148337704};
+  const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  double vol = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int e = 0; e < (DIM == 3 ? 3 : 1); ++e) {
+        double xi[3] = {0.5 + 0.5 * gx[a], 0.5 + 0.5 * gx[b], DIM == 3 ? 0.5 + 0.5 * gx[e] : 0.0};
+        double x[3], Jm[3][3];
+        cell_map<DIM>(nodes, g.n, i, j, k, xi, x, Jm);
+        double w = DIM == 3 ? 0.125 * gw[a] * gw[b] * gw[e] : 0.25 * gw[a] * gw[b];
+        vol += w * det_dim<DIM>(Jm);
+      }
+  met[(long)MT::VOL * N + c] = vol;
+  double pos[S::NGP][3];
+  for (int f = 0; f < 2 * DIM; ++f) {
+    int ax = f / 2, side = f & 1;
+    int ta[2] = {0, 0}, nt = 0;
+    for (int q = 0; q < DIM; ++q)
+      if (q != ax) ta[nt++] = q;
+    for (int kk = 0; kk < S::GPF; ++kk) {
+      int gp = f * S::GPF + kk;
+      double xi[3];
+      for (int a = 0; a < 3; ++a) xi[a] = a < DIM ? gp_delta<DIM>(gp, a) + 0.5 : 0.0;
+      xi[ax] = side;
+      double x[3], Jm[3][3];
+      cell_map<DIM>(nodes, g.n, i, j, k, xi, x, Jm);
+      for (int a = 0; a < 3; ++a) pos[gp][a] = x[a];
+      double w = 1.0 / S::GPF;
+      double A[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+      if (DIM == 3) {
+        double u0[3] = {Jm[0][ta[0]], Jm[1][ta[0]], Jm[2][ta[0]]};
+        double u1[3] = {Jm[0][ta[1]], Jm[1][ta[1]], Jm[2][ta[1]]};
+        double cr[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2], u0[0] * u1[1] - u0[1] * u1[0]};
+        double sg = ax == 1 ? -1.0 : 1.0;
+        for (int a = 0; a < 3; ++a) {
+          A[a] = sg * w * cr[a];
+          T[a] = u0[a];
+        }
+      } else {
+        double tv[2] = {Jm[0][ta[0]], Jm[1][ta[0]]};
+        double sg = ax == 0 ? 1.0 : -1.0;
+        A[0] = sg * w * tv[1];
+        A[1] = -sg * w * tv[0];
+        T[0] = tv[0];
+        T[1] = tv[1];
+      }
+      for (int a = 0; a < 3; ++a) met[(long)(MT::AREA + gp * 3 + a) * N + c] = A[a];
+      if (side)
+        for (int a = 0; a < 3; ++a) met[(long)(MT::TANG + (ax * S::GPF + kk) * 3 + a) * N + c] = T[a];
+    }
+  }
+  for (int ax = 0; ax < DIM; ++ax)
+    for (int kk = 0; kk < S::GPF; ++kk) {
+      int glo = (2 * ax) * S::GPF + kk, ghi = (2 * ax + 1) * S::GPF + kk;
+      double s = 0.0;
+      for (int a = 0; a < DIM; ++a) {
+        double d = pos[ghi][a] - pos[glo][a];
+        s += d * d;
+      }
+      met[(long)(MT::LEN + ax * S::GPF + kk) * N + c] = sqrt(s);
+    }
+}
+
+template <int DIM>
+__global__ void k_metrics(const double* __restrict__ nodes, DevGeo g, double* __restrict__ met) {
+  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  metrics_cell<DIM>(nodes, g, c, met);
+}
+
+/* ------------------------------------------------------------------ */
+/* initial data                                                        */
+/* ------------------------------------------------------------------ */
+#define CGKS_G5X0 0.90617984593866399280
+#define CGKS_G5X1 0.53846931010568309104
+CGKS_HD double g5x(int q) {
+  return q == 0 ? -CGKS_G5X0 : q == 1 ? -CGKS_G5X1 : q == 2 ? 0.0 : q == 3 ? CGKS_G5X1 : CGKS_G5X0;
+}
+CGKS_HD double g5w(int q) {
+  return (q == 0 || q == 4) ? 0.23692688505618908751 : (q == 1 || q == 3) ? 0.47862867049936646804
+                                                                          : 0.56888888888888888889;
+}
+template <int DIM> __host__ __device__ constexpr int npts_cell() { return (DIM == 3 ? 125 : 25) + Sz<DIM>::NGP; }
+
+/* physical position of reference point xi of cell (i,j,k) */
+template <int DIM>
+CGKS_HD void ref_to_phys(const double* nodes, const DevGeo& g, const double* lo, int i, int j, int k,
+                            const double* xi, double* x, double* detJ) {
+  if (nodes) {
+    double J[3][3];
+    cell_map<DIM>(nodes, g.n, i, j, k, xi, x, J);
+    *detJ = det_dim<DIM>(J);
+  } else {
+    int ii[3] = {i, j, k};
+    double d = 1.0;
+    for (int a = 0; a < DIM; ++a) {
+      x[a] = lo[a] + (ii[a] + xi[a]) * g.h[a];
+      d *= g.h[a];
+    }
+    *detJ = d;
+  }
+}
+
+template <int DIM>
+CGKS_HD void init_point(const double* __restrict__ nodes, const DevGeo& g, const double* lo3, long cell0, long t,
+                        double* __restrict__ pts) {
+  const int NP = npts_cell<DIM>();
+  long cl = t / NP;
+  int q = (int)(t % NP);
+  long c = cell0 + cl;
+  int i, j, k;
+  cell_ijk(g, c, i, j, k);
+  double lo[3] = {lo3[0], lo3[1], lo3[2]};
+  double xi[3] = {0.0, 0.0, 0.0}, x[3], dj;
+  const int NVOL = DIM == 3 ? 125 : 25;
+  if (q < NVOL) {
+    int qx = q % 5, qy = (q / 5) % 5, qz = q / 25;
+    xi[0] = 0.5 + 0.5 * g5x(qx);
+    xi[1] = 0.5 + 0.5 * g5x(qy);
+    if (DIM == 3) xi[2] = 0.5 + 0.5 * g5x(qz);
+  } else {
+    int gp = q - NVOL;
+    for (int a = 0; a < DIM; ++a) xi[a] = gp_delta<DIM>(gp, a) + 0.5;
+  }
+  ref_to_phys<DIM>(nodes, g, lo, i, j, k, xi, x, &dj);
+  for (int a = 0; a < DIM; ++a) pts[t * DIM + a] = x[a];
+}
+
+template <int DIM>
+__global__ void k_init_points(const double* __restrict__ nodes, DevGeo g, const double* lo3, long cell0, long ncells,
+                              double* __restrict__ pts) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= ncells * npts_cell<DIM>()) return;
+  init_point<DIM>(nodes, g, lo3, cell0, t, pts);
+}
+
+template <int DIM>
+CGKS_HD void init_cell(const double* __restrict__ nodes, const DevGeo& g, const Phys& ph, const double* lo3, long cell0,
+                       long cl, const double* __restrict__ prims, double* __restrict__ U) {
+  typedef Sz<DIM> S;
+  const int NV = S::NV, NP = npts_cell<DIM>(), NVOL = DIM == 3 ? 125 : 25;
+  const long N = g.ncell;
+  long c = cell0 + cl;
+  int i, j, k;
+  cell_ijk(g, c, i, j, k);
+  double lo[3] = {lo3[0], lo3[1], lo3[2]};
+  const double* pr = prims + cl * NP * NV;
+  double sum[NV], wsum = 0.0;
+  for (int v = 0; v < NV; ++v) sum[v] = 0.0;
+  for (int q = 0; q < NVOL; ++q) {
+    int qx = q % 5, qy = (q / 5) % 5, qz = q / 25;
+    double xi[3] = {0.5 + 0.5 * g5x(qx), 0.5 + 0.5 * g5x(qy), DIM == 3 ? 0.5 + 0.5 * g5x(qz) : 0.0};
+    double x[3], dj;
+    ref_to_phys<DIM>(nodes, g, lo, i, j, k, xi, x, &dj);
+    double w = g5w(qx) * g5w(qy) * (DIM == 3 ? g5w(qz) : 1.0) * dj;
+    const double* p = pr + q * NV;
+    double ke = 0.0;
+    for (int a = 0; a < DIM; ++a) ke += p[1 + a] * p[1 + a];
+    double W[NV];
+    W[0] = p[0];
+    for (int a = 0; a < DIM; ++a) W[1 + a] = p[0] * p[1 + a];
+    W[NV - 1] = p[NV - 1] / (ph.gamma - 1.0) + 0.5 * p[0] * ke;
+    for (int v = 0; v < NV; ++v) sum[v] += w * W[v];
+    wsum += w;
+  }
+  for (int v = 0; v < NV; ++v) U[(long)v * N + c] = sum[v] / wsum;
+  /* face-point values -> gradient and line derivatives */
+  const double vol = met_vol<DIM>(g, c);
+  for (int v = 0; v < NV; ++v) {
+    double gr[3] = {0.0, 0.0, 0.0};
+    double val[S::NGP];
+    for (int gp = 0; gp < S::NGP; ++gp) {
+      const double* p = pr + (NVOL + gp) * NV;
+      double W;
+      if (v == 0) W = p[0];
+      else if (v < NV - 1) W = p[0] * p[v];
+      else {
+        double ke = 0.0;
+        for (int a = 0; a < DIM; ++a) ke += p[1 + a] * p[1 + a];
+        W = p[NV - 1] / (ph.gamma - 1.0) + 0.5 * p[0] * ke;
+      }
+      val[gp] = W;
+      double sgn = ((gp / S::GPF) & 1) ? 1.0 : -1.0;
+      for (int a = 0; a < DIM; ++a) gr[a] += sgn * W * met_area<DIM>(g, c, gp, a);
+    }
+    for (int a = 0; a < DIM; ++a) U[((long)(1 + a) * NV + v) * N + c] = gr[a] / vol;
+    for (int s = 0; s < S::NL; ++s) {
+      int ax = s / S::GPF, kk = s % S::GPF;
+      double d = val[(2 * ax + 1) * S::GPF + kk] - val[(2 * ax) * S::GPF + kk];
+      U[((long)(1 + DIM + s) * NV + v) * N + c] = d / met_len<DIM>(g, c, s);
+    }
+  }
+}
+
+template <int DIM>
+__global__ void k_init_from_prims(const double* __restrict__ nodes, DevGeo g, Phys ph, const double* lo3, long cell0,
+                                  long ncells, const double* __restrict__ prims, double* __restrict__ U) {
+  long cl = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (cl >= ncells) return;
+  init_cell<DIM>(nodes, g, ph, lo3, cell0, cl, prims, U);
+}
+
+}  // namespace cgks

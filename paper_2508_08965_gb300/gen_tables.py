@@ -1,0 +1,384 @@
+"""Exact generator of the reconstruction tables of the CUDA library.
+
+Run ``python -m paper_2508_08965_gb300.gen_tables`` to rewrite
+``csrc/cgks_tables.h``; the header is committed so that the build needs only
+nvcc.
+
+What is tabulated (standard reference cell [0,1]^dim of Sec. 4, centroid 1/2,
+h = 1, so delta = xi - 1/2 lies in [-1/2, 1/2]^dim):
+
+* the quartic zero-mean basis of Eq. (base) (1 <= |d| <= 4: 34 terms in 3-D,
+  14 in 2-D), ordered by reflection-parity class;
+* the matrix M with a = M d for the constrained least squares of
+  Eq. (compact-big-ref): face-neighbour averages exact, edge-neighbour
+  averages (weight 1), face-neighbour gradients (h1' = 2), edge-neighbour
+  directional derivatives (h2' = 1, unit directions along the shared edge and
+  toward the neighbour centroid) and the target cell's line differences
+  (h3' = 3) in the least-squares sense; neighbours are unit cells at integer
+  offsets;
+* the Gram matrices of the GENO smoothness indicators (all derivatives
+  1 <= |l| <= 4, and |l| = 1 alone);
+* basis values and gradients at the face Gauss points (2-point Gauss per
+  tangential direction, +-1/(2 sqrt 3)).
+
+All entries are computed exactly: rationals plus rational multiples of sqrt(3)
+(the Gauss points), solved by fraction-exact Gaussian elimination on the KKT
+system, and rounded once to double.
+
+Data vector order used by the kernels (per variable):
+  [Q0,
+   for each face neighbour m (-x,+x,-y,+y[,-z,+z]): Q_m, (J0^T grad Q)_m (dim),
+   for each edge neighbour n: Q_n, tv_n . (J0^T grad Q)_n with the integer
+     directions tv = e_edge (3-D only) and tv = sum of the offset's non-zero
+     signed unit vectors (not normalised; the weight carries 1/|tv|^2),
+   line differences s = axis*gpf + k]
+Edge neighbours are taken in increasing offset order (o_z, o_y, o_x
+lexicographic, -1 < +1) among offsets with exactly two non-zero entries.
+"""
+import itertools
+import os
+from decimal import Decimal, getcontext
+from fractions import Fraction as Fr
+
+getcontext().prec = 60
+SQRT3 = Decimal(3).sqrt()
+
+
+class Q3:
+    """Number a + b sqrt(3) with rational a, b."""
+    __slots__ = ("a", "b")
+
+    def __init__(self, a=0, b=0):
+        self.a, self.b = Fr(a), Fr(b)
+
+    def __add__(self, o):
+        o = _q(o)
+        return Q3(self.a + o.a, self.b + o.b)
+
+    __radd__ = __add__
+
+    def __sub__(self, o):
+        o = _q(o)
+        return Q3(self.a - o.a, self.b - o.b)
+
+    def __rsub__(self, o):
+        return _q(o) - self
+
+    def __mul__(self, o):
+        o = _q(o)
+        return Q3(self.a * o.a + 3 * self.b * o.b, self.a * o.b + self.b * o.a)
+
+    __rmul__ = __mul__
+
+    def __neg__(self):
+        return Q3(-self.a, -self.b)
+
+    def to_float(self):
+        v = Decimal(self.a.numerator) / Decimal(self.a.denominator) + \
+            Decimal(self.b.numerator) / Decimal(self.b.denominator) * SQRT3
+        return float(v)
+
+    def is_zero(self):
+        return self.a == 0 and self.b == 0
+
+
+def _q(x):
+    return x if isinstance(x, Q3) else Q3(x, 0)
+
+
+G = Q3(0, Fr(1, 6))  # 1/(2 sqrt 3) = sqrt(3)/6
+HALF = Fr(1, 2)
+
+
+def fact(n):
+    f = 1
+    for i in range(2, n + 1):
+        f *= i
+    return f
+
+
+def ipow(x, e):
+    r = Q3(1)
+    for _ in range(e):
+        r = r * x
+    return r
+
+
+def int_mono(e, lo, hi):
+    """int_lo^hi t^e / e! dt (rational bounds)."""
+    return (Fr(hi) ** (e + 1) - Fr(lo) ** (e + 1)) / fact(e + 1)
+
+
+def basis(dim):
+    """exponents with 1 <= |d| <= 4 grouped by parity class (d mod 2), then degree."""
+    ex = [e for e in itertools.product(range(5), repeat=dim) if 1 <= sum(e) <= 4]
+    ex.sort(key=lambda e: (tuple(x % 2 for x in e), sum(e), tuple(-x for x in e)))
+    return ex
+
+
+def stencil(dim):
+    faces = []
+    for ax in range(dim):
+        for s in (-1, 1):
+            o = [0] * dim
+            o[ax] = s
+            faces.append(tuple(o))
+    edges = []
+    for o in itertools.product((-1, 0, 1), repeat=dim):
+        o = tuple(reversed(o))  # o_x fastest varying in the product -> reverse
+        if sum(1 for x in o if x != 0) == 2:
+            edges.append(o)
+    edges.sort(key=lambda o: tuple(reversed(o)))
+    return faces, edges
+
+
+def gpf(dim):
+    return 4 if dim == 3 else 2
+
+
+def gp_delta(dim, ax, side, k):
+    ta = [a for a in range(dim) if a != ax]
+    d = [Q3(0)] * dim
+    d[ax] = Q3(HALF if side else -HALF)
+    d[ta[0]] = G if (k & 1) else -G
+    if dim == 3:
+        d[ta[1]] = G if (k & 2) else -G
+    return d
+
+
+def tau_dirs(dim, o):
+    """directions of the edge-neighbour derivatives as integer vectors tv with
+    the squared inverse norm 1/|tv|^2: along the shared edge (3-D only) and
+    toward the neighbour centroid."""
+    nz = [a for a in range(dim) if o[a] != 0]
+    out = []
+    if dim == 3:
+        z = [a for a in range(3) if o[a] == 0][0]
+        t1 = [0] * 3
+        t1[z] = 1
+        out.append((t1, Fr(1)))
+    t2 = [0] * dim
+    for a in nz:
+        t2[a] = o[a]
+    out.append((t2, Fr(1, 2)))  # |t2|^2 = 2 -> unit vector t2/sqrt(2)
+    return out
+
+
+def mean_basis(e):
+    m = Fr(1)
+    for x in e:
+        m *= int_mono(x, -HALF, HALF)
+    return m
+
+
+def avg_basis(e, o):
+    v = Fr(1)
+    for i, x in enumerate(e):
+        v *= int_mono(x, o[i] - HALF, o[i] + HALF)
+    return v - mean_basis(e)
+
+
+def avg_dbasis(e, k, o):
+    if e[k] == 0:
+        return Fr(0)
+    v = Fr(1)
+    for i, x in enumerate(e):
+        xx = x - (1 if i == k else 0)
+        v *= int_mono(xx, o[i] - HALF, o[i] + HALF)
+    return v
+
+
+def eval_basis(e, d):
+    v = Q3(1)
+    for i, x in enumerate(e):
+        v = v * ipow(d[i], x) * Fr(1, fact(x))
+    return v - mean_basis(e)
+
+
+def eval_dbasis(e, k, d):
+    if e[k] == 0:
+        return Q3(0)
+    v = Q3(1)
+    for i, x in enumerate(e):
+        xx = x - (1 if i == k else 0)
+        v = v * ipow(d[i], xx) * Fr(1, fact(xx))
+    return v
+
+
+def solve_exact(K, B):
+    """Solve K X = B exactly (K, B lists of lists of Fractions)."""
+    n, m = len(K), len(B[0])
+    A = [row[:] + brow[:] for row, brow in zip(K, B)]
+    for c in range(n):
+        p = next(r for r in range(c, n) if A[r][c] != 0)
+        A[c], A[p] = A[p], A[c]
+        inv = 1 / A[c][c]
+        A[c] = [x * inv for x in A[c]]
+        for r in range(n):
+            if r != c and A[r][c] != 0:
+                f = A[r][c]
+                A[r] = [x - f * y for x, y in zip(A[r], A[c])]
+    return [row[n:] for row in A]
+
+
+def build(dim):
+    ex = basis(dim)
+    nb = len(ex)
+    faces, edges = stencil(dim)
+    g = gpf(dim)
+    ntau = 2 if dim == 3 else 1
+    # data index map
+    idx = {"Q0": 0}
+    c = 1
+    for m in range(len(faces)):
+        idx[("fQ", m)] = c
+        c += 1
+        for k in range(dim):
+            idx[("fG", m, k)] = c
+            c += 1
+    for n in range(len(edges)):
+        idx[("eQ", n)] = c
+        c += 1
+        for t in range(ntau):
+            idx[("eT", n, t)] = c
+            c += 1
+    for s in range(dim * g):
+        idx[("L", s)] = c
+        c += 1
+    nd = c
+    # equality rows (face averages) and least-squares rows: (coef row as Q3, weight^2, rhs column dict)
+    eq_rows, ls_rows = [], []
+    for m, o in enumerate(faces):
+        eq_rows.append(([Q3(avg_basis(e, o)) for e in ex], {idx[("fQ", m)]: Q3(1), 0: Q3(-1)}))
+    for n, o in enumerate(edges):
+        ls_rows.append(([Q3(avg_basis(e, o)) for e in ex], Fr(1), {idx[("eQ", n)]: Q3(1), 0: Q3(-1)}))
+    for m, o in enumerate(faces):
+        for k in range(dim):
+            ls_rows.append(([Q3(avg_dbasis(e, k, o)) for e in ex], Fr(4), {idx[("fG", m, k)]: Q3(1)}))
+    for n, o in enumerate(edges):
+        for t, (tv, s2) in enumerate(tau_dirs(dim, o)):
+            row = [Q3(sum(tv[k] * avg_dbasis(e, k, o) for k in range(dim))) for e in ex]
+            # the kernel loads tv . (J0^T grad Q) with the integer vector tv; the unit
+            # direction is tv/|tv|, so the 1/|tv|^2 factor goes into the weight
+            ls_rows.append((row, s2, {idx[("eT", n, t)]: Q3(1)}))
+    for ax in range(dim):
+        for k in range(g):
+            hi, lo = gp_delta(dim, ax, 1, k), gp_delta(dim, ax, 0, k)
+            row = [eval_basis(e, hi) - eval_basis(e, lo) for e in ex]
+            ls_rows.append((row, Fr(9), {idx[("L", ax * g + k)]: Q3(1)}))
+    # KKT: [sum w2 r r^T, C^T; C, 0][a; mu] = [sum w2 r rhs; rhs_eq]
+    nk = nb + len(eq_rows)
+    KQ = [[Q3(0)] * nb for _ in range(nb)]
+    Br = [[Fr(0)] * nd for _ in range(nk)]
+    Bs = [[Fr(0)] * nd for _ in range(nk)]
+    for row, w2, rhs in ls_rows:
+        for i in range(nb):
+            if row[i].is_zero():
+                continue
+            for j in range(nb):
+                if row[j].is_zero():
+                    continue
+                KQ[i][j] = KQ[i][j] + row[i] * row[j] * w2
+            for col, r in rhs.items():
+                v = row[i] * r * w2
+                Br[i][col] += v.a
+                Bs[i][col] += v.b
+    K = [[Fr(0)] * nk for _ in range(nk)]
+    for i in range(nb):
+        for j in range(nb):
+            # the sqrt(3) parts of the line rows cancel over the symmetric Gauss points
+            assert KQ[i][j].b == 0
+            K[i][j] = KQ[i][j].a
+    for q, (row, rhs) in enumerate(eq_rows):
+        for i in range(nb):
+            assert row[i].b == 0
+            K[i][nb + q] = row[i].a
+            K[nb + q][i] = row[i].a
+        for col, r in rhs.items():
+            Br[nb + q][col] += r.a
+    Xr = solve_exact(K, Br)
+    Xs = solve_exact(K, Bs)
+    M = [[Q3(Xr[i][j], Xs[i][j]) for j in range(nd)] for i in range(nb)]
+    # Gram matrices
+    GH = [[Fr(0)] * nb for _ in range(nb)]
+    GL = [[Fr(0)] * nb for _ in range(nb)]
+    lrange = [l for l in itertools.product(range(5), repeat=dim) if 1 <= sum(l) <= 4]
+    for i, ei in enumerate(ex):
+        for j, ej in enumerate(ex):
+            sh = sl = Fr(0)
+            for l in lrange:
+                v = Fr(1)
+                for a in range(dim):
+                    p, q = ei[a] - l[a], ej[a] - l[a]
+                    if p < 0 or q < 0:
+                        v = Fr(0)
+                        break
+                    v *= int_mono(p + q, -HALF, HALF) * fact(p + q) / (fact(p) * fact(q))
+                sh += v
+                if sum(l) == 1:
+                    sl += v
+            GH[i][j], GL[i][j] = sh, sl
+    # Gauss point tables: gp = (2*axis+side)*gpf + k
+    ngp = 2 * dim * g
+    PV = [[None] * nb for _ in range(ngp)]
+    PD = [[[None] * nb for _ in range(dim)] for _ in range(ngp)]
+    POS = []
+    for f in range(2 * dim):
+        for k in range(g):
+            gp = f * g + k
+            d = gp_delta(dim, f // 2, f & 1, k)
+            POS.append(d)
+            for b, e in enumerate(ex):
+                PV[gp][b] = eval_basis(e, d)
+                for kk in range(dim):
+                    PD[gp][kk][b] = eval_dbasis(e, kk, d)
+    return dict(ex=ex, nb=nb, nd=nd, M=M, GH=GH, GL=GL, PV=PV, PD=PD, POS=POS, faces=faces,
+                edges=edges, ngp=ngp)
+
+
+def _fmt(x):
+    if isinstance(x, Q3):
+        x = x.to_float()
+    elif isinstance(x, Fr):
+        x = float(Decimal(x.numerator) / Decimal(x.denominator))
+    return repr(float(x))
+
+
+def emit(path):
+    out = ["/* Generated by paper_2508_08965_gb300/gen_tables.py -- do not edit.",
+           "   Exact reconstruction tables of the CGKS-5 reference cell, rounded once to double. */",
+           "#pragma once", "#ifndef CGKS_TABLE", "#define CGKS_TABLE __constant__", "#endif",
+           "/* the Gauss-point tables live in global memory: the constant bank holds 64 KB */",
+           "#ifndef CGKS_GTABLE", "#define CGKS_GTABLE __device__ const", "#endif", ""]
+    for dim in (2, 3):
+        t = build(dim)
+        nb, nd, ngp = t["nb"], t["nd"], t["ngp"]
+        p = "T%d" % dim
+        out.append("/* %d-D: %d basis terms, %d data per variable, %d face Gauss points */" % (dim, nb, nd, ngp))
+        out.append("#define %s_NB %d" % (p, nb))
+        out.append("#define %s_ND %d" % (p, nd))
+        out.append("#define %s_NGP %d" % (p, ngp))
+        out.append("static const int %s_EXP[%d][3] = {%s};" % (
+            p, nb, ", ".join("{%s}" % ", ".join(str(x) for x in list(e) + [0] * (3 - dim)) for e in t["ex"])))
+        out.append("CGKS_TABLE double %s_M[%d][%d] = {" % (p, nb, nd))
+        out += ["  {%s}," % ", ".join(_fmt(x) for x in row) for row in t["M"]]
+        out.append("};")
+        for name in ("GH", "GL"):
+            out.append("CGKS_TABLE double %s_%s[%d][%d] = {" % (p, name, nb, nb))
+            out += ["  {%s}," % ", ".join(_fmt(x) for x in row) for row in t[name]]
+            out.append("};")
+        out.append("CGKS_GTABLE double %s_PV[%d][%d] = {" % (p, ngp, nb))
+        out += ["  {%s}," % ", ".join(_fmt(x) for x in row) for row in t["PV"]]
+        out.append("};")
+        out.append("CGKS_GTABLE double %s_PD[%d][%d][%d] = {" % (p, ngp, dim, nb))
+        for gp in range(ngp):
+            out.append("  {%s}," % ", ".join("{%s}" % ", ".join(_fmt(x) for x in t["PD"][gp][k]) for k in range(dim)))
+        out.append("};")
+        out.append("")
+    with open(path, "w") as f:
+        f.write("\n".join(out) + "\n")
+
+
+if __name__ == "__main__":
+    here = os.path.dirname(os.path.abspath(__file__))
+    emit(os.path.join(here, "csrc", "cgks_tables.h"))
