@@ -124,8 +124,20 @@ def test_sod_strip_nonlinear(orc, cg):
         m.step(5)
         sg, _ = m.get_state()
         assert class_scaled_diff(sg, o.get_state()) <= 1e-10
-    assert (o.chi() < 0.5).any()
-    assert np.allclose(m.chi(), o.chi(), rtol=0, atol=1e-9)
+    # chi of one more step.  Where the stencil holds only rounding noise (the
+    # undisturbed states) the smoothness indicators are noise and chi is not
+    # determined; compare chi where the density varies by more than 1e-6
+    rho = o.get_state()[0, 0]
+    var = np.zeros_like(rho)
+    for dj in (-1, 0, 1):
+        for di in (-1, 0, 1):
+            var = np.maximum(var, np.abs(np.roll(np.roll(rho, dj, 0), di, 1) - rho))
+    o.step(1)
+    m.step(1)
+    mask = var > 1e-6
+    co, cgp = o.chi(), m.chi()
+    assert (co[:, mask] < 0.5).any()
+    assert np.abs(co[:, mask] - cgp[:, mask]).max() <= 1e-9
     m.close()
 
 
