@@ -51,7 +51,8 @@ typedef enum {
   CGKS_ENONPHYS = -4,    /* non-positive density/pressure that even chi = 0 cannot cure */
   CGKS_ETIMEOUT = -5,    /* reserved: a bounded device wait gave up */
   CGKS_ESTATE = -6,      /* call made in the wrong state */
-  CGKS_EUNSUPPORTED = -7 /* option not available in this build */
+  CGKS_EUNSUPPORTED = -7, /* option not available in this build */
+  CGKS_ETOOLARGE = -8     /* problem larger than a fixed-size buffer of the library */
 } cgks_status;
 
 enum { CGKS_BC_PERIODIC = 0 };
@@ -126,6 +127,24 @@ cgks_status cgks_get_chi(cgks_ctx* ctx, double* dst, int is_device);
    milliseconds.  names receives up to cap entries; returns the count. */
 cgks_status cgks_profile_enable(cgks_ctx* ctx, int on);
 int cgks_profile_read(cgks_ctx* ctx, const char** names, long* launches, double* total_ms, int cap);
+
+/* Time step of a state the caller holds on the device, computed without
+   allocating any device memory.  The paper has no counterpart: this exists
+   for callers that cannot call cudaMalloc -- e.g. an application whose device
+   memory is reserved up front by another allocator, or a timed loop that
+   must not pay for allocation, which can synchronise the device.
+   desc: a uniform box (nodes must be NULL, else CGKS_EUNSUPPORTED) with dim,
+   n, lo, hi, gamma, mu, cfl, dt_fixed and stream as for cgks_create_mesh;
+   dev_state: device pointer to a state in the public layout; *dt_out (host)
+   receives the same dt as cgks_compute_dt would for that state.  At most
+   CGKS_DT_NOALLOC_MAX_CELLS cells, else CGKS_ETOOLARGE.  The work space is a
+   fixed array of (CGKS_DT_NOALLOC_MAX_CELLS/256 + 1) 8-byte words that every
+   GPU loading the library holds until the process exits; the first call on a
+   device also looks up that array's device address.  All calls share the
+   array: calls whose kernels overlap on the GPU race.  Synchronises the
+   stream. */
+#define CGKS_DT_NOALLOC_MAX_CELLS 16777216
+cgks_status cgks_compute_dt_noalloc(const cgks_mesh_desc* desc, const double* dev_state, double* dt_out);
 
 /* Copy the last error message (NUL-terminated, truncated to cap). */
 cgks_status cgks_last_error(const cgks_ctx* ctx, char* msg, size_t cap);

@@ -12,7 +12,7 @@ import numpy as np
 from . import build as _build
 
 STATUS_NAMES = {0: "CGKS_OK", -1: "CGKS_EINVAL", -2: "CGKS_ENOMEM", -3: "CGKS_ECUDA", -4: "CGKS_ENONPHYS",
-                -5: "CGKS_ETIMEOUT", -6: "CGKS_ESTATE", -7: "CGKS_EUNSUPPORTED"}
+                -5: "CGKS_ETIMEOUT", -6: "CGKS_ESTATE", -7: "CGKS_EUNSUPPORTED", -8: "CGKS_ETOOLARGE"}
 
 
 class CgksError(RuntimeError):
@@ -33,7 +33,7 @@ class MeshDesc(C.Structure):
 EXPORTS = ["cgks_create_mesh", "cgks_destroy", "cgks_num_vars", "cgks_num_fields", "cgks_num_cells",
            "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_compute_dt", "cgks_init_points_per_cell",
            "cgks_init_points", "cgks_init_from_prims", "cgks_get_chi", "cgks_profile_enable",
-           "cgks_profile_read", "cgks_last_error"]
+           "cgks_profile_read", "cgks_last_error", "cgks_compute_dt_noalloc"]
 
 _lib = None
 
@@ -68,6 +68,7 @@ def lib(build_if_missing=True):
     L.cgks_profile_enable.argtypes = [vp, C.c_int]
     L.cgks_profile_read.argtypes = [vp, C.POINTER(C.c_char_p), lp, dp, C.c_int]
     L.cgks_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
+    L.cgks_compute_dt_noalloc.argtypes = [C.POINTER(MeshDesc), vp, dp]
     _lib = L
     return L
 
@@ -207,3 +208,25 @@ class Mesh:
         ms = (C.c_double * 16)()
         n = lib().cgks_profile_read(self._h, names, launches, ms, 16)
         return {names[i].decode(): (launches[i], ms[i]) for i in range(n)}
+
+
+def compute_dt_noalloc(state, dim, n, lo, hi, gamma=1.4, mu=0.0, cfl=0.5, dt_fixed=0.0, stream=None):
+    """dt of a device state (torch CUDA float64 tensor, public layout) on a
+    uniform box, without any device allocation by the library (for callers
+    that cannot allocate: see cgks_compute_dt_noalloc in include/cgks.h).
+    Returns (status, dt); status 0 is CGKS_OK."""
+    torch = _torch()
+    assert isinstance(state, torch.Tensor) and state.is_cuda and state.dtype == torch.float64
+    d = MeshDesc()
+    d.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    for a in range(3):
+        d.n[a] = int(nn[a])
+        d.lo[a] = float(lo[a]) if a < len(lo) else 0.0
+        d.hi[a] = float(hi[a]) if a < len(hi) else 1.0
+    d.gamma, d.mu, d.cfl, d.dt_fixed = gamma, mu, cfl, dt_fixed
+    st = stream if stream is not None else torch.cuda.current_stream()
+    d.stream = C.c_void_p(st.cuda_stream)
+    dt = C.c_double(0.0)
+    status = lib().cgks_compute_dt_noalloc(C.byref(d), C.c_void_p(state.data_ptr()), C.byref(dt))
+    return status, dt.value
