@@ -4,7 +4,7 @@ Metric: cell-updates/s per S2O4 step (cells x steps / time) on the 3-D
 Taylor-Green vortex (Ma 0.1, Re 1600, Pr 0.72, gamma 1.4) on a periodic
 uniform [0, 2 pi]^3 mesh, 128^3 by default, plain FP64.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv128|tgv256|vortex64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv128|tgv256|tgv64|vortex64]
   python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 A step is one full S2O4 step (time-step reduction, two stages of
@@ -29,16 +29,22 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "tgv128": dict(dim=3, n=(128, 128, 128), desc="3-D Taylor-Green vortex 128^3, Ma 0.1, Re 1600, Pr 0.72, FP64"),
     "tgv256": dict(dim=3, n=(256, 256, 256), desc="3-D Taylor-Green vortex 256^3, Ma 0.1, Re 1600, Pr 0.72, FP64"),
+    "tgv64": dict(dim=3, n=(64, 64, 64), desc="3-D Taylor-Green vortex 64^3 (profiling size), Ma 0.1, Re 1600, FP64"),
     "vortex64": dict(dim=2, n=(64, 64), desc="2-D isentropic vortex 64^2 over [0,10]^2, eps 5"),
 }
 
-# FP64 work per unit of the dominant kernels, counted from the executed FP64
-# instructions (ncu, sass op counters) on a small case of the same kernels:
-# flops = 2 x DFMA + DADD + DMUL (+ the multi-instruction sequences of
-# division, sqrt and the special functions counted as executed).
+# FP64 work per unit of the two compute kernels, from the executed FP64
+# instructions of an ncu capture (TGV 64^3, same kernels): flops = 2 DFMA +
+# DADD + DMUL (division, sqrt and the special functions enter through the
+# instructions they execute).  recon: per cell; flux: per face Gauss point.
 FLOPS_PER_UNIT = {
-    ("recon", 3): None,  # per cell
-    ("flux", 3): None,   # per face Gauss point
+    ("recon", 3): 8.982e4,
+    ("flux", 3): 9.260e3,
+}
+# DRAM bytes per unit of the same capture (read + write), for `traffic`
+DRAM_BYTES_PER_UNIT = {
+    ("recon", 3): (0.296693e9 + 0.963135e9) / 262144,
+    ("flux", 3): (1.811688e9 + 7.160444e9) / (262144 * 12),
 }
 
 
@@ -282,9 +288,13 @@ def main():
     peak = fp64_alu_peak_tflops(sm_mhz=2070.0)
     if fpu:
         achieved = fpu * units / (avg_ms / 1e3) / 1e12
+        dbu = DRAM_BYTES_PER_UNIT.get((name, spec["dim"]))
         roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz (derived; probe 1.19-1.20)"}
+                "frac": achieved / peak, "traffic": dbu * units if dbu else None,
+                "flops_per_launch": fpu * units, "avg_launch_ms": avg_ms,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz, derived "
+                               "(an FMA-chain probe measured 1.19-1.20 TFLOP/s)",
+                "traffic_source": "ncu dram__bytes_read+write of a 64^3 capture, scaled by units"}
     else:
         roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "note": "flops per unit not yet counted"}
