@@ -38,13 +38,13 @@ WORKLOADS = {
 # DADD + DMUL (division, sqrt and the special functions enter through the
 # instructions they execute).  recon: per cell; flux: per face Gauss point.
 FLOPS_PER_UNIT = {
-    ("recon", 3): 8.982e4,
-    ("flux", 3): 9.260e3,
+    ("recon", 3): 2.175e4,
+    ("flux", 3): 4.520e3,
 }
 # DRAM bytes per unit of the same capture (read + write), for `traffic`
 DRAM_BYTES_PER_UNIT = {
-    ("recon", 3): (0.296693e9 + 0.963135e9) / 262144,
-    ("flux", 3): (1.811688e9 + 7.160444e9) / (262144 * 12),
+    ("recon", 3): (0.299e9 + 0.983e9) / 262144,
+    ("flux", 3): (1.009e9 + 0.810e9) / (262144 * 12),
 }
 
 
@@ -141,14 +141,14 @@ def cpu_baseline(wl, sample_cells=None):
     dim = spec["dim"]
     kw = mesh_kwargs(wl)
     if dim == 3:
-        m = sample_cells or 24
+        m = sample_cells or 40
         n = (m, m, m)
     else:
         n = (64, 64)
     orc = o.Oracle(dim, n, **kw)
     orc.init(field_fn(wl))
     orc.step(1)  # warm-up (builds tables, touches memory)
-    steps = 2 if dim == 3 else 20
+    steps = 3 if dim == 3 else 20
     t0 = time.perf_counter()
     orc.step(steps)
     el = time.perf_counter() - t0

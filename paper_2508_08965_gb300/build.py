@@ -9,7 +9,7 @@ SRC = os.path.join(HERE, "csrc", "cgks.cu")
 SRC_NOALLOC = os.path.join(HERE, "csrc", "cgks_noalloc.cu")
 LIB = os.path.join(HERE, "libcgks.so")
 DEPS = [os.path.join(HERE, "csrc", f) for f in ("cgks.cu", "cgks_noalloc.cu", "cgks_device.cuh", "cgks_kernels.cuh",
-                                                "cgks_tables.h")] + \
+                                                "cgks_tables.h", "cgks_recon_gen.cuh")] + \
     [os.path.join(ROOT, "include", "cgks.h")]
 
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",

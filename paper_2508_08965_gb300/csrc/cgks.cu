@@ -113,16 +113,29 @@ static cgks_status run_stage(cgks_ctx* ctx, const double* Uin, int stage, double
   const long N = ctx->ncell;
   const int B = 128;
   prof_begin(ctx, KID_RECON);
-  k_recon<DIM><<<cdiv(N, B), B, 0, ctx->stream>>>(Uin, ctx->geo, ctx->ph, ctx->gpL, ctx->gpR, ctx->chi,
-                                                  stage == 1 ? 1 : 0, ctx->st);
+  if (ctx->geo.curvi)
+    k_recon<DIM, true><<<cdiv(N, B), B, 0, ctx->stream>>>(Uin, ctx->geo, ctx->ph, ctx->gpL, ctx->gpR, ctx->chi,
+                                                          stage == 1 ? 1 : 0, ctx->st);
+  else
+    k_recon<DIM, false><<<cdiv(N, B), B, 0, ctx->stream>>>(Uin, ctx->geo, ctx->ph, ctx->gpL, ctx->gpR, ctx->chi,
+                                                           stage == 1 ? 1 : 0, ctx->st);
   prof_end(ctx);
   long nf = (long)DIM * Sz<DIM>::GPF * N;
   prof_begin(ctx, KID_FLUX);
-  k_flux<DIM><<<cdiv(nf, B), B, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, ctx->gpL, ctx->gpR, ctx->flux,
-                                                  ctx->st);
+  if (ctx->geo.curvi)
+    k_flux<DIM, true><<<cdiv(nf, B), B, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, ctx->gpL, ctx->gpR,
+                                                          ctx->flux, ctx->st);
+  else
+    k_flux<DIM, false><<<cdiv(nf, B), B, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, ctx->gpL, ctx->gpR,
+                                                           ctx->flux, ctx->st);
   prof_end(ctx);
   prof_begin(ctx, KID_UPDATE);
-  k_update<DIM><<<cdiv(N, B), B, 0, ctx->stream>>>(ctx->geo, ctx->dts, stage, Uin, ctx->flux, ctx->stash, Uout);
+  if (ctx->geo.curvi)
+    k_update<DIM, true><<<cdiv(N, B), B, 0, ctx->stream>>>(ctx->geo, ctx->dts, stage, Uin, ctx->flux, ctx->stash,
+                                                           Uout);
+  else
+    k_update<DIM, false><<<cdiv(N, B), B, 0, ctx->stream>>>(ctx->geo, ctx->dts, stage, Uin, ctx->flux, ctx->stash,
+                                                            Uout);
   prof_end(ctx);
   CK(cudaGetLastError());
   return CGKS_OK;

@@ -145,203 +145,176 @@ template <int DIM> CGKS_HD double met_len(const DevGeo& g, long c, int s) {
 /* ===================================================================== */
 /* (a) reconstruction of one variable of one cell                        */
 /* ===================================================================== */
-/* Loads the data vector of Eq. (compact-big-ref) in the order of the
-   generated tables, forms a = M d, the linear sub-stencil gradients of
+#include "cgks_recon_gen.cuh"
+
+/* data access of the reconstruction of variable v of cell c: own average and
+   line differences (reference frame: stored derivative x line length), and
+   neighbour averages and gradients mapped to the target's reference frame
+   with J0^T (Sec. 4).  CURVI = false: J0 = diag(h). */
+template <int DIM, bool CURVI> struct ReconLd {
+  const double* __restrict__ U;
+  DevGeo g;
+  long c;
+  int ci, cj, ck, v;
+  double J0[3][3];
+  CGKS_HD double q0() const { return U[(long)v * g.ncell + c]; }
+  CGKS_HD double avg(int ox, int oy, int oz) const {
+    return U[(long)v * g.ncell + nbr(g, ci, cj, ck, ox, oy, oz)];
+  }
+  CGKS_HD void grefv(int ox, int oy, int oz, double* out) const {
+    const long nb = nbr(g, ci, cj, ck, ox, oy, oz);
+    double gp[3];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) gp[r] = U[((long)(1 + r) * (DIM + 2) + v) * g.ncell + nb];
+    if constexpr (CURVI) {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) s += J0[r][k] * gp[r];
+        out[k] = s;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) out[k] = g.h[k] * gp[k];
+    }
+  }
+  CGKS_HD double line(int s) const {
+    return U[((long)(1 + DIM + s) * (DIM + 2) + v) * g.ncell + c] * met_len<DIM>(g, c, s);
+  }
+};
+
+/* Reconstruction of Eq. (compact-big-ref) on the reference cell: a = M d by the
+   generated symmetry-reduced code, the linear sub-stencil gradients of
    Eq. (compact-sub-2) (closed form: the face-neighbour difference along the
-   connecting axis, the mean of the four (two) line differences along each
-   other axis), the GENO weights, and writes the blended value and physical
-   gradient at every face Gauss point.  chi_force >= 0 overrides chi.
-   Returns chi. */
-template <int DIM>
+   connecting axis, the mean of the line differences along each other axis),
+   the GENO weights, and the blended value and physical gradient at every
+   face Gauss point (Eq. weno-new, reverse transform of Sec. 4).
+   chi_force >= 0 overrides chi.  Returns chi. */
+template <int DIM, bool CURVI>
 CGKS_HD double recon_var(const double* __restrict__ U, const DevGeo& g, const Phys& ph, long c, int ci, int cj,
                          int ck, int v, double chi_force, double* __restrict__ gpL, double* __restrict__ gpR) {
   typedef Sz<DIM> S;
   const long N = g.ncell;
-  const int NV = S::NV;
+  constexpr int NV = S::NV;
+  ReconLd<DIM, CURVI> ld;
+  ld.U = U;
+  ld.g = g;
+  ld.c = c;
+  ld.ci = ci;
+  ld.cj = cj;
+  ld.ck = ck;
+  ld.v = v;
+  if constexpr (CURVI) {
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) ld.J0[r][q] = met_J0<DIM>(g, c, r, q);
+  }
   double a[S::NB];
-#pragma unroll
-  for (int b = 0; b < S::NB; ++b) a[b] = 0.0;
-  double J0[3][3];
-#pragma unroll
-  for (int r = 0; r < DIM; ++r)
-#pragma unroll
-    for (int q = 0; q < DIM; ++q) J0[r][q] = met_J0<DIM>(g, c, r, q);
-
-  const double q0 = U[(long)v * N + c];
-#pragma unroll
-  for (int b = 0; b < S::NB; ++b) a[b] += tabM<DIM>(b, 0) * q0;
-  int col = 1;
-  double qf[2 * DIM];
-  /* face neighbours -x,+x,-y,+y(,-z,+z): average and J0^T grad */
-#pragma unroll
-  for (int m = 0; m < 2 * DIM; ++m) {
-    int o[3] = {0, 0, 0};
-    o[m / 2] = (m & 1) ? 1 : -1;
-    long nb = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
-    double q = U[(long)v * N + nb];
-    qf[m] = q;
-#pragma unroll
-    for (int b = 0; b < S::NB; ++b) a[b] += tabM<DIM>(b, col) * q;
-    ++col;
-    double gp[3];
-#pragma unroll
-    for (int r = 0; r < DIM; ++r) gp[r] = U[((long)(1 + r) * NV + v) * N + nb];
-#pragma unroll
-    for (int kk = 0; kk < DIM; ++kk) {
-      double s = 0.0;
-#pragma unroll
-      for (int r = 0; r < DIM; ++r) s += J0[r][kk] * gp[r];
-#pragma unroll
-      for (int b = 0; b < S::NB; ++b) a[b] += tabM<DIM>(b, col) * s;
-      ++col;
-    }
-  }
-  /* edge (3-D) / corner (2-D) neighbours, offsets in (oz, oy, ox) order */
-#pragma unroll
-  for (int oz = (DIM == 3 ? -1 : 0); oz <= (DIM == 3 ? 1 : 0); ++oz)
-#pragma unroll
-    for (int oy = -1; oy <= 1; ++oy)
-#pragma unroll
-      for (int ox = -1; ox <= 1; ++ox) {
-        int nzc = (ox != 0) + (oy != 0) + (oz != 0);
-        if (nzc != 2) continue;
-        long nb = nbr(g, ci, cj, ck, ox, oy, oz);
-        double q = U[(long)v * N + nb];
-#pragma unroll
-        for (int b = 0; b < S::NB; ++b) a[b] += tabM<DIM>(b, col) * q;
-        ++col;
-        double gp[3], gr[3];
-#pragma unroll
-        for (int r = 0; r < DIM; ++r) gp[r] = U[((long)(1 + r) * NV + v) * N + nb];
-#pragma unroll
-        for (int kk = 0; kk < DIM; ++kk) {
-          double s = 0.0;
-#pragma unroll
-          for (int r = 0; r < DIM; ++r) s += J0[r][kk] * gp[r];
-          gr[kk] = s;
-        }
-        int o[3] = {ox, oy, oz};
-        if (DIM == 3) { /* along the shared edge: the axis with zero offset */
-          int ze = ox == 0 ? 0 : (oy == 0 ? 1 : 2);
-          double d = gr[ze];
-#pragma unroll
-          for (int b = 0; b < S::NB; ++b) a[b] += tabM<DIM>(b, col) * d;
-          ++col;
-        }
-        { /* toward the neighbour centroid (un-normalised offset vector) */
-          double d = 0.0;
-#pragma unroll
-          for (int kk = 0; kk < DIM; ++kk) d += o[kk] * gr[kk];
-#pragma unroll
-          for (int b = 0; b < S::NB; ++b) a[b] += tabM<DIM>(b, col) * d;
-          ++col;
-        }
-      }
-  /* own line differences (reference frame): stored derivative x length */
-  double lsum[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-  for (int s = 0; s < S::NL; ++s) {
-    double d = U[((long)(1 + DIM + s) * NV + v) * N + c] * met_len<DIM>(g, c, s);
-    lsum[s / S::GPF] += d;
-#pragma unroll
-    for (int b = 0; b < S::NB; ++b) a[b] += tabM<DIM>(b, col) * d;
-    ++col;
-  }
+  if constexpr (DIM == 3) gen_coeffs_3d(ld, a);
+  else gen_coeffs_2d(ld, a);
+  const double q0 = ld.q0();
 
   /* GENO path function (Sec. 3.3) */
   double chi;
   if (chi_force >= 0.0) {
     chi = chi_force;
   } else {
-    double ish = 0.0, isl = 0.0;
-#pragma unroll
-    for (int b = 0; b < S::NB; ++b) {
-      double th = 0.0, tl = 0.0;
-#pragma unroll
-      for (int q = 0; q < S::NB; ++q) {
-        th += tabGH<DIM>(b, q) * a[q];
-        tl += tabGL<DIM>(b, q) * a[q];
-      }
-      ish += a[b] * th;
-      isl += a[b] * tl;
-    }
+    const double ish = DIM == 3 ? gen_ish_3d(a) : gen_ish_2d(a);
+    const double isl = DIM == 3 ? gen_isl_3d(a) : gen_isl_2d(a);
     const double eps = 1e-15;
     double ist = ish - isl;
     if (ist < 0.0) ist = 0.0;
-    double rh = ist / (ish + eps), rl = ist / (isl + eps);
-    double ah = 1.0 + rh * rh, al = 1.0 + rl * rl;
-    double alpha = 2.0 * ah / (ah + al);
+    const double rh = ist / (ish + eps), rl = ist / (isl + eps);
+    const double ah = 1.0 + rh * rh, al = 1.0 + rl * rl;
+    const double alpha = 2.0 * ah / (ah + al);
     chi = tanh(ph.c_chi * alpha) / tanh(ph.c_chi);
   }
   /* linear sub-stencil polynomials and their WENO weights (d_m = 1/(2 dim)) */
   double bbar[3] = {0.0, 0.0, 0.0};
   {
+    double lsum[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int s = 0; s < S::NL; ++s) lsum[s / S::GPF] += ld.line(s);
     double bm[2 * DIM][3], wb[2 * DIM], ws = 0.0;
 #pragma unroll
     for (int m = 0; m < 2 * DIM; ++m) {
-      int ax = m / 2;
-      double sg = (m & 1) ? 1.0 : -1.0;
+      const int ax = m / 2;
+      int o[3] = {0, 0, 0};
+      o[ax] = (m & 1) ? 1 : -1;
+      const double qf = ld.avg(o[0], o[1], o[2]);
+      const double sg = (m & 1) ? 1.0 : -1.0;
       double is = 0.0;
 #pragma unroll
       for (int kk = 0; kk < DIM; ++kk) {
-        double bv = (kk == ax) ? sg * (qf[m] - q0) : lsum[kk] * (1.0 / S::GPF);
+        const double bv = (kk == ax) ? sg * (qf - q0) : lsum[kk] * (1.0 / S::GPF);
         bm[m][kk] = bv;
         is += bv * bv;
       }
-      double t = is + 1e-15;
-      double t2 = t * t;
+      const double t = is + 1e-15;
+      const double t2 = t * t;
       wb[m] = (1.0 / (2 * DIM)) / (t2 * t2 * t);
       ws += wb[m];
     }
+    const double iws = 1.0 / ws;
 #pragma unroll
     for (int m = 0; m < 2 * DIM; ++m) {
-      double w = wb[m] / ws;
+      const double w = wb[m] * iws;
 #pragma unroll
       for (int kk = 0; kk < DIM; ++kk) bbar[kk] += w * bm[m][kk];
     }
   }
   double JiT[3][3];
+  if constexpr (CURVI) {
 #pragma unroll
-  for (int r = 0; r < DIM; ++r)
+    for (int r = 0; r < DIM; ++r)
 #pragma unroll
-    for (int q = 0; q < DIM; ++q) JiT[r][q] = met_JiT<DIM>(g, c, r, q);
-  /* blended values at the face Gauss points, Eq. (weno-new) */
-#pragma unroll 1
-  for (int gp = 0; gp < S::NGP; ++gp) {
-    double v4 = q0, g4[3] = {0.0, 0.0, 0.0};
+      for (int q = 0; q < DIM; ++q) JiT[r][q] = met_JiT<DIM>(g, c, r, q);
+  }
+  const double base4 = q0 - (DIM == 3 ? gen_mean_3d(a) : gen_mean_2d(a));
+  /* blended values at the face Gauss points, Eq. (weno-new), axis by axis */
 #pragma unroll
-    for (int b = 0; b < S::NB; ++b) {
-      v4 += a[b] * tabPV<DIM>(gp, b);
-#pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) g4[kk] += a[b] * tabPD<DIM>(gp, kk, b);
-    }
-    double v1 = q0;
-#pragma unroll
-    for (int kk = 0; kk < DIM; ++kk) v1 += bbar[kk] * gp_delta<DIM>(gp, kk);
-    double val = chi * v4 + (1.0 - chi) * v1;
-    double gref[3];
-#pragma unroll
-    for (int kk = 0; kk < DIM; ++kk) gref[kk] = chi * g4[kk] + (1.0 - chi) * bbar[kk];
-    int f = gp / S::GPF, k = gp % S::GPF, ax = f / 2, side = f & 1;
-    double* dst;
-    long cell;
-    if (side) {
-      dst = gpL;
-      cell = c;
+  for (int ax = 0; ax < DIM; ++ax) {
+    double pv[2 * S::GPF], pg[2 * S::GPF][DIM];
+    if constexpr (DIM == 3) {
+      if (ax == 0) gen_gp_3d_ax0(a, pv, pg);
+      else if (ax == 1) gen_gp_3d_ax1(a, pv, pg);
+      else gen_gp_3d_ax2(a, pv, pg);
     } else {
-      dst = gpR;
-      int o[3] = {0, 0, 0};
-      o[ax] = -1;
-      cell = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
+      if (ax == 0) gen_gp_2d_ax0(a, pv, pg);
+      else gen_gp_2d_ax1(a, pv, pg);
     }
-    long base = ((long)((ax * S::GPF + k) * NV + v) * (1 + DIM)) * N + cell;
-    dst[base] = val;
+    int o[3] = {0, 0, 0};
+    o[ax] = -1;
+    const long clo = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
 #pragma unroll
-    for (int kk = 0; kk < DIM; ++kk) {
-      double s = 0.0;
+    for (int i = 0; i < 2 * S::GPF; ++i) {
+      const int side = i / S::GPF, k = i % S::GPF;
+      const int gp = (2 * ax + side) * S::GPF + k;
+      double v1 = q0;
 #pragma unroll
-      for (int r = 0; r < DIM; ++r) s += JiT[kk][r] * gref[r];
-      dst[base + (long)(1 + kk) * N] = s;
+      for (int kk = 0; kk < DIM; ++kk) v1 += bbar[kk] * gp_delta<DIM>(gp, kk);
+      const double val = chi * (base4 + pv[i]) + (1.0 - chi) * v1;
+      double gref[3];
+#pragma unroll
+      for (int kk = 0; kk < DIM; ++kk) gref[kk] = chi * pg[i][kk] + (1.0 - chi) * bbar[kk];
+      double* dst = side ? gpL : gpR;
+      const long cell = side ? c : clo;
+      const long b = ((long)((ax * S::GPF + k) * NV + v) * (1 + DIM)) * N + cell;
+      dst[b] = val;
+#pragma unroll
+      for (int kk = 0; kk < DIM; ++kk) {
+        double sg;
+        if constexpr (CURVI) {
+          sg = 0.0;
+#pragma unroll
+          for (int r = 0; r < DIM; ++r) sg += JiT[kk][r] * gref[r];
+        } else {
+          sg = gref[kk] / g.h[kk];
+        }
+        dst[b + (long)(1 + kk) * N] = sg;
+      }
     }
   }
   return chi;
@@ -380,292 +353,463 @@ CGKS_HD bool cell_states_physical(const DevGeo& g, const Phys& ph, long c, int c
 /* ===================================================================== */
 /* (b) gas-kinetic interface solution at one Gauss point (Sec. 2)        */
 /* ===================================================================== */
-template <int DIM> struct Maxw {
-  double rho, U[3], lam;
+/* math wrappers so that the same code serves FP64 and FP32 */
+CGKS_HD double cg_erfc(double x) { return erfc(x); }
+CGKS_HD float cg_erfc(float x) { return erfcf(x); }
+CGKS_HD double cg_exp(double x) { return exp(x); }
+CGKS_HD float cg_exp(float x) { return expf(x); }
+CGKS_HD double cg_expm1(double x) { return expm1(x); }
+CGKS_HD float cg_expm1(float x) { return expm1f(x); }
+CGKS_HD double cg_sqrt(double x) { return sqrt(x); }
+CGKS_HD float cg_sqrt(float x) { return sqrtf(x); }
+CGKS_HD double cg_fabs(double x) { return fabs(x); }
+CGKS_HD float cg_fabs(float x) { return fabsf(x); }
+
+enum { REG_FULL = 0, REG_POS = 1, REG_NEG = 2 };
+
+/* Maxwellian of a conservative state: macroscopic scalars plus the two base
+   moments <u^0>, <u^1> of the normal direction over the full space or a half
+   space (the latter need erfc and exp, so they are kept, not recomputed). */
+template <typename T, int DIM> struct MxS {
+  T rho, irho, U[3], lam, p, i2l, u0, u1, xi2, xi4;
+};
+/* normalised 1-D moment tables up to order 6, built from MxS by recurrence */
+template <typename T> struct MxT {
+  T u[7], v[7], w[7];
 };
 
-/* normalised moments <u^n> (normal direction, full or half space), <v^n>,
-   <w^n> (full), <xi^2>, <xi^4> */
-struct Mom {
-  double u[7], v[7], w[7], xi2, xi4;
-};
-
-CGKS_HD void mom1d_full(double U, double lam, double* m) {
-  m[0] = 1.0;
-  m[1] = U;
-  for (int n = 0; n + 2 < 7; ++n) m[n + 2] = U * m[n + 1] + (n + 1) / (2.0 * lam) * m[n];
-}
-
-/* region: 0 full, 1 u > 0, 2 u < 0 */
-template <int DIM>
-CGKS_HD void moments(const Maxw<DIM>& g, double K, int region, Mom& T) {
-  if (region == 0) {
-    mom1d_full(g.U[0], g.lam, T.u);
+/* returns false for a non-positive density or pressure */
+template <typename T, int DIM>
+CGKS_HD bool mx_init(const T* W, T gam, T K, int region, MxS<T, DIM>& m) {
+  m.rho = W[0];
+  m.irho = T(1) / W[0];
+  T ke = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) m.U[i] = T(0);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    m.U[i] = W[1 + i] * m.irho;
+    ke += m.U[i] * W[1 + i];
+  }
+  m.p = (gam - T(1)) * (W[DIM + 1] - T(0.5) * ke);
+  if (!(m.rho > T(0)) || !(m.p > T(0))) return false;
+  m.i2l = m.p * m.irho; /* 1/(2 lambda) = p/rho */
+  m.lam = T(0.5) / m.i2l;
+  if (region == REG_FULL) {
+    m.u0 = T(1);
+    m.u1 = m.U[0];
   } else {
-    double sl = sqrt(g.lam);
-    double e = 0.5 * exp(-g.lam * g.U[0] * g.U[0]) / sqrt(3.14159265358979323846 * g.lam);
-    if (region == 1) {
-      T.u[0] = 0.5 * erfc(-sl * g.U[0]);
-      T.u[1] = g.U[0] * T.u[0] + e;
+    const T sl = cg_sqrt(m.lam);
+    const T e = T(0.5) * cg_exp(-m.lam * m.U[0] * m.U[0]) / cg_sqrt(T(3.14159265358979323846) * m.lam);
+    if (region == REG_POS) {
+      m.u0 = T(0.5) * cg_erfc(-sl * m.U[0]);
+      m.u1 = m.U[0] * m.u0 + e;
     } else {
-      T.u[0] = 0.5 * erfc(sl * g.U[0]);
-      T.u[1] = g.U[0] * T.u[0] - e;
+      m.u0 = T(0.5) * cg_erfc(sl * m.U[0]);
+      m.u1 = m.U[0] * m.u0 - e;
     }
-    for (int n = 0; n + 2 < 7; ++n) T.u[n + 2] = g.U[0] * T.u[n + 1] + (n + 1) / (2.0 * g.lam) * T.u[n];
   }
-  mom1d_full(g.U[1], g.lam, T.v);
-  if (DIM == 3) {
-    mom1d_full(g.U[2], g.lam, T.w);
-  } else {
-    T.w[0] = 1.0;
-    for (int n = 1; n < 7; ++n) T.w[n] = 0.0;
-  }
-  T.xi2 = K / (2.0 * g.lam);
-  T.xi4 = (K * K + 2.0 * K) / (4.0 * g.lam * g.lam);
+  m.xi2 = K * m.i2l;
+  m.xi4 = (K * K + T(2) * K) * m.i2l * m.i2l;
+  return true;
 }
 
-/* <u^a v^b w^c psi> */
-template <int DIM>
-CGKS_HD void mpsi(const Mom& T, int a, int b, int c, double* o) {
-  double m0 = T.u[a] * T.v[b] * T.w[c];
-  o[0] = m0;
-  o[1] = T.u[a + 1] * T.v[b] * T.w[c];
-  o[2] = T.u[a] * T.v[b + 1] * T.w[c];
-  double e = T.u[a + 2] * T.v[b] * T.w[c] + T.u[a] * T.v[b + 2] * T.w[c] + m0 * T.xi2;
-  if (DIM == 3) {
-    o[3] = T.u[a] * T.v[b] * T.w[c + 1];
-    e += T.u[a] * T.v[b] * T.w[c + 2];
+template <typename T, int DIM>
+CGKS_HD void mx_tables(const MxS<T, DIM>& m, MxT<T>& t) {
+  t.u[0] = m.u0;
+  t.u[1] = m.u1;
+  t.v[0] = T(1);
+  t.v[1] = m.U[1];
+  t.w[0] = T(1);
+  t.w[1] = DIM == 3 ? m.U[2] : T(0);
+#pragma unroll
+  for (int n = 0; n < 5; ++n) {
+    const T c = T(n + 1) * m.i2l;
+    t.u[n + 2] = m.U[0] * t.u[n + 1] + c * t.u[n];
+    t.v[n + 2] = m.U[1] * t.v[n + 1] + c * t.v[n];
+    t.w[n + 2] = DIM == 3 ? m.U[2] * t.w[n + 1] + c * t.w[n] : T(0);
   }
-  o[DIM + 1] = 0.5 * e;
 }
 
-/* <xi^2 u^a v^b w^c psi> */
-template <int DIM>
-CGKS_HD void mpsi_xi2(const Mom& T, int a, int b, int c, double* o) {
-  double m0 = T.u[a] * T.v[b] * T.w[c];
-  o[0] = m0 * T.xi2;
-  o[1] = T.u[a + 1] * T.v[b] * T.w[c] * T.xi2;
-  o[2] = T.u[a] * T.v[b + 1] * T.w[c] * T.xi2;
-  double e = (T.u[a + 2] * T.v[b] * T.w[c] + T.u[a] * T.v[b + 2] * T.w[c]) * T.xi2 + m0 * T.xi4;
-  if (DIM == 3) {
-    o[3] = T.u[a] * T.v[b] * T.w[c + 1] * T.xi2;
-    e += T.u[a] * T.v[b] * T.w[c + 2] * T.xi2;
+/* out_i = < (al . psi) u^A v^B w^C psi_i >, psi = (1, u, v[, w], (u^2+v^2[+w^2]+xi^2)/2) */
+template <typename T, int DIM, int A, int B, int C>
+CGKS_HD void mvec(const MxS<T, DIM>& s, const MxT<T>& m, const T* al, T* out) {
+#define CG_M(i, j, k) (m.u[(i)] * m.v[(j)] * m.w[(k)])
+  const T M0 = CG_M(A, B, C), Ma1 = CG_M(A + 1, B, C), Mb1 = CG_M(A, B + 1, C);
+  const T Ma2 = CG_M(A + 2, B, C), Mb2 = CG_M(A, B + 2, C), Mab = CG_M(A + 1, B + 1, C);
+  T Mc1 = T(0), Mc2 = T(0), Mac = T(0), Mbc = T(0), Ec = T(0);
+  T E0 = Ma2 + Mb2 + s.xi2 * M0;
+  T Ea = CG_M(A + 3, B, C) + CG_M(A + 1, B + 2, C) + s.xi2 * Ma1;
+  T Eb = CG_M(A + 2, B + 1, C) + CG_M(A, B + 3, C) + s.xi2 * Mb1;
+  T EE = CG_M(A + 4, B, C) + CG_M(A, B + 4, C) + T(2) * CG_M(A + 2, B + 2, C) + T(2) * s.xi2 * (Ma2 + Mb2) +
+         s.xi4 * M0;
+  if constexpr (DIM == 3) {
+    Mc1 = CG_M(A, B, C + 1);
+    Mc2 = CG_M(A, B, C + 2);
+    Mac = CG_M(A + 1, B, C + 1);
+    Mbc = CG_M(A, B + 1, C + 1);
+    E0 += Mc2;
+    Ea += CG_M(A + 1, B, C + 2);
+    Eb += CG_M(A, B + 1, C + 2);
+    Ec = T(0.5) * (CG_M(A + 2, B, C + 1) + CG_M(A, B + 2, C + 1) + CG_M(A, B, C + 3) + s.xi2 * Mc1);
+    EE += CG_M(A, B, C + 4) + T(2) * CG_M(A + 2, B, C + 2) + T(2) * CG_M(A, B + 2, C + 2) + T(2) * s.xi2 * Mc2;
   }
-  o[DIM + 1] = 0.5 * e;
+#undef CG_M
+  E0 *= T(0.5);
+  Ea *= T(0.5);
+  Eb *= T(0.5);
+  EE *= T(0.25);
+  const T a0 = al[0], a1 = al[1], a2 = al[2], ae = al[DIM + 1];
+  const T a3 = DIM == 3 ? al[DIM == 3 ? 3 : 0] : T(0);
+  out[0] = a0 * M0 + a1 * Ma1 + a2 * Mb1 + a3 * Mc1 + ae * E0;
+  out[1] = a0 * Ma1 + a1 * Ma2 + a2 * Mab + a3 * Mac + ae * Ea;
+  out[2] = a0 * Mb1 + a1 * Mab + a2 * Mb2 + a3 * Mbc + ae * Eb;
+  if constexpr (DIM == 3) out[3] = a0 * Mc1 + a1 * Mac + a2 * Mbc + a3 * Mc2 + ae * Ec;
+  out[DIM + 1] = a0 * E0 + a1 * Ea + a2 * Eb + a3 * Ec + ae * EE;
 }
 
-/* <(al . psi) u^a v^b w^c psi> */
-template <int DIM>
-CGKS_HD void mapsi(const Mom& T, const double* al, int a, int b, int c, double* o) {
-  const int NV = DIM + 2;
-  double t[NV], e[NV];
-  mpsi<DIM>(T, a, b, c, t);
-  for (int i = 0; i < NV; ++i) o[i] = al[0] * t[i];
-  mpsi<DIM>(T, a + 1, b, c, t);
-  for (int i = 0; i < NV; ++i) o[i] += al[1] * t[i];
-  mpsi<DIM>(T, a, b + 1, c, t);
-  for (int i = 0; i < NV; ++i) o[i] += al[2] * t[i];
-  if (DIM == 3) {
-    mpsi<DIM>(T, a, b, c + 1, t);
-    for (int i = 0; i < NV; ++i) o[i] += al[3] * t[i];
+/* <u^A psi> */
+template <typename T, int DIM, int A>
+CGKS_HD void mpsi_u(const MxS<T, DIM>& s, const MxT<T>& m, T* out) {
+  out[0] = m.u[A];
+  out[1] = m.u[A + 1];
+  out[2] = m.u[A] * m.v[1];
+  T e = m.u[A + 2] + m.u[A] * m.v[2] + s.xi2 * m.u[A];
+  if constexpr (DIM == 3) {
+    out[3] = m.u[A] * m.w[1];
+    e += m.u[A] * m.w[2];
   }
-  mpsi<DIM>(T, a + 2, b, c, e);
-  mpsi<DIM>(T, a, b + 2, c, t);
-  for (int i = 0; i < NV; ++i) e[i] += t[i];
-  if (DIM == 3) {
-    mpsi<DIM>(T, a, b, c + 2, t);
-    for (int i = 0; i < NV; ++i) e[i] += t[i];
-  }
-  mpsi_xi2<DIM>(T, a, b, c, t);
-  for (int i = 0; i < NV; ++i) o[i] += 0.5 * al[NV - 1] * (e[i] + t[i]);
+  out[DIM + 1] = T(0.5) * e;
 }
 
 /* micro-slope: solve <a psi psi^T> = b in closed form (D = K + dim = 2/(gamma-1)) */
-template <int DIM>
-CGKS_HD void slope(const Maxw<DIM>& g, double D, const double* b, double* a) {
-  double q2 = 0.0, R[3], uR = 0.0;
+template <typename T, int DIM>
+CGKS_HD void slope_solve(const MxS<T, DIM>& g, T D, T iD, const T* b, T* a) {
+  T q2 = T(0), R[3], uR = T(0);
+#pragma unroll
   for (int i = 0; i < DIM; ++i) {
     q2 += g.U[i] * g.U[i];
     R[i] = b[1 + i] - g.U[i] * b[0];
     uR += g.U[i] * R[i];
   }
-  double th = q2 + D / (2.0 * g.lam);
-  double Re = 2.0 * b[DIM + 1] - th * b[0];
-  double ae = 4.0 * g.lam * g.lam / D * (Re - 2.0 * uR);
-  double s = 0.0;
+  const T th = q2 + D * g.i2l;
+  const T Re = T(2) * b[DIM + 1] - th * b[0];
+  const T ae = T(4) * g.lam * g.lam * iD * (Re - T(2) * uR);
+  T s = T(0);
+#pragma unroll
   for (int i = 0; i < DIM; ++i) {
-    a[1 + i] = 2.0 * g.lam * R[i] - g.U[i] * ae;
+    a[1 + i] = T(2) * g.lam * R[i] - g.U[i] * ae;
     s += g.U[i] * a[1 + i];
   }
   a[DIM + 1] = ae;
-  a[0] = b[0] - s - 0.5 * ae * th;
+  a[0] = b[0] - s - T(0.5) * ae * th;
 }
 
-template <int DIM>
-CGKS_HD bool maxw_of(const double* W, double gam, Maxw<DIM>& m) {
-  m.rho = W[0];
-  double ke = 0.0;
-  for (int i = 0; i < 3; ++i) m.U[i] = 0.0;
+/* Euler flux along local axis j of a Maxwellian state, and its Jacobian
+   applied to dW: for a Maxwellian, rho <(a.psi) u_j psi> = (dF_j/dW) dW when
+   rho <a psi> = dW, which replaces the compatibility moments */
+template <typename T, int DIM>
+CGKS_HD void euler_flux(const MxS<T, DIM>& g, const T* W, int j, T* F) {
+  const T H = (W[DIM + 1] + g.p) * g.irho;
+  const T mj = W[1 + j];
+  F[0] = mj;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) F[1 + i] = mj * g.U[i] + (i == j ? g.p : T(0));
+  F[DIM + 1] = H * mj;
+}
+
+template <typename T, int DIM>
+CGKS_HD void euler_jvp(const MxS<T, DIM>& g, T gam, const T* W, int j, const T* dW, T* out) {
+  const T H = (W[DIM + 1] + g.p) * g.irho;
+  T q2 = T(0), um = T(0);
+#pragma unroll
   for (int i = 0; i < DIM; ++i) {
-    m.U[i] = W[1 + i] / W[0];
-    ke += m.U[i] * W[1 + i];
+    q2 += g.U[i] * g.U[i];
+    um += g.U[i] * dW[1 + i];
   }
-  double p = (gam - 1.0) * (W[DIM + 1] - 0.5 * ke);
-  m.lam = W[0] / (2.0 * p);
-  return (W[0] > 0.0) && (p > 0.0);
+  const T dp = (gam - T(1)) * (dW[DIM + 1] - um + T(0.5) * q2 * dW[0]);
+  const T uj = g.U[j], dmj = dW[1 + j];
+  out[0] = dmj;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) out[1 + i] = uj * dW[1 + i] + g.U[i] * dmj - uj * g.U[i] * dW[0] + (i == j ? dp : T(0));
+  out[DIM + 1] = uj * (dW[DIM + 1] + dp) + H * (dmj - uj * dW[0]);
 }
 
 /* time integrals over [0, dl] of the six coefficient functions of Eq. (flux) */
-CGKS_HD void tcoef(double tau, double dl, double* c) {
-  if (tau <= 0.0) {
-    c[0] = dl; c[1] = 0.0; c[2] = 0.5 * dl * dl; c[3] = 0.0; c[4] = 0.0; c[5] = 0.0;
+template <typename T>
+CGKS_HD void tcoef(T tau, T dl, T* c) {
+  if (tau <= T(0)) {
+    c[0] = dl; c[1] = T(0); c[2] = T(0.5) * dl * dl; c[3] = T(0); c[4] = T(0); c[5] = T(0);
     return;
   }
-  double em = -expm1(-dl / tau);
-  double ex = exp(-dl / tau);
+  const T x = dl / tau;
+  const T em = -cg_expm1(-x);
+  const T ex = cg_exp(-x);
   c[0] = dl - tau * em;
-  c[1] = 2.0 * tau * tau - tau * (dl + 2.0 * tau) * ex - tau * dl;
-  c[2] = 0.5 * dl * dl - tau * dl + tau * tau * em;
+  c[1] = T(2) * tau * tau - tau * (dl + T(2) * tau) * ex - tau * dl;
+  c[2] = T(0.5) * dl * dl - tau * dl + tau * tau * em;
   c[3] = tau * em;
-  c[4] = -2.0 * tau * tau + tau * (dl + 2.0 * tau) * ex;
+  c[4] = T(-2) * tau * tau + tau * (dl + T(2) * tau) * ex;
   c[5] = -tau * tau * em;
 }
 
-/* Local frame (x normal): W* values, dW*[j][v] derivatives along local axis j.
-   out[part*NV + v], parts F^n, F_t^n, Q^l(0), (dQ/dt)^l, Q^r(0), (dQ/dt)^r.
-   Returns false on a non-physical state. */
-template <int DIM>
-CGKS_HD bool gks_point(const Phys& ph, double dt, const double* WL, const double* dWL, const double* WR,
-                       const double* dWR, double* out) {
-  const int NV = DIM + 2;
-  const double gam = ph.gamma;
-  const double D = 2.0 / (gam - 1.0);
-  const double K = D - DIM;
-  Maxw<DIM> gl, gr, g0;
-  if (!maxw_of<DIM>(WL, gam, gl) || !maxw_of<DIM>(WR, gam, gr)) return false;
-  Mom Tlp, Trn, Tlf, Trf, T0;
-  moments<DIM>(gl, K, 1, Tlp);
-  moments<DIM>(gr, K, 2, Trn);
-  double W0[NV], t1[NV], t2[NV];
-  mpsi<DIM>(Tlp, 0, 0, 0, t1);
-  mpsi<DIM>(Trn, 0, 0, 0, t2);
-  for (int i = 0; i < NV; ++i) W0[i] = gl.rho * t1[i] + gr.rho * t2[i];
-  if (!maxw_of<DIM>(W0, gam, g0)) return false;
-  moments<DIM>(g0, K, 0, T0);
-  moments<DIM>(gl, K, 0, Tlf);
-  moments<DIM>(gr, K, 0, Trf);
-  /* spatial micro-slopes of the two sides and of g0 */
-  double al[DIM][NV], ar[DIM][NV], a0[DIM][NV];
-  for (int j = 0; j < DIM; ++j) {
-    double b[NV];
-    for (int i = 0; i < NV; ++i) b[i] = dWL[j * NV + i] / gl.rho;
-    slope<DIM>(gl, D, b, al[j]);
-    for (int i = 0; i < NV; ++i) b[i] = dWR[j * NV + i] / gr.rho;
-    slope<DIM>(gr, D, b, ar[j]);
-    mapsi<DIM>(Tlp, al[j], 0, 0, 0, t1);
-    mapsi<DIM>(Trn, ar[j], 0, 0, 0, t2);
-    for (int i = 0; i < NV; ++i) b[i] = (gl.rho * t1[i] + gr.rho * t2[i]) / g0.rho;
-    slope<DIM>(g0, D, b, a0[j]);
+/* one side (the left half Maxwellian for u > 0 or the right one for u < 0):
+   its slopes along each local axis, its share of the g0 slopes dW0, its
+   compatibility right-hand side and time slope, and its flux parts 4 and 5
+   (and their psi-moments for the heat-flux fix) */
+template <typename T, int DIM, int J>
+CGKS_HD void side_dir(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, const T* W, const T* dWj,
+                      const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, T* Qn, T* Qt, T* bs, T* dW0j) {
+  constexpr int NV = DIM + 2;
+  constexpr int E0 = J == 0, E1 = J == 1, E2 = J == 2;
+  T b[NV], a[NV], t1[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) b[i] = dWj[i] * s.irho;
+  slope_solve<T, DIM>(s, D, iD, b, a);
+  mvec<T, DIM, 0, 0, 0>(s, t, a, t1);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) dW0j[i] += s.rho * t1[i];
+  euler_jvp<T, DIM>(s, gam, W, J, dWj, t1);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) bs[i] -= t1[i] * s.irho;
+  mvec<T, DIM, 1 + E0, E1, E2>(s, t, a, t1);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    Fn[i] += cn[4] * s.rho * t1[i];
+    Ft[i] += ct[4] * s.rho * t1[i];
   }
-  /* time slopes: compatibility <(a.u + A) psi> = 0 */
-  double bl[NV], br[NV], b0[NV];
-  for (int i = 0; i < NV; ++i) bl[i] = br[i] = b0[i] = 0.0;
-  for (int j = 0; j < DIM; ++j) {
-    int e0 = j == 0, e1 = j == 1, e2 = j == 2;
-    mapsi<DIM>(Tlf, al[j], e0, e1, e2, t1);
-    for (int i = 0; i < NV; ++i) bl[i] -= t1[i];
-    mapsi<DIM>(Trf, ar[j], e0, e1, e2, t1);
-    for (int i = 0; i < NV; ++i) br[i] -= t1[i];
-    mapsi<DIM>(T0, a0[j], e0, e1, e2, t1);
-    for (int i = 0; i < NV; ++i) b0[i] -= t1[i];
+  if (prfix) {
+    mvec<T, DIM, E0, E1, E2>(s, t, a, t1);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      Qn[i] += cn[4] * s.rho * t1[i];
+      Qt[i] += ct[4] * s.rho * t1[i];
+    }
   }
-  double Al[NV], Ar[NV], A0[NV];
-  slope<DIM>(gl, D, bl, Al);
-  slope<DIM>(gr, D, br, Ar);
-  slope<DIM>(g0, D, b0, A0);
-  /* collision time (Sec. 6) */
-  double pl = gl.rho / (2.0 * gl.lam), pr = gr.rho / (2.0 * gr.lam), p0 = g0.rho / (2.0 * g0.lam);
-  double jump = fabs((pl - pr) / (pl + pr));
-  double tau = 0.0;
-  if (ph.tau_mode == 1) tau = 0.05 * dt + 5.0 * jump * dt;
-  else if (ph.tau_mode == 2) tau = ph.mu / p0 + 5.0 * jump * dt;
-  double cf[6], chf[6], cn[6], ct[6];
-  tcoef(tau, dt, cf);
-  tcoef(tau, 0.5 * dt, chf);
-  for (int i = 0; i < 6; ++i) {
-    cn[i] = (4.0 * chf[i] - cf[i]) / dt;
-    ct[i] = 4.0 * (cf[i] - 2.0 * chf[i]) / (dt * dt);
+}
+
+template <typename T, int DIM, class Ld>
+CGKS_HD void side_all(const MxS<T, DIM>& s, T gam, T D, T iD, const T* W, const Ld& ld, int side, const T* cn,
+                      const T* ct, bool prfix, T* Fn, T* Ft, T* Qn, T* Qt, T* bs, T* dW0) {
+  constexpr int NV = DIM + 2;
+  MxT<T> t;
+  mx_tables<T, DIM>(s, t);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) bs[i] = T(0);
+  T dWj[NV];
+  ld.grad(side, 0, dWj);
+  side_dir<T, DIM, 0>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, Qn, Qt, bs, dW0);
+  ld.grad(side, 1, dWj);
+  side_dir<T, DIM, 1>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, Qn, Qt, bs, dW0 + NV);
+  if constexpr (DIM == 3) {
+    ld.grad(side, 2, dWj);
+    side_dir<T, DIM, 2>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, Qn, Qt, bs, dW0 + 2 * NV);
+  }
+  T A[NV], t1[NV];
+  slope_solve<T, DIM>(s, D, iD, bs, A);
+  mvec<T, DIM, 1, 0, 0>(s, t, A, t1);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    Fn[i] += cn[5] * s.rho * t1[i];
+    Ft[i] += ct[5] * s.rho * t1[i];
+  }
+  if (prfix) {
+    mvec<T, DIM, 0, 0, 0>(s, t, A, t1);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      Qn[i] += cn[5] * s.rho * t1[i];
+      Qt[i] += ct[5] * s.rho * t1[i];
+    }
+  }
+}
+
+/* g0 along local axis j: slope from dW0_j, flux part 1 and the compatibility
+   right-hand side (whose psi-moment is the Euler Jacobian product) */
+template <typename T, int DIM, int J>
+CGKS_HD void g0_dir(const MxS<T, DIM>& z, const MxT<T>& t, T gam, T D, T iD, const T* W0, const T* dW0j,
+                    const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, T* Qn, T* Qt, T* b0) {
+  constexpr int NV = DIM + 2;
+  constexpr int E0 = J == 0, E1 = J == 1, E2 = J == 2;
+  T b[NV], a[NV], t1[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) b[i] = dW0j[i] * z.irho;
+  slope_solve<T, DIM>(z, D, iD, b, a);
+  mvec<T, DIM, 1 + E0, E1, E2>(z, t, a, t1);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    Fn[i] += cn[1] * z.rho * t1[i];
+    Ft[i] += ct[1] * z.rho * t1[i];
+  }
+  euler_jvp<T, DIM>(z, gam, W0, J, dW0j, t1);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) b0[i] -= t1[i] * z.irho;
+  if (prfix) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      Qn[i] += cn[1] * t1[i];
+      Qt[i] += ct[1] * t1[i];
+    }
+  }
+}
+
+/* The interface solution in the local frame (x normal to the face).
+   WL, WR: conservative states (normal momentum first); dWL, dWR: DIM x NV
+   derivatives along the local axes.  out[part*NV + v], parts F^n, F_t^n,
+   Q^l(0), (dQ/dt)^l, Q^r(0), (dQ/dt)^r.  Returns false on a non-physical state.
+   Readings: g0 and its slopes from the kinetic collision of the two half
+   Maxwellians; f^n, f_t^n from the time integrals over dt and dt/2; the
+   interface values of the two-sided model with tau0 = 5|pl-pr|/(pl+pr) dt. */
+template <typename T, int DIM, class Ld>
+CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const Ld& ld, T* out) {
+  constexpr int NV = DIM + 2;
+  const T gam = T(ph.gamma);
+  const T D = T(2) / (gam - T(1));
+  const T iD = T(1) / D;
+  const T K = D - T(DIM);
+  MxS<T, DIM> l, r, z;
+  if (!mx_init<T, DIM>(WL, gam, K, REG_POS, l) || !mx_init<T, DIM>(WR, gam, K, REG_NEG, r)) return false;
+  /* equilibrium state W0 and flux part 3 from the two half Maxwellians */
+  T W0[NV], H3[NV], t1[NV], t2[NV];
+  {
+    MxT<T> t;
+    mx_tables<T, DIM>(l, t);
+    mpsi_u<T, DIM, 0>(l, t, t1);
+    mpsi_u<T, DIM, 1>(l, t, t2);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      W0[i] = l.rho * t1[i];
+      H3[i] = l.rho * t2[i];
+    }
+    mx_tables<T, DIM>(r, t);
+    mpsi_u<T, DIM, 0>(r, t, t1);
+    mpsi_u<T, DIM, 1>(r, t, t2);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      W0[i] += r.rho * t1[i];
+      H3[i] += r.rho * t2[i];
+    }
+  }
+  if (!mx_init<T, DIM>(W0, gam, K, REG_FULL, z)) return false;
+  /* collision time (Sec. 6) and the time-integral coefficients */
+  const T jump = cg_fabs((l.p - r.p) / (l.p + r.p));
+  T tau = T(0);
+  if (ph.tau_mode == 1) tau = T(0.05) * dt + T(5) * jump * dt;
+  else if (ph.tau_mode == 2) tau = T(ph.mu) / z.p + T(5) * jump * dt;
+  T cn[6], ct[6];
+  {
+    T cf[6], chf[6];
+    tcoef<T>(tau, dt, cf);
+    tcoef<T>(tau, T(0.5) * dt, chf);
+    const T idt = T(1) / dt;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      cn[i] = (T(4) * chf[i] - cf[i]) * idt;
+      ct[i] = T(4) * (cf[i] - T(2) * chf[i]) * idt * idt;
+    }
   }
   const bool prfix = ph.mu > 0.0 && ph.prandtl > 0.0 && ph.prandtl != 1.0;
-  double Fn[NV], Ft[NV], Qn[NV], Qt[NV];
-  for (int i = 0; i < NV; ++i) Fn[i] = Ft[i] = Qn[i] = Qt[i] = 0.0;
-  for (int pass = 0; pass < (prfix ? 2 : 1); ++pass) {
-    const int xu = pass == 0 ? 1 : 0; /* u-moment for fluxes, none for Q */
-    double* An = pass == 0 ? Fn : Qn;
-    double* At = pass == 0 ? Ft : Qt;
-    double part[NV], s1[NV], s2[NV];
-    /* g0 */
-    mpsi<DIM>(T0, xu, 0, 0, s1);
-    for (int i = 0; i < NV; ++i) { part[i] = g0.rho * s1[i]; An[i] += cn[0] * part[i]; At[i] += ct[0] * part[i]; }
-    for (int i = 0; i < NV; ++i) part[i] = 0.0;
-    for (int j = 0; j < DIM; ++j) {
-      mapsi<DIM>(T0, a0[j], xu + (j == 0), j == 1, j == 2, s1);
-      for (int i = 0; i < NV; ++i) part[i] += g0.rho * s1[i];
-    }
-    for (int i = 0; i < NV; ++i) { An[i] += cn[1] * part[i]; At[i] += ct[1] * part[i]; }
-    mapsi<DIM>(T0, A0, xu, 0, 0, s1);
-    for (int i = 0; i < NV; ++i) { part[i] = g0.rho * s1[i]; An[i] += cn[2] * part[i]; At[i] += ct[2] * part[i]; }
-    /* g_l H(u) + g_r (1 - H(u)) */
-    mpsi<DIM>(Tlp, xu, 0, 0, s1);
-    mpsi<DIM>(Trn, xu, 0, 0, s2);
-    for (int i = 0; i < NV; ++i) {
-      part[i] = gl.rho * s1[i] + gr.rho * s2[i];
-      An[i] += cn[3] * part[i];
-      At[i] += ct[3] * part[i];
-    }
-    for (int i = 0; i < NV; ++i) part[i] = 0.0;
-    for (int j = 0; j < DIM; ++j) {
-      mapsi<DIM>(Tlp, al[j], xu + (j == 0), j == 1, j == 2, s1);
-      mapsi<DIM>(Trn, ar[j], xu + (j == 0), j == 1, j == 2, s2);
-      for (int i = 0; i < NV; ++i) part[i] += gl.rho * s1[i] + gr.rho * s2[i];
-    }
-    for (int i = 0; i < NV; ++i) { An[i] += cn[4] * part[i]; At[i] += ct[4] * part[i]; }
-    mapsi<DIM>(Tlp, Al, xu, 0, 0, s1);
-    mapsi<DIM>(Trn, Ar, xu, 0, 0, s2);
-    for (int i = 0; i < NV; ++i) {
-      part[i] = gl.rho * s1[i] + gr.rho * s2[i];
-      An[i] += cn[5] * part[i];
-      At[i] += ct[5] * part[i];
-    }
+  T Fn[NV], Ft[NV], Qn[NV], Qt[NV], bl[NV], br[NV], b0[NV], dW0[DIM * NV];
+  euler_flux<T, DIM>(z, W0, 0, t1); /* part 0: rho0 <u psi> of g0 */
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    Fn[i] = cn[0] * t1[i] + cn[3] * H3[i];
+    Ft[i] = ct[0] * t1[i] + ct[3] * H3[i];
+    Qn[i] = (cn[0] + cn[3]) * W0[i];
+    Qt[i] = (ct[0] + ct[3]) * W0[i];
+    b0[i] = T(0);
+  }
+#pragma unroll
+  for (int i = 0; i < DIM * NV; ++i) dW0[i] = T(0);
+  side_all<T, DIM>(l, gam, D, iD, WL, ld, 0, cn, ct, prfix, Fn, Ft, Qn, Qt, bl, dW0);
+  side_all<T, DIM>(r, gam, D, iD, WR, ld, 1, cn, ct, prfix, Fn, Ft, Qn, Qt, br, dW0);
+  {
+    MxT<T> t;
+    mx_tables<T, DIM>(z, t);
+    g0_dir<T, DIM, 0>(z, t, gam, D, iD, W0, dW0, cn, ct, prfix, Fn, Ft, Qn, Qt, b0);
+    g0_dir<T, DIM, 1>(z, t, gam, D, iD, W0, dW0 + NV, cn, ct, prfix, Fn, Ft, Qn, Qt, b0);
+    if constexpr (DIM == 3) g0_dir<T, DIM, 2>(z, t, gam, D, iD, W0, dW0 + 2 * NV, cn, ct, prfix, Fn, Ft, Qn, Qt, b0);
+  }
+  /* part 2: rho0 <A0 u psi> = (dF_x/dW)(rho0 b0), psi-moment rho0 b0 */
+#pragma unroll
+  for (int i = 0; i < NV; ++i) t2[i] = z.rho * b0[i];
+  euler_jvp<T, DIM>(z, gam, W0, 0, t2, t1);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    Fn[i] += cn[2] * t1[i];
+    Ft[i] += ct[2] * t1[i];
   }
   if (prfix) { /* heat-flux correction F_E += (1/Pr - 1) q about the interface velocity */
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      Qn[i] += cn[2] * t2[i];
+      Qt[i] += ct[2] * t2[i];
+    }
+    const T f = T(1) / T(ph.prandtl) - T(1);
+#pragma unroll
     for (int pass = 0; pass < 2; ++pass) {
-      double* F = pass == 0 ? Fn : Ft;
-      double* Q = pass == 0 ? Qn : Qt;
-      double uf = 0.0, uq = 0.0, u2 = 0.0;
+      T* F = pass == 0 ? Fn : Ft;
+      T* Q = pass == 0 ? Qn : Qt;
+      T uf = T(0), uq = T(0), u2 = T(0);
+#pragma unroll
       for (int i = 0; i < DIM; ++i) {
-        uf += g0.U[i] * F[1 + i];
-        uq += g0.U[i] * Q[1 + i];
-        u2 += g0.U[i] * g0.U[i];
+        uf += z.U[i] * F[1 + i];
+        uq += z.U[i] * Q[1 + i];
+        u2 += z.U[i] * z.U[i];
       }
-      double q = (F[DIM + 1] - uf + 0.5 * u2 * F[0]) - g0.U[0] * (Q[DIM + 1] - uq + 0.5 * u2 * Q[0]);
-      F[DIM + 1] += (1.0 / ph.prandtl - 1.0) * q;
+      T q = (F[DIM + 1] - uf + T(0.5) * u2 * F[0]) - z.U[0] * (Q[DIM + 1] - uq + T(0.5) * u2 * Q[0]);
+      F[DIM + 1] += f * q;
     }
   }
   /* interface values for the derivative update (temporal discretisation section) */
-  double tau0 = 5.0 * jump * dt;
-  double w = tau0 > 0.0 ? exp(-dt / tau0) : 0.0;
+  const T tau0 = T(5) * jump * dt;
+  const T w = tau0 > T(0) ? cg_exp(-dt / tau0) : T(0);
+#pragma unroll
   for (int i = 0; i < NV; ++i) {
     out[i] = Fn[i];
     out[NV + i] = Ft[i];
-    double dq0 = g0.rho * b0[i];
-    out[2 * NV + i] = (1.0 - w) * W0[i] + w * WL[i];
-    out[3 * NV + i] = (1.0 - w) * dq0 + w * gl.rho * bl[i];
-    out[4 * NV + i] = (1.0 - w) * W0[i] + w * WR[i];
-    out[5 * NV + i] = (1.0 - w) * dq0 + w * gr.rho * br[i];
+    const T dq0 = z.rho * b0[i];
+    out[2 * NV + i] = (T(1) - w) * W0[i] + w * WL[i];
+    out[3 * NV + i] = (T(1) - w) * dq0 + w * l.rho * bl[i];
+    out[4 * NV + i] = (T(1) - w) * W0[i] + w * WR[i];
+    out[5 * NV + i] = (T(1) - w) * dq0 + w * r.rho * br[i];
   }
   return true;
 }
+
+/* derivative loader over local arrays dWL, dWR (DIM x NV each) */
+template <typename T, int DIM> struct ArrLd {
+  const T* dL;
+  const T* dR;
+  CGKS_HD void grad(int side, int j, T* o) const {
+    const T* src = (side == 0 ? dL : dR) + j * (DIM + 2);
+    for (int i = 0; i < DIM + 2; ++i) o[i] = src[i];
+  }
+};
+
+template <typename T, int DIM>
+CGKS_HD bool gks_point(const Phys& ph, T dt, const T* WL, const T* dWL, const T* WR, const T* dWR, T* out) {
+  ArrLd<T, DIM> ld{dWL, dWR};
+  return gks_point_ld<T, DIM>(ph, dt, WL, WR, ld, out);
+}
+
+/* derivative loader of the Cartesian path: reads the local-frame derivative of
+   side 0 (left, gpL) or 1 (right, gpR) along local axis j from global memory,
+   through the signed-permutation frame */
+template <int DIM> struct CartLd {
+  const double* gl;
+  const double* gr;
+  long base, N, c;
+  int p[3], s[3];
+  CGKS_HD void grad(int side, int j, double* o) const {
+    const double* src = side == 0 ? gl : gr;
+#pragma unroll
+    for (int v = 0; v < DIM + 2; ++v) {
+      int vg = v, sv = 1;
+      if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
+      o[v] = (sv * s[j]) * src[(base + vg * (1 + DIM) + 1 + p[j]) * N + c];
+    }
+  }
+};
 
 /* local orthonormal frame rows (n, t1, t2): n along the area vector, t1 from
    the face tangent (3-D); t = (-n_y, n_x) in 2-D */
@@ -690,155 +834,267 @@ CGKS_HD void face_frame(const double* A, const double* T, double R[3][3]) {
   for (int a = 0; a < 3; ++a) { R[0][a] = n[a]; R[1][a] = t1[a]; R[2][a] = t2[a]; }
 }
 
-/* global-frame Gauss-point state (value + gradient per variable) -> local frame */
+/* Cartesian face frames as signed permutations: local axis i = s[i] e_{p[i]}.
+   They equal face_frame for axis-aligned faces: (x,y,z), (y,x,-z), (z,x,y);
+   2-D: (x,y), (y,-x). */
 template <int DIM>
-CGKS_HD void to_local(const double R[3][3], const double* st /* NV*(1+DIM) */, double* W, double* dW) {
+CGKS_HD void cart_frame(int ax, int* p, int* s) {
+  if (DIM == 2) {
+    p[0] = ax; p[1] = 1 - ax; s[0] = 1; s[1] = ax == 0 ? 1 : -1;
+    return;
+  }
+  if (ax == 0) { p[0] = 0; p[1] = 1; p[2] = 2; s[0] = s[1] = s[2] = 1; }
+  else if (ax == 1) { p[0] = 1; p[1] = 0; p[2] = 2; s[0] = 1; s[1] = 1; s[2] = -1; }
+  else { p[0] = 2; p[1] = 0; p[2] = 1; s[0] = s[1] = s[2] = 1; }
+}
+
+/* global-frame Gauss-point state (value + gradient per variable) -> local frame */
+template <typename T, int DIM>
+CGKS_HD void to_local(const double R[3][3], const T* st /* NV*(1+DIM) */, T* W, T* dW) {
   const int NV = DIM + 2;
-  double gv[NV][3];
+  T gv[NV][3];
   for (int v = 0; v < NV; ++v) {
     W[v] = st[v * (1 + DIM)];
     for (int k = 0; k < DIM; ++k) gv[v][k] = st[v * (1 + DIM) + 1 + k];
   }
-  double m[3];
+  T m[3];
   for (int i = 0; i < DIM; ++i) {
-    m[i] = 0.0;
-    for (int a = 0; a < DIM; ++a) m[i] += R[i][a] * W[1 + a];
+    m[i] = T(0);
+    for (int a = 0; a < DIM; ++a) m[i] += T(R[i][a]) * W[1 + a];
   }
   for (int i = 0; i < DIM; ++i) W[1 + i] = m[i];
-  double gr[NV][3];
+  T gr[NV][3];
   for (int k = 0; k < DIM; ++k) {
     gr[0][k] = gv[0][k];
     gr[NV - 1][k] = gv[NV - 1][k];
     for (int i = 0; i < DIM; ++i) {
-      double s = 0.0;
-      for (int a = 0; a < DIM; ++a) s += R[i][a] * gv[1 + a][k];
+      T s = T(0);
+      for (int a = 0; a < DIM; ++a) s += T(R[i][a]) * gv[1 + a][k];
       gr[1 + i][k] = s;
     }
   }
   for (int j = 0; j < DIM; ++j)
     for (int v = 0; v < NV; ++v) {
-      double s = 0.0;
-      for (int k = 0; k < DIM; ++k) s += R[j][k] * gr[v][k];
+      T s = T(0);
+      for (int k = 0; k < DIM; ++k) s += T(R[j][k]) * gr[v][k];
       dW[j * NV + v] = s;
     }
 }
 
-template <int DIM>
-CGKS_HD void to_global(const double R[3][3], double* F) {
-  double m[3];
+template <typename T, int DIM>
+CGKS_HD void to_global(const double R[3][3], T* F) {
+  T m[3];
   for (int a = 0; a < DIM; ++a) {
-    m[a] = 0.0;
-    for (int i = 0; i < DIM; ++i) m[a] += R[i][a] * F[1 + i];
+    m[a] = T(0);
+    for (int i = 0; i < DIM; ++i) m[a] += T(R[i][a]) * F[1 + i];
   }
   for (int a = 0; a < DIM; ++a) F[1 + a] = m[a];
 }
 
-/* one face Gauss point: gather, rotate, solve, rotate back, store */
-template <int DIM>
+/* one face Gauss point: gather, rotate, solve, rotate back, store.
+   CURVI selects at compile time between the Cartesian signed-permutation
+   frames and general face frames. */
+template <int DIM, bool CURVI>
 CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, double dt, int ax, int k, long c,
                         const double* __restrict__ gpL, const double* __restrict__ gpR, double* __restrict__ flux) {
   typedef Sz<DIM> S;
-  const int NV = S::NV;
+  constexpr int NV = S::NV;
   const long N = g.ncell;
+  const long base = (long)((ax * S::GPF + k) * NV) * (1 + DIM);
+  double WL[NV], WR[NV], out[6 * NV];
+  if constexpr (!CURVI) {
+    /* value and momentum: W_loc[1+i] = s_i m_{p_i}; derivative along local j:
+       s_j d/dx_{p_j} of the local variable (loaded when its side needs it) */
+    CartLd<DIM> ld;
+    ld.gl = gpL;
+    ld.gr = gpR;
+    ld.base = base;
+    ld.N = N;
+    ld.c = c;
+    cart_frame<DIM>(ax, ld.p, ld.s);
+    const int* p = ld.p;
+    const int* s = ld.s;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      int vg = v, sv = 1;
+      if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
+      const long b = (base + vg * (1 + DIM)) * N + c;
+      WL[v] = sv * gpL[b];
+      WR[v] = sv * gpR[b];
+    }
+    bool ok = gks_point_ld<double, DIM>(ph, dt, WL, WR, ld, out);
+    const long fb = (long)((ax * S::GPF + k) * 6) * NV;
+#pragma unroll
+    for (int part = 0; part < 6; ++part) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        int vg = v, sv = 1;
+        if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
+        flux[(fb + part * NV + vg) * N + c] = sv * out[part * NV + v];
+      }
+    }
+    return ok;
+  } else {
+  double dWL[DIM * NV], dWR[DIM * NV];
   double sl[NV * (1 + DIM)], sr[NV * (1 + DIM)];
-  long base = (long)((ax * S::GPF + k) * NV) * (1 + DIM);
   for (int q = 0; q < NV * (1 + DIM); ++q) {
     sl[q] = gpL[(base + q) * N + c];
     sr[q] = gpR[(base + q) * N + c];
   }
-  double A[3], T[3];
+  double A[3], Tt[3];
   int gp = (2 * ax + 1) * S::GPF + k;
   for (int a = 0; a < 3; ++a) {
     A[a] = a < DIM ? met_area<DIM>(g, c, gp, a) : 0.0;
-    T[a] = a < DIM ? met_tang<DIM>(g, c, ax, k, a) : 0.0;
+    Tt[a] = a < DIM ? met_tang<DIM>(g, c, ax, k, a) : 0.0;
   }
   double R[3][3];
-  face_frame<DIM>(A, T, R);
-  double WL[NV], dWL[DIM * NV], WR[NV], dWR[DIM * NV], out[6 * NV];
-  to_local<DIM>(R, sl, WL, dWL);
-  to_local<DIM>(R, sr, WR, dWR);
-  bool ok = gks_point<DIM>(ph, dt, WL, dWL, WR, dWR, out);
-  for (int p = 0; p < 6; ++p) to_global<DIM>(R, out + p * NV);
-  long fb = (long)((ax * S::GPF + k) * 6) * NV;
+  face_frame<DIM>(A, Tt, R);
+  to_local<double, DIM>(R, sl, WL, dWL);
+  to_local<double, DIM>(R, sr, WR, dWR);
+  bool ok = gks_point<double, DIM>(ph, dt, WL, dWL, WR, dWR, out);
+  for (int p = 0; p < 6; ++p) to_global<double, DIM>(R, out + p * NV);
+  const long fb = (long)((ax * S::GPF + k) * 6) * NV;
   for (int q = 0; q < 6 * NV; ++q) flux[(fb + q) * N + c] = out[q];
   return ok;
+  }
 }
 
 /* ===================================================================== */
 /* (c) accumulation and S2O4 update of one cell                          */
 /* ===================================================================== */
 /* stage 1: Uout = U* ; stash = {Q^n + dt L + dt^2/6 L_t ; D(Q^n(x_G))}
-   stage 2: Uout = U^{n+1} = {stash + dt^2/3 L_t* ; stash_D + dt D((dQ/dt)*(x_G))} */
-template <int DIM>
+   stage 2: Uout = U^{n+1} = {stash + dt^2/3 L_t* ; stash_D + dt D((dQ/dt)*(x_G))}
+   L = -(1/|Omega|) sum_faces sum_k F.n S (Eq. semi with Gauss quadrature); the
+   gradient by Gauss' theorem (Eq. derivative) and the line derivatives by
+   Eq. (derivative-l) from the interface values of each side.  CURVI = false:
+   axis-aligned cells, where both reduce to differences divided by h. */
+template <int DIM, bool CURVI>
 CGKS_HD void update_cell(const DevGeo& g, double dt, int stage, long c, int ci, int cj, int ck,
                          const double* __restrict__ Uin, const double* __restrict__ flux,
                          double* __restrict__ stash, double* __restrict__ Uout) {
   typedef Sz<DIM> S;
-  const int NV = S::NV, GPF = S::GPF;
+  constexpr int NV = S::NV, GPF = S::GPF;
   const long N = g.ncell;
-  const double vol = met_vol<DIM>(g, c);
   long lo[3];
+#pragma unroll
   for (int ax = 0; ax < DIM; ++ax) {
     int o[3] = {0, 0, 0};
     o[ax] = -1;
     lo[ax] = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
   }
+  double ivol, ih[3] = {1.0, 1.0, 1.0};
+  double sh[DIM][GPF], sl[DIM][GPF];
+  if constexpr (CURVI) {
+    ivol = 1.0 / met_vol<DIM>(g, c);
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax)
+#pragma unroll
+      for (int k = 0; k < GPF; ++k) {
+        const int ghi = (2 * ax + 1) * GPF + k;
+        double a2 = 0.0, b2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const double ah = met_area<DIM>(g, c, ghi, a), al = met_area<DIM>(g, lo[ax], ghi, a);
+          a2 += ah * ah;
+          b2 += al * al;
+        }
+        sh[ax][k] = sqrt(a2);
+        sl[ax][k] = sqrt(b2);
+      }
+  } else {
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) ih[ax] = 1.0 / g.h[ax];
+    ivol = 1.0;
+  }
+  const double hdt = 0.5 * dt, edt2 = 0.125 * dt * dt, sdt2 = dt * dt / 6.0, tdt2 = dt * dt / 3.0;
+#pragma unroll 1
   for (int v = 0; v < NV; ++v) {
     double L = 0.0, Lt = 0.0;
     double qn[S::NGP], qt[S::NGP];
+#pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
+      double la = 0.0, lta = 0.0;
+#pragma unroll
       for (int k = 0; k < GPF; ++k) {
-        long fb = (long)((ax * GPF + k) * 6) * NV + v;
-        int ghi = (2 * ax + 1) * GPF + k, glo = (2 * ax) * GPF + k;
-        double sh = 0.0, sl = 0.0;
-        for (int a = 0; a < DIM; ++a) {
-          double ah = met_area<DIM>(g, c, ghi, a);
-          double al = met_area<DIM>(g, lo[ax], ghi, a);
-          sh += ah * ah;
-          sl += al * al;
+        const long fb = (long)((ax * GPF + k) * 6) * NV + v;
+        const int ghi = (2 * ax + 1) * GPF + k, glo = (2 * ax) * GPF + k;
+        const double fh = flux[(fb + 0 * NV) * N + c], fl = flux[(fb + 0 * NV) * N + lo[ax]];
+        const double fth = flux[(fb + 1 * NV) * N + c], ftl = flux[(fb + 1 * NV) * N + lo[ax]];
+        if constexpr (CURVI) {
+          la += -fh * sh[ax][k] + fl * sl[ax][k];
+          lta += -fth * sh[ax][k] + ftl * sl[ax][k];
+        } else {
+          la += fl - fh;
+          lta += ftl - fth;
         }
-        sh = sqrt(sh);
-        sl = sqrt(sl);
-        L += -flux[(fb + 0 * NV) * N + c] * sh + flux[(fb + 0 * NV) * N + lo[ax]] * sl;
-        Lt += -flux[(fb + 1 * NV) * N + c] * sh + flux[(fb + 1 * NV) * N + lo[ax]] * sl;
         qn[ghi] = flux[(fb + 2 * NV) * N + c];
         qt[ghi] = flux[(fb + 3 * NV) * N + c];
         qn[glo] = flux[(fb + 4 * NV) * N + lo[ax]];
         qt[glo] = flux[(fb + 5 * NV) * N + lo[ax]];
       }
+      if constexpr (CURVI) {
+        L += la;
+        Lt += lta;
+      } else {
+        L += la * ih[ax] * (1.0 / GPF);
+        Lt += lta * ih[ax] * (1.0 / GPF);
+      }
     }
-    L /= vol;
-    Lt /= vol;
+    L *= ivol;
+    Lt *= ivol;
     const long iavg = (long)v * N + c;
     if (stage == 1) {
-      double q = Uin[iavg];
-      Uout[iavg] = q + 0.5 * dt * L + 0.125 * dt * dt * Lt;
-      stash[iavg] = q + dt * L + dt * dt / 6.0 * Lt;
+      const double q = Uin[iavg];
+      Uout[iavg] = q + hdt * L + edt2 * Lt;
+      stash[iavg] = q + dt * L + sdt2 * Lt;
     } else {
-      Uout[iavg] = stash[iavg] + dt * dt / 3.0 * Lt;
+      Uout[iavg] = stash[iavg] + tdt2 * Lt;
     }
-    /* derivative fields: gradient (Gauss' theorem) and line derivatives */
+    /* line derivatives, then the gradient */
+    double ln[S::NL], lt[S::NL];
+#pragma unroll
+    for (int s2 = 0; s2 < S::NL; ++s2) {
+      const int ax = s2 / GPF, k = s2 % GPF;
+      const double il = CURVI ? 1.0 / met_len<DIM>(g, c, s2) : ih[ax];
+      ln[s2] = (qn[(2 * ax + 1) * GPF + k] - qn[(2 * ax) * GPF + k]) * il;
+      lt[s2] = (qt[(2 * ax + 1) * GPF + k] - qt[(2 * ax) * GPF + k]) * il;
+    }
+#pragma unroll
     for (int f = 1; f < S::NF; ++f) {
-      double dn = 0.0, dtv = 0.0;
+      double dn, dtv;
       if (f <= DIM) {
-        int kk = f - 1;
-        for (int gp = 0; gp < S::NGP; ++gp) {
-          double sgn = ((gp / GPF) & 1) ? 1.0 : -1.0;
-          double A = met_area<DIM>(g, c, gp, kk);
-          dn += sgn * qn[gp] * A;
-          dtv += sgn * qt[gp] * A;
+        const int kk = f - 1;
+        if constexpr (CURVI) {
+          dn = 0.0;
+          dtv = 0.0;
+#pragma unroll
+          for (int gp = 0; gp < S::NGP; ++gp) {
+            const double sgn = ((gp / GPF) & 1) ? 1.0 : -1.0;
+            const double A = sgn * met_area<DIM>(g, c, gp, kk);
+            dn += qn[gp] * A;
+            dtv += qt[gp] * A;
+          }
+          dn *= ivol;
+          dtv *= ivol;
+        } else {
+          /* Gauss' theorem on an axis-aligned cell: the mean of the line derivatives */
+          dn = 0.0;
+          dtv = 0.0;
+#pragma unroll
+          for (int k = 0; k < GPF; ++k) {
+            dn += ln[kk * GPF + k];
+            dtv += lt[kk * GPF + k];
+          }
+          dn *= (1.0 / GPF);
+          dtv *= (1.0 / GPF);
         }
-        dn /= vol;
-        dtv /= vol;
       } else {
-        int s = f - 1 - DIM, ax = s / GPF, k = s % GPF;
-        double len = met_len<DIM>(g, c, s);
-        dn = (qn[(2 * ax + 1) * GPF + k] - qn[(2 * ax) * GPF + k]) / len;
-        dtv = (qt[(2 * ax + 1) * GPF + k] - qt[(2 * ax) * GPF + k]) / len;
+        dn = ln[f - 1 - DIM];
+        dtv = lt[f - 1 - DIM];
       }
       const long idx = ((long)f * NV + v) * N + c;
       if (stage == 1) {
-        Uout[idx] = dn + 0.5 * dt * dtv;
+        Uout[idx] = dn + hdt * dtv;
         stash[idx] = dn;
       } else {
         Uout[idx] = stash[idx] + dt * dtv;

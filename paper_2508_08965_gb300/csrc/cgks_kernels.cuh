@@ -19,7 +19,7 @@ struct DtState {
   double dt, t, t_end, dt_fixed;
 };
 
-template <int DIM>
+template <int DIM, bool CURVI>
 __global__ void __launch_bounds__(128) k_recon(const double* __restrict__ U, DevGeo g, Phys ph,
                                                double* __restrict__ gpL, double* __restrict__ gpR,
                                                double* __restrict__ chi, int record_chi, int* __restrict__ st) {
@@ -31,18 +31,18 @@ __global__ void __launch_bounds__(128) k_recon(const double* __restrict__ U, Dev
   double force = ph.linear ? 1.0 : -1.0;
   double cs[NV];
 #pragma unroll 1
-  for (int v = 0; v < NV; ++v) cs[v] = recon_var<DIM>(U, g, ph, c, i, j, k, v, force, gpL, gpR);
+  for (int v = 0; v < NV; ++v) cs[v] = recon_var<DIM, CURVI>(U, g, ph, c, i, j, k, v, force, gpL, gpR);
   if (!cell_states_physical<DIM>(g, ph, c, i, j, k, gpL, gpR)) {
     atomicAdd(&st[ST_FALLBACK], 1);
 #pragma unroll 1
-    for (int v = 0; v < NV; ++v) cs[v] = recon_var<DIM>(U, g, ph, c, i, j, k, v, 0.0, gpL, gpR);
+    for (int v = 0; v < NV; ++v) cs[v] = recon_var<DIM, CURVI>(U, g, ph, c, i, j, k, v, 0.0, gpL, gpR);
     if (!cell_states_physical<DIM>(g, ph, c, i, j, k, gpL, gpR)) atomicOr(&st[ST_NONPHYS], 1);
   }
   if (record_chi)
     for (int v = 0; v < NV; ++v) chi[(long)v * g.ncell + c] = cs[v];
 }
 
-template <int DIM>
+template <int DIM, bool CURVI>
 __global__ void __launch_bounds__(128) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
                                               const double* __restrict__ gpL, const double* __restrict__ gpR,
                                               double* __restrict__ flux, int* __restrict__ st) {
@@ -54,10 +54,10 @@ __global__ void __launch_bounds__(128) k_flux(DevGeo g, Phys ph, const DtState* 
   int k = r % Sz<DIM>::GPF, ax = r / Sz<DIM>::GPF;
   double dt = dts->dt;
   if (!(dt > 0.0)) return;
-  if (!flux_point<DIM>(g, ph, dt, ax, k, c, gpL, gpR, flux)) atomicOr(&st[ST_FLUX], 1);
+  if (!flux_point<DIM, CURVI>(g, ph, dt, ax, k, c, gpL, gpR, flux)) atomicOr(&st[ST_FLUX], 1);
 }
 
-template <int DIM>
+template <int DIM, bool CURVI>
 __global__ void __launch_bounds__(128) k_update(DevGeo g, const DtState* __restrict__ dts, int stage,
                                                 const double* __restrict__ Uin, const double* __restrict__ flux,
                                                 double* __restrict__ stash, double* __restrict__ Uout) {
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(128) k_update(DevGeo g, const DtState* __restr
   if (!(dt > 0.0)) return;
   int i, j, k;
   cell_ijk(g, c, i, j, k);
-  update_cell<DIM>(g, dt, stage, c, i, j, k, Uin, flux, stash, Uout);
+  update_cell<DIM, CURVI>(g, dt, stage, c, i, j, k, Uin, flux, stash, Uout);
 }
 
 /* max over cells of the rate; positive doubles order like their bit patterns */

@@ -1,8 +1,8 @@
 """Exact generator of the reconstruction tables of the CUDA library.
 
 Run ``python -m paper_2508_08965_gb300.gen_tables`` to rewrite
-``csrc/cgks_tables.h``; the header is committed so that the build needs only
-nvcc.
+``csrc/cgks_tables.h`` and ``csrc/cgks_recon_gen.cuh``; both headers are
+committed so that the build needs only nvcc.
 
 What is tabulated (standard reference cell [0,1]^dim of Sec. 4, centroid 1/2,
 h = 1, so delta = xi - 1/2 lies in [-1/2, 1/2]^dim):
@@ -379,6 +379,327 @@ def emit(path):
         f.write("\n".join(out) + "\n")
 
 
-if __name__ == "__main__":
+
+
+# ---------------------------------------------------------------------------
+# Straight-line reconstruction code exploiting the reflection symmetry of the
+# reference stencil.
+#
+# The least-squares problem is invariant under the reflections delta_s ->
+# -delta_s of the reference cell, and the basis functions are eigenfunctions
+# of them (parity class c = exponents mod 2).  Hence a_b, for b in class c,
+# depends only on the class-c characters of the data: for every orbit o of
+# data items under the reflection group, f_{c,o} = sum_S chi_c(S) sgn(S,o)
+# d_{R_S(o)} and a_b = sum_o M[b,o] / |stab(o)| f_{c(b),o}.  The face Gauss
+# points of one axis form one orbit too, so their values and gradients are a
+# Walsh-Hadamard transform of per-class sums.  The Gram matrices of the
+# smoothness indicators are block diagonal in the classes.
+# ---------------------------------------------------------------------------
+
+def _items(dim):
+    """data items in the order of build(): (kind, index...)"""
+    faces, edges = stencil(dim)
+    ntau = 2 if dim == 3 else 1
+    it = [("Q0",)]
+    for m in range(len(faces)):
+        it.append(("fQ", m))
+        for k in range(dim):
+            it.append(("fG", m, k))
+    for n in range(len(edges)):
+        it.append(("eQ", n))
+        for t in range(ntau):
+            it.append(("eT", n, t))
+    for s in range(dim * gpf(dim)):
+        it.append(("L", s))
+    return it
+
+
+def _reflect(dim, item, s):
+    """image of a data item under the reflection of axis s: (item', sign)"""
+    faces, edges = stencil(dim)
+    kind = item[0]
+    if kind == "Q0":
+        return item, 1
+    if kind in ("fQ", "fG"):
+        o = list(faces[item[1]])
+        o[s] = -o[s]
+        m2 = faces.index(tuple(o))
+        if kind == "fQ":
+            return ("fQ", m2), 1
+        return ("fG", m2, item[2]), (-1 if item[2] == s else 1)
+    if kind in ("eQ", "eT"):
+        o = list(edges[item[1]])
+        o[s] = -o[s]
+        n2 = edges.index(tuple(o))
+        if kind == "eQ":
+            return ("eQ", n2), 1
+        t = item[2]
+        if dim == 3 and t == 0:  # along the shared edge: flips when the edge axis is reflected
+            z0 = [a for a in range(3) if edges[item[1]][a] == 0][0]
+            return ("eT", n2, t), (-1 if s == z0 else 1)
+        return ("eT", n2, t), 1  # toward the centroid: invariant
+    if kind == "L":
+        g = gpf(dim)
+        d, k = item[1] // g, item[1] % g
+        if s == d:
+            return item, -1
+        ta = [a for a in range(dim) if a != d]
+        bit = 1 if ta[0] == s else 2
+        return ("L", d * g + (k ^ bit)), 1
+    raise ValueError(item)
+
+
+def _group(dim):
+    return [tuple(a for a in range(dim) if (S >> a) & 1) for S in range(1 << dim)]
+
+
+def _act(dim, item, S):
+    sign = 1
+    for s in S:
+        item, sg = _reflect(dim, item, s)
+        sign *= sg
+    return item, sign
+
+
+def _classes(dim):
+    return list(itertools.product((0, 1), repeat=dim))
+
+
+def _chi(c, S):
+    v = 1
+    for s in S:
+        if c[s]:
+            v = -v
+    return v
+
+
+def symmetry_plan(dim):
+    """orbits of data items and, per orbit and class, the signed item sums"""
+    items = _items(dim)
+    pos = {it: i for i, it in enumerate(items)}
+    G = _group(dim)
+    seen, orbits = set(), []
+    for it in items:
+        if it in seen:
+            continue
+        orb = sorted({_act(dim, it, S)[0] for S in G}, key=lambda x: pos[x])
+        seen |= set(orb)
+        rep = it
+        stab = sum(1 for S in G if _act(dim, rep, S)[0] == rep)
+        feats = {}
+        for c in _classes(dim):
+            coef = {}
+            for S in G:
+                img, sg = _act(dim, rep, S)
+                coef[img] = coef.get(img, 0) + _chi(c, S) * sg
+            coef = {k: v for k, v in coef.items() if v != 0}
+            if coef:
+                feats[c] = coef
+        orbits.append((rep, orb, stab, feats))
+    return items, pos, orbits
+
+
+def _lit(x):
+    return repr(float(x))
+
+
+def emit_recon_code(path):
+    out = ["/* Generated by paper_2508_08965_gb300/gen_tables.py -- do not edit.",
+           "   Straight-line CGKS-5 reconstruction on the reference cell using its",
+           "   reflection symmetry (see gen_tables.py).  Ld is a loader with",
+           "   q0(), avg(ox,oy,oz), grefv(ox,oy,oz,g[dim]) (neighbour gradient in the",
+           "   target's reference frame) and line(s) (own reference line difference). */",
+           "#pragma once", ""]
+    for dim in (2, 3):
+        t = build(dim)
+        ex, nb = t["ex"], t["nb"]
+        M = [[x.to_float() for x in row] for row in t["M"]]
+        items, pos, orbits = symmetry_plan(dim)
+        cls = [tuple(x % 2 for x in e) for e in ex]
+        faces, edges = stencil(dim)
+        # numerical check of the orbit formula against M
+        import random
+        rnd = random.Random(5)
+        dvec = [rnd.uniform(-1, 1) for _ in items]
+        for b in range(nb):
+            ref = sum(M[b][j] * dvec[j] for j in range(len(items)))
+            acc = 0.0
+            for rep, orb, stab, feats in orbits:
+                if cls[b] in feats:
+                    f = sum(cf * dvec[pos[it]] for it, cf in feats[cls[b]].items())
+                    acc += M[b][pos[rep]] / stab * f
+            assert abs(acc - ref) < 1e-12 * (1 + abs(ref)), (dim, b, acc, ref)
+        # group orbits by the neighbour set they read
+        def nb_offsets(it):
+            if it[0] in ("fQ", "fG"):
+                return (faces[it[1]],)
+            if it[0] in ("eQ", "eT"):
+                return (edges[it[1]],)
+            return ((0,) * dim,)
+        groups = {}
+        for o in orbits:
+            key = tuple(sorted({nb_offsets(it)[0] for it in o[1]}))
+            groups.setdefault(key, []).append(o)
+        fn = []
+        fn.append("template <class Ld>")
+        fn.append("CGKS_HD void gen_coeffs_%dd(const Ld& ld, double* __restrict__ a) {" % dim)
+        fn.append("#pragma unroll")
+        fn.append("  for (int b = 0; b < %d; ++b) a[b] = 0.0;" % nb)
+
+        def off3(o):
+            o = list(o) + [0] * (3 - dim)
+            return "%d, %d, %d" % tuple(o)
+
+        for key, orbs in groups.items():
+            fn.append("  {")
+            var = {}
+            for o in key:
+                if all(x == 0 for x in o):
+                    continue
+                nm = "n" + "".join("m" if x < 0 else ("p" if x > 0 else "z") for x in o)
+                fn.append("    const double %sQ = ld.avg(%s);" % (nm, off3(o)))
+                fn.append("    double %sG[%d];" % (nm, dim))
+                fn.append("    ld.grefv(%s, %sG);" % (off3(o), nm))
+                var[o] = nm
+
+            def item_expr(it):
+                if it[0] == "Q0":
+                    return "ld.q0()"
+                if it[0] == "L":
+                    return "ld.line(%d)" % it[1]
+                if it[0] == "fQ":
+                    return "%sQ" % var[faces[it[1]]]
+                if it[0] == "fG":
+                    return "%sG[%d]" % (var[faces[it[1]]], it[2])
+                if it[0] == "eQ":
+                    return "%sQ" % var[edges[it[1]]]
+                o = edges[it[1]]
+                nm = var[o]
+                if dim == 3 and it[2] == 0:
+                    z0 = [a for a in range(3) if o[a] == 0][0]
+                    return "%sG[%d]" % (nm, z0)
+                terms = ["%s%sG[%d]" % ("+" if o[a] > 0 else "-", nm, a) for a in range(dim) if o[a] != 0]
+                return "(%s)" % " ".join(terms).lstrip("+")
+
+            for rep, orb, stab, feats in orbs:
+                for c, coef in feats.items():
+                    expr = " ".join("%s%s" % ("+" if cf > 0 else "-", item_expr(it)) if abs(cf) == 1 else
+                                    "%s%d.0*%s" % ("+" if cf > 0 else "-", abs(cf), item_expr(it))
+                                    for it, cf in coef.items()).lstrip("+")
+                    rows = [b for b in range(nb) if cls[b] == c and M[b][pos[rep]] != 0.0]
+                    if not rows:
+                        continue
+                    fn.append("    { const double f = %s;" % expr)
+                    for b in rows:
+                        fn.append("      a[%d] = fma(%s, f, a[%d]);" % (b, _lit(M[b][pos[rep]] / stab), b))
+                    fn.append("    }")
+            fn.append("  }")
+        fn.append("}")
+        fn.append("")
+        # Gram quadratic forms (block diagonal by class)
+        GH = [[float(x) for x in row] for row in t["GH"]]
+        GL = [[float(x) for x in row] for row in t["GL"]]
+        for name, Gm in (("ish", GH), ("isl", GL)):
+            fn.append("CGKS_HD double gen_%s_%dd(const double* __restrict__ a) {" % (name, dim))
+            fn.append("  double s = 0.0;")
+            for i in range(nb):
+                terms = []
+                if Gm[i][i] != 0.0:
+                    terms.append((_lit(Gm[i][i]), i))
+                for j in range(i + 1, nb):
+                    if Gm[i][j] != 0.0:
+                        assert cls[i] == cls[j]
+                        terms.append((_lit(2.0 * Gm[i][j]), j))
+                if not terms:
+                    continue
+                fn.append("  { double r = 0.0;")
+                for cst, j in terms:
+                    fn.append("    r = fma(%s, a[%d], r);" % (cst, j))
+                fn.append("    s = fma(a[%d], r, s); }" % i)
+            fn.append("  return s;")
+            fn.append("}")
+            fn.append("")
+        # mean of the P4 correction: sum_b a_b mean_b
+        fn.append("CGKS_HD double gen_mean_%dd(const double* __restrict__ a) {" % dim)
+        fn.append("  double s = 0.0;")
+        for b, e in enumerate(ex):
+            mb = mean_basis(e)
+            if mb != 0:
+                fn.append("  s = fma(%s, a[%d], s);" % (_lit(float(mb)), b))
+        fn.append("  return s;")
+        fn.append("}")
+        fn.append("")
+        # face Gauss points of axis AX: values and reference gradients of P4 - Q0 + mean
+        g = gpf(dim)
+        npts = 2 * g
+        for ax in range(dim):
+            ta = [a for a in range(dim) if a != ax]
+            # representative x0: +1/2 along ax, +g along the tangential axes
+            x0 = [Q3(0)] * dim
+            x0[ax] = Q3(HALF)
+            for a in ta:
+                x0[a] = G
+            fn.append("/* axis %d: out_v[i], out_g[i][k] for the %d Gauss points i = side*%d + k */" % (ax, npts, g))
+            fn.append("CGKS_HD void gen_gp_%dd_ax%d(const double* __restrict__ a, double* __restrict__ out_v, "
+                      "double (* __restrict__ out_g)[%d]) {" % (dim, ax, dim))
+            C = _classes(dim)
+            # class sums of values and of each derivative
+            for ci, c in enumerate(C):
+                terms = []
+                for b, e in enumerate(ex):
+                    if cls[b] != c:
+                        continue
+                    v = Q3(1)
+                    for i2 in range(dim):
+                        v = v * ipow(x0[i2], e[i2]) * Fr(1, fact(e[i2]))
+                    terms.append((v.to_float(), b))
+                fn.append("  double S%d = 0.0;" % ci)
+                for v, b in terms:
+                    if v != 0.0:
+                        fn.append("  S%d = fma(%s, a[%d], S%d);" % (ci, _lit(v), b, ci))
+                for k in range(dim):
+                    fn.append("  double D%d_%d = 0.0;" % (ci, k))
+                    for b, e in enumerate(ex):
+                        if cls[b] != c or e[k] == 0:
+                            continue
+                        v = Q3(1)
+                        for i2 in range(dim):
+                            ee = e[i2] - (1 if i2 == k else 0)
+                            v = v * ipow(x0[i2], ee) * Fr(1, fact(ee))
+                        fn.append("  D%d_%d = fma(%s, a[%d], D%d_%d);" % (ci, k, _lit(v.to_float()), b, ci, k))
+            # each Gauss point is R_S x0 for the set S of negated axes
+            for side in (0, 1):
+                for k in range(g):
+                    S = []
+                    if side == 0:
+                        S.append(ax)
+                    if not (k & 1):
+                        S.append(ta[0])
+                    if dim == 3 and not (k & 2):
+                        S.append(ta[1])
+                    i = side * g + k
+                    ve = " ".join("%sS%d" % ("+" if _chi(c, S) > 0 else "-", ci) for ci, c in enumerate(C)).lstrip("+")
+                    fn.append("  out_v[%d] = %s;" % (i, ve))
+                    for kk in range(dim):
+                        # derivative along kk at R_S x0: sum_c chi_{c xor e_kk}(S) D_c,kk
+                        te = []
+                        for ci, c in enumerate(C):
+                            c2 = list(c)
+                            c2[kk] ^= 1
+                            te.append("%sD%d_%d" % ("+" if _chi(tuple(c2), S) > 0 else "-", ci, kk))
+                        fn.append("  out_g[%d][%d] = %s;" % (i, kk, " ".join(te).lstrip("+")))
+            fn.append("}")
+            fn.append("")
+        out += fn
+    with open(path, "w") as f:
+        f.write("\n".join(out) + "\n")
+
+
+def emit_all():
     here = os.path.dirname(os.path.abspath(__file__))
     emit(os.path.join(here, "csrc", "cgks_tables.h"))
+    emit_recon_code(os.path.join(here, "csrc", "cgks_recon_gen.cuh"))
+
+
+if __name__ == "__main__":
+    emit_all()

@@ -2,20 +2,27 @@
 import numpy as np
 
 
-def class_scaled_diff(a, b):
-    """max |a - b| / scale, scale = max |b| over the same variable class
-    (density, momentum vector, energy) and field group (cell averages, or all
-    derivative fields).  Momentum components share a scale because they form
-    one vector; derivative fields share one because they are differences of
-    the same interface values."""
+def class_scaled_diff(a, b, h=None):
+    """max |a - b| / scale over variable classes (density, momentum vector,
+    energy) and field groups (cell averages; all derivative fields).
+
+    Averages: scale = max |b| of the class.  Momentum components share a
+    scale because they form one vector.
+    Derivative fields: they are difference quotients of interface values of
+    size ~|average|, so their rounding is ~eps |average| / h whatever their
+    own size; with h (the smallest cell size) given, their scale is
+    max(max |b|, max |average| / h).  Without h the derivative scale is
+    max |b| alone (stricter for small derivatives)."""
     nf, nv = b.shape[0], b.shape[1]
     classes = [[0], list(range(1, nv - 1)), [nv - 1]]
-    groups = [[0], list(range(1, nf))]
     worst = 0.0
-    for g in groups:
-        for c in classes:
+    for c in classes:
+        avg = np.abs(b[np.ix_([0], c)]).max()
+        for g in ([0], list(range(1, nf))):
             ix = np.ix_(g, c)
             sc = np.abs(b[ix]).max()
+            if g != [0] and h is not None:
+                sc = max(sc, avg / h)
             if sc == 0.0:
                 sc = 1.0
             worst = max(worst, np.abs(a[ix] - b[ix]).max() / sc)
