@@ -46,6 +46,18 @@ DRAM_BYTES_PER_UNIT = {
     ("recon", 3): (0.299e9 + 0.983e9) / 262144,
     ("flux", 3): (1.009e9 + 0.810e9) / (262144 * 12),
 }
+# the same for the FP32 form (flops = 2 FFMA + FADD + FMUL; ncu, TGV 64^3);
+# update: per (cell, variable)
+FLOPS_PER_UNIT_FP32 = {
+    ("recon", 3): 1.683e4,
+    ("flux", 3): 4.318e3,
+    ("update", 3): 156.0,
+}
+DRAM_BYTES_PER_UNIT_FP32 = {
+    ("recon", 3): 2294.0,
+    ("flux", 3): 268.0,
+    ("update", 3): 422.0,
+}
 
 
 # kernels launched per S2O4 step: time-step reduction (reset, rate, final),
@@ -132,6 +144,49 @@ def fp64_alu_peak_tflops(sm_count=152, sm_mhz=2070.0):
     return sm_count * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def fp32_alu_peak_tflops(sm_count=152, sm_mhz=2070.0):
+    """FP32 FMA pipe peak: 128 FP32 FMA per clock per SM (a probe of this
+    project measured 72.9-73.3 TFLOP/s)."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def roofline(prof, spec, ncell, precision):
+    """Roofline of the dominant kernel of a timed form: its executed flops per
+    unit (ncu counts) times the units of one launch, over its average
+    CUDA-event launch time, against the ALU pipe peak of its precision."""
+    name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_ms = tot_ms / max(launches, 1)
+    dim = spec["dim"]
+    if name == "update":
+        units = ncell * (dim + 2)
+    elif name in ("recon", "dt"):
+        units = ncell
+    else:
+        units = ncell * dim * (4 if dim == 3 else 2)
+    table = FLOPS_PER_UNIT if precision == 0 else FLOPS_PER_UNIT_FP32
+    dram = DRAM_BYTES_PER_UNIT if precision == 0 else DRAM_BYTES_PER_UNIT_FP32
+    fpu = table.get((name, dim))
+    if precision == 0:
+        peak = fp64_alu_peak_tflops()
+        src = ("FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz, derived (an FMA-chain probe measured "
+               "1.19-1.20 TFLOP/s)")
+    else:
+        peak = fp32_alu_peak_tflops()
+        src = ("FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz, derived (an FMA-chain probe measured "
+               "72.9-73.3 TFLOP/s)")
+    out = {"bound": "alu", "kernel": name, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+           "traffic": None, "avg_launch_ms": avg_ms, "peak_source": src}
+    if fpu:
+        achieved = fpu * units / (avg_ms / 1e3) / 1e12
+        dbu = dram.get((name, dim))
+        out.update({"achieved": achieved, "frac": achieved / peak, "flops_per_launch": fpu * units,
+                    "traffic": dbu * units if dbu else None,
+                    "traffic_source": "ncu dram__bytes_read+write of a 64^3 capture, scaled by units"})
+    else:
+        out["note"] = "flops per unit not yet counted for this kernel"
+    return out
+
+
 def cpu_baseline(wl, sample_cells=None):
     """Time the CPU oracle, as it stands, on a bounded sample of the workload:
     the same analytic field and physics on a smaller periodic mesh (same
@@ -205,6 +260,7 @@ def main():
     ap.add_argument("--workload", default="tgv128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-fp32", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -230,30 +286,41 @@ def main():
     wl = args.workload
     spec = WORKLOADS[wl]
     stream = torch.cuda.Stream()
-    mesh = Mesh(spec["dim"], spec["n"], stream=stream, **mesh_kwargs(wl))
-    mesh.init(field_fn(wl))
-    ncell = mesh.ncell
-    for _ in range(args.warmup):
-        mesh.step(1)
-    # timed region: K whole steps on the context stream, profiled per kernel
-    mesh.profile(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        mesh.step(args.steps)
-        e1.record(stream)
+    peaks = measured_peaks()
+
+    def timed_form(precision, s0=None):
+        """Warm up, then time K whole steps of one form on the context stream
+        with per-kernel CUDA events; returns the mesh, its start state, the
+        time, the per-kernel profile and the clock record."""
+        mesh = Mesh(spec["dim"], spec["n"], stream=stream, precision=precision, **mesh_kwargs(wl))
+        if s0 is None:
+            mesh.init(field_fn(wl))
+            s0 = mesh.get_state()[0]
+        else:
+            mesh.set_state(s0, 0.0)
+        for _ in range(args.warmup):
+            mesh.step(1)
+        mesh.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
         torch.cuda.synchronize()
-    barrier()
-    ms = e0.elapsed_time(e1)
-    prof = mesh.profile_read()
-    mesh.profile(False)
-    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            mesh.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = mesh.profile_read()
+        mesh.profile(False)
+        ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        return mesh, s0, float(ms_t.item()), prof, clk
+
+    mesh, s_init, ms, prof, clk = timed_form(0)
+    ncell = mesh.ncell
     value = world * ncell * args.steps / (ms / 1e3)
 
     # end to end through the C-ABI with host buffers: every step copies the
@@ -262,6 +329,7 @@ def main():
     h_in = torch.empty(shape, dtype=torch.float64, pin_memory=True)
     h_out = torch.empty(shape, dtype=torch.float64, pin_memory=True)
     mesh.get_state(h_in.numpy())
+    s_fp64 = h_in.numpy().copy()  # FP64 state after the warm-up and timed steps
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -276,30 +344,36 @@ def main():
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_s = float(e2e_t.item())
     state_bytes = int(np.prod(shape)) * 8
-
-    peaks = measured_peaks()
-    sm_mhz = clk.summary()["sm_max_mhz"] or 2070.0
-    # dominant kernel and its FP64 roofline
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (launches, tot_ms) = dom
-    avg_ms = tot_ms / max(launches, 1)
-    fpu = FLOPS_PER_UNIT.get((name, spec["dim"]))
-    units = ncell if name in ("recon", "update", "dt") else ncell * spec["dim"] * (4 if spec["dim"] == 3 else 2)
-    peak = fp64_alu_peak_tflops(sm_mhz=2070.0)
-    if fpu:
-        achieved = fpu * units / (avg_ms / 1e3) / 1e12
-        dbu = DRAM_BYTES_PER_UNIT.get((name, spec["dim"]))
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": dbu * units if dbu else None,
-                "flops_per_launch": fpu * units, "avg_launch_ms": avg_ms,
-                "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz, derived "
-                               "(an FMA-chain probe measured 1.19-1.20 TFLOP/s)",
-                "traffic_source": "ncu dram__bytes_read+write of a 64^3 capture, scaled by units"}
-    else:
-        roof = {"bound": "alu", "kernel": name, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "note": "flops per unit not yet counted"}
+    mesh.close()
     kernels = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)}
                for k, v in prof.items()}
+
+    # the FP32 form from the same initial state and the same number of steps;
+    # its error is stated against the FP64 form (itself parity-checked against
+    # the FP64 oracle)
+    forms = {}
+    if not args.no_fp32:
+        m32, _, ms32, prof32, clk32 = timed_form(1, s_init)
+        s32, _ = m32.get_state()
+        m32.close()
+        e = s32[0, 0] - s_fp64[0, 0]
+        dim = spec["dim"]
+
+        def ke(st):
+            return float(np.mean(0.5 * (st[0, 1:1 + dim] ** 2).sum(axis=0) / st[0, 0]))
+
+        forms["fp32"] = {
+            "value": world * ncell * args.steps / (ms32 / 1e3), "unit": "cell-updates/s",
+            "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": ms / ms32,
+            "dtype": "f32 reconstruction/flux/weights/derivative fields; f64 averages, accumulation, metrics",
+            "error_vs_fp64": {"steps": args.warmup + args.steps,
+                              "density_l2": float(np.sqrt(np.mean(e * e))),
+                              "density_linf": float(np.abs(e).max()),
+                              "kinetic_energy_rel": abs(ke(s32) - ke(s_fp64)) / ke(s_fp64)},
+            "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in prof32.items()},
+            "roofline": roofline(prof32, spec, ncell, 1),
+            "clocks": clk32.summary(),
+        }
 
     line = {
         "metric": "cell-updates/s per S2O4 step", "value": value, "unit": "cell-updates/s",
@@ -312,22 +386,21 @@ def main():
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
         "gpu_launches": args.steps * KERNELS_PER_STEP,
         "kernels": kernels,
-        "roofline": roof,
+        "roofline": roofline(prof, spec, ncell, 0),
         "clocks": clk.summary(),
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
+        "forms": forms,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(wl)
-        except Exception as e:  # the oracle is a reported baseline only
-            line["cpu_baseline"] = {"error": str(e)}
+        except Exception as ex:  # the oracle is a reported baseline only
+            line["cpu_baseline"] = {"error": str(ex)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    mesh.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
-
 
 if __name__ == "__main__":
     sys.exit(main())

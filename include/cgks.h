@@ -74,7 +74,9 @@ typedef struct {
   double dt_fixed;      /* > 0: constant time step instead of the CFL rule */
   int linear;           /* 1: linear CGKS-5 (chi = 1) */
   double c_chi;         /* GENO path-function constant C (<= 0: default 100) */
-  int precision;        /* 0: FP64 throughout */
+  int precision;        /* 0: FP64 throughout; 1: reconstruction, interface flux,
+                           weights and derivative fields in FP32, cell averages
+                           (accumulated across the S2O4 stages) and metrics in FP64 */
   void* stream;         /* cudaStream_t to queue work on; NULL = default stream */
 } cgks_mesh_desc;
 

@@ -82,11 +82,14 @@ class Mesh:
     """One library context: a mesh, its device state and metrics.
 
     Arguments follow cgks_mesh_desc.  ``stream`` is a torch.cuda.Stream (or
-    None for torch's current stream at construction time).
+    None for torch's current stream at construction time).  precision 0 is
+    FP64 throughout; 1 runs reconstruction, interface flux and weights in
+    FP32 with FP64 cell averages and metrics.
     """
 
     def __init__(self, dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=1.4, mu=0.0,
-                 prandtl=1.0, tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=0.0, stream=None):
+                 prandtl=1.0, tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=0.0, stream=None,
+                 precision=0):
         torch = _torch()
         L = lib()
         d = MeshDesc()
@@ -102,7 +105,8 @@ class Mesh:
             d.nodes = self._nodes.ctypes.data_as(C.POINTER(C.c_double))
         d.gamma, d.mu, d.prandtl, d.tau_mode = gamma, mu, prandtl, tau_mode
         d.cfl, d.dt_fixed, d.linear, d.c_chi = cfl, dt_fixed, int(linear), c_chi
-        d.precision = 0
+        d.precision = int(precision)
+        self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         d.stream = C.c_void_p(self.stream.cuda_stream)
         h = C.c_void_p()

@@ -35,6 +35,7 @@ struct cgks_ctx {
   int dim, nv, nf;
   int n[3];
   long ncell;
+  int prec;                 /* 0: FP64; 1: FP32 bulk with FP64 averages */
   cgks_mesh_desc desc;
   cudaStream_t stream;
   DevGeo geo;
@@ -42,12 +43,24 @@ struct cgks_ctx {
   double* d_nodes = nullptr;
   double* d_met = nullptr;
   double* d_lo = nullptr;
-  double* U = nullptr;      /* current state */
-  double* Us = nullptr;     /* intermediate state */
-  double* stash = nullptr;  /* stage-1 stash */
-  double* gpL = nullptr;
-  double* gpR = nullptr;
-  double* flux = nullptr;
+  /* state buffers.  FP64: full public-layout arrays U (current), Us
+     (intermediate) and a stash, with the derivative fields right after the
+     averages.  FP32: FP64 averages and FP32 derivative fields in separate
+     arrays, plus a public-layout FP64 staging buffer for copies in and out. */
+  double* U = nullptr;
+  double* Us = nullptr;
+  double* stash = nullptr;
+  double* avg[2] = {nullptr, nullptr};
+  void* der[2] = {nullptr, nullptr};
+  double* savg = nullptr;
+  void* sder = nullptr;
+  void* f32 = nullptr;      /* FP32 derivative storage (3 arrays) */
+  float* avh[2] = {nullptr, nullptr}; /* FP32 form: exact hi + lo pairs of the averages */
+  float* avl[2] = {nullptr, nullptr};
+  float* pairs = nullptr;
+  void* gpL = nullptr;
+  void* gpR = nullptr;
+  void* flux = nullptr;
   double* chi = nullptr;
   DtState* dts = nullptr;
   int* st = nullptr;
@@ -108,44 +121,49 @@ static void prof_fold(cgks_ctx* ctx) {
   p.rec.clear();
 }
 
-template <int DIM>
-static cgks_status run_stage(cgks_ctx* ctx, const double* Uin, int stage, double* Uout) {
+template <typename T, int DIM, bool CURVI>
+static void launch_stage(cgks_ctx* ctx, int stage) {
   const long N = ctx->ncell;
   const int B = 128;
+  const int in = stage == 1 ? 0 : 1, out = stage == 1 ? 1 : 0;
+  T* gpL = (T*)ctx->gpL;
+  T* gpR = (T*)ctx->gpR;
+  T* fx = (T*)ctx->flux;
   prof_begin(ctx, KID_RECON);
-  if (ctx->geo.curvi)
-    k_recon<DIM, true><<<cdiv(N, B), B, 0, ctx->stream>>>(Uin, ctx->geo, ctx->ph, ctx->gpL, ctx->gpR, ctx->chi,
-                                                          stage == 1 ? 1 : 0, ctx->st);
-  else
-    k_recon<DIM, false><<<cdiv(N, B), B, 0, ctx->stream>>>(Uin, ctx->geo, ctx->ph, ctx->gpL, ctx->gpR, ctx->chi,
-                                                           stage == 1 ? 1 : 0, ctx->st);
+  k_recon<T, DIM, CURVI><<<cdiv(N, B), B, 0, ctx->stream>>>(ctx->avg[in], ctx->avh[in], ctx->avl[in],
+                                                            (const T*)ctx->der[in], ctx->geo, ctx->ph, gpL, gpR,
+                                                            ctx->chi, stage == 1 ? 1 : 0, ctx->st);
   prof_end(ctx);
-  long nf = (long)DIM * Sz<DIM>::GPF * N;
+  const long nf = (long)DIM * Sz<DIM>::GPF * N;
   prof_begin(ctx, KID_FLUX);
-  if (ctx->geo.curvi)
-    k_flux<DIM, true><<<cdiv(nf, B), B, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, ctx->gpL, ctx->gpR,
-                                                          ctx->flux, ctx->st);
-  else
-    k_flux<DIM, false><<<cdiv(nf, B), B, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, ctx->gpL, ctx->gpR,
-                                                           ctx->flux, ctx->st);
+  k_flux<T, DIM, CURVI><<<cdiv(nf, B), B, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, gpL, gpR, fx, ctx->st);
   prof_end(ctx);
   prof_begin(ctx, KID_UPDATE);
-  if (ctx->geo.curvi)
-    k_update<DIM, true><<<cdiv(N, B), B, 0, ctx->stream>>>(ctx->geo, ctx->dts, stage, Uin, ctx->flux, ctx->stash,
-                                                           Uout);
-  else
-    k_update<DIM, false><<<cdiv(N, B), B, 0, ctx->stream>>>(ctx->geo, ctx->dts, stage, Uin, ctx->flux, ctx->stash,
-                                                            Uout);
+  k_update<T, DIM, CURVI><<<cdiv((long)Sz<DIM>::NV * N, B), B, 0, ctx->stream>>>(
+      ctx->geo, ctx->dts, stage, ctx->avg[in], fx, ctx->savg, (T*)ctx->sder, ctx->avg[out], (T*)ctx->der[out],
+      ctx->avh[out], ctx->avl[out]);
   prof_end(ctx);
+}
+
+template <int DIM>
+static cgks_status run_stage(cgks_ctx* ctx, int stage) {
+  const bool cv = ctx->geo.curvi != 0;
+  if (ctx->prec == 0) {
+    if (cv) launch_stage<double, DIM, true>(ctx, stage);
+    else launch_stage<double, DIM, false>(ctx, stage);
+  } else {
+    if (cv) launch_stage<float, DIM, true>(ctx, stage);
+    else launch_stage<float, DIM, false>(ctx, stage);
+  }
   CK(cudaGetLastError());
   return CGKS_OK;
 }
 
 template <int DIM>
-static cgks_status run_dt(cgks_ctx* ctx, const double* U) {
+static cgks_status run_dt(cgks_ctx* ctx, const double* avg) {
   prof_begin(ctx, KID_DT);
   k_dt_reset<<<1, 1, 0, ctx->stream>>>(ctx->dts);
-  k_dt_rate<DIM><<<cdiv(ctx->ncell, 256), 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, U, ctx->dts);
+  k_dt_rate<DIM><<<cdiv(ctx->ncell, 256), 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, avg, ctx->dts);
   k_dt_final<<<1, 1, 0, ctx->stream>>>(ctx->ph, ctx->dts, ctx->st);
   prof_end(ctx);
   CK(cudaGetLastError());
@@ -155,10 +173,28 @@ static cgks_status run_dt(cgks_ctx* ctx, const double* U) {
 template <int DIM>
 static cgks_status run_step(cgks_ctx* ctx) {
   cgks_status s;
-  if ((s = run_dt<DIM>(ctx, ctx->U)) != CGKS_OK) return s;
-  if ((s = run_stage<DIM>(ctx, ctx->U, 1, ctx->Us)) != CGKS_OK) return s;
-  if ((s = run_stage<DIM>(ctx, ctx->Us, 2, ctx->U)) != CGKS_OK) return s;
+  if ((s = run_dt<DIM>(ctx, ctx->avg[0])) != CGKS_OK) return s;
+  if ((s = run_stage<DIM>(ctx, 1)) != CGKS_OK) return s;
+  if ((s = run_stage<DIM>(ctx, 2)) != CGKS_OK) return s;
   k_time_advance<<<1, 1, 0, ctx->stream>>>(ctx->dts);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+/* FP32 form: staging (public layout, U) <-> internal arrays of the current state */
+static cgks_status split_in(cgks_ctx* ctx) {
+  if (ctx->prec == 0) return CGKS_OK;
+  const long navg = (long)ctx->nv * ctx->ncell, nder = (long)(ctx->nf - 1) * ctx->nv * ctx->ncell;
+  k_split<float><<<cdiv(navg + nder, 256), 256, 0, ctx->stream>>>(ctx->U, ctx->avg[0], ctx->avh[0], ctx->avl[0],
+                                                                  (float*)ctx->der[0], navg, nder);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+static cgks_status join_out(cgks_ctx* ctx) {
+  if (ctx->prec == 0) return CGKS_OK;
+  const long navg = (long)ctx->nv * ctx->ncell, nder = (long)(ctx->nf - 1) * ctx->nv * ctx->ncell;
+  k_join<float><<<cdiv(navg + nder, 256), 256, 0, ctx->stream>>>(ctx->avg[0], (const float*)ctx->der[0], ctx->U, navg,
+                                                                 nder);
   CK(cudaGetLastError());
   return CGKS_OK;
 }
@@ -171,7 +207,7 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   if (d->dim != 2 && d->dim != 3) return CGKS_EINVAL;
   for (int a = 0; a < d->dim; ++a)
     if (d->n[a] < 3) return CGKS_EINVAL;
-  if (d->precision != 0) return CGKS_EUNSUPPORTED;
+  if (d->precision != 0 && d->precision != 1) return CGKS_EUNSUPPORTED;
   for (int f = 0; f < 2 * d->dim; ++f)
     if (d->bc[f] != CGKS_BC_PERIODIC) return CGKS_EUNSUPPORTED;
   if (!(d->gamma > 1.0) || d->mu < 0.0 || !(d->cfl > 0.0) || d->tau_mode < 0 || d->tau_mode > 2)
@@ -187,6 +223,7 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   ctx->n[2] = d->dim == 3 ? d->n[2] : 1;
   ctx->ncell = (long)ctx->n[0] * ctx->n[1] * ctx->n[2];
   ctx->stream = (cudaStream_t)d->stream;
+  ctx->prec = d->precision;
   ctx->ph.gamma = d->gamma;
   ctx->ph.mu = d->mu;
   ctx->ph.prandtl = d->prandtl > 0.0 ? d->prandtl : 1.0;
@@ -194,10 +231,18 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   ctx->ph.c_chi = d->c_chi > 0.0 ? d->c_chi : 100.0;
   ctx->ph.tau_mode = d->tau_mode;
   ctx->ph.linear = d->linear;
+  ctx->ph.gammaf = (float)ctx->ph.gamma;
+  ctx->ph.muf = (float)ctx->ph.mu;
+  ctx->ph.prandtlf = (float)ctx->ph.prandtl;
+  ctx->ph.c_chif = (float)ctx->ph.c_chi;
+  ctx->ph.prfix = (ctx->ph.mu > 0.0 && ctx->ph.prandtl > 0.0 && ctx->ph.prandtl != 1.0) ? 1 : 0;
   DevGeo& g = ctx->geo;
   for (int a = 0; a < 3; ++a) {
     g.n[a] = ctx->n[a];
     g.h[a] = a < d->dim ? (d->hi[a] - d->lo[a]) / d->n[a] : 1.0;
+    g.ih[a] = 1.0 / g.h[a];
+    g.hf[a] = (float)g.h[a];
+    g.ihf[a] = (float)g.ih[a];
   }
   g.ncell = ctx->ncell;
   g.curvi = d->nodes ? 1 : 0;
@@ -205,9 +250,11 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   const long N = ctx->ncell;
   const int dim = ctx->dim, nv = ctx->nv, nf = ctx->nf;
   const int gpf = dim == 3 ? 4 : 2;
-  size_t st_sz = sizeof(double) * (size_t)nf * nv * N;
-  size_t gp_sz = sizeof(double) * (size_t)dim * gpf * nv * (1 + dim) * N;
-  size_t fx_sz = sizeof(double) * (size_t)dim * gpf * 6 * nv * N;
+  const size_t st_sz = sizeof(double) * (size_t)nf * nv * N;
+  const size_t rsz = ctx->prec == 0 ? sizeof(double) : sizeof(float);
+  const size_t gp_sz = rsz * (size_t)dim * gpf * nv * (1 + dim) * N;
+  const size_t fx_sz = rsz * (size_t)dim * gpf * 6 * nv * N;
+  const size_t navg = (size_t)nv * N, nder = (size_t)(nf - 1) * nv * N;
 #define ALLOC(p, sz)                                                                         \
   do {                                                                                       \
     if (cudaMalloc((void**)&(p), (sz)) != cudaSuccess) {                                     \
@@ -217,8 +264,31 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
     }                                                                                        \
   } while (0)
   ALLOC(ctx->U, st_sz);
-  ALLOC(ctx->Us, st_sz);
-  ALLOC(ctx->stash, st_sz);
+  if (ctx->prec == 0) {
+    ALLOC(ctx->Us, st_sz);
+    ALLOC(ctx->stash, st_sz);
+    ctx->avg[0] = ctx->U;
+    ctx->der[0] = ctx->U + navg;
+    ctx->avg[1] = ctx->Us;
+    ctx->der[1] = ctx->Us + navg;
+    ctx->savg = ctx->stash;
+    ctx->sder = ctx->stash + navg;
+  } else {
+    /* averages: three FP64 arrays in one allocation; derivatives: three FP32 */
+    ALLOC(ctx->Us, sizeof(double) * navg * 3);
+    ALLOC(ctx->f32, sizeof(float) * nder * 3);
+    ctx->avg[0] = ctx->Us;
+    ctx->avg[1] = ctx->Us + navg;
+    ctx->savg = ctx->Us + 2 * navg;
+    ctx->der[0] = (float*)ctx->f32;
+    ctx->der[1] = (float*)ctx->f32 + nder;
+    ctx->sder = (float*)ctx->f32 + 2 * nder;
+    ALLOC(ctx->pairs, sizeof(float) * navg * 4);
+    ctx->avh[0] = ctx->pairs;
+    ctx->avl[0] = ctx->pairs + navg;
+    ctx->avh[1] = ctx->pairs + 2 * navg;
+    ctx->avl[1] = ctx->pairs + 3 * navg;
+  }
   ALLOC(ctx->gpL, gp_sz);
   ALLOC(ctx->gpR, gp_sz);
   ALLOC(ctx->flux, fx_sz);
@@ -259,6 +329,8 @@ void cgks_destroy(cgks_ctx* ctx) {
   cudaFree(ctx->U);
   cudaFree(ctx->Us);
   cudaFree(ctx->stash);
+  cudaFree(ctx->f32);
+  cudaFree(ctx->pairs);
   cudaFree(ctx->gpL);
   cudaFree(ctx->gpR);
   cudaFree(ctx->flux);
@@ -280,6 +352,8 @@ cgks_status cgks_set_state(cgks_ctx* ctx, const double* src, int is_device, doub
   if (!ctx || !src) return CGKS_EINVAL;
   size_t sz = sizeof(double) * (size_t)ctx->nf * ctx->nv * ctx->ncell;
   CK(cudaMemcpyAsync(ctx->U, src, sz, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  cgks_status r0 = split_in(ctx);
+  if (r0 != CGKS_OK) return r0;
   ctx->t = t;
   DtState init{};
   init.t = t;
@@ -292,6 +366,8 @@ cgks_status cgks_set_state(cgks_ctx* ctx, const double* src, int is_device, doub
 cgks_status cgks_get_state(cgks_ctx* ctx, double* dst, int is_device, double* t) {
   if (!ctx || !dst) return CGKS_EINVAL;
   size_t sz = sizeof(double) * (size_t)ctx->nf * ctx->nv * ctx->ncell;
+  cgks_status r0 = join_out(ctx);
+  if (r0 != CGKS_OK) return r0;
   CK(cudaMemcpyAsync(dst, ctx->U, sz, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   DtState h;
   CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
@@ -349,7 +425,7 @@ cgks_status cgks_compute_dt(cgks_ctx* ctx, double* dt) {
   double keep_end = h.t_end;
   h.t_end = 0.0;
   CK(cudaMemcpyAsync(ctx->dts, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
-  cgks_status r = ctx->dim == 3 ? run_dt<3>(ctx, ctx->U) : run_dt<2>(ctx, ctx->U);
+  cgks_status r = ctx->dim == 3 ? run_dt<3>(ctx, ctx->avg[0]) : run_dt<2>(ctx, ctx->avg[0]);
   if (r != CGKS_OK) return r;
   CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -390,6 +466,13 @@ cgks_status cgks_init_from_prims(cgks_ctx* ctx, long cell0, long ncells, const d
     k_init_from_prims<2><<<cdiv(ncells, 128), 128, 0, ctx->stream>>>(ctx->d_nodes, ctx->geo, ctx->ph, ctx->d_lo,
                                                                      cell0, ncells, dev_prims, ctx->U);
   CK(cudaGetLastError());
+  if (ctx->prec == 1) {
+    const long tot = (long)ctx->nf * ctx->nv * ncells;
+    k_split_cells<float><<<cdiv(tot, 256), 256, 0, ctx->stream>>>(ctx->U, ctx->avg[0], ctx->avh[0], ctx->avl[0],
+                                                                  (float*)ctx->der[0], ctx->ncell, ctx->nv, ctx->nf,
+                                                                  cell0, ncells);
+    CK(cudaGetLastError());
+  }
   DtState init{};
   init.t = 0.0;
   init.dt_fixed = ctx->desc.dt_fixed;

@@ -54,14 +54,14 @@ template <int DIM> CGKS_HD double tabPD(int g, int k, int b) {
 #define CGKS_GQ 0.28867513459481288225
 
 /* reference position delta of face Gauss point gp = (2*ax+side)*GPF + k */
-template <int DIM> CGKS_HD double gp_delta(int gp, int a) {
+template <int DIM, typename T = double> CGKS_HD T gp_delta(int gp, int a) {
   const int GPF = Sz<DIM>::GPF;
   int f = gp / GPF, k = gp % GPF, ax = f / 2, side = f & 1;
-  if (a == ax) return side ? 0.5 : -0.5;
+  if (a == ax) return side ? T(0.5) : T(-0.5);
   int t = 0;  /* rank of `a` among the tangential axes */
   for (int q = 0; q < a; ++q) if (q != ax) ++t;
   int bit = (t == 0) ? (k & 1) : (k & 2);
-  return bit ? CGKS_GQ : -CGKS_GQ;
+  return bit ? T(CGKS_GQ) : T(-CGKS_GQ);
 }
 
 /* ---------------- mesh description ---------------- */
@@ -81,13 +81,26 @@ struct DevGeo {
   long ncell;
   int curvi;          /* 0: uniform box with spacing h */
   double h[3];
+  double ih[3];       /* 1/h */
+  float hf[3], ihf[3]; /* the same in FP32, so FP32 kernels need no conversions */
   const double* met;  /* curvilinear metrics (Met<DIM>), or null */
 };
 
 struct Phys {
   double gamma, mu, prandtl, cfl, c_chi;
   int tau_mode, linear;
+  /* FP32 copies and the heat-flux-fix switch (mu > 0 and Pr != 1) */
+  float gammaf, muf, prandtlf, c_chif;
+  int prfix;
 };
+
+/* the physics constants in T */
+template <typename T> CGKS_HD T ph_gamma(const Phys& p) { if constexpr (sizeof(T) == 4) return p.gammaf; else return p.gamma; }
+template <typename T> CGKS_HD T ph_mu(const Phys& p) { if constexpr (sizeof(T) == 4) return p.muf; else return p.mu; }
+template <typename T> CGKS_HD T ph_pr(const Phys& p) { if constexpr (sizeof(T) == 4) return p.prandtlf; else return p.prandtl; }
+template <typename T> CGKS_HD T ph_cchi(const Phys& p) { if constexpr (sizeof(T) == 4) return p.c_chif; else return p.c_chi; }
+template <typename T> CGKS_HD T geo_h(const DevGeo& g, int a) { if constexpr (sizeof(T) == 4) return g.hf[a]; else return g.h[a]; }
+template <typename T> CGKS_HD T geo_ih(const DevGeo& g, int a) { if constexpr (sizeof(T) == 4) return g.ihf[a]; else return g.ih[a]; }
 
 CGKS_HD long cell_index(const DevGeo& g, int i, int j, int k) {
   return i + (long)g.n[0] * (j + (long)g.n[1] * k);
@@ -142,217 +155,6 @@ template <int DIM> CGKS_HD double met_len(const DevGeo& g, long c, int s) {
   return g.met[(long)(Met<DIM>::LEN + s) * g.ncell + c];
 }
 
-/* ===================================================================== */
-/* (a) reconstruction of one variable of one cell                        */
-/* ===================================================================== */
-#include "cgks_recon_gen.cuh"
-
-/* data access of the reconstruction of variable v of cell c: own average and
-   line differences (reference frame: stored derivative x line length), and
-   neighbour averages and gradients mapped to the target's reference frame
-   with J0^T (Sec. 4).  CURVI = false: J0 = diag(h). */
-template <int DIM, bool CURVI> struct ReconLd {
-  const double* __restrict__ U;
-  DevGeo g;
-  long c;
-  int ci, cj, ck, v;
-  double J0[3][3];
-  CGKS_HD double q0() const { return U[(long)v * g.ncell + c]; }
-  CGKS_HD double avg(int ox, int oy, int oz) const {
-    return U[(long)v * g.ncell + nbr(g, ci, cj, ck, ox, oy, oz)];
-  }
-  CGKS_HD void grefv(int ox, int oy, int oz, double* out) const {
-    const long nb = nbr(g, ci, cj, ck, ox, oy, oz);
-    double gp[3];
-#pragma unroll
-    for (int r = 0; r < DIM; ++r) gp[r] = U[((long)(1 + r) * (DIM + 2) + v) * g.ncell + nb];
-    if constexpr (CURVI) {
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        double s = 0.0;
-#pragma unroll
-        for (int r = 0; r < DIM; ++r) s += J0[r][k] * gp[r];
-        out[k] = s;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) out[k] = g.h[k] * gp[k];
-    }
-  }
-  CGKS_HD double line(int s) const {
-    return U[((long)(1 + DIM + s) * (DIM + 2) + v) * g.ncell + c] * met_len<DIM>(g, c, s);
-  }
-};
-
-/* Reconstruction of Eq. (compact-big-ref) on the reference cell: a = M d by the
-   generated symmetry-reduced code, the linear sub-stencil gradients of
-   Eq. (compact-sub-2) (closed form: the face-neighbour difference along the
-   connecting axis, the mean of the line differences along each other axis),
-   the GENO weights, and the blended value and physical gradient at every
-   face Gauss point (Eq. weno-new, reverse transform of Sec. 4).
-   chi_force >= 0 overrides chi.  Returns chi. */
-template <int DIM, bool CURVI>
-CGKS_HD double recon_var(const double* __restrict__ U, const DevGeo& g, const Phys& ph, long c, int ci, int cj,
-                         int ck, int v, double chi_force, double* __restrict__ gpL, double* __restrict__ gpR) {
-  typedef Sz<DIM> S;
-  const long N = g.ncell;
-  constexpr int NV = S::NV;
-  ReconLd<DIM, CURVI> ld;
-  ld.U = U;
-  ld.g = g;
-  ld.c = c;
-  ld.ci = ci;
-  ld.cj = cj;
-  ld.ck = ck;
-  ld.v = v;
-  if constexpr (CURVI) {
-#pragma unroll
-    for (int r = 0; r < DIM; ++r)
-#pragma unroll
-      for (int q = 0; q < DIM; ++q) ld.J0[r][q] = met_J0<DIM>(g, c, r, q);
-  }
-  double a[S::NB];
-  if constexpr (DIM == 3) gen_coeffs_3d(ld, a);
-  else gen_coeffs_2d(ld, a);
-  const double q0 = ld.q0();
-
-  /* GENO path function (Sec. 3.3) */
-  double chi;
-  if (chi_force >= 0.0) {
-    chi = chi_force;
-  } else {
-    const double ish = DIM == 3 ? gen_ish_3d(a) : gen_ish_2d(a);
-    const double isl = DIM == 3 ? gen_isl_3d(a) : gen_isl_2d(a);
-    const double eps = 1e-15;
-    double ist = ish - isl;
-    if (ist < 0.0) ist = 0.0;
-    const double rh = ist / (ish + eps), rl = ist / (isl + eps);
-    const double ah = 1.0 + rh * rh, al = 1.0 + rl * rl;
-    const double alpha = 2.0 * ah / (ah + al);
-    chi = tanh(ph.c_chi * alpha) / tanh(ph.c_chi);
-  }
-  /* linear sub-stencil polynomials and their WENO weights (d_m = 1/(2 dim)) */
-  double bbar[3] = {0.0, 0.0, 0.0};
-  {
-    double lsum[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int s = 0; s < S::NL; ++s) lsum[s / S::GPF] += ld.line(s);
-    double bm[2 * DIM][3], wb[2 * DIM], ws = 0.0;
-#pragma unroll
-    for (int m = 0; m < 2 * DIM; ++m) {
-      const int ax = m / 2;
-      int o[3] = {0, 0, 0};
-      o[ax] = (m & 1) ? 1 : -1;
-      const double qf = ld.avg(o[0], o[1], o[2]);
-      const double sg = (m & 1) ? 1.0 : -1.0;
-      double is = 0.0;
-#pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) {
-        const double bv = (kk == ax) ? sg * (qf - q0) : lsum[kk] * (1.0 / S::GPF);
-        bm[m][kk] = bv;
-        is += bv * bv;
-      }
-      const double t = is + 1e-15;
-      const double t2 = t * t;
-      wb[m] = (1.0 / (2 * DIM)) / (t2 * t2 * t);
-      ws += wb[m];
-    }
-    const double iws = 1.0 / ws;
-#pragma unroll
-    for (int m = 0; m < 2 * DIM; ++m) {
-      const double w = wb[m] * iws;
-#pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) bbar[kk] += w * bm[m][kk];
-    }
-  }
-  double JiT[3][3];
-  if constexpr (CURVI) {
-#pragma unroll
-    for (int r = 0; r < DIM; ++r)
-#pragma unroll
-      for (int q = 0; q < DIM; ++q) JiT[r][q] = met_JiT<DIM>(g, c, r, q);
-  }
-  const double base4 = q0 - (DIM == 3 ? gen_mean_3d(a) : gen_mean_2d(a));
-  /* blended values at the face Gauss points, Eq. (weno-new), axis by axis */
-#pragma unroll
-  for (int ax = 0; ax < DIM; ++ax) {
-    double pv[2 * S::GPF], pg[2 * S::GPF][DIM];
-    if constexpr (DIM == 3) {
-      if (ax == 0) gen_gp_3d_ax0(a, pv, pg);
-      else if (ax == 1) gen_gp_3d_ax1(a, pv, pg);
-      else gen_gp_3d_ax2(a, pv, pg);
-    } else {
-      if (ax == 0) gen_gp_2d_ax0(a, pv, pg);
-      else gen_gp_2d_ax1(a, pv, pg);
-    }
-    int o[3] = {0, 0, 0};
-    o[ax] = -1;
-    const long clo = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
-#pragma unroll
-    for (int i = 0; i < 2 * S::GPF; ++i) {
-      const int side = i / S::GPF, k = i % S::GPF;
-      const int gp = (2 * ax + side) * S::GPF + k;
-      double v1 = q0;
-#pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) v1 += bbar[kk] * gp_delta<DIM>(gp, kk);
-      const double val = chi * (base4 + pv[i]) + (1.0 - chi) * v1;
-      double gref[3];
-#pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) gref[kk] = chi * pg[i][kk] + (1.0 - chi) * bbar[kk];
-      double* dst = side ? gpL : gpR;
-      const long cell = side ? c : clo;
-      const long b = ((long)((ax * S::GPF + k) * NV + v) * (1 + DIM)) * N + cell;
-      dst[b] = val;
-#pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) {
-        double sg;
-        if constexpr (CURVI) {
-          sg = 0.0;
-#pragma unroll
-          for (int r = 0; r < DIM; ++r) sg += JiT[kk][r] * gref[r];
-        } else {
-          sg = gref[kk] / g.h[kk];
-        }
-        dst[b + (long)(1 + kk) * N] = sg;
-      }
-    }
-  }
-  return chi;
-}
-
-/* positivity of the reconstructed Gauss-point states of a cell (C18 reading:
-   the states just written by this thread are read back) */
-template <int DIM>
-CGKS_HD bool cell_states_physical(const DevGeo& g, const Phys& ph, long c, int ci, int cj, int ck,
-                                  const double* __restrict__ gpL, const double* __restrict__ gpR) {
-  typedef Sz<DIM> S;
-  const long N = g.ncell;
-  for (int gp = 0; gp < S::NGP; ++gp) {
-    int f = gp / S::GPF, k = gp % S::GPF, ax = f / 2, side = f & 1;
-    const double* src;
-    long cell;
-    if (side) {
-      src = gpL;
-      cell = c;
-    } else {
-      src = gpR;
-      int o[3] = {0, 0, 0};
-      o[ax] = -1;
-      cell = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
-    }
-    double w[S::NV];
-    for (int v = 0; v < S::NV; ++v) w[v] = src[((long)((ax * S::GPF + k) * S::NV + v) * (1 + DIM)) * N + cell];
-    double ke = 0.0;
-    for (int i = 0; i < DIM; ++i) ke += w[1 + i] * w[1 + i];
-    double p = (ph.gamma - 1.0) * (w[DIM + 1] - 0.5 * ke / w[0]);
-    if (!(w[0] > 0.0) || !(p > 0.0)) return false;
-  }
-  return true;
-}
-
-/* ===================================================================== */
-/* (b) gas-kinetic interface solution at one Gauss point (Sec. 2)        */
-/* ===================================================================== */
 /* math wrappers so that the same code serves FP64 and FP32 */
 CGKS_HD double cg_erfc(double x) { return erfc(x); }
 CGKS_HD float cg_erfc(float x) { return erfcf(x); }
@@ -364,7 +166,271 @@ CGKS_HD double cg_sqrt(double x) { return sqrt(x); }
 CGKS_HD float cg_sqrt(float x) { return sqrtf(x); }
 CGKS_HD double cg_fabs(double x) { return fabs(x); }
 CGKS_HD float cg_fabs(float x) { return fabsf(x); }
+CGKS_HD double cg_fma(double a, double b, double c) { return fma(a, b, c); }
+CGKS_HD float cg_fma(float a, float b, float c) { return fmaf(a, b, c); }
+CGKS_HD double cg_tanh(double x) { return tanh(x); }
+CGKS_HD float cg_tanh(float x) { return tanhf(x); }
 
+/* ===================================================================== */
+/* (a) reconstruction of one variable of one cell                        */
+/* ===================================================================== */
+#include "cgks_recon_gen.cuh"
+
+/* data access of the reconstruction of variable v of cell c.  Averages are
+   handed over relative to the cell's own average: the reconstruction depends
+   on differences only, so the large offsets never enter T arithmetic.  FP64:
+   differences of the FP64 averages.  FP32: every average is also kept as an
+   exact pair hi + lo of FP32 numbers (written by the update), so the
+   difference is (hi_k - hi_0) + (lo_k - lo_0), computed in FP32 without the
+   FP64 pipe.  Gradients are mapped to the target's reference frame with J0^T
+   (Sec. 4; CURVI = false: J0 = diag(h)); line differences are the stored
+   derivatives times the line length.  der: [(f-1)][v][cell] in T, f >= 1. */
+template <typename T, int DIM, bool CURVI> struct ReconLd {
+  const double* __restrict__ avgp;  /* FP64 averages [v][cell] (FP64 form) */
+  const float* __restrict__ avh;    /* hi and lo parts [v][cell] (FP32 form) */
+  const float* __restrict__ avl;
+  const T* __restrict__ der;
+  DevGeo g;
+  long c;
+  int ci, cj, ck, v;
+  double q0d;
+  float q0h, q0l;
+  T J0[3][3];
+  CGKS_HD void init_q0() {
+    if constexpr (sizeof(T) == 4) {
+      q0h = avh[(long)v * g.ncell + c];
+      q0l = avl[(long)v * g.ncell + c];
+      q0d = 0.0;
+    } else {
+      q0d = avgp[(long)v * g.ncell + c];
+    }
+  }
+  CGKS_HD T q0() const { return T(0); }
+  CGKS_HD T avg(int ox, int oy, int oz) const {
+    const long i = (long)v * g.ncell + nbr(g, ci, cj, ck, ox, oy, oz);
+    if constexpr (sizeof(T) == 4) return (avh[i] - q0h) + (avl[i] - q0l);
+    else return T(avgp[i] - q0d);
+  }
+  /* the full value q0 + rel at a Gauss point, stored in T */
+  CGKS_HD T full(T rel) const {
+    if constexpr (sizeof(T) == 4) return q0h + (q0l + rel);
+    else return T(q0d + double(rel));
+  }
+  CGKS_HD void grefv(int ox, int oy, int oz, T* out) const {
+    const long nb = nbr(g, ci, cj, ck, ox, oy, oz);
+    T gp[3];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) gp[r] = der[((long)r * (DIM + 2) + v) * g.ncell + nb];
+    if constexpr (CURVI) {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        T s = T(0);
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) s += J0[r][k] * gp[r];
+        out[k] = s;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) out[k] = geo_h<T>(g, k) * gp[k];
+    }
+  }
+  CGKS_HD T line(int s) const {
+    const T len = CURVI ? T(met_len<DIM>(g, c, s)) : geo_h<T>(g, s / Sz<DIM>::GPF);
+    return der[((long)(DIM + s) * (DIM + 2) + v) * g.ncell + c] * len;
+  }
+};
+
+/* Reconstruction of Eq. (compact-big-ref) on the reference cell: a = M d by the
+   generated symmetry-reduced code, the linear sub-stencil gradients of
+   Eq. (compact-sub-2) (closed form: the face-neighbour difference along the
+   connecting axis, the mean of the line differences along each other axis),
+   the GENO weights, and the blended value and physical gradient at every
+   face Gauss point (Eq. weno-new, reverse transform of Sec. 4), stored in T.
+   chi_force >= 0 overrides chi.  Returns chi. */
+template <typename T, int DIM, bool CURVI>
+CGKS_HD T recon_var(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
+                    const T* __restrict__ der, const DevGeo& g, const Phys& ph, long c, int ci, int cj, int ck, int v,
+                    T chi_force, T* __restrict__ gpL, T* __restrict__ gpR) {
+  typedef Sz<DIM> S;
+  const long N = g.ncell;
+  constexpr int NV = S::NV;
+  ReconLd<T, DIM, CURVI> ld;
+  ld.avgp = avg;
+  ld.avh = avh;
+  ld.avl = avl;
+  ld.der = der;
+  ld.g = g;
+  ld.c = c;
+  ld.ci = ci;
+  ld.cj = cj;
+  ld.ck = ck;
+  ld.v = v;
+  ld.init_q0();
+  if constexpr (CURVI) {
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) ld.J0[r][q] = T(met_J0<DIM>(g, c, r, q));
+  }
+  T a[S::NB];
+  if constexpr (DIM == 3) gen_coeffs_3d<T>(ld, a);
+  else gen_coeffs_2d<T>(ld, a);
+
+  /* GENO path function (Sec. 3.3) */
+  T chi;
+  if (chi_force >= T(0)) {
+    chi = chi_force;
+  } else {
+    T ish, isl;
+    if constexpr (DIM == 3) {
+      ish = gen_ish_3d<T>(a);
+      isl = gen_isl_3d<T>(a);
+    } else {
+      ish = gen_ish_2d<T>(a);
+      isl = gen_isl_2d<T>(a);
+    }
+    const T eps = T(1e-15);
+    T ist = ish - isl;
+    if (ist < T(0)) ist = T(0);
+    const T rh = ist / (ish + eps), rl = ist / (isl + eps);
+    const T ah = T(1) + rh * rh, al = T(1) + rl * rl;
+    const T alpha = T(2) * ah / (ah + al);
+    chi = cg_tanh(ph_cchi<T>(ph) * alpha) / cg_tanh(ph_cchi<T>(ph));
+  }
+  /* linear sub-stencil polynomials and their WENO weights (d_m = 1/(2 dim)).
+     omega_m = (IS_m + eps)^-5 / sum_m' (IS_m' + eps)^-5, evaluated through the
+     ratios (IS_min + eps)/(IS_m + eps) <= 1, which stays finite in FP32. */
+  T bbar[3] = {T(0), T(0), T(0)};
+  {
+    T lsum[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int s = 0; s < S::NL; ++s) lsum[s / S::GPF] += ld.line(s);
+    T bm[2 * DIM][3], tis[2 * DIM];
+#pragma unroll
+    for (int m = 0; m < 2 * DIM; ++m) {
+      const int ax = m / 2;
+      int o[3] = {0, 0, 0};
+      o[ax] = (m & 1) ? 1 : -1;
+      const T qf = ld.avg(o[0], o[1], o[2]);
+      const T sg = (m & 1) ? T(1) : T(-1);
+      T is = T(0);
+#pragma unroll
+      for (int kk = 0; kk < DIM; ++kk) {
+        const T bv = (kk == ax) ? sg * qf : lsum[kk] * (T(1) / T(S::GPF));
+        bm[m][kk] = bv;
+        is += bv * bv;
+      }
+      tis[m] = is + T(1e-15);
+    }
+    T tmin = tis[0];
+#pragma unroll
+    for (int m = 1; m < 2 * DIM; ++m) tmin = tis[m] < tmin ? tis[m] : tmin;
+    T wb[2 * DIM], ws = T(0);
+#pragma unroll
+    for (int m = 0; m < 2 * DIM; ++m) {
+      const T r = tmin / tis[m];
+      const T r2 = r * r;
+      wb[m] = r2 * r2 * r;
+      ws += wb[m];
+    }
+    const T iws = T(1) / ws;
+#pragma unroll
+    for (int m = 0; m < 2 * DIM; ++m) {
+      const T w = wb[m] * iws;
+#pragma unroll
+      for (int kk = 0; kk < DIM; ++kk) bbar[kk] += w * bm[m][kk];
+    }
+  }
+  T JiT[3][3];
+  if constexpr (CURVI) {
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) JiT[r][q] = T(met_JiT<DIM>(g, c, r, q));
+  }
+  T mean4;
+  if constexpr (DIM == 3) mean4 = gen_mean_3d<T>(a);
+  else mean4 = gen_mean_2d<T>(a);
+  /* blended values at the face Gauss points, Eq. (weno-new), axis by axis */
+#pragma unroll 1
+  for (int ax = 0; ax < DIM; ++ax) {
+    T pv[2 * S::GPF], pg[2 * S::GPF][DIM];
+    if constexpr (DIM == 3) {
+      if (ax == 0) gen_gp_3d_ax0<T>(a, pv, pg);
+      else if (ax == 1) gen_gp_3d_ax1<T>(a, pv, pg);
+      else gen_gp_3d_ax2<T>(a, pv, pg);
+    } else {
+      if (ax == 0) gen_gp_2d_ax0<T>(a, pv, pg);
+      else gen_gp_2d_ax1<T>(a, pv, pg);
+    }
+    int o[3] = {0, 0, 0};
+    o[ax] = -1;
+    const long clo = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
+#pragma unroll
+    for (int i = 0; i < 2 * S::GPF; ++i) {
+      const int side = i / S::GPF, k = i % S::GPF;
+      const int gp = (2 * ax + side) * S::GPF + k;
+      T v1 = T(0);
+#pragma unroll
+      for (int kk = 0; kk < DIM; ++kk) v1 += bbar[kk] * gp_delta<DIM, T>(gp, kk);
+      const T rel = chi * (pv[i] - mean4) + (T(1) - chi) * v1;
+      T gref[3];
+#pragma unroll
+      for (int kk = 0; kk < DIM; ++kk) gref[kk] = chi * pg[i][kk] + (T(1) - chi) * bbar[kk];
+      T* dst = side ? gpL : gpR;
+      const long cell = side ? c : clo;
+      const long b = ((long)((ax * S::GPF + k) * NV + v) * (1 + DIM)) * N + cell;
+      dst[b] = ld.full(rel);
+#pragma unroll
+      for (int kk = 0; kk < DIM; ++kk) {
+        T sg;
+        if constexpr (CURVI) {
+          sg = T(0);
+#pragma unroll
+          for (int r = 0; r < DIM; ++r) sg += JiT[kk][r] * gref[r];
+        } else {
+          sg = gref[kk] * geo_ih<T>(g, kk);
+        }
+        dst[b + (long)(1 + kk) * N] = sg;
+      }
+    }
+  }
+  return chi;
+}
+
+/* positivity of the reconstructed Gauss-point states of a cell (C18 reading:
+   the states just written by this thread are read back) */
+template <typename T, int DIM>
+CGKS_HD bool cell_states_physical(const DevGeo& g, const Phys& ph, long c, int ci, int cj, int ck,
+                                  const T* __restrict__ gpL, const T* __restrict__ gpR) {
+  typedef Sz<DIM> S;
+  const long N = g.ncell;
+  for (int gp = 0; gp < S::NGP; ++gp) {
+    int f = gp / S::GPF, k = gp % S::GPF, ax = f / 2, side = f & 1;
+    const T* src;
+    long cell;
+    if (side) {
+      src = gpL;
+      cell = c;
+    } else {
+      src = gpR;
+      int o[3] = {0, 0, 0};
+      o[ax] = -1;
+      cell = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
+    }
+    T w[S::NV];
+    for (int v = 0; v < S::NV; ++v) w[v] = src[((long)((ax * S::GPF + k) * S::NV + v) * (1 + DIM)) * N + cell];
+    T ke = T(0);
+    for (int i = 0; i < DIM; ++i) ke += w[1 + i] * w[1 + i];
+    const T p = (ph_gamma<T>(ph) - T(1)) * (w[DIM + 1] - T(0.5) * ke / w[0]);
+    if (!(w[0] > T(0)) || !(p > T(0))) return false;
+  }
+  return true;
+}
+
+/* ===================================================================== */
+/* (b) gas-kinetic interface solution at one Gauss point (Sec. 2)        */
+/* ===================================================================== */
 enum { REG_FULL = 0, REG_POS = 1, REG_NEG = 2 };
 
 /* Maxwellian of a conservative state: macroscopic scalars plus the two base
@@ -662,7 +728,7 @@ CGKS_HD void g0_dir(const MxS<T, DIM>& z, const MxT<T>& t, T gam, T D, T iD, con
 template <typename T, int DIM, class Ld>
 CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const Ld& ld, T* out) {
   constexpr int NV = DIM + 2;
-  const T gam = T(ph.gamma);
+  const T gam = ph_gamma<T>(ph);
   const T D = T(2) / (gam - T(1));
   const T iD = T(1) / D;
   const T K = D - T(DIM);
@@ -694,7 +760,7 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   const T jump = cg_fabs((l.p - r.p) / (l.p + r.p));
   T tau = T(0);
   if (ph.tau_mode == 1) tau = T(0.05) * dt + T(5) * jump * dt;
-  else if (ph.tau_mode == 2) tau = T(ph.mu) / z.p + T(5) * jump * dt;
+  else if (ph.tau_mode == 2) tau = ph_mu<T>(ph) / z.p + T(5) * jump * dt;
   T cn[6], ct[6];
   {
     T cf[6], chf[6];
@@ -707,7 +773,7 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
       ct[i] = T(4) * (cf[i] - T(2) * chf[i]) * idt * idt;
     }
   }
-  const bool prfix = ph.mu > 0.0 && ph.prandtl > 0.0 && ph.prandtl != 1.0;
+  const bool prfix = ph.prfix != 0;
   T Fn[NV], Ft[NV], Qn[NV], Qt[NV], bl[NV], br[NV], b0[NV], dW0[DIM * NV];
   euler_flux<T, DIM>(z, W0, 0, t1); /* part 0: rho0 <u psi> of g0 */
 #pragma unroll
@@ -744,7 +810,7 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
       Qn[i] += cn[2] * t2[i];
       Qt[i] += ct[2] * t2[i];
     }
-    const T f = T(1) / T(ph.prandtl) - T(1);
+    const T f = T(1) / ph_pr<T>(ph) - T(1);
 #pragma unroll
     for (int pass = 0; pass < 2; ++pass) {
       T* F = pass == 0 ? Fn : Ft;
@@ -795,18 +861,18 @@ CGKS_HD bool gks_point(const Phys& ph, T dt, const T* WL, const T* dWL, const T*
 /* derivative loader of the Cartesian path: reads the local-frame derivative of
    side 0 (left, gpL) or 1 (right, gpR) along local axis j from global memory,
    through the signed-permutation frame */
-template <int DIM> struct CartLd {
-  const double* gl;
-  const double* gr;
+template <typename T, int DIM> struct CartLd {
+  const T* gl;
+  const T* gr;
   long base, N, c;
   int p[3], s[3];
-  CGKS_HD void grad(int side, int j, double* o) const {
-    const double* src = side == 0 ? gl : gr;
+  CGKS_HD void grad(int side, int j, T* o) const {
+    const T* src = side == 0 ? gl : gr;
 #pragma unroll
     for (int v = 0; v < DIM + 2; ++v) {
       int vg = v, sv = 1;
       if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
-      o[v] = (sv * s[j]) * src[(base + vg * (1 + DIM) + 1 + p[j]) * N + c];
+      o[v] = T(sv * s[j]) * src[(base + vg * (1 + DIM) + 1 + p[j]) * N + c];
     }
   }
 };
@@ -894,18 +960,18 @@ CGKS_HD void to_global(const double R[3][3], T* F) {
 /* one face Gauss point: gather, rotate, solve, rotate back, store.
    CURVI selects at compile time between the Cartesian signed-permutation
    frames and general face frames. */
-template <int DIM, bool CURVI>
-CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, double dt, int ax, int k, long c,
-                        const double* __restrict__ gpL, const double* __restrict__ gpR, double* __restrict__ flux) {
+template <typename T, int DIM, bool CURVI>
+CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, long c,
+                        const T* __restrict__ gpL, const T* __restrict__ gpR, T* __restrict__ flux) {
   typedef Sz<DIM> S;
   constexpr int NV = S::NV;
   const long N = g.ncell;
   const long base = (long)((ax * S::GPF + k) * NV) * (1 + DIM);
-  double WL[NV], WR[NV], out[6 * NV];
+  T WL[NV], WR[NV], out[6 * NV];
   if constexpr (!CURVI) {
     /* value and momentum: W_loc[1+i] = s_i m_{p_i}; derivative along local j:
        s_j d/dx_{p_j} of the local variable (loaded when its side needs it) */
-    CartLd<DIM> ld;
+    CartLd<T, DIM> ld;
     ld.gl = gpL;
     ld.gr = gpR;
     ld.base = base;
@@ -919,10 +985,10 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, double dt, int ax, int 
       int vg = v, sv = 1;
       if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
       const long b = (base + vg * (1 + DIM)) * N + c;
-      WL[v] = sv * gpL[b];
-      WR[v] = sv * gpR[b];
+      WL[v] = T(sv) * gpL[b];
+      WR[v] = T(sv) * gpR[b];
     }
-    bool ok = gks_point_ld<double, DIM>(ph, dt, WL, WR, ld, out);
+    bool ok = gks_point_ld<T, DIM>(ph, dt, WL, WR, ld, out);
     const long fb = (long)((ax * S::GPF + k) * 6) * NV;
 #pragma unroll
     for (int part = 0; part < 6; ++part) {
@@ -930,13 +996,13 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, double dt, int ax, int 
       for (int v = 0; v < NV; ++v) {
         int vg = v, sv = 1;
         if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
-        flux[(fb + part * NV + vg) * N + c] = sv * out[part * NV + v];
+        flux[(fb + part * NV + vg) * N + c] = T(sv) * out[part * NV + v];
       }
     }
     return ok;
   } else {
-  double dWL[DIM * NV], dWR[DIM * NV];
-  double sl[NV * (1 + DIM)], sr[NV * (1 + DIM)];
+  T dWL[DIM * NV], dWR[DIM * NV];
+  T sl[NV * (1 + DIM)], sr[NV * (1 + DIM)];
   for (int q = 0; q < NV * (1 + DIM); ++q) {
     sl[q] = gpL[(base + q) * N + c];
     sr[q] = gpR[(base + q) * N + c];
@@ -949,10 +1015,10 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, double dt, int ax, int 
   }
   double R[3][3];
   face_frame<DIM>(A, Tt, R);
-  to_local<double, DIM>(R, sl, WL, dWL);
-  to_local<double, DIM>(R, sr, WR, dWR);
-  bool ok = gks_point<double, DIM>(ph, dt, WL, dWL, WR, dWR, out);
-  for (int p = 0; p < 6; ++p) to_global<double, DIM>(R, out + p * NV);
+  to_local<T, DIM>(R, sl, WL, dWL);
+  to_local<T, DIM>(R, sr, WR, dWR);
+  bool ok = gks_point<T, DIM>(ph, dt, WL, dWL, WR, dWR, out);
+  for (int p = 0; p < 6; ++p) to_global<T, DIM>(R, out + p * NV);
   const long fb = (long)((ax * S::GPF + k) * 6) * NV;
   for (int q = 0; q < 6 * NV; ++q) flux[(fb + q) * N + c] = out[q];
   return ok;
@@ -962,143 +1028,122 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, double dt, int ax, int 
 /* ===================================================================== */
 /* (c) accumulation and S2O4 update of one cell                          */
 /* ===================================================================== */
-/* stage 1: Uout = U* ; stash = {Q^n + dt L + dt^2/6 L_t ; D(Q^n(x_G))}
-   stage 2: Uout = U^{n+1} = {stash + dt^2/3 L_t* ; stash_D + dt D((dQ/dt)*(x_G))}
+/* S2O4 update of variable v of cell c (temporal discretisation section):
+   stage 1: out = U* ; stash = {Q^n + dt L + dt^2/6 L_t ; D(Q^n(x_G))}
+   stage 2: out = U^{n+1} = {stash + dt^2/3 L_t* ; stash_D + dt D((dQ/dt)*(x_G))}
    L = -(1/|Omega|) sum_faces sum_k F.n S (Eq. semi with Gauss quadrature); the
    gradient by Gauss' theorem (Eq. derivative) and the line derivatives by
    Eq. (derivative-l) from the interface values of each side.  CURVI = false:
    axis-aligned cells, where both reduce to differences divided by h. */
-template <int DIM, bool CURVI>
-CGKS_HD void update_cell(const DevGeo& g, double dt, int stage, long c, int ci, int cj, int ck,
-                         const double* __restrict__ Uin, const double* __restrict__ flux,
-                         double* __restrict__ stash, double* __restrict__ Uout) {
+template <typename T, int DIM, bool CURVI>
+CGKS_HD void update_var(const DevGeo& g, double dt, int stage, long c, int ci, int cj, int ck, int v,
+                        const double* __restrict__ avg_in, const T* __restrict__ flux,
+                        double* __restrict__ stash_avg, T* __restrict__ stash_der, double* __restrict__ avg_out,
+                        T* __restrict__ der_out, float* __restrict__ avh_out, float* __restrict__ avl_out) {
   typedef Sz<DIM> S;
   constexpr int NV = S::NV, GPF = S::GPF;
   const long N = g.ncell;
-  long lo[3];
+  const T tdt = T(dt), hdt = T(0.5) * tdt;
+  T ivol = T(1);
+  if constexpr (CURVI) ivol = T(1.0 / met_vol<DIM>(g, c));
+  /* L and dL/dt accumulate in FP64 from per-face sums in T: both cells of a
+     face form the same face sum in the same order, so the face enters them
+     with exactly opposite values and domain sums are conserved to FP64
+     rounding */
+  double L = 0.0, Lt = 0.0;
+  T gn[3] = {T(0), T(0), T(0)}, gt[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int ax = 0; ax < DIM; ++ax) {
     int o[3] = {0, 0, 0};
     o[ax] = -1;
-    lo[ax] = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
-  }
-  double ivol, ih[3] = {1.0, 1.0, 1.0};
-  double sh[DIM][GPF], sl[DIM][GPF];
-  if constexpr (CURVI) {
-    ivol = 1.0 / met_vol<DIM>(g, c);
+    const long lo = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
+    const T ih = CURVI ? T(1) : geo_ih<T>(g, ax);
+    T sh_f = T(0), sl_f = T(0), sth_f = T(0), stl_f = T(0); /* face sums, high and low face */
 #pragma unroll
-    for (int ax = 0; ax < DIM; ++ax)
-#pragma unroll
-      for (int k = 0; k < GPF; ++k) {
-        const int ghi = (2 * ax + 1) * GPF + k;
-        double a2 = 0.0, b2 = 0.0;
+    for (int k = 0; k < GPF; ++k) {
+      const long fb = (long)((ax * GPF + k) * 6) * NV + v;
+      const int ghi = (2 * ax + 1) * GPF + k, glo = (2 * ax) * GPF + k;
+      const T fh = flux[(fb + 0 * NV) * N + c], fl = flux[(fb + 0 * NV) * N + lo];
+      const T fth = flux[(fb + 1 * NV) * N + c], ftl = flux[(fb + 1 * NV) * N + lo];
+      const T qnh = flux[(fb + 2 * NV) * N + c], qth = flux[(fb + 3 * NV) * N + c];
+      const T qnl = flux[(fb + 4 * NV) * N + lo], qtl = flux[(fb + 5 * NV) * N + lo];
+      if constexpr (CURVI) {
+        T a2 = T(0), b2 = T(0);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-          const double ah = met_area<DIM>(g, c, ghi, a), al = met_area<DIM>(g, lo[ax], ghi, a);
+          const T ah = T(met_area<DIM>(g, c, ghi, a)), al = T(met_area<DIM>(g, lo, ghi, a));
           a2 += ah * ah;
           b2 += al * al;
+          /* Gauss' theorem with the cell's own outward area vectors */
+          const T Al = T(met_area<DIM>(g, c, glo, a));
+          gn[a] += qnh * ah - qnl * Al;
+          gt[a] += qth * ah - qtl * Al;
         }
-        sh[ax][k] = sqrt(a2);
-        sl[ax][k] = sqrt(b2);
-      }
-  } else {
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) ih[ax] = 1.0 / g.h[ax];
-    ivol = 1.0;
-  }
-  const double hdt = 0.5 * dt, edt2 = 0.125 * dt * dt, sdt2 = dt * dt / 6.0, tdt2 = dt * dt / 3.0;
-#pragma unroll 1
-  for (int v = 0; v < NV; ++v) {
-    double L = 0.0, Lt = 0.0;
-    double qn[S::NGP], qt[S::NGP];
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      double la = 0.0, lta = 0.0;
-#pragma unroll
-      for (int k = 0; k < GPF; ++k) {
-        const long fb = (long)((ax * GPF + k) * 6) * NV + v;
-        const int ghi = (2 * ax + 1) * GPF + k, glo = (2 * ax) * GPF + k;
-        const double fh = flux[(fb + 0 * NV) * N + c], fl = flux[(fb + 0 * NV) * N + lo[ax]];
-        const double fth = flux[(fb + 1 * NV) * N + c], ftl = flux[(fb + 1 * NV) * N + lo[ax]];
-        if constexpr (CURVI) {
-          la += -fh * sh[ax][k] + fl * sl[ax][k];
-          lta += -fth * sh[ax][k] + ftl * sl[ax][k];
-        } else {
-          la += fl - fh;
-          lta += ftl - fth;
-        }
-        qn[ghi] = flux[(fb + 2 * NV) * N + c];
-        qt[ghi] = flux[(fb + 3 * NV) * N + c];
-        qn[glo] = flux[(fb + 4 * NV) * N + lo[ax]];
-        qt[glo] = flux[(fb + 5 * NV) * N + lo[ax]];
-      }
-      if constexpr (CURVI) {
-        L += la;
-        Lt += lta;
+        const T sh = cg_sqrt(a2), sl = cg_sqrt(b2);
+        sh_f += fh * sh;
+        sl_f += fl * sl;
+        sth_f += fth * sh;
+        stl_f += ftl * sl;
       } else {
-        L += la * ih[ax] * (1.0 / GPF);
-        Lt += lta * ih[ax] * (1.0 / GPF);
+        sh_f += fh;
+        sl_f += fl;
+        sth_f += fth;
+        stl_f += ftl;
       }
-    }
-    L *= ivol;
-    Lt *= ivol;
-    const long iavg = (long)v * N + c;
-    if (stage == 1) {
-      const double q = Uin[iavg];
-      Uout[iavg] = q + hdt * L + edt2 * Lt;
-      stash[iavg] = q + dt * L + sdt2 * Lt;
-    } else {
-      Uout[iavg] = stash[iavg] + tdt2 * Lt;
-    }
-    /* line derivatives, then the gradient */
-    double ln[S::NL], lt[S::NL];
-#pragma unroll
-    for (int s2 = 0; s2 < S::NL; ++s2) {
-      const int ax = s2 / GPF, k = s2 % GPF;
-      const double il = CURVI ? 1.0 / met_len<DIM>(g, c, s2) : ih[ax];
-      ln[s2] = (qn[(2 * ax + 1) * GPF + k] - qn[(2 * ax) * GPF + k]) * il;
-      lt[s2] = (qt[(2 * ax + 1) * GPF + k] - qt[(2 * ax) * GPF + k]) * il;
-    }
-#pragma unroll
-    for (int f = 1; f < S::NF; ++f) {
-      double dn, dtv;
-      if (f <= DIM) {
-        const int kk = f - 1;
-        if constexpr (CURVI) {
-          dn = 0.0;
-          dtv = 0.0;
-#pragma unroll
-          for (int gp = 0; gp < S::NGP; ++gp) {
-            const double sgn = ((gp / GPF) & 1) ? 1.0 : -1.0;
-            const double A = sgn * met_area<DIM>(g, c, gp, kk);
-            dn += qn[gp] * A;
-            dtv += qt[gp] * A;
-          }
-          dn *= ivol;
-          dtv *= ivol;
-        } else {
-          /* Gauss' theorem on an axis-aligned cell: the mean of the line derivatives */
-          dn = 0.0;
-          dtv = 0.0;
-#pragma unroll
-          for (int k = 0; k < GPF; ++k) {
-            dn += ln[kk * GPF + k];
-            dtv += lt[kk * GPF + k];
-          }
-          dn *= (1.0 / GPF);
-          dtv *= (1.0 / GPF);
-        }
-      } else {
-        dn = ln[f - 1 - DIM];
-        dtv = lt[f - 1 - DIM];
+      /* line derivative s = ax*GPF + k, Eq. (derivative-l) */
+      const int s2 = ax * GPF + k;
+      const T il = CURVI ? T(1.0 / met_len<DIM>(g, c, s2)) : ih;
+      const T ln = (qnh - qnl) * il, lt = (qth - qtl) * il;
+      if constexpr (!CURVI) {
+        gn[ax] += ln;
+        gt[ax] += lt;
       }
-      const long idx = ((long)f * NV + v) * N + c;
+      const long idx = ((long)(DIM + s2) * NV + v) * N + c;
       if (stage == 1) {
-        Uout[idx] = dn + hdt * dtv;
-        stash[idx] = dn;
+        der_out[idx] = ln + hdt * lt;
+        stash_der[idx] = ln;
       } else {
-        Uout[idx] = stash[idx] + dt * dtv;
+        der_out[idx] = stash_der[idx] + tdt * lt;
       }
+    }
+    const double w = CURVI ? 1.0 : g.ih[ax] * (1.0 / GPF);
+    L += w * (double(sl_f) - double(sh_f));
+    Lt += w * (double(stl_f) - double(sth_f));
+  }
+  if constexpr (CURVI) {
+    const double iv = 1.0 / met_vol<DIM>(g, c);
+    L *= iv;
+    Lt *= iv;
+  }
+  /* cell averages accumulate in FP64 across the S2O4 stages */
+  const long iavg = (long)v * N + c;
+  const double Ld = L, Ltd = Lt;
+  double out;
+  if (stage == 1) {
+    const double q = avg_in[iavg];
+    out = q + 0.5 * dt * Ld + 0.125 * dt * dt * Ltd;
+    stash_avg[iavg] = q + dt * Ld + dt * dt / 6.0 * Ltd;
+  } else {
+    out = stash_avg[iavg] + dt * dt / 3.0 * Ltd;
+  }
+  avg_out[iavg] = out;
+  if constexpr (sizeof(T) == 4) {
+    const float h = float(out);
+    avh_out[iavg] = h;
+    avl_out[iavg] = float(out - double(h));
+  }
+  /* gradient: Gauss' theorem (Eq. derivative); on an axis-aligned cell the
+     mean of the line derivatives */
+#pragma unroll
+  for (int kk = 0; kk < DIM; ++kk) {
+    const T dn = CURVI ? gn[kk] * ivol : gn[kk] * T(1.0 / GPF);
+    const T dtv = CURVI ? gt[kk] * ivol : gt[kk] * T(1.0 / GPF);
+    const long idx = ((long)kk * NV + v) * N + c;
+    if (stage == 1) {
+      der_out[idx] = dn + hdt * dtv;
+      stash_der[idx] = dn;
+    } else {
+      der_out[idx] = stash_der[idx] + tdt * dtv;
     }
   }
 }
@@ -1113,37 +1158,45 @@ CGKS_HD double cell_rate(const DevGeo& g, const Phys& ph, const double* __restri
   const long N = g.ncell;
   double W[DIM + 2];
   for (int v = 0; v < DIM + 2; ++v) W[v] = U[(long)v * N + c];
-  double rho = W[0], ke = 0.0, Uv[3];
+  const double rho = W[0], irho = 1.0 / rho;
+  double ke = 0.0, Uv[3];
   for (int i = 0; i < DIM; ++i) {
-    Uv[i] = W[1 + i] / rho;
+    Uv[i] = W[1 + i] * irho;
     ke += Uv[i] * W[1 + i];
   }
-  double p = (ph.gamma - 1.0) * (W[DIM + 1] - 0.5 * ke);
-  double snd = sqrt(ph.gamma * p / rho);
-  double vol = met_vol<DIM>(g, c);
+  const double p = (ph.gamma - 1.0) * (W[DIM + 1] - 0.5 * ke);
+  const double snd = sqrt(ph.gamma * p * irho);
   double rate = 0.0, hmin = 1e300;
-  for (int ax = 0; ax < DIM; ++ax) {
-    double A0[3] = {0.0, 0.0, 0.0}, A1[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < Sz<DIM>::GPF; ++k)
-      for (int a = 0; a < DIM; ++a) {
-        A0[a] += met_area<DIM>(g, c, (2 * ax) * Sz<DIM>::GPF + k, a);
-        A1[a] += met_area<DIM>(g, c, (2 * ax + 1) * Sz<DIM>::GPF + k, a);
-      }
-    double s0 = 0.0, s1 = 0.0, nn[3], ns = 0.0;
-    for (int a = 0; a < DIM; ++a) {
-      s0 += A0[a] * A0[a];
-      s1 += A1[a] * A1[a];
-      nn[a] = A0[a] + A1[a];
-      ns += nn[a] * nn[a];
+  if (!g.curvi) {
+    for (int ax = 0; ax < DIM; ++ax) {
+      rate += (fabs(Uv[ax]) + snd) * g.ih[ax];
+      hmin = g.h[ax] < hmin ? g.h[ax] : hmin;
     }
-    double h = vol / (0.5 * (sqrt(s0) + sqrt(s1)));
-    double un = 0.0;
-    for (int a = 0; a < DIM; ++a) un += Uv[a] * nn[a] / sqrt(ns);
-    rate += (fabs(un) + snd) / h;
-    if (h < hmin) hmin = h;
+  } else {
+    const double vol = met_vol<DIM>(g, c);
+    for (int ax = 0; ax < DIM; ++ax) {
+      double A0[3] = {0.0, 0.0, 0.0}, A1[3] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < Sz<DIM>::GPF; ++k)
+        for (int a = 0; a < DIM; ++a) {
+          A0[a] += met_area<DIM>(g, c, (2 * ax) * Sz<DIM>::GPF + k, a);
+          A1[a] += met_area<DIM>(g, c, (2 * ax + 1) * Sz<DIM>::GPF + k, a);
+        }
+      double s0 = 0.0, s1 = 0.0, nn[3], ns = 0.0;
+      for (int a = 0; a < DIM; ++a) {
+        s0 += A0[a] * A0[a];
+        s1 += A1[a] * A1[a];
+        nn[a] = A0[a] + A1[a];
+        ns += nn[a] * nn[a];
+      }
+      const double h = vol / (0.5 * (sqrt(s0) + sqrt(s1)));
+      double un = 0.0;
+      for (int a = 0; a < DIM; ++a) un += Uv[a] * nn[a] / sqrt(ns);
+      rate += (fabs(un) + snd) / h;
+      if (h < hmin) hmin = h;
+    }
   }
   if (ph.mu > 0.0) {
-    double rv = 3.0 * ph.mu / (rho * hmin * hmin);
+    const double rv = 3.0 * ph.mu * irho / (hmin * hmin);
     if (rv > rate) rate = rv;
   }
   if (!(rho > 0.0) || !(p > 0.0) || !(rate == rate)) rate = 1e300; /* flags a bad state */

@@ -19,55 +19,109 @@ struct DtState {
   double dt, t, t_end, dt_fixed;
 };
 
-template <int DIM, bool CURVI>
-__global__ void __launch_bounds__(128) k_recon(const double* __restrict__ U, DevGeo g, Phys ph,
-                                               double* __restrict__ gpL, double* __restrict__ gpR,
-                                               double* __restrict__ chi, int record_chi, int* __restrict__ st) {
+/* FP32 kernels fit 3 blocks of 128 threads per SM (168 registers); the FP64
+   ones keep 2 (they are bound by the FP64 pipe, and spill more when capped) */
+template <typename T> constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
+
+template <typename T, int DIM, bool CURVI>
+__global__ void __launch_bounds__(128, min_blocks<T>())
+    k_recon(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
+            const T* __restrict__ der, DevGeo g, Phys ph, T* __restrict__ gpL, T* __restrict__ gpR,
+            double* __restrict__ chi, int record_chi, int* __restrict__ st) {
   long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   int i, j, k;
   cell_ijk(g, c, i, j, k);
   const int NV = Sz<DIM>::NV;
-  double force = ph.linear ? 1.0 : -1.0;
-  double cs[NV];
+  const T force = ph.linear ? T(1) : T(-1);
+  T cs[NV];
 #pragma unroll 1
-  for (int v = 0; v < NV; ++v) cs[v] = recon_var<DIM, CURVI>(U, g, ph, c, i, j, k, v, force, gpL, gpR);
-  if (!cell_states_physical<DIM>(g, ph, c, i, j, k, gpL, gpR)) {
+  for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI>(avg, avh, avl, der, g, ph, c, i, j, k, v, force, gpL, gpR);
+  if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) {
     atomicAdd(&st[ST_FALLBACK], 1);
 #pragma unroll 1
-    for (int v = 0; v < NV; ++v) cs[v] = recon_var<DIM, CURVI>(U, g, ph, c, i, j, k, v, 0.0, gpL, gpR);
-    if (!cell_states_physical<DIM>(g, ph, c, i, j, k, gpL, gpR)) atomicOr(&st[ST_NONPHYS], 1);
+    for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI>(avg, avh, avl, der, g, ph, c, i, j, k, v, T(0), gpL, gpR);
+    if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) atomicOr(&st[ST_NONPHYS], 1);
   }
   if (record_chi)
-    for (int v = 0; v < NV; ++v) chi[(long)v * g.ncell + c] = cs[v];
+    for (int v = 0; v < NV; ++v) chi[(long)v * g.ncell + c] = double(cs[v]);
 }
 
-template <int DIM, bool CURVI>
-__global__ void __launch_bounds__(128) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
-                                              const double* __restrict__ gpL, const double* __restrict__ gpR,
-                                              double* __restrict__ flux, int* __restrict__ st) {
+template <typename T, int DIM, bool CURVI>
+__global__ void __launch_bounds__(128, min_blocks<T>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
+                                              const T* __restrict__ gpL, const T* __restrict__ gpR,
+                                              T* __restrict__ flux, int* __restrict__ st) {
   long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long N = g.ncell;
   if (t >= (long)DIM * Sz<DIM>::GPF * N) return;
   long c = t % N;
   int r = (int)(t / N);
   int k = r % Sz<DIM>::GPF, ax = r / Sz<DIM>::GPF;
-  double dt = dts->dt;
+  const double dt = dts->dt;
   if (!(dt > 0.0)) return;
-  if (!flux_point<DIM, CURVI>(g, ph, dt, ax, k, c, gpL, gpR, flux)) atomicOr(&st[ST_FLUX], 1);
+  if (!flux_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c, gpL, gpR, flux)) atomicOr(&st[ST_FLUX], 1);
 }
 
-template <int DIM, bool CURVI>
+template <typename T, int DIM, bool CURVI>
 __global__ void __launch_bounds__(128) k_update(DevGeo g, const DtState* __restrict__ dts, int stage,
-                                                const double* __restrict__ Uin, const double* __restrict__ flux,
-                                                double* __restrict__ stash, double* __restrict__ Uout) {
-  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
-  double dt = dts->dt;
+                                                const double* __restrict__ avg_in, const T* __restrict__ flux,
+                                                double* __restrict__ stash_avg, T* __restrict__ stash_der,
+                                                double* __restrict__ avg_out, T* __restrict__ der_out,
+                                                float* __restrict__ avh_out, float* __restrict__ avl_out) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long N = g.ncell;
+  if (t >= (long)Sz<DIM>::NV * N) return;
+  const double dt = dts->dt;
   if (!(dt > 0.0)) return;
+  const long c = t % N;
+  const int v = (int)(t / N);
   int i, j, k;
   cell_ijk(g, c, i, j, k);
-  update_cell<DIM, CURVI>(g, dt, stage, c, i, j, k, Uin, flux, stash, Uout);
+  update_var<T, DIM, CURVI>(g, dt, stage, c, i, j, k, v, avg_in, flux, stash_avg, stash_der, avg_out, der_out,
+                            avh_out, avl_out);
+}
+
+/* public FP64 layout <-> FP64 averages + derivative fields in T */
+template <typename T>
+__global__ void k_split(const double* __restrict__ full, double* __restrict__ avg, float* __restrict__ avh,
+                        float* __restrict__ avl, T* __restrict__ der, long navg, long nder) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t < navg) {
+    const double x = full[t];
+    avg[t] = x;
+    const float h = float(x);
+    avh[t] = h;
+    avl[t] = float(x - double(h));
+  } else if (t < navg + nder) {
+    der[t - navg] = T(full[t]);
+  }
+}
+/* the same split restricted to cells [cell0, cell0 + ncells) of every field */
+template <typename T>
+__global__ void k_split_cells(const double* __restrict__ full, double* __restrict__ avg, float* __restrict__ avh,
+                              float* __restrict__ avl, T* __restrict__ der, long N, int nv, int nf, long cell0,
+                              long ncells) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= (long)nf * nv * ncells) return;
+  const long cl = t % ncells, fv = t / ncells;
+  const long idx = fv * N + cell0 + cl;
+  const long navg = (long)nv * N;
+  if (idx < navg) {
+    const double x = full[idx];
+    avg[idx] = x;
+    const float h = float(x);
+    avh[idx] = h;
+    avl[idx] = float(x - double(h));
+  } else {
+    der[idx - navg] = T(full[idx]);
+  }
+}
+template <typename T>
+__global__ void k_join(const double* __restrict__ avg, const T* __restrict__ der, double* __restrict__ full, long navg,
+                       long nder) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t < navg) full[t] = avg[t];
+  else if (t < navg + nder) full[t] = double(der[t - navg]);
 }
 
 /* max over cells of the rate; positive doubles order like their bit patterns */

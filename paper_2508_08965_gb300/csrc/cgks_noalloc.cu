@@ -115,6 +115,9 @@ extern "C" cgks_status cgks_compute_dt_noalloc(const cgks_mesh_desc* d, const do
   for (int a = 0; a < 3; ++a) {
     g.n[a] = a < d->dim ? d->n[a] : 1;
     g.h[a] = a < d->dim ? (d->hi[a] - d->lo[a]) / d->n[a] : 1.0;
+    g.ih[a] = 1.0 / g.h[a];
+    g.hf[a] = (float)g.h[a];
+    g.ihf[a] = (float)g.ih[a];
   }
   g.ncell = ncell;
   g.curvi = 0;

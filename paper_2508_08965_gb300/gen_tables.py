@@ -500,15 +500,16 @@ def symmetry_plan(dim):
 
 
 def _lit(x):
-    return repr(float(x))
+    return "T(%s)" % repr(float(x))
 
 
 def emit_recon_code(path):
     out = ["/* Generated by paper_2508_08965_gb300/gen_tables.py -- do not edit.",
            "   Straight-line CGKS-5 reconstruction on the reference cell using its",
-           "   reflection symmetry (see gen_tables.py).  Ld is a loader with",
-           "   q0(), avg(ox,oy,oz), grefv(ox,oy,oz,g[dim]) (neighbour gradient in the",
-           "   target's reference frame) and line(s) (own reference line difference). */",
+           "   reflection symmetry (see gen_tables.py), generic in the real type T.",
+           "   Ld is a loader with q0(), avg(ox,oy,oz), grefv(ox,oy,oz,g[dim])",
+           "   (neighbour gradient in the target's reference frame) and line(s) (own",
+           "   reference line difference); averages may be given relative to q0. */",
            "#pragma once", ""]
     for dim in (2, 3):
         t = build(dim)
@@ -541,10 +542,10 @@ def emit_recon_code(path):
             key = tuple(sorted({nb_offsets(it)[0] for it in o[1]}))
             groups.setdefault(key, []).append(o)
         fn = []
-        fn.append("template <class Ld>")
-        fn.append("CGKS_HD void gen_coeffs_%dd(const Ld& ld, double* __restrict__ a) {" % dim)
+        fn.append("template <typename T, class Ld>")
+        fn.append("CGKS_HD void gen_coeffs_%dd(const Ld& ld, T* __restrict__ a) {" % dim)
         fn.append("#pragma unroll")
-        fn.append("  for (int b = 0; b < %d; ++b) a[b] = 0.0;" % nb)
+        fn.append("  for (int b = 0; b < %d; ++b) a[b] = T(0);" % nb)
 
         def off3(o):
             o = list(o) + [0] * (3 - dim)
@@ -557,8 +558,8 @@ def emit_recon_code(path):
                 if all(x == 0 for x in o):
                     continue
                 nm = "n" + "".join("m" if x < 0 else ("p" if x > 0 else "z") for x in o)
-                fn.append("    const double %sQ = ld.avg(%s);" % (nm, off3(o)))
-                fn.append("    double %sG[%d];" % (nm, dim))
+                fn.append("    const T %sQ = ld.avg(%s);" % (nm, off3(o)))
+                fn.append("    T %sG[%d];" % (nm, dim))
                 fn.append("    ld.grefv(%s, %sG);" % (off3(o), nm))
                 var[o] = nm
 
@@ -584,14 +585,14 @@ def emit_recon_code(path):
             for rep, orb, stab, feats in orbs:
                 for c, coef in feats.items():
                     expr = " ".join("%s%s" % ("+" if cf > 0 else "-", item_expr(it)) if abs(cf) == 1 else
-                                    "%s%d.0*%s" % ("+" if cf > 0 else "-", abs(cf), item_expr(it))
+                                    "%sT(%d)*%s" % ("+" if cf > 0 else "-", abs(cf), item_expr(it))
                                     for it, cf in coef.items()).lstrip("+")
                     rows = [b for b in range(nb) if cls[b] == c and M[b][pos[rep]] != 0.0]
                     if not rows:
                         continue
-                    fn.append("    { const double f = %s;" % expr)
+                    fn.append("    { const T f = %s;" % expr)
                     for b in rows:
-                        fn.append("      a[%d] = fma(%s, f, a[%d]);" % (b, _lit(M[b][pos[rep]] / stab), b))
+                        fn.append("      a[%d] = cg_fma(%s, f, a[%d]);" % (b, _lit(M[b][pos[rep]] / stab), b))
                     fn.append("    }")
             fn.append("  }")
         fn.append("}")
@@ -600,8 +601,9 @@ def emit_recon_code(path):
         GH = [[float(x) for x in row] for row in t["GH"]]
         GL = [[float(x) for x in row] for row in t["GL"]]
         for name, Gm in (("ish", GH), ("isl", GL)):
-            fn.append("CGKS_HD double gen_%s_%dd(const double* __restrict__ a) {" % (name, dim))
-            fn.append("  double s = 0.0;")
+            fn.append("template <typename T>")
+            fn.append("CGKS_HD T gen_%s_%dd(const T* __restrict__ a) {" % (name, dim))
+            fn.append("  T s = T(0);")
             for i in range(nb):
                 terms = []
                 if Gm[i][i] != 0.0:
@@ -612,20 +614,21 @@ def emit_recon_code(path):
                         terms.append((_lit(2.0 * Gm[i][j]), j))
                 if not terms:
                     continue
-                fn.append("  { double r = 0.0;")
+                fn.append("  { T r = T(0);")
                 for cst, j in terms:
-                    fn.append("    r = fma(%s, a[%d], r);" % (cst, j))
-                fn.append("    s = fma(a[%d], r, s); }" % i)
+                    fn.append("    r = cg_fma(%s, a[%d], r);" % (cst, j))
+                fn.append("    s = cg_fma(a[%d], r, s); }" % i)
             fn.append("  return s;")
             fn.append("}")
             fn.append("")
         # mean of the P4 correction: sum_b a_b mean_b
-        fn.append("CGKS_HD double gen_mean_%dd(const double* __restrict__ a) {" % dim)
-        fn.append("  double s = 0.0;")
+        fn.append("template <typename T>")
+        fn.append("CGKS_HD T gen_mean_%dd(const T* __restrict__ a) {" % dim)
+        fn.append("  T s = T(0);")
         for b, e in enumerate(ex):
             mb = mean_basis(e)
             if mb != 0:
-                fn.append("  s = fma(%s, a[%d], s);" % (_lit(float(mb)), b))
+                fn.append("  s = cg_fma(%s, a[%d], s);" % (_lit(float(mb)), b))
         fn.append("  return s;")
         fn.append("}")
         fn.append("")
@@ -640,8 +643,9 @@ def emit_recon_code(path):
             for a in ta:
                 x0[a] = G
             fn.append("/* axis %d: out_v[i], out_g[i][k] for the %d Gauss points i = side*%d + k */" % (ax, npts, g))
-            fn.append("CGKS_HD void gen_gp_%dd_ax%d(const double* __restrict__ a, double* __restrict__ out_v, "
-                      "double (* __restrict__ out_g)[%d]) {" % (dim, ax, dim))
+            fn.append("template <typename T>")
+            fn.append("CGKS_HD void gen_gp_%dd_ax%d(const T* __restrict__ a, T* __restrict__ out_v, "
+                      "T (* __restrict__ out_g)[%d]) {" % (dim, ax, dim))
             C = _classes(dim)
             # class sums of values and of each derivative
             for ci, c in enumerate(C):
@@ -653,12 +657,12 @@ def emit_recon_code(path):
                     for i2 in range(dim):
                         v = v * ipow(x0[i2], e[i2]) * Fr(1, fact(e[i2]))
                     terms.append((v.to_float(), b))
-                fn.append("  double S%d = 0.0;" % ci)
+                fn.append("  T S%d = T(0);" % ci)
                 for v, b in terms:
                     if v != 0.0:
-                        fn.append("  S%d = fma(%s, a[%d], S%d);" % (ci, _lit(v), b, ci))
+                        fn.append("  S%d = cg_fma(%s, a[%d], S%d);" % (ci, _lit(v), b, ci))
                 for k in range(dim):
-                    fn.append("  double D%d_%d = 0.0;" % (ci, k))
+                    fn.append("  T D%d_%d = T(0);" % (ci, k))
                     for b, e in enumerate(ex):
                         if cls[b] != c or e[k] == 0:
                             continue
@@ -666,7 +670,7 @@ def emit_recon_code(path):
                         for i2 in range(dim):
                             ee = e[i2] - (1 if i2 == k else 0)
                             v = v * ipow(x0[i2], ee) * Fr(1, fact(ee))
-                        fn.append("  D%d_%d = fma(%s, a[%d], D%d_%d);" % (ci, k, _lit(v.to_float()), b, ci, k))
+                        fn.append("  D%d_%d = cg_fma(%s, a[%d], D%d_%d);" % (ci, k, _lit(v.to_float()), b, ci, k))
             # each Gauss point is R_S x0 for the set S of negated axes
             for side in (0, 1):
                 for k in range(g):

@@ -1,0 +1,89 @@
+"""The FP32 form (precision 1): reconstruction, interface flux, weights and
+derivative fields in FP32; cell averages, their S2O4 accumulation and the
+metrics in FP64.  Its error is stated against the FP64 CPU oracle on the
+Taylor-Green vortex (BASELINE bound: density L2 <= 1e-5); conservation holds
+to FP64 rounding because the averages accumulate in FP64."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_08965_gb300 as p
+    p.lib()
+    return p
+
+
+TGV = dict(mu=1 / 1600, prandtl=0.72, tau_mode=2)
+
+
+def tgv(x, y, z):
+    return synth.taylor_green_3d(x, y, z)
+
+
+@pytest.mark.parametrize("steps", [1, 20])
+def test_fp32_tgv_error_against_oracle(orc, cg, steps):
+    n = (16, 16, 16)
+    o = orc.Oracle(3, n, lo=(0, 0, 0), hi=(2 * math.pi,) * 3, **TGV)
+    o.init(tgv)
+    s0 = o.get_state()
+    m = cg.Mesh(3, n, lo=(0, 0, 0), hi=(2 * math.pi,) * 3, precision=1, **TGV)
+    m.set_state(s0)
+    o.step(steps)
+    m.step(steps)
+    sg, _ = m.get_state()
+    so = o.get_state()
+    e = sg[0, 0] - so[0, 0]
+    l2 = math.sqrt(np.mean(e * e))
+    ke = lambda s: np.mean(0.5 * (s[0, 1] ** 2 + s[0, 2] ** 2 + s[0, 3] ** 2) / s[0, 0])
+    dke = abs(ke(sg) - ke(so)) / ke(so)
+    print("fp32 TGV 16^3 after %d steps: density L2 %.3e, kinetic energy rel %.3e" % (steps, l2, dke))
+    assert l2 <= 1e-6
+    assert dke <= 1e-5
+    m.close()
+
+
+def test_fp32_conserves_in_fp64(cg):
+    n = (16, 16, 16)
+    m = cg.Mesh(3, n, lo=(0, 0, 0), hi=(2 * math.pi,) * 3, precision=1, **TGV)
+    m.init(tgv)
+    s0, _ = m.get_state()
+    m.step(20)
+    s1, _ = m.get_state()
+    sums0 = s0[0].sum(axis=(1, 2, 3))
+    sums1 = s1[0].sum(axis=(1, 2, 3))
+    mag = np.abs(s0[0]).sum(axis=(1, 2, 3))
+    mag[1:4] = mag[1:4].max()  # momentum components share one scale (rho W starts at zero)
+    assert np.all(np.abs(sums1 - sums0) <= 1e-13 * mag)
+    m.close()
+
+
+def test_fp32_vortex_and_curvilinear_close_to_fp64(cg):
+    from parity import class_scaled_diff
+    for dim, n, lo, hi, fn, nodes, kw in [
+        (2, (48, 40), (0, 0), (10, 10), lambda x, y: synth.isentropic_vortex_2d(x, y), None, {}),
+        (3, (12, 12, 12), (0, 0, 0), (2 * math.pi,) * 3, tgv, synth.perturbed_nodes_3d((12, 12, 12)), TGV),
+    ]:
+        a = cg.Mesh(dim, n, lo=lo, hi=hi, nodes=nodes, precision=0, **kw)
+        b = cg.Mesh(dim, n, lo=lo, hi=hi, nodes=nodes, precision=1, **kw)
+        a.init(fn)
+        s0, _ = a.get_state()
+        b.set_state(s0)
+        a.step(10)
+        b.step(10)
+        sa, _ = a.get_state()
+        sb, _ = b.get_state()
+        h = min((hi[q] - lo[q]) / n[q] for q in range(dim))
+        assert class_scaled_diff(sb, sa, h) <= 1e-5
+        assert np.abs(sb[0, 0] - sa[0, 0]).max() <= 1e-5
+        a.close()
+        b.close()
