@@ -739,6 +739,7 @@ struct orc_ctx {
   /* work */
   double* gpv;    /* per cell: ngp x nv x (1+dim) physical values/gradients */
   double* fx;     /* per face point: 6 nv */
+  double* fxlo;   /* low boundary faces of non-periodic axes */
   double* L1; double* Lt1; double* D1; double* L2; double* Lt2; double* Dt;
   int err;
 };
@@ -880,11 +881,20 @@ static void build_geo(orc_ctx* c) {
 /* ------------------------------------------------------------------------ */
 /* 6. Context, state and initial data.                                      */
 /* ------------------------------------------------------------------------ */
+/* boundary kinds of orc_desc.bc */
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_SLIP = 2, BC_NOSLIP = 3 };
+
 orc_ctx* orc_create(const orc_desc* d) {
   const ref_t* R = get_ref(d->dim);
   if (!R) return NULL;
+  for (int f = 0; f < 2 * d->dim; ++f) {
+    if (d->bc[f] < BC_PERIODIC || d->bc[f] > BC_NOSLIP) return NULL;
+    if (d->bc[f] >= BC_SLIP && d->nodes) return NULL; /* a mirror is a reflection only on a box */
+    if ((d->bc[f] == BC_PERIODIC) != (d->bc[f ^ 1] == BC_PERIODIC)) return NULL;
+  }
   orc_ctx* c = calloc(1, sizeof(orc_ctx));
   c->d = *d;
+  if (d->dim == 2) c->d.bc[4] = c->d.bc[5] = BC_PERIODIC;
   c->R = R;
   c->dim = d->dim;
   c->nv = R->nv;
@@ -904,6 +914,7 @@ orc_ctx* orc_create(const orc_desc* d) {
   c->chi = calloc((size_t)c->nv * c->ncell, sizeof(double));
   c->gpv = calloc((size_t)c->ncell * R->ngp * c->nv * (1 + c->dim), sizeof(double));
   c->fx = calloc((size_t)c->ncell * c->dim * R->gpf * 6 * c->nv, sizeof(double));
+  c->fxlo = calloc((size_t)c->ncell * c->dim * R->gpf * 6 * c->nv, sizeof(double));
   long nd = (long)(c->nf - 1) * c->nv * c->ncell;
   c->L1 = calloc((size_t)c->nv * c->ncell, sizeof(double));
   c->Lt1 = calloc((size_t)c->nv * c->ncell, sizeof(double));
@@ -917,7 +928,7 @@ orc_ctx* orc_create(const orc_desc* d) {
 
 void orc_destroy(orc_ctx* c) {
   if (!c) return;
-  free(c->nodes); free(c->geo); free(c->U); free(c->chi); free(c->gpv); free(c->fx);
+  free(c->nodes); free(c->geo); free(c->U); free(c->chi); free(c->gpv); free(c->fx); free(c->fxlo);
   free(c->L1); free(c->Lt1); free(c->L2); free(c->Lt2); free(c->D1); free(c->Dt);
   free(c);
 }
@@ -1092,12 +1103,51 @@ double orc_compute_dt(orc_ctx* c) {
 /* ------------------------------------------------------------------------ */
 /* 8. One stage: reconstruction, interface solution, accumulation.          */
 /* ------------------------------------------------------------------------ */
+
+/* Boundaries (reading of the ghost-cell treatment): beyond a periodic face
+   the index wraps; beyond an outflow face it is clamped (the ghost copies the
+   boundary cell); beyond a wall it is mirrored and the ghost carries the
+   mirror image of the cell's data: reflecting axis a negates the normal
+   momentum (slip) or every momentum component (no-slip), and negates
+   derivatives along a. */
+static long nbr_bc(const orc_ctx* c, long id, const int* o, int* mirror, int* noslip) {
+  int ii[3] = {(int)(id % c->n[0]), (int)((id / c->n[0]) % c->n[1]),
+               c->dim == 3 ? (int)(id / ((long)c->n[0] * c->n[1])) : 0};
+  *mirror = 0;
+  *noslip = 0;
+  for (int a = 0; a < c->dim; ++a) {
+    int x = ii[a] + o[a];
+    if (x < 0 || x >= c->n[a]) {
+      int bc = c->d.bc[2 * a + (x < 0 ? 0 : 1)];
+      if (bc == BC_PERIODIC) x = (x + c->n[a]) % c->n[a];
+      else if (bc == BC_OUTFLOW) x = x < 0 ? 0 : c->n[a] - 1;
+      else {
+        x = x < 0 ? -1 - x : 2 * c->n[a] - 1 - x;
+        *mirror |= 1 << a;
+        if (bc == BC_NOSLIP) *noslip |= 1 << a;
+      }
+    }
+    ii[a] = x;
+  }
+  return cidx(c, ii[0], ii[1], ii[2]);
+}
+
 static long nbr(const orc_ctx* c, long id, const int* o) {
-  int i = id % c->n[0], j = (id / c->n[0]) % c->n[1], k = c->dim == 3 ? id / ((long)c->n[0] * c->n[1]) : 0;
-  i = (i + o[0] + c->n[0]) % c->n[0];
-  j = (j + o[1] + c->n[1]) % c->n[1];
-  if (c->dim == 3) k = (k + o[2] + c->n[2]) % c->n[2];
-  return cidx(c, i, j, k);
+  int m, ns;
+  return nbr_bc(c, id, o, &m, &ns);
+}
+
+/* sign of variable v (and of its derivative along axis k, k < 0: the value)
+   in the mirror image across the axes in `mirror` */
+static double mirror_sign(int dim, int v, int k, int mirror, int noslip) {
+  double s = 1.0;
+  for (int a = 0; a < dim; ++a) {
+    if (!((mirror >> a) & 1)) continue;
+    int mom = v >= 1 && v <= dim;
+    if (mom && (((noslip >> a) & 1) || v == 1 + a)) s = -s;
+    if (k == a) s = -s;
+  }
+  return s;
 }
 
 /* reconstruct all variables of one cell at its face Gauss points, physical
@@ -1112,22 +1162,24 @@ static void recon_cell(orc_ctx* c, const double* S, long id, int record_chi) {
     double* d = dat[v];
     d[0] = S[(0 * nv + v) * N + id];
     for (int m = 0; m < 2 * dim; ++m) {
-      long nb = nbr(c, id, R->face_off[m]);
-      d[R->d_face + m] = S[(0 * nv + v) * N + nb];
+      int mi, ns;
+      long nb = nbr_bc(c, id, R->face_off[m], &mi, &ns);
+      d[R->d_face + m] = mirror_sign(dim, v, -1, mi, ns) * S[(0 * nv + v) * N + nb];
       /* reference-frame gradient J0^T (grad Q)_{1,m} with the target's J0 */
       for (int k = 0; k < dim; ++k) {
         double s = 0;
-        for (int r = 0; r < dim; ++r) s += G->J0[r][k] * S[((1 + r) * nv + v) * N + nb];
+        for (int r = 0; r < dim; ++r) s += G->J0[r][k] * mirror_sign(dim, v, r, mi, ns) * S[((1 + r) * nv + v) * N + nb];
         d[R->d_fgrad + m * dim + k] = s;
       }
     }
     for (int n = 0; n < R->ne; ++n) {
-      long nb = nbr(c, id, R->edge_off[n]);
-      d[R->d_edge + n] = S[(0 * nv + v) * N + nb];
+      int mi, ns;
+      long nb = nbr_bc(c, id, R->edge_off[n], &mi, &ns);
+      d[R->d_edge + n] = mirror_sign(dim, v, -1, mi, ns) * S[(0 * nv + v) * N + nb];
       double g[3];
       for (int k = 0; k < dim; ++k) {
         double s = 0;
-        for (int r = 0; r < dim; ++r) s += G->J0[r][k] * S[((1 + r) * nv + v) * N + nb];
+        for (int r = 0; r < dim; ++r) s += G->J0[r][k] * mirror_sign(dim, v, r, mi, ns) * S[((1 + r) * nv + v) * N + nb];
         g[k] = s;
       }
       for (int t = 0; t < R->ntau; ++t) {
@@ -1223,6 +1275,19 @@ static void rotate_out(int dim, double Rm[3][3], double* F) {
   for (int a = 0; a < dim; ++a) F[1 + a] = m[a];
 }
 
+/* A wall face (adiabatic; the paper's non-slip adiabatic wall and its slip
+   counterpart) lets no mass and no energy through, and the gas on it moves
+   along the wall (slip) or rests (no-slip): the flux from the mirrored states
+   keeps its momentum part, its mass and energy parts are zero, and the
+   interface values carry zero normal (slip) or zero total (no-slip) momentum. */
+static void wall_face(int dim, int ax, int bc, int nv, double* out) {
+  out[0] = out[nv] = 0.0;
+  out[dim + 1] = out[nv + dim + 1] = 0.0;
+  for (int p = 2; p < 6; ++p)
+    for (int i = 0; i < dim; ++i)
+      if (bc == BC_NOSLIP || i == ax) out[p * nv + 1 + i] = 0.0;
+}
+
 static int stage(orc_ctx* c, const double* S, double dt, double* Lout, double* Ltout, double* Dn, double* Dtn,
                  int record_chi) {
   const ref_t* R = c->R;
@@ -1232,25 +1297,49 @@ static int stage(orc_ctx* c, const double* S, double dt, double* Lout, double* L
   int err = 0;
 #pragma omp parallel for schedule(dynamic, 64)
   for (long id = 0; id < N; ++id) recon_cell(c, S, id, record_chi);
-  /* interface solutions: face (axis, cell L) between L and its +axis neighbour */
+  /* interface solutions: face (axis, cell L) between L and its +axis
+     neighbour; at a non-periodic face the missing side is the mirror image
+     (wall) or a copy (outflow) of the interior side's Gauss-point state */
 #pragma omp parallel for schedule(dynamic, 64) reduction(| : err)
   for (long id = 0; id < N; ++id) {
+    int ii[3] = {(int)(id % c->n[0]), (int)((id / c->n[0]) % c->n[1]),
+                 dim == 3 ? (int)(id / ((long)c->n[0] * c->n[1])) : 0};
     for (int ax = 0; ax < dim; ++ax) {
       int o[3] = {0, 0, 0};
       o[ax] = 1;
       long rid = nbr(c, id, o);
+      const int hi_bnd = ii[ax] == c->n[ax] - 1 && c->d.bc[2 * ax + 1] != BC_PERIODIC;
+      const int lo_bnd = ii[ax] == 0 && c->d.bc[2 * ax] != BC_PERIODIC;
       for (int q = 0; q < gpf; ++q) {
         int gl = (2 * ax + 1) * gpf + q, gr = (2 * ax) * gpf + q;
-        const double* A = c->geo[id].area[gl];
-        double Rm[3][3];
-        frame(dim, A, c->geo[id].tang[gl], Rm);
-        double WL[MAXV], dWL[3 * MAXV], WR[MAXV], dWR[3 * MAXV];
-        rotate_in(dim, Rm, c->gpv + id * stride + gl * nv * (1 + dim), nv, WL, dWL);
-        rotate_in(dim, Rm, c->gpv + rid * stride + gr * nv * (1 + dim), nv, WR, dWR);
-        double* out = c->fx + ((id * dim + ax) * gpf + q) * 6 * nv;
-        int st = gks_point(dim, c->d.gamma, c->d.mu, c->d.prandtl, c->d.tau_mode, dt, WL, dWL, WR, dWR, out);
-        if (st) err |= 1;
-        for (int p = 0; p < 6; ++p) rotate_out(dim, Rm, out + p * nv);
+        for (int pass = 0; pass < 1 + lo_bnd; ++pass) {
+          /* pass 0: the high face of this cell; pass 1: its low boundary face */
+          const int gown = pass == 0 ? gl : gr;
+          const double* A = c->geo[id].area[gown];
+          double Rm[3][3];
+          frame(dim, A, c->geo[id].tang[gown], Rm);
+          double st_in[MAXV * 4], st_bc[MAXV * 4];
+          const double* own = c->gpv + id * stride + gown * nv * (1 + dim);
+          const int bnd = pass == 0 ? hi_bnd : 1;
+          const int bc = c->d.bc[2 * ax + (pass == 0 ? 1 : 0)];
+          if (bnd) {
+            int mi = bc == BC_OUTFLOW ? 0 : 1 << ax, ns = bc == BC_NOSLIP ? 1 << ax : 0;
+            for (int v = 0; v < nv; ++v)
+              for (int k = -1; k < dim; ++k)
+                st_bc[v * (1 + dim) + 1 + k] = mirror_sign(dim, v, k, mi, ns) * own[v * (1 + dim) + 1 + k];
+          }
+          const double* sl = pass == 0 ? own : st_bc;
+          const double* sr = pass == 0 ? (bnd ? st_bc : c->gpv + rid * stride + gr * nv * (1 + dim)) : own;
+          double WL[MAXV], dWL[3 * MAXV], WR[MAXV], dWR[3 * MAXV];
+          rotate_in(dim, Rm, sl, nv, WL, dWL);
+          rotate_in(dim, Rm, sr, nv, WR, dWR);
+          double* out = pass == 0 ? c->fx + ((id * dim + ax) * gpf + q) * 6 * nv
+                                  : c->fxlo + ((id * dim + ax) * gpf + q) * 6 * nv;
+          int st = gks_point(dim, c->d.gamma, c->d.mu, c->d.prandtl, c->d.tau_mode, dt, WL, dWL, WR, dWR, out);
+          if (st) err |= 1;
+          for (int p = 0; p < 6; ++p) rotate_out(dim, Rm, out + p * nv);
+          if (bnd && bc >= BC_SLIP) wall_face(dim, ax, bc, nv, out);
+        }
       }
     }
   }
@@ -1263,10 +1352,14 @@ static int stage(orc_ctx* c, const double* S, double dt, double* Lout, double* L
     const cellgeo_t* G = &c->geo[id];
     double Lc[MAXV] = {0}, Ltc[MAXV] = {0};
     double qn[MAXGP][MAXV], qt[MAXGP][MAXV];
+    const int ii0 = (int)(id % c->n[0]), ii1 = (int)((id / c->n[0]) % c->n[1]);
+    const int ii2 = dim == 3 ? (int)(id / ((long)c->n[0] * c->n[1])) : 0;
+    const int iis[3] = {ii0, ii1, ii2};
     for (int ax = 0; ax < dim; ++ax) {
       int o[3] = {0, 0, 0};
       o[ax] = -1;
       long lid = nbr(c, id, o);
+      const int lo_bnd = iis[ax] == 0 && c->d.bc[2 * ax] != BC_PERIODIC;
       for (int q = 0; q < gpf; ++q) {
         /* high face: this cell is the left side */
         const double* fh = c->fx + ((id * dim + ax) * gpf + q) * 6 * nv;
@@ -1274,9 +1367,11 @@ static int stage(orc_ctx* c, const double* S, double dt, double* Lout, double* L
         double sh = 0;
         for (int a = 0; a < dim; ++a) sh += Ah[a] * Ah[a];
         sh = sqrt(sh);
-        /* low face: this cell is the right side of the face owned by lid */
-        const double* fl = c->fx + ((lid * dim + ax) * gpf + q) * 6 * nv;
-        const double* Al = c->geo[lid].area[(2 * ax + 1) * gpf + q];
+        /* low face: this cell is the right side of the face owned by lid, or of
+           its own boundary face */
+        const double* fl = lo_bnd ? c->fxlo + ((id * dim + ax) * gpf + q) * 6 * nv
+                                  : c->fx + ((lid * dim + ax) * gpf + q) * 6 * nv;
+        const double* Al = lo_bnd ? G->area[(2 * ax) * gpf + q] : c->geo[lid].area[(2 * ax + 1) * gpf + q];
         double sl = 0;
         for (int a = 0; a < dim; ++a) sl += Al[a] * Al[a];
         sl = sqrt(sl);

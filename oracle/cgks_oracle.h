@@ -35,6 +35,8 @@ typedef struct {
   double dt_fixed;    /* > 0: use this time step instead of the CFL rule */
   int linear;         /* 1: force chi = 1 (linear CGKS-5) */
   double c_chi;       /* path-function constant C in chi = tanh(C alpha)/tanh(C) */
+  int bc[6];          /* per domain face -x,+x,-y,+y,-z,+z: 0 periodic, 1 outflow,
+                         2 slip wall, 3 no-slip wall (walls: axis-aligned meshes) */
 } orc_desc;
 
 typedef struct orc_ctx orc_ctx;

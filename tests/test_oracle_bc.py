@@ -1,0 +1,177 @@
+"""Boundary pins of the oracle (not GPU).
+
+B1  Slip wall = mirror symmetry: a walled box evolves exactly like the upper
+    half of the periodic box of twice the length holding the state and its
+    mirror image (reflection symmetry of the Euler equations), in 2-D and 3-D,
+    linear and nonlinear.
+B2  No-slip wall, viscous: a shear wave between two walls decays at the
+    Stokes rate exp(-nu pi^2 t).
+B3  A closed box of walls conserves mass and energy.
+B4  Outflow: a uniform moving state stays uniform; Sod's problem in a box with
+    outflow ends against the exact Riemann solution.
+"""
+import numpy as np
+import pytest
+
+import mirror
+import riemann_exact
+from parity import class_scaled_diff
+
+SLIP, NOSLIP, OUTFLOW = 2, 3, 1
+
+
+def _smooth2(x, y):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x + 0.3) * np.cos(2 * np.pi * y)
+    u = 0.3 * np.sin(np.pi * x) + 0.1 * np.cos(2 * np.pi * y + 0.7) * x
+    v = 0.2 * np.cos(2 * np.pi * y) + 0.1 * x
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * x - 0.4)
+    return [rho, u, v, p]
+
+
+def _smooth3(x, y, z):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x + 0.3) * np.cos(2 * np.pi * y) + 0.1 * z
+    u = 0.2 * np.cos(2 * np.pi * y) + 0.1 * z
+    v = 0.2 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * z + 0.2)
+    w = 0.3 * np.sin(np.pi * z) * (1.0 + 0.2 * np.cos(2 * np.pi * x))
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * z - 0.4) + 0.05 * np.sin(2 * np.pi * y)
+    return [rho, u, v, w, p]
+
+
+def _wall_vs_doubled(orc, dim, n, a, field, noslip=False, steps=3, **kw):
+    lo = [0.0] * dim
+    hi = [1.0] * dim
+    bc = [0] * 6
+    bc[2 * a] = bc[2 * a + 1] = NOSLIP if noslip else SLIP
+    w = orc.Oracle(dim, n, lo=lo, hi=hi, bc=bc, **kw)
+    w.init(field)
+    n2 = list(n)
+    n2[a] *= 2
+    lo2 = list(lo)
+    lo2[a] = -1.0
+    p = orc.Oracle(dim, n2, lo=lo2, hi=hi, **kw)
+    p.set_state(mirror.extend(w.get_state(), dim, a, noslip))
+    for _ in range(steps):
+        dt = w.dt()
+        assert abs(p.dt() - dt) <= 1e-13 * dt
+        w.step_dt(dt)
+        p.step_dt(dt)
+    sw, sp = w.get_state(), p.get_state()
+    h = 1.0 / n[a]
+    up = mirror.upper_half(sp, dim, a)
+    lowm = mirror.reflect(np.take(sp, np.arange(n[a]), axis=2 + dim - 1 - a), dim, a, noslip)
+    return class_scaled_diff(sw, up, h), class_scaled_diff(lowm, sw, h)
+
+
+@pytest.mark.parametrize("linear", [True, False])
+@pytest.mark.parametrize("a", [0, 1])
+def test_slip_wall_is_mirror_symmetry_2d(orc, linear, a):
+    d_up, d_lo = _wall_vs_doubled(orc, 2, (12, 10), a, _smooth2, linear=linear)
+    assert d_up < 1e-12 and d_lo < 1e-12
+
+
+def test_slip_wall_is_mirror_symmetry_3d(orc):
+    d_up, d_lo = _wall_vs_doubled(orc, 3, (6, 5, 8), 2, _smooth3, steps=2)
+    assert d_up < 1e-12 and d_lo < 1e-12
+
+
+def test_slip_wall_shock_capturing(orc):
+    """Nonlinear weights, shock-capturing collision time and a jump next to
+    the wall still commute with the reflection."""
+    def jump(x, y):
+        rho = np.where(x < 0.3, 1.0, 0.4) + 0.05 * np.sin(2 * np.pi * y)
+        p = np.where(x < 0.3, 1.0, 0.3)
+        return [rho, 0.2 + 0 * x, 0.1 * np.cos(2 * np.pi * y), p]
+    d_up, d_lo = _wall_vs_doubled(orc, 2, (16, 6), 0, jump, tau_mode=1, steps=4)
+    assert d_up < 1e-11 and d_lo < 1e-11
+
+
+def test_noslip_wall_stokes_shear_decay(orc):
+    """A shear wave v = A sin(pi x) between no-slip walls at x = 0 and 1 decays
+    as exp(-nu pi^2 t) (Stokes; at Ma 0.1 and A = 0.05 the compressible
+    corrections are far below the tolerance).  The wall makes v vanish at
+    the walls; slip walls, which let it slide, miss the rate by about 1 %."""
+    A, mu, gamma, T = 0.05, 0.01, 1.4, 0.5
+    p0 = 1.0 / (gamma * 0.1 ** 2)
+    exact = np.exp(-mu * np.pi ** 2 * T)
+    rel = {}
+    for kind in (NOSLIP, SLIP):
+        for n in ((8, 16) if kind == NOSLIP else (8,)):
+            h = 1.0 / n
+            o = orc.Oracle(2, (n, 4), lo=(0, 0), hi=(1, 4 * h), bc=[kind, kind, 0, 0], mu=mu,
+                           tau_mode=2)
+            o.init(lambda x, y: [1 + 0 * x, 0 * x, A * np.sin(np.pi * x), p0 + 0 * x])
+            o.advance_to(T)
+            s = o.get_state()
+            xl = np.arange(n) * h
+            mode = A * (np.cos(np.pi * xl) - np.cos(np.pi * (xl + h))) / (np.pi * h)
+            v = s[0, 2, 0, :] / s[0, 0, 0, :]
+            rel[kind, n] = abs((v @ mode) / (mode @ mode) / exact - 1.0)
+    assert rel[NOSLIP, 8] < 5e-5 and rel[NOSLIP, 16] < 5e-6
+    assert rel[NOSLIP, 16] < rel[NOSLIP, 8]
+    assert rel[SLIP, 8] > 5e-3
+
+
+@pytest.mark.parametrize("kind", [SLIP, NOSLIP])
+def test_closed_box_conserves_mass_and_energy(orc, kind):
+    o = orc.Oracle(2, (12, 10), bc=[kind] * 4, mu=1e-3 if kind == NOSLIP else 0.0,
+                   tau_mode=2 if kind == NOSLIP else 0)
+    o.init(_smooth2)
+    vol = 1.0 / 120
+    s0 = o.get_state()
+    o.step(5)
+    s1 = o.get_state()
+    for v in (0, 3):
+        m0, m1 = s0[0, v].sum() * vol, s1[0, v].sum() * vol
+        assert abs(m1 - m0) <= 1e-13 * abs(m0)
+
+
+def test_closed_box_3d_noslip_conserves(orc):
+    o = orc.Oracle(3, (5, 4, 6), bc=[NOSLIP, NOSLIP, SLIP, SLIP, NOSLIP, NOSLIP], mu=1e-3,
+                   tau_mode=2, prandtl=0.72)
+    o.init(_smooth3)
+    s0 = o.get_state()
+    o.step(2)
+    s1 = o.get_state()
+    for v in (0, 4):
+        assert abs(s1[0, v].sum() - s0[0, v].sum()) <= 1e-13 * abs(s0[0, v].sum())
+
+
+def test_outflow_keeps_uniform_moving_state(orc):
+    o = orc.Oracle(2, (8, 6), bc=[OUTFLOW] * 4)
+    o.init(lambda x, y: [1.2 + 0 * x, 0.7 + 0 * x, -0.4 + 0 * x, 0.9 + 0 * x])
+    s0 = o.get_state()
+    o.step(4)
+    s1 = o.get_state()
+    assert np.abs(s1 - s0).max() < 1e-13
+
+
+def test_outflow_sod_against_exact_riemann(orc):
+    """Sod on [0, 1] with outflow at both ends: the waves reach neither end by
+    t = 0.2, so the boundary must not disturb the exact solution."""
+    L, R = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+
+    def init(x, y):
+        left = x < 0.5
+        return [np.where(left, L[0], R[0]), 0 * x, 0 * x, np.where(left, L[2], R[2])]
+
+    errs = []
+    for nx in (100, 200):
+        h = 1.0 / nx
+        o = orc.Oracle(2, (nx, 2), lo=(0, 0), hi=(1, 2 * h), tau_mode=1,
+                       bc=[OUTFLOW, OUTFLOW, 0, 0])
+        o.init(init)
+        o.advance_to(0.2)
+        s = o.get_state()
+        rho = s[0, 0, 0, :]
+        xc = (np.arange(nx) + 0.5) * h
+        ex = riemann_exact.sample(L, R, xc, 0.2, x0=0.5)
+        errs.append(np.mean(np.abs(rho - ex[0])))
+        assert abs(rho[0] - 1.0) < 1e-12 and abs(rho[-1] - 0.125) < 1e-12
+    assert errs[1] < errs[0] < 0.01
+
+
+def test_bad_boundary_codes_rejected(orc):
+    with pytest.raises(RuntimeError):
+        orc.Oracle(2, (4, 4), bc=[7, 7, 0, 0])
+    with pytest.raises(RuntimeError):
+        orc.Oracle(2, (4, 4), bc=[SLIP, 0, 0, 0])
