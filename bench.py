@@ -60,9 +60,10 @@ DRAM_BYTES_PER_UNIT_FP32 = {
 }
 
 
-# kernels launched per S2O4 step: time-step reduction (reset, rate, final),
-# two stages x (reconstruction, interface flux, update), time advance
-KERNELS_PER_STEP = 3 + 2 * 3 + 1
+# kernels launched per S2O4 step: time-step reduction (reset, FP32 screen,
+# FP64 rate of the candidates, final), two stages x (reconstruction,
+# interface flux, update), time advance
+KERNELS_PER_STEP = 4 + 2 * 3 + 1
 
 
 def mesh_kwargs(wl):

@@ -55,7 +55,24 @@ typedef enum {
   CGKS_ETOOLARGE = -8     /* problem larger than a fixed-size buffer of the library */
 } cgks_status;
 
-enum { CGKS_BC_PERIODIC = 0 };
+/* Boundary kinds, per domain face (the paper names its wall and far-field
+   conditions in the cylinder and jet tests without formulas; these are
+   ghost-cell readings).  Opposite faces are periodic together or not at all.
+   PERIODIC: the mesh wraps.
+   OUTFLOW: zero-gradient; the stencil's ghosts copy the boundary cell and the
+     boundary face sees the interior Gauss-point state on both sides.
+   SLIP_WALL / NOSLIP_WALL (uniform boxes only): ghosts are mirror images --
+     the normal momentum (no-slip: all momentum) and derivatives along the
+     normal change sign; the face solves the GKS problem against the mirror
+     image of the interior Gauss-point state, then passes no mass and no energy
+     (adiabatic) and its interface values carry no normal (no-slip: no)
+     momentum. */
+enum {
+  CGKS_BC_PERIODIC = 0,
+  CGKS_BC_OUTFLOW = 1,
+  CGKS_BC_SLIP_WALL = 2,
+  CGKS_BC_NOSLIP_WALL = 3
+};
 
 /* Mesh and physics description.  Uniform box when nodes == NULL. */
 typedef struct {
@@ -64,7 +81,9 @@ typedef struct {
   const double* nodes;  /* host, (n0+1)(n1+1)[(n2+1)] x dim node coordinates, i fastest,
                            or NULL for the box [lo, hi]; copied */
   double lo[3], hi[3];
-  int bc[6];            /* boundary kinds per face (-x,+x,-y,+y,-z,+z); periodic only */
+  int bc[6];            /* CGKS_BC_* per face (-x,+x,-y,+y,-z,+z); a code outside the
+                           list or a periodic face opposite a non-periodic one:
+                           CGKS_EINVAL; a wall with nodes != NULL: CGKS_EUNSUPPORTED */
   double gamma;         /* specific heat ratio */
   double mu;            /* dynamic viscosity; 0 = inviscid */
   double prandtl;       /* Prandtl number for the heat-flux correction (used when mu > 0) */

@@ -30,6 +30,9 @@ class MeshDesc(C.Structure):
                 ("stream", C.c_void_p)]
 
 
+# boundary kinds of MeshDesc.bc (CGKS_BC_* of include/cgks.h)
+BC_PERIODIC, BC_OUTFLOW, BC_SLIP_WALL, BC_NOSLIP_WALL = 0, 1, 2, 3
+
 EXPORTS = ["cgks_create_mesh", "cgks_destroy", "cgks_num_vars", "cgks_num_fields", "cgks_num_cells",
            "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_compute_dt", "cgks_init_points_per_cell",
            "cgks_init_points", "cgks_init_from_prims", "cgks_get_chi", "cgks_profile_enable",
@@ -89,7 +92,7 @@ class Mesh:
 
     def __init__(self, dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=1.4, mu=0.0,
                  prandtl=1.0, tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=0.0, stream=None,
-                 precision=0):
+                 precision=0, bc=None):
         torch = _torch()
         L = lib()
         d = MeshDesc()
@@ -105,6 +108,8 @@ class Mesh:
             d.nodes = self._nodes.ctypes.data_as(C.POINTER(C.c_double))
         d.gamma, d.mu, d.prandtl, d.tau_mode = gamma, mu, prandtl, tau_mode
         d.cfl, d.dt_fixed, d.linear, d.c_chi = cfl, dt_fixed, int(linear), c_chi
+        for f in range(6):
+            d.bc[f] = int(bc[f]) if bc is not None and f < len(bc) else BC_PERIODIC
         d.precision = int(precision)
         self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -5,15 +5,16 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "csrc", "cgks.cu")
-SRC_NOALLOC = os.path.join(HERE, "csrc", "cgks_noalloc.cu")
+CSRC = os.path.join(HERE, "csrc")
+# translation units, compiled in parallel and linked into one library
+SRCS = [os.path.join(CSRC, f) for f in ("cgks.cu", "cgks_stage_f64.cu", "cgks_stage_f32.cu", "cgks_noalloc.cu")]
 LIB = os.path.join(HERE, "libcgks.so")
-DEPS = [os.path.join(HERE, "csrc", f) for f in ("cgks.cu", "cgks_noalloc.cu", "cgks_device.cuh", "cgks_kernels.cuh",
-                                                "cgks_tables.h", "cgks_recon_gen.cuh")] + \
+DEPS = SRCS + [os.path.join(CSRC, f) for f in ("cgks_device.cuh", "cgks_kernels.cuh", "cgks_ctx.h", "cgks_stage.inc",
+                                               "cgks_tables.h", "cgks_recon_gen.cuh")] + \
     [os.path.join(ROOT, "include", "cgks.h")]
 
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
-              "-Xcompiler", "-fPIC", "-shared", "--fmad=true"]
+              "-Xcompiler", "-fPIC", "--fmad=true"]
 
 
 def nvcc():
@@ -26,11 +27,28 @@ def build(force=False, verbose=False):
     """Compile libcgks.so next to this file; returns its path."""
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in DEPS):
         return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + NVCC_FLAGS + ["-o", tmp, SRC, SRC_NOALLOC]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
+    tag = ".tmp%d" % os.getpid()
+    objs, procs = [], []
+    for src in SRCS:
+        obj = os.path.join(CSRC, os.path.basename(src)[:-3] + tag + ".o")
+        cmd = [nvcc()] + NVCC_FLAGS + ["-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        objs.append(obj)
+        procs.append(subprocess.Popen(cmd))
+    failed = [p.wait() for p in procs]
+    try:
+        if any(failed):
+            raise subprocess.CalledProcessError(max(failed), "nvcc")
+        tmp = LIB + tag
+        cmd = [nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.check_call(cmd)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -7,67 +7,17 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/cgks.h"
 #include "cgks_kernels.cuh"
+#include "cgks_ctx.h"
 
 using namespace cgks;
-
-namespace {
-
-enum KernelId { KID_RECON, KID_FLUX, KID_UPDATE, KID_DT, KID_N };
-const char* kKernelNames[KID_N] = {"recon", "flux", "update", "dt"};
-
-struct Prof {
-  bool on = false;
-  std::vector<cudaEvent_t> pool;
-  std::vector<std::pair<int, int>> rec;  /* (kernel id, event index of start) */
-  long launches[KID_N] = {0};
-  double ms[KID_N] = {0};
-};
-
-}  // namespace
-
-struct cgks_ctx {
-  int dim, nv, nf;
-  int n[3];
-  long ncell;
-  int prec;                 /* 0: FP64; 1: FP32 bulk with FP64 averages */
-  cgks_mesh_desc desc;
-  cudaStream_t stream;
-  DevGeo geo;
-  Phys ph;
-  double* d_nodes = nullptr;
-  double* d_met = nullptr;
-  double* d_lo = nullptr;
-  /* state buffers.  FP64: full public-layout arrays U (current), Us
-     (intermediate) and a stash, with the derivative fields right after the
-     averages.  FP32: FP64 averages and FP32 derivative fields in separate
-     arrays, plus a public-layout FP64 staging buffer for copies in and out. */
-  double* U = nullptr;
-  double* Us = nullptr;
-  double* stash = nullptr;
-  double* avg[2] = {nullptr, nullptr};
-  void* der[2] = {nullptr, nullptr};
-  double* savg = nullptr;
-  void* sder = nullptr;
-  void* f32 = nullptr;      /* FP32 derivative storage (3 arrays) */
-  float* avh[2] = {nullptr, nullptr}; /* FP32 form: exact hi + lo pairs of the averages */
-  float* avl[2] = {nullptr, nullptr};
-  float* pairs = nullptr;
-  void* gpL = nullptr;
-  void* gpR = nullptr;
-  void* flux = nullptr;
-  double* chi = nullptr;
-  DtState* dts = nullptr;
-  int* st = nullptr;
-  double t = 0.0;
-  std::string err;
-  Prof prof;
-};
+using namespace cgks_host;
 
 static cgks_status fail(cgks_ctx* c, cgks_status s, const char* fmt, ...) {
   if (c) {
@@ -87,27 +37,7 @@ static cgks_status fail(cgks_ctx* c, cgks_status s, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(ctx, CGKS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-static long cdiv(long a, long b) { return (a + b - 1) / b; }
 
-/* ---- profiling: CUDA events around each launch on the context stream ---- */
-static void prof_begin(cgks_ctx* ctx, int kid) {
-  if (!ctx->prof.on) return;
-  Prof& p = ctx->prof;
-  size_t need = p.rec.size() * 2 + 2;
-  while (p.pool.size() < need) {
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    p.pool.push_back(e);
-  }
-  int idx = (int)p.rec.size() * 2;
-  p.rec.push_back({kid, idx});
-  cudaEventRecord(p.pool[idx], ctx->stream);
-}
-static void prof_end(cgks_ctx* ctx) {
-  if (!ctx->prof.on) return;
-  Prof& p = ctx->prof;
-  cudaEventRecord(p.pool[p.rec.back().second + 1], ctx->stream);
-}
 static void prof_fold(cgks_ctx* ctx) {
   Prof& p = ctx->prof;
   if (p.rec.empty()) return;
@@ -121,49 +51,35 @@ static void prof_fold(cgks_ctx* ctx) {
   p.rec.clear();
 }
 
-template <typename T, int DIM, bool CURVI>
-static void launch_stage(cgks_ctx* ctx, int stage) {
-  const long N = ctx->ncell;
-  const int B = 128;
-  const int in = stage == 1 ? 0 : 1, out = stage == 1 ? 1 : 0;
-  T* gpL = (T*)ctx->gpL;
-  T* gpR = (T*)ctx->gpR;
-  T* fx = (T*)ctx->flux;
-  prof_begin(ctx, KID_RECON);
-  k_recon<T, DIM, CURVI><<<cdiv(N, B), B, 0, ctx->stream>>>(ctx->avg[in], ctx->avh[in], ctx->avl[in],
-                                                            (const T*)ctx->der[in], ctx->geo, ctx->ph, gpL, gpR,
-                                                            ctx->chi, stage == 1 ? 1 : 0, ctx->st);
-  prof_end(ctx);
-  const long nf = (long)DIM * Sz<DIM>::GPF * N;
-  prof_begin(ctx, KID_FLUX);
-  k_flux<T, DIM, CURVI><<<cdiv(nf, B), B, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, gpL, gpR, fx, ctx->st);
-  prof_end(ctx);
-  prof_begin(ctx, KID_UPDATE);
-  k_update<T, DIM, CURVI><<<cdiv((long)Sz<DIM>::NV * N, B), B, 0, ctx->stream>>>(
-      ctx->geo, ctx->dts, stage, ctx->avg[in], fx, ctx->savg, (T*)ctx->sder, ctx->avg[out], (T*)ctx->der[out],
-      ctx->avh[out], ctx->avl[out]);
-  prof_end(ctx);
-}
-
 template <int DIM>
 static cgks_status run_stage(cgks_ctx* ctx, int stage) {
   const bool cv = ctx->geo.curvi != 0;
+  const bool wall = ctx->walls;
   if (ctx->prec == 0) {
-    if (cv) launch_stage<double, DIM, true>(ctx, stage);
-    else launch_stage<double, DIM, false>(ctx, stage);
+    if (cv) launch_stage<double, DIM, true, false>(ctx, stage);
+    else if (wall) launch_stage<double, DIM, false, true>(ctx, stage);
+    else launch_stage<double, DIM, false, false>(ctx, stage);
   } else {
-    if (cv) launch_stage<float, DIM, true>(ctx, stage);
-    else launch_stage<float, DIM, false>(ctx, stage);
+    if (cv) launch_stage<float, DIM, true, false>(ctx, stage);
+    else if (wall) launch_stage<float, DIM, false, true>(ctx, stage);
+    else launch_stage<float, DIM, false, false>(ctx, stage);
   }
   CK(cudaGetLastError());
   return CGKS_OK;
 }
 
 template <int DIM>
-static cgks_status run_dt(cgks_ctx* ctx, const double* avg) {
+static cgks_status run_dt(cgks_ctx* ctx, const double* avg, const float* avh) {
   prof_begin(ctx, KID_DT);
+  const long nb = cdiv(ctx->ncell, 256);
   k_dt_reset<<<1, 1, 0, ctx->stream>>>(ctx->dts);
-  k_dt_rate<DIM><<<cdiv(ctx->ncell, 256), 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, avg, ctx->dts);
+  if (avh) {
+    k_dt_screen<DIM, float><<<nb, 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, avh, ctx->dts);
+    k_dt_rate<DIM, float><<<nb, 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, avh, avg, ctx->dts);
+  } else {
+    k_dt_screen<DIM, double><<<nb, 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, avg, ctx->dts);
+    k_dt_rate<DIM, double><<<nb, 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, avg, avg, ctx->dts);
+  }
   k_dt_final<<<1, 1, 0, ctx->stream>>>(ctx->ph, ctx->dts, ctx->st);
   prof_end(ctx);
   CK(cudaGetLastError());
@@ -173,7 +89,7 @@ static cgks_status run_dt(cgks_ctx* ctx, const double* avg) {
 template <int DIM>
 static cgks_status run_step(cgks_ctx* ctx) {
   cgks_status s;
-  if ((s = run_dt<DIM>(ctx, ctx->avg[0])) != CGKS_OK) return s;
+  if ((s = run_dt<DIM>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr)) != CGKS_OK) return s;
   if ((s = run_stage<DIM>(ctx, 1)) != CGKS_OK) return s;
   if ((s = run_stage<DIM>(ctx, 2)) != CGKS_OK) return s;
   k_time_advance<<<1, 1, 0, ctx->stream>>>(ctx->dts);
@@ -208,8 +124,11 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   for (int a = 0; a < d->dim; ++a)
     if (d->n[a] < 3) return CGKS_EINVAL;
   if (d->precision != 0 && d->precision != 1) return CGKS_EUNSUPPORTED;
-  for (int f = 0; f < 2 * d->dim; ++f)
-    if (d->bc[f] != CGKS_BC_PERIODIC) return CGKS_EUNSUPPORTED;
+  for (int f = 0; f < 2 * d->dim; ++f) {
+    if (d->bc[f] < CGKS_BC_PERIODIC || d->bc[f] > CGKS_BC_NOSLIP_WALL) return CGKS_EINVAL;
+    if ((d->bc[f] == CGKS_BC_PERIODIC) != (d->bc[f ^ 1] == CGKS_BC_PERIODIC)) return CGKS_EINVAL;
+    if (d->bc[f] >= CGKS_BC_SLIP_WALL && d->nodes) return CGKS_EUNSUPPORTED;
+  }
   if (!(d->gamma > 1.0) || d->mu < 0.0 || !(d->cfl > 0.0) || d->tau_mode < 0 || d->tau_mode > 2)
     return CGKS_EINVAL;
   ctx = new cgks_ctx();
@@ -247,6 +166,15 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   g.ncell = ctx->ncell;
   g.curvi = d->nodes ? 1 : 0;
   g.met = nullptr;
+  g.rmet = nullptr;
+  g.nplane = 0;
+  g.bcm = 0;
+  ctx->walls = false;
+  for (int f = 0; f < 2 * d->dim; ++f) {
+    g.bcm |= d->bc[f] << (2 * f);
+    if (d->bc[f] >= CGKS_BC_SLIP_WALL) ctx->walls = true;
+    if (d->bc[f] != CGKS_BC_PERIODIC) g.nplane = std::max(g.nplane, ctx->ncell / ctx->n[f / 2]);
+  }
   const long N = ctx->ncell;
   const int dim = ctx->dim, nv = ctx->nv, nf = ctx->nf;
   const int gpf = dim == 3 ? 4 : 2;
@@ -292,6 +220,7 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   ALLOC(ctx->gpL, gp_sz);
   ALLOC(ctx->gpR, gp_sz);
   ALLOC(ctx->flux, fx_sz);
+  if (g.nplane > 0) ALLOC(ctx->fxb, rsz * (size_t)dim * gpf * 6 * nv * g.nplane);
   ALLOC(ctx->chi, sizeof(double) * (size_t)nv * N);
   ALLOC(ctx->dts, sizeof(DtState));
   ALLOC(ctx->st, sizeof(int) * ST_N);
@@ -311,6 +240,12 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
     else k_metrics<2><<<cdiv(N, 128), 128, 0, ctx->stream>>>(ctx->d_nodes, g, ctx->d_met);
     CK(cudaGetLastError());
     g.met = ctx->d_met;
+    int nrm = dim == 3 ? RateMet<3>::N : RateMet<2>::N;
+    ALLOC(ctx->d_rmet, sizeof(float) * (size_t)nrm * N);
+    if (dim == 3) k_rate_metrics<3><<<cdiv(N, 128), 128, 0, ctx->stream>>>(g, ctx->d_rmet);
+    else k_rate_metrics<2><<<cdiv(N, 128), 128, 0, ctx->stream>>>(g, ctx->d_rmet);
+    CK(cudaGetLastError());
+    g.rmet = ctx->d_rmet;
   }
 #undef ALLOC
   DtState init{};
@@ -334,12 +269,14 @@ void cgks_destroy(cgks_ctx* ctx) {
   cudaFree(ctx->gpL);
   cudaFree(ctx->gpR);
   cudaFree(ctx->flux);
+  cudaFree(ctx->fxb);
   cudaFree(ctx->chi);
   cudaFree(ctx->dts);
   cudaFree(ctx->st);
   cudaFree(ctx->d_lo);
   cudaFree(ctx->d_nodes);
   cudaFree(ctx->d_met);
+  cudaFree(ctx->d_rmet);
   for (auto e : ctx->prof.pool) cudaEventDestroy(e);
   delete ctx;
 }
@@ -425,7 +362,8 @@ cgks_status cgks_compute_dt(cgks_ctx* ctx, double* dt) {
   double keep_end = h.t_end;
   h.t_end = 0.0;
   CK(cudaMemcpyAsync(ctx->dts, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
-  cgks_status r = ctx->dim == 3 ? run_dt<3>(ctx, ctx->avg[0]) : run_dt<2>(ctx, ctx->avg[0]);
+  cgks_status r = ctx->dim == 3 ? run_dt<3>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr)
+                                 : run_dt<2>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr);
   if (r != CGKS_OK) return r;
   CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

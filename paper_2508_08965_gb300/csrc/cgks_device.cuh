@@ -84,6 +84,26 @@ struct DevGeo {
   double ih[3];       /* 1/h */
   float hf[3], ihf[3]; /* the same in FP32, so FP32 kernels need no conversions */
   const double* met;  /* curvilinear metrics (Met<DIM>), or null */
+  const float* rmet;  /* curvilinear: FP32 CFL metric per cell (RateMet<DIM>), or null */
+  int bcm;            /* boundary kind (BcKind) of domain face f = -x,+x,-y,+y,-z,+z in bits
+                         2f..2f+1: shifts, not an array, so that no copy of DevGeo is
+                         indexed at run time (which would put it in local memory) */
+  long nplane;        /* slots of the low-boundary face array per (axis, Gauss point):
+                         the largest ncell / n[axis] over non-periodic axes, else 0 */
+};
+
+/* boundary kinds (the values of the public CGKS_BC_* codes) */
+enum BcKind { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_SLIP = 2, BC_NOSLIP = 3 };
+CGKS_HD int geo_bc(const DevGeo& g, int f) { return (g.bcm >> (2 * f)) & 3; }
+
+/* FP32 CFL metric of a curvilinear cell, [k * ncell + cell]: per axis the
+   direction w = n/(|n| h) and 1/h (n the mean face normal, h = vol / mean
+   face area), then the smallest h */
+template <int DIM> struct RateMet {
+  static constexpr int W = 0;            /* DIM*DIM: w[ax][a] */
+  static constexpr int IH = DIM * DIM;   /* DIM: 1/h per axis */
+  static constexpr int HMIN = IH + DIM;  /* 1 */
+  static constexpr int N = HMIN + 1;
 };
 
 struct Phys {
@@ -118,6 +138,94 @@ CGKS_HD long nbr(const DevGeo& g, int i, int j, int k, int ox, int oy, int oz) {
   b = b < 0 ? b + g.n[1] : (b >= g.n[1] ? b - g.n[1] : b);
   c = c < 0 ? c + g.n[2] : (c >= g.n[2] ? c - g.n[2] : c);
   return cell_index(g, a, b, c);
+}
+
+/* neighbour through the domain boundaries: periodic faces wrap, outflow
+   faces clamp (the ghost copies the boundary cell), walls mirror the index
+   and the ghost holds the mirror image of the cell.  *mm receives the axes
+   mirrored (bits 0-2) and which of them are no-slip walls (bits 3-5). */
+CGKS_HD long nbr_bc(const DevGeo& g, int i, int j, int k, int ox, int oy, int oz, int* mm) {
+  int x[3] = {i + ox, j + oy, k + oz};
+  int m = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (x[a] < 0 || x[a] >= g.n[a]) {
+      const int hi = x[a] >= g.n[a] ? 1 : 0;
+      const int bc = geo_bc(g, 2 * a + hi);
+      if (bc == BC_PERIODIC) x[a] += hi ? -g.n[a] : g.n[a];
+      else if (bc == BC_OUTFLOW) x[a] = hi ? g.n[a] - 1 : 0;
+      else {
+        x[a] = hi ? 2 * g.n[a] - 1 - x[a] : -1 - x[a];
+        m |= (1 << a) | (bc == BC_NOSLIP ? (8 << a) : 0);
+      }
+    }
+  }
+  *mm = m;
+  return cell_index(g, x[0], x[1], x[2]);
+}
+
+/* The stencil neighbours of one cell, resolved once: the linear-index
+   offsets of the -1 and +1 neighbours along each axis (through the
+   boundaries as nbr_bc resolves them) and their mirror bits, so that a
+   neighbour (ox, oy, oz) in {-1, 0, 1}^DIM costs additions only. */
+template <int DIM> struct NbrOff {
+  int lo[3], hi[3];
+  int mlo, mhi; /* nbr_bc's mm format; the bits of different axes are disjoint */
+  CGKS_HD void setup(const DevGeo& g, int ci, int cj, int ck) {
+    const int x[3] = {ci, cj, ck};
+    int stride = 1;
+    mlo = mhi = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int n = g.n[a];
+      const int bits = (1 << a);
+      if (x[a] > 0) lo[a] = -stride;
+      else {
+        const int bc = geo_bc(g, 2 * a);
+        lo[a] = bc == BC_PERIODIC ? (n - 1) * stride : 0;
+        if (bc >= BC_SLIP) mlo |= bits | (bc == BC_NOSLIP ? bits << 3 : 0);
+      }
+      if (x[a] < n - 1) hi[a] = stride;
+      else {
+        const int bc = geo_bc(g, 2 * a + 1);
+        hi[a] = bc == BC_PERIODIC ? -(n - 1) * stride : 0;
+        if (bc >= BC_SLIP) mhi |= bits | (bc == BC_NOSLIP ? bits << 3 : 0);
+      }
+      stride *= n;
+    }
+  }
+  /* WALL = false: the mesh has no wall, no neighbour is a mirror image */
+  template <bool WALL> CGKS_HD long at(long c, int ox, int oy, int oz, int* mm) const {
+    long i = c;
+    int m = 0;
+    if (ox < 0) { i += lo[0]; m |= mlo & 0x9; } else if (ox > 0) { i += hi[0]; m |= mhi & 0x9; }
+    if (oy < 0) { i += lo[1]; m |= mlo & 0x12; } else if (oy > 0) { i += hi[1]; m |= mhi & 0x12; }
+    if (DIM == 3) {
+      if (oz < 0) { i += lo[2]; m |= mlo & 0x24; } else if (oz > 0) { i += hi[2]; m |= mhi & 0x24; }
+    }
+    *mm = WALL ? m : 0;
+    return i;
+  }
+};
+
+/* 1 if variable v changes sign in the mirror image across the axes of mm:
+   the momentum component along a mirrored axis, and every momentum
+   component at a no-slip mirror; a derivative along a mirrored axis changes
+   sign once more (mirror_odd ^ ((mm >> axis) & 1)) */
+template <int DIM> CGKS_HD int mirror_odd(int v, int mm) {
+  if (!mm || v < 1 || v > DIM) return 0;
+  int f = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+    if ((mm >> a) & 1) f ^= (v == 1 + a || ((mm >> (3 + a)) & 1)) ? 1 : 0;
+  return f;
+}
+
+/* index of the cell (i, j, k) within its boundary plane normal to axis ax */
+CGKS_HD long plane_index(const DevGeo& g, int ax, int i, int j, int k) {
+  if (ax == 0) return j + (long)g.n[1] * k;
+  if (ax == 1) return i + (long)g.n[0] * k;
+  return i + (long)g.n[0] * j;
 }
 
 template <int DIM> CGKS_HD double met_J0(const DevGeo& g, long c, int r, int q) {
@@ -184,8 +292,9 @@ CGKS_HD float cg_tanh(float x) { return tanhf(x); }
    difference is (hi_k - hi_0) + (lo_k - lo_0), computed in FP32 without the
    FP64 pipe.  Gradients are mapped to the target's reference frame with J0^T
    (Sec. 4; CURVI = false: J0 = diag(h)); line differences are the stored
-   derivatives times the line length.  der: [(f-1)][v][cell] in T, f >= 1. */
-template <typename T, int DIM, bool CURVI> struct ReconLd {
+   derivatives times the line length.  der: [(f-1)][v][cell] in T, f >= 1.
+   WALL: neighbours beyond a wall are mirror images (signs by mirror_odd). */
+template <typename T, int DIM, bool CURVI, bool WALL> struct ReconLd {
   const double* __restrict__ avgp;  /* FP64 averages [v][cell] (FP64 form) */
   const float* __restrict__ avh;    /* hi and lo parts [v][cell] (FP32 form) */
   const float* __restrict__ avl;
@@ -193,6 +302,7 @@ template <typename T, int DIM, bool CURVI> struct ReconLd {
   DevGeo g;
   long c;
   int ci, cj, ck, v;
+  NbrOff<DIM> nb;
   double q0d;
   float q0h, q0l;
   T J0[3][3];
@@ -207,7 +317,12 @@ template <typename T, int DIM, bool CURVI> struct ReconLd {
   }
   CGKS_HD T q0() const { return T(0); }
   CGKS_HD T avg(int ox, int oy, int oz) const {
-    const long i = (long)v * g.ncell + nbr(g, ci, cj, ck, ox, oy, oz);
+    int mm;
+    const long i = (long)v * g.ncell + nb.template at<WALL>(c, ox, oy, oz, &mm);
+    if (WALL && mirror_odd<DIM>(v, mm)) {
+      if constexpr (sizeof(T) == 4) return (-avh[i] - q0h) + (-avl[i] - q0l);
+      else return T(-avgp[i] - q0d);
+    }
     if constexpr (sizeof(T) == 4) return (avh[i] - q0h) + (avl[i] - q0l);
     else return T(avgp[i] - q0d);
   }
@@ -217,10 +332,17 @@ template <typename T, int DIM, bool CURVI> struct ReconLd {
     else return T(q0d + double(rel));
   }
   CGKS_HD void grefv(int ox, int oy, int oz, T* out) const {
-    const long nb = nbr(g, ci, cj, ck, ox, oy, oz);
+    int mm;
+    const long ni = nb.template at<WALL>(c, ox, oy, oz, &mm);
     T gp[3];
 #pragma unroll
-    for (int r = 0; r < DIM; ++r) gp[r] = der[((long)r * (DIM + 2) + v) * g.ncell + nb];
+    for (int r = 0; r < DIM; ++r) gp[r] = der[((long)r * (DIM + 2) + v) * g.ncell + ni];
+    if (WALL && mm) {
+      const int f = mirror_odd<DIM>(v, mm);
+#pragma unroll
+      for (int r = 0; r < DIM; ++r)
+        if (f ^ ((mm >> r) & 1)) gp[r] = -gp[r];
+    }
     if constexpr (CURVI) {
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
@@ -247,14 +369,14 @@ template <typename T, int DIM, bool CURVI> struct ReconLd {
    the GENO weights, and the blended value and physical gradient at every
    face Gauss point (Eq. weno-new, reverse transform of Sec. 4), stored in T.
    chi_force >= 0 overrides chi.  Returns chi. */
-template <typename T, int DIM, bool CURVI>
+template <typename T, int DIM, bool CURVI, bool WALL>
 CGKS_HD T recon_var(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
                     const T* __restrict__ der, const DevGeo& g, const Phys& ph, long c, int ci, int cj, int ck, int v,
                     T chi_force, T* __restrict__ gpL, T* __restrict__ gpR) {
   typedef Sz<DIM> S;
   const long N = g.ncell;
   constexpr int NV = S::NV;
-  ReconLd<T, DIM, CURVI> ld;
+  ReconLd<T, DIM, CURVI, WALL> ld;
   ld.avgp = avg;
   ld.avh = avh;
   ld.avl = avl;
@@ -265,6 +387,7 @@ CGKS_HD T recon_var(const double* __restrict__ avg, const float* __restrict__ av
   ld.cj = cj;
   ld.ck = ck;
   ld.v = v;
+  ld.nb.setup(g, ci, cj, ck);
   ld.init_q0();
   if constexpr (CURVI) {
 #pragma unroll
@@ -1025,6 +1148,118 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
   }
 }
 
+/* ---- boundary faces ---------------------------------------------------- */
+/* In the face frame (local axis 0 = the wall normal) the mirror image of a
+   state negates the normal momentum (every momentum component at a no-slip
+   wall) and derivatives along the normal; an outflow image is a copy. */
+template <int DIM> CGKS_HD int image_odd(int kind, int v, int j /* -1: the value */) {
+  if (kind == BC_OUTFLOW) return 0;
+  const int f = (v == 1 || (kind == BC_NOSLIP && v >= 1 && v <= DIM)) ? 1 : 0;
+  return f ^ (j == 0 ? 1 : 0);
+}
+
+/* derivative loader of a boundary face: the real side's derivatives from
+   global memory (CartLd), the image side's from the same with image_odd */
+template <typename T, int DIM> struct BndLd {
+  CartLd<T, DIM> cl;
+  int real, kind;
+  CGKS_HD void grad(int side, int j, T* o) const {
+    cl.grad(real, j, o);
+    if (side != real) {
+#pragma unroll
+      for (int v = 0; v < DIM + 2; ++v)
+        if (image_odd<DIM>(kind, v, j)) o[v] = -o[v];
+    }
+  }
+};
+
+/* A wall face (adiabatic: the paper's non-slip adiabatic wall and its slip
+   counterpart) passes no mass and no energy, and the gas on it slides along
+   the wall (slip) or rests (no-slip): in the face frame the mass and energy
+   parts of F and F_t are zero and the interface values (parts 2..5) carry no
+   normal (slip) or no (no-slip) momentum */
+template <typename T, int DIM> CGKS_HD void wall_face_local(int kind, T* out) {
+  constexpr int NV = DIM + 2;
+  out[0] = out[NV - 1] = T(0);
+  out[NV] = out[2 * NV - 1] = T(0);
+#pragma unroll
+  for (int part = 2; part < 6; ++part)
+#pragma unroll
+    for (int i = 1; i <= DIM; ++i)
+      if (i == 1 || kind == BC_NOSLIP) out[part * NV + i] = T(0);
+}
+
+/* One Gauss point of a domain-boundary face: the GKS problem between the
+   Gauss-point state of the boundary cell (side `real`: 0 = it is the left
+   state, at the high boundary; 1 = the right state, at the low boundary),
+   read from face slot c, and its image; the result goes to
+   out[(part * NV + var) * ns + oidx] of the point's block.  Curvilinear
+   meshes take outflow only (the image is a copy); the frame comes from the
+   area vector of Gauss point fgp of cell fc. */
+template <typename T, int DIM, bool CURVI>
+CGKS_HD bool flux_bnd_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, long c, long fc, int fgp,
+                            int real, int kind, const T* __restrict__ gpL, const T* __restrict__ gpR,
+                            T* __restrict__ out_arr, long ns, long oidx) {
+  typedef Sz<DIM> S;
+  constexpr int NV = S::NV;
+  const long N = g.ncell;
+  const long base = (long)((ax * S::GPF + k) * NV) * (1 + DIM);
+  const long fb = (long)((ax * S::GPF + k) * 6) * NV;
+  T WL[NV], WR[NV], out[6 * NV];
+  const T* src = real ? gpR : gpL;
+  if constexpr (!CURVI) {
+    BndLd<T, DIM> ld;
+    ld.cl.gl = gpL;
+    ld.cl.gr = gpR;
+    ld.cl.base = base;
+    ld.cl.N = N;
+    ld.cl.c = c;
+    ld.real = real;
+    ld.kind = kind;
+    cart_frame<DIM>(ax, ld.cl.p, ld.cl.s);
+    const int* p = ld.cl.p;
+    const int* sg = ld.cl.s;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      int vg = v, sv = 1;
+      if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = sg[v - 1]; }
+      const T w = T(sv) * src[(base + vg * (1 + DIM)) * N + c];
+      const T wi = image_odd<DIM>(kind, v, -1) ? -w : w;
+      WL[v] = real ? wi : w;
+      WR[v] = real ? w : wi;
+    }
+    bool ok = gks_point_ld<T, DIM>(ph, dt, WL, WR, ld, out);
+    if (kind >= BC_SLIP) wall_face_local<T, DIM>(kind, out);
+#pragma unroll
+    for (int part = 0; part < 6; ++part) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        int vg = v, sv = 1;
+        if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = sg[v - 1]; }
+        out_arr[(fb + part * NV + vg) * ns + oidx] = T(sv) * out[part * NV + v];
+      }
+    }
+    return ok;
+  } else {
+    T dW[DIM * NV];
+    T st[NV * (1 + DIM)];
+    for (int q = 0; q < NV * (1 + DIM); ++q) st[q] = src[(base + q) * N + c];
+    double A[3], Tt[3];
+    for (int a = 0; a < 3; ++a) {
+      A[a] = a < DIM ? met_area<DIM>(g, fc, fgp, a) : 0.0;
+      Tt[a] = a < DIM ? met_tang<DIM>(g, fc, ax, k, a) : 0.0;
+    }
+    double R[3][3];
+    face_frame<DIM>(A, Tt, R);
+    to_local<T, DIM>(R, st, WL, dW);
+    for (int v = 0; v < NV; ++v) WR[v] = WL[v];
+    bool ok = gks_point<T, DIM>(ph, dt, WL, dW, WR, dW, out);
+    for (int part = 0; part < 6; ++part) to_global<T, DIM>(R, out + part * NV);
+    for (int q = 0; q < 6 * NV; ++q) out_arr[(fb + q) * ns + oidx] = out[q];
+    return ok;
+  }
+}
+
 /* ===================================================================== */
 /* (c) accumulation and S2O4 update of one cell                          */
 /* ===================================================================== */
@@ -1037,7 +1272,7 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
    axis-aligned cells, where both reduce to differences divided by h. */
 template <typename T, int DIM, bool CURVI>
 CGKS_HD void update_var(const DevGeo& g, double dt, int stage, long c, int ci, int cj, int ck, int v,
-                        const double* __restrict__ avg_in, const T* __restrict__ flux,
+                        const double* __restrict__ avg_in, const T* __restrict__ flux, const T* __restrict__ fxb,
                         double* __restrict__ stash_avg, T* __restrict__ stash_der, double* __restrict__ avg_out,
                         T* __restrict__ der_out, float* __restrict__ avh_out, float* __restrict__ avl_out) {
   typedef Sz<DIM> S;
@@ -1057,21 +1292,28 @@ CGKS_HD void update_var(const DevGeo& g, double dt, int stage, long c, int ci, i
     int o[3] = {0, 0, 0};
     o[ax] = -1;
     const long lo = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
+    /* the low face of a cell on a non-periodic low boundary lives in fxb */
+    const int cc[3] = {ci, cj, ck};
+    const bool lowb = geo_bc(g, 2 * ax) != BC_PERIODIC && cc[ax] == 0;
+    const T* __restrict__ fsrc = lowb ? fxb : flux;
+    const long fs = lowb ? g.nplane : N;
+    const long fi = lowb ? plane_index(g, ax, ci, cj, ck) : lo;
     const T ih = CURVI ? T(1) : geo_ih<T>(g, ax);
     T sh_f = T(0), sl_f = T(0), sth_f = T(0), stl_f = T(0); /* face sums, high and low face */
 #pragma unroll
     for (int k = 0; k < GPF; ++k) {
       const long fb = (long)((ax * GPF + k) * 6) * NV + v;
       const int ghi = (2 * ax + 1) * GPF + k, glo = (2 * ax) * GPF + k;
-      const T fh = flux[(fb + 0 * NV) * N + c], fl = flux[(fb + 0 * NV) * N + lo];
-      const T fth = flux[(fb + 1 * NV) * N + c], ftl = flux[(fb + 1 * NV) * N + lo];
+      const T fh = flux[(fb + 0 * NV) * N + c], fl = fsrc[(fb + 0 * NV) * fs + fi];
+      const T fth = flux[(fb + 1 * NV) * N + c], ftl = fsrc[(fb + 1 * NV) * fs + fi];
       const T qnh = flux[(fb + 2 * NV) * N + c], qth = flux[(fb + 3 * NV) * N + c];
-      const T qnl = flux[(fb + 4 * NV) * N + lo], qtl = flux[(fb + 5 * NV) * N + lo];
+      const T qnl = fsrc[(fb + 4 * NV) * fs + fi], qtl = fsrc[(fb + 5 * NV) * fs + fi];
       if constexpr (CURVI) {
         T a2 = T(0), b2 = T(0);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-          const T ah = T(met_area<DIM>(g, c, ghi, a)), al = T(met_area<DIM>(g, lo, ghi, a));
+          const T ah = T(met_area<DIM>(g, c, ghi, a));
+          const T al = T(lowb ? met_area<DIM>(g, c, glo, a) : met_area<DIM>(g, lo, ghi, a));
           a2 += ah * ah;
           b2 += al * al;
           /* Gauss' theorem with the cell's own outward area vectors */
@@ -1201,6 +1443,58 @@ CGKS_HD double cell_rate(const DevGeo& g, const Phys& ph, const double* __restri
   }
   if (!(rho > 0.0) || !(p > 0.0) || !(rate == rate)) rate = 1e300; /* flags a bad state */
   return rate;
+}
+
+/* Bounds on the FP64 rate of cell_rate from the FP32 averages W: the FP32
+   rate r with its relative error bound eta.  The inputs carry a relative
+   error of at most 2^-24 (one rounding from FP64) and about 20 further
+   roundings follow; the pressure, a difference, amplifies those by up to
+   E/(E - ke/2).  eta = 64 u (2 + E/(E - ke/2)) covers the whole with a wide
+   margin.  Where FP32 cannot decide (a non-positive or non-finite value, or
+   eta >= 1/4) the bounds are [0, inf): the cell is always evaluated in FP64
+   and never raises the threshold. */
+template <int DIM>
+__device__ __forceinline__ void cell_rate_bounds_f32(const DevGeo& g, const Phys& ph, const float* W, long c,
+                                                     float* lo, float* hi) {
+  const float rho = W[0], irho = 1.0f / rho;
+  float ke = 0.0f, Uv[3];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    Uv[i] = W[1 + i] * irho;
+    ke = fmaf(Uv[i], W[1 + i], ke);
+  }
+  const float pe = W[DIM + 1] - 0.5f * ke;
+  const float p = (ph.gammaf - 1.0f) * pe;
+  const float snd = sqrtf(ph.gammaf * p * irho);
+  float rate = 0.0f, hmin;
+  if (!g.curvi) {
+    hmin = g.hf[0];
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      rate = fmaf(fabsf(Uv[ax]) + snd, g.ihf[ax], rate);
+      hmin = fminf(hmin, g.hf[ax]);
+    }
+  } else {
+    const long N = g.ncell;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      float un = 0.0f;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) un = fmaf(Uv[a], g.rmet[(RateMet<DIM>::W + ax * DIM + a) * N + c], un);
+      rate += fabsf(un);
+      rate = fmaf(snd, g.rmet[(RateMet<DIM>::IH + ax) * N + c], rate);
+    }
+    hmin = g.rmet[RateMet<DIM>::HMIN * N + c];
+  }
+  if (ph.muf > 0.0f) rate = fmaxf(rate, 3.0f * ph.muf * irho / (hmin * hmin));
+  const float eta = 64.0f * 5.9604645e-8f * (2.0f + W[DIM + 1] / pe);
+  if (!(rho > 0.0f) || !(p > 0.0f) || !(rate <= 1.0e37f) || !(eta < 0.25f)) {
+    *lo = 0.0f;
+    *hi = __int_as_float(0x7f800000);
+    return;
+  }
+  *lo = rate * (1.0f - eta);
+  *hi = rate * (1.0f + eta);
 }
 
 }  // namespace cgks

@@ -15,7 +15,9 @@ enum { ST_NONPHYS = 0, ST_FALLBACK = 1, ST_FLUX = 2, ST_DT = 3, ST_N = 4 };
 
 /* time-step bookkeeping on the device: [0] rate bits (max), [1] dt, [2] t, [3] t_end */
 struct DtState {
-  unsigned long long rate_bits;
+  unsigned long long rate_bits; /* FP64 maximum rate (bit pattern; orders like the value) */
+  unsigned int lo_bits;         /* FP32 screening: largest lower bound of a cell's rate */
+  unsigned int pad;
   double dt, t, t_end, dt_fixed;
 };
 
@@ -23,7 +25,7 @@ struct DtState {
    ones keep 2 (they are bound by the FP64 pipe, and spill more when capped) */
 template <typename T> constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
 
-template <typename T, int DIM, bool CURVI>
+template <typename T, int DIM, bool CURVI, bool WALL>
 __global__ void __launch_bounds__(128, min_blocks<T>())
     k_recon(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
             const T* __restrict__ der, DevGeo g, Phys ph, T* __restrict__ gpL, T* __restrict__ gpR,
@@ -36,17 +38,19 @@ __global__ void __launch_bounds__(128, min_blocks<T>())
   const T force = ph.linear ? T(1) : T(-1);
   T cs[NV];
 #pragma unroll 1
-  for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI>(avg, avh, avl, der, g, ph, c, i, j, k, v, force, gpL, gpR);
+  for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, v, force, gpL, gpR);
   if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) {
     atomicAdd(&st[ST_FALLBACK], 1);
 #pragma unroll 1
-    for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI>(avg, avh, avl, der, g, ph, c, i, j, k, v, T(0), gpL, gpR);
+    for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, v, T(0), gpL, gpR);
     if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) atomicOr(&st[ST_NONPHYS], 1);
   }
   if (record_chi)
     for (int v = 0; v < NV; ++v) chi[(long)v * g.ncell + c] = double(cs[v]);
 }
 
+/* one thread per face slot (the face above cell c along the axis) and
+   Gauss point; slots on a non-periodic high boundary are left to k_flux_bnd */
 template <typename T, int DIM, bool CURVI>
 __global__ void __launch_bounds__(128, min_blocks<T>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
                                               const T* __restrict__ gpL, const T* __restrict__ gpR,
@@ -59,12 +63,56 @@ __global__ void __launch_bounds__(128, min_blocks<T>()) k_flux(DevGeo g, Phys ph
   int k = r % Sz<DIM>::GPF, ax = r / Sz<DIM>::GPF;
   const double dt = dts->dt;
   if (!(dt > 0.0)) return;
+  if (geo_bc(g, 2 * ax + 1) != BC_PERIODIC) {
+    int ijk[3];
+    cell_ijk(g, c, ijk[0], ijk[1], ijk[2]);
+    if (ijk[ax] == g.n[ax] - 1) return;
+  }
   if (!flux_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c, gpL, gpR, flux)) atomicOr(&st[ST_FLUX], 1);
+}
+
+/* the faces on the non-periodic domain boundaries: thread
+   ((side * DIM + ax) * GPF + k) * nplane + plane.  In a plane normal to ax,
+   c0 is the cell on the low boundary and c1 the one on the high boundary;
+   slot c1 holds both c1's high-face state (gpL) and c0's low-face state
+   (gpR).  The high face goes to flux at slot c1, the low face to fxb. */
+template <typename T, int DIM, bool CURVI>
+__global__ void __launch_bounds__(128) k_flux_bnd(DevGeo g, Phys ph, const DtState* __restrict__ dts,
+                                                  const T* __restrict__ gpL, const T* __restrict__ gpR,
+                                                  T* __restrict__ flux, T* __restrict__ fxb, int* __restrict__ st) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= 2L * DIM * Sz<DIM>::GPF * g.nplane) return;
+  const double dt = dts->dt;
+  if (!(dt > 0.0)) return;
+  const long pidx = t % g.nplane;
+  int r = (int)(t / g.nplane);
+  const int k = r % Sz<DIM>::GPF;
+  r /= Sz<DIM>::GPF;
+  const int ax = r % DIM, side = r / DIM; /* side 1: high boundary */
+  const int bc = geo_bc(g, 2 * ax + side);
+  const long N = g.ncell;
+  if (bc == BC_PERIODIC || pidx >= N / g.n[ax]) return;
+  int ijk[3] = {0, 0, 0};
+  const int a0 = ax == 0 ? 1 : 0, a1 = ax == 2 ? 1 : 2;
+  ijk[a0] = (int)(pidx % g.n[a0]);
+  ijk[a1] = (int)(pidx / g.n[a0]);
+  const long c0 = cell_index(g, ijk[0], ijk[1], ijk[2]);
+  ijk[ax] = g.n[ax] - 1;
+  const long c1 = cell_index(g, ijk[0], ijk[1], ijk[2]);
+  bool ok;
+  if (side)
+    ok = flux_bnd_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c1, c1, (2 * ax + 1) * Sz<DIM>::GPF + k, 0, bc, gpL,
+                                       gpR, flux, N, c1);
+  else
+    ok = flux_bnd_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c1, c0, (2 * ax) * Sz<DIM>::GPF + k, 1, bc, gpL, gpR,
+                                       fxb, g.nplane, pidx);
+  if (!ok) atomicOr(&st[ST_FLUX], 1);
 }
 
 template <typename T, int DIM, bool CURVI>
 __global__ void __launch_bounds__(128) k_update(DevGeo g, const DtState* __restrict__ dts, int stage,
                                                 const double* __restrict__ avg_in, const T* __restrict__ flux,
+                                                const T* __restrict__ fxb,
                                                 double* __restrict__ stash_avg, T* __restrict__ stash_der,
                                                 double* __restrict__ avg_out, T* __restrict__ der_out,
                                                 float* __restrict__ avh_out, float* __restrict__ avl_out) {
@@ -77,7 +125,7 @@ __global__ void __launch_bounds__(128) k_update(DevGeo g, const DtState* __restr
   const int v = (int)(t / N);
   int i, j, k;
   cell_ijk(g, c, i, j, k);
-  update_var<T, DIM, CURVI>(g, dt, stage, c, i, j, k, v, avg_in, flux, stash_avg, stash_der, avg_out, der_out,
+  update_var<T, DIM, CURVI>(g, dt, stage, c, i, j, k, v, avg_in, flux, fxb, stash_avg, stash_der, avg_out, der_out,
                             avh_out, avl_out);
 }
 
@@ -125,32 +173,70 @@ __global__ void k_join(const double* __restrict__ avg, const T* __restrict__ der
 }
 
 /* max over cells of the rate; positive doubles order like their bit patterns */
-template <int DIM>
-__global__ void __launch_bounds__(256) k_dt_rate(DevGeo g, Phys ph, const double* __restrict__ U,
-                                                 DtState* __restrict__ dts) {
-  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  double r = 0.0;
-  if (c < g.ncell) r = cell_rate<DIM>(g, ph, U, c);
-  unsigned long long bits = (unsigned long long)__double_as_longlong(r);
-  for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
-    bits = ob > bits ? ob : bits;
-  }
-  __shared__ unsigned long long wmax[8];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) wmax[wid] = bits;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long m = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
-    atomicMax(&dts->rate_bits, m);
-  }
+/* The CFL maximum in two passes.  Bounds on every cell's rate from FP32
+   arithmetic (cell_rate_bounds_f32) cost a few FP32 operations; pass 1 takes
+   the largest lower bound over the mesh, and pass 2 evaluates the FP64 rate
+   only where the upper bound reaches it -- the cells that can hold the FP64
+   maximum -- so dt equals the FP64 maximum exactly while the FP64 pipe sees a
+   handful of cells.  S: the averages the FP32 bounds read (the FP64 averages,
+   converted, or the FP32 form's rounded hi parts). */
+template <int DIM, typename S>
+__device__ __forceinline__ void rate_bounds(const DevGeo& g, const Phys& ph, const S* __restrict__ src, long c,
+                                            float* lo, float* hi) {
+  float W[DIM + 2];
+#pragma unroll
+  for (int v = 0; v < DIM + 2; ++v) W[v] = (float)src[(long)v * g.ncell + c];
+  cell_rate_bounds_f32<DIM>(g, ph, W, c, lo, hi);
 }
 
-__global__ void k_dt_reset(DtState* dts) { dts->rate_bits = 0ull; }
+template <typename U>
+__device__ __forceinline__ U block_max(U x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    U y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  __shared__ U wmax[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wmax[wid] = x;
+  __syncthreads();
+  U m = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
+  return m; /* valid in thread 0 */
+}
+
+template <int DIM, typename S>
+__global__ void __launch_bounds__(256) k_dt_screen(DevGeo g, Phys ph, const S* __restrict__ src,
+                                                   DtState* __restrict__ dts) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  float lo = 0.0f, hi;
+  if (c < g.ncell) rate_bounds<DIM, S>(g, ph, src, c, &lo, &hi);
+  const unsigned int m = block_max<unsigned int>(__float_as_uint(lo));
+  if (threadIdx.x == 0) atomicMax(&dts->lo_bits, m);
+}
+
+template <int DIM, typename S>
+__global__ void __launch_bounds__(256) k_dt_rate(DevGeo g, Phys ph, const S* __restrict__ src,
+                                                 const double* __restrict__ U, DtState* __restrict__ dts) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  double r = 0.0;
+  if (c < g.ncell) {
+    float lo, hi;
+    rate_bounds<DIM, S>(g, ph, src, c, &lo, &hi);
+    if (hi >= __uint_as_float(dts->lo_bits)) r = cell_rate<DIM>(g, ph, U, c);
+  }
+  const unsigned long long m = block_max<unsigned long long>((unsigned long long)__double_as_longlong(r));
+  if (threadIdx.x == 0) atomicMax(&dts->rate_bits, m);
+}
+
+static __global__ void k_dt_reset(DtState* dts) {
+  dts->rate_bits = 0ull;
+  dts->lo_bits = 0u;
+}
 
 /* dt = CFL / max rate, or the fixed step; shortened to reach t_end */
-__global__ void k_dt_final(Phys ph, DtState* dts, int* st) {
+static __global__ void k_dt_final(Phys ph, DtState* dts, int* st) {
   double rate = __longlong_as_double((long long)dts->rate_bits);
   double dt;
   if (dts->dt_fixed > 0.0) dt = dts->dt_fixed;
@@ -163,7 +249,7 @@ __global__ void k_dt_final(Phys ph, DtState* dts, int* st) {
   dts->dt = dt;
 }
 
-__global__ void k_time_advance(DtState* dts) { dts->t += dts->dt; }
+static __global__ void k_time_advance(DtState* dts) { dts->t += dts->dt; }
 
 /* ------------------------------------------------------------------ */
 /* metrics from node coordinates (Sec. 4 J0, Appendix volume)           */
@@ -328,6 +414,37 @@ CGKS_HD double g5w(int q) {
   return (q == 0 || q == 4) ? 0.23692688505618908751 : (q == 1 || q == 3) ? 0.47862867049936646804
                                                                           : 0.56888888888888888889;
 }
+/* FP32 CFL metric of each curvilinear cell (RateMet<DIM>) from the FP64
+   metrics, by the same formulas as the curvilinear branch of cell_rate */
+template <int DIM>
+__global__ void k_rate_metrics(DevGeo g, float* __restrict__ rmet) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const long N = g.ncell;
+  const double vol = met_vol<DIM>(g, c);
+  double hmin = 1e300;
+  for (int ax = 0; ax < DIM; ++ax) {
+    double A0[3] = {0.0, 0.0, 0.0}, A1[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < Sz<DIM>::GPF; ++k)
+      for (int a = 0; a < DIM; ++a) {
+        A0[a] += met_area<DIM>(g, c, (2 * ax) * Sz<DIM>::GPF + k, a);
+        A1[a] += met_area<DIM>(g, c, (2 * ax + 1) * Sz<DIM>::GPF + k, a);
+      }
+    double s0 = 0.0, s1 = 0.0, nn[3], ns = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+      s0 += A0[a] * A0[a];
+      s1 += A1[a] * A1[a];
+      nn[a] = A0[a] + A1[a];
+      ns += nn[a] * nn[a];
+    }
+    const double h = vol / (0.5 * (sqrt(s0) + sqrt(s1)));
+    for (int a = 0; a < DIM; ++a) rmet[(RateMet<DIM>::W + ax * DIM + a) * N + c] = (float)(nn[a] / sqrt(ns) / h);
+    rmet[(RateMet<DIM>::IH + ax) * N + c] = (float)(1.0 / h);
+    if (h < hmin) hmin = h;
+  }
+  rmet[RateMet<DIM>::HMIN * N + c] = (float)hmin;
+}
+
 template <int DIM> __host__ __device__ constexpr int npts_cell() { return (DIM == 3 ? 125 : 25) + Sz<DIM>::NGP; }
 
 /* physical position of reference point xi of cell (i,j,k) */

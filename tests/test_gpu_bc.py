@@ -1,0 +1,151 @@
+"""GPU parity of the boundary conditions (through the C-ABI) against the
+oracle, whose walls are pinned by mirror symmetry and Stokes decay.
+
+Bar as for the periodic sweep: class-scaled 1e-12 after one step and 1e-9
+after many (FP64); the FP32 form within its own bound.  Closed boxes
+conserve mass and energy on the GPU too.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from parity import class_scaled_diff
+
+pytestmark = pytest.mark.gpu
+
+P, OUT, SLIP, NOSLIP = 0, 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_08965_gb300 as p
+    p.lib()
+    return p
+
+
+def s2(x, y):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x + 0.3) * np.cos(2 * np.pi * y)
+    u = 0.3 * np.sin(np.pi * x) + 0.1 * np.cos(2 * np.pi * y + 0.7) * x
+    v = 0.2 * np.cos(2 * np.pi * y) + 0.1 * x
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * x - 0.4)
+    return [rho, u, v, p]
+
+
+def s3(x, y, z):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x + 0.3) * np.cos(2 * np.pi * y) + 0.1 * z
+    u = 0.2 * np.cos(2 * np.pi * y) + 0.1 * z
+    v = 0.2 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * z + 0.2)
+    w = 0.3 * np.sin(np.pi * z) * (1.0 + 0.2 * np.cos(2 * np.pi * x))
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * z - 0.4) + 0.05 * np.sin(2 * np.pi * y)
+    return [rho, u, v, w, p]
+
+
+def tgv(x, y, z):
+    return synth.taylor_green_3d(x, y, z)
+
+
+VISC = {"mu": 2e-3, "tau_mode": 2, "prandtl": 0.72}
+CASES = [
+    ("slip-x-2d", 2, (40, 33), [SLIP, SLIP, P, P], {}),
+    ("slip-y-2d-shock", 2, (33, 40), [P, P, SLIP, SLIP], {"tau_mode": 1}),
+    ("noslip-outflow-2d", 2, (37, 29), [NOSLIP, NOSLIP, OUT, OUT], VISC),
+    ("mixed-2d", 2, (29, 37), [OUT, OUT, NOSLIP, SLIP], {"tau_mode": 1}),
+    ("walls-3d", 3, (9, 10, 11), [NOSLIP, NOSLIP, SLIP, SLIP, OUT, OUT], VISC),
+    ("outflow-z-3d", 3, (8, 7, 12), [P, P, P, P, NOSLIP, OUT], VISC),
+]
+
+
+def pair(orc, cg, dim, n, bc, kw, fn=None, nodes=None, lo=None, hi=None, precision=0):
+    lo = lo or (0.0,) * dim
+    hi = hi or (1.0,) * dim
+    o = orc.Oracle(dim, n, lo=lo, hi=hi, nodes=nodes, bc=bc, **kw)
+    o.init(fn or (s2 if dim == 2 else s3))
+    m = cg.Mesh(dim, n, lo=lo, hi=hi, nodes=nodes, bc=bc, precision=precision, **kw)
+    m.set_state(o.get_state())
+    return o, m
+
+
+def hmin(n):
+    return min(1.0 / x for x in n)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_boundary_one_step(orc, cg, case):
+    name, dim, n, bc, kw = case
+    o, m = pair(orc, cg, dim, n, bc, kw)
+    assert abs(m.compute_dt() - o.dt()) <= 1e-14 * o.dt()
+    o.step(1)
+    m.step(1)
+    sg, _ = m.get_state()
+    assert class_scaled_diff(sg, o.get_state(), hmin(n)) <= 1e-12
+    m.close()
+
+
+@pytest.mark.parametrize("case", CASES[:1] + CASES[2:3] + CASES[4:5], ids=["slip-x-2d", "noslip-outflow-2d",
+                                                                         "walls-3d"])
+def test_boundary_many_steps(orc, cg, case):
+    name, dim, n, bc, kw = case
+    o, m = pair(orc, cg, dim, n, bc, kw)
+    steps = 40 if dim == 3 else 100
+    o.step(steps)
+    m.step(steps)
+    sg, tg = m.get_state()
+    assert abs(tg - o.time()) <= 1e-12 * o.time()
+    assert class_scaled_diff(sg, o.get_state(), hmin(n)) <= 1e-9
+    m.close()
+
+
+def test_outflow_curvilinear(orc, cg):
+    n = (8, 8, 8)
+    nodes = synth.perturbed_nodes_3d(n)
+    kw = {"mu": 1 / 1600, "prandtl": 0.72, "tau_mode": 2}
+    o, m = pair(orc, cg, 3, n, [OUT, OUT, P, P, OUT, OUT], kw, fn=tgv, nodes=nodes, lo=(0, 0, 0),
+                hi=(2 * math.pi,) * 3)
+    o.step(2)
+    m.step(2)
+    sg, _ = m.get_state()
+    assert class_scaled_diff(sg, o.get_state(), 0.7 * 2 * math.pi / 8) <= 1e-12
+    m.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_closed_box_conserves(orc, cg, precision, dim):
+    n = (24, 20) if dim == 2 else (10, 9, 8)
+    bc = [NOSLIP, NOSLIP, SLIP, SLIP, NOSLIP, SLIP][:2 * dim]
+    o, m = pair(orc, cg, dim, n, bc, VISC, precision=precision)
+    s0, _ = m.get_state()
+    m.step(20)
+    s1, _ = m.get_state()
+    for v in (0, dim + 1):
+        a, b = s0[0, v].sum(), s1[0, v].sum()
+        assert abs(b - a) <= 1e-13 * abs(a)
+    m.close()
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[4]], ids=["noslip-outflow-2d", "walls-3d"])
+def test_boundary_fp32_form(orc, cg, case):
+    name, dim, n, bc, kw = case
+    o, m = pair(orc, cg, dim, n, bc, kw, precision=1)
+    o.step(10)
+    m.step(10)
+    sg, _ = m.get_state()
+    so = o.get_state()
+    rho_l2 = np.sqrt(np.mean((sg[0, 0] - so[0, 0]) ** 2)) / np.sqrt(np.mean(so[0, 0] ** 2))
+    assert rho_l2 < 1e-6
+    m.close()
+
+
+def test_bad_boundaries_rejected(cg):
+    with pytest.raises(cg.CgksError):
+        cg.Mesh(2, (8, 8), bc=[7, 7, 0, 0])
+    with pytest.raises(cg.CgksError):
+        cg.Mesh(2, (8, 8), bc=[SLIP, P, P, P])
+    nodes = synth.perturbed_nodes_3d((6, 6, 6))
+    with pytest.raises(cg.CgksError):
+        cg.Mesh(3, (6, 6, 6), nodes=nodes, bc=[SLIP, SLIP, P, P, P, P])

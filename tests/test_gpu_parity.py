@@ -173,3 +173,38 @@ def test_library_init_matches_oracle_init(orc, cg):
         sg, _ = m.get_state()
         assert class_scaled_diff(sg, o.get_state()) <= 1e-12
         m.close()
+
+
+def _random_state(dim, n, seed, mach_max):
+    """Averages of random states spanning Mach 1e-3..mach_max (derivative
+    fields zero): the time step must not depend on how the maximum is found."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(reversed(n))
+    rho = 10 ** rng.uniform(-2, 1, shape)
+    c = 10 ** rng.uniform(-1, 1, shape)
+    p = rho * c * c / 1.4
+    u = rng.normal(size=(dim,) + shape)
+    u *= (10 ** rng.uniform(-3, np.log10(mach_max), shape) * c / np.linalg.norm(u, axis=0))
+    nf = 1 + dim + dim * (4 if dim == 3 else 2)
+    s = np.zeros((nf, dim + 2) + shape)
+    s[0, 0] = rho
+    s[0, 1:1 + dim] = rho * u
+    s[0, dim + 1] = p / 0.4 + 0.5 * rho * (u * u).sum(0)
+    return s
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("dim,n,curvi,mu", [(2, (64, 48), False, 0.0), (3, (10, 11, 12), True, 1e-3),
+                                             (3, (16, 16, 16), False, 1e-3)])
+def test_time_step_equals_fp64_maximum(orc, cg, precision, dim, n, curvi, mu):
+    lo, hi = (0,) * dim, ((2 * math.pi,) * 3 if curvi else (1,) * dim)
+    nodes = synth.perturbed_nodes_3d(n) if curvi else None
+    for seed, mach in ((1, 0.5), (2, 300.0)):
+        s = _random_state(dim, n, seed, mach)
+        o = orc.Oracle(dim, n, lo=lo, hi=hi, nodes=nodes, mu=mu)
+        o.set_state(s)
+        m = cg.Mesh(dim, n, lo=lo, hi=hi, nodes=nodes, mu=mu, precision=precision)
+        m.set_state(s)
+        dg, do = m.compute_dt(), o.dt()
+        assert abs(dg - do) <= 1e-14 * do, (seed, dg, do)
+        m.close()
