@@ -170,6 +170,57 @@ cgks_status cgks_compute_dt_noalloc(const cgks_mesh_desc* desc, const double* de
 /* Copy the last error message (NUL-terminated, truncated to cap). */
 cgks_status cgks_last_error(const cgks_ctx* ctx, char* msg, size_t cap);
 
+/* ---- Batched ensemble ----------------------------------------------------
+   Many independent meshes (cases) of uneven size advancing together: one
+   launch per kernel and phase covers every case, and a run of nsteps S2O4
+   steps is captured once as a CUDA graph and replayed.  The paper has no
+   counterpart; each case computes exactly what cgks_step computes for it
+   (its own CFL time step, time, boundaries and physics).  Cases are uniform
+   boxes (nodes == NULL) of one dim and one precision; their descriptors'
+   stream fields are ignored in favour of the batch's stream. */
+typedef struct cgks_batch cgks_batch;
+
+/* Launch configuration of the batched kernels.  The reconstruction works on
+   tiles of tile_x x tile_y cells of one (i, j) plane (tile_x * tile_y <= 128,
+   one thread per cell); the other kernels on tiles of 128 (256 for the time
+   step) work items.  *_blocks = 0 launches one block per tile; n > 0 a
+   persistent grid of n blocks per SM that walks the tiles. */
+typedef struct {
+  int tile_x, tile_y;
+  int recon_blocks;
+  int flux_blocks;   /* also the boundary faces */
+  int update_blocks; /* also the time-step reduction */
+} cgks_batch_tiles;
+
+/* Validates every descriptor (as cgks_create_mesh, plus: equal dim and
+   precision, nodes == NULL else CGKS_EUNSUPPORTED) and allocates all cases'
+   arrays.  stream: cudaStream_t for all work (must be non-NULL for graphs
+   and tuning).  States start at zero: set each case with
+   cgks_batch_set_state. */
+cgks_status cgks_batch_create(const cgks_mesh_desc* descs, int ncase, void* stream, cgks_batch** out);
+void cgks_batch_destroy(cgks_batch* b);
+int cgks_batch_num_cases(const cgks_batch* b);
+long cgks_batch_num_cells(const cgks_batch* b);
+/* State of case k in the public layout of that case's mesh (as
+   cgks_set_state / cgks_get_state). */
+cgks_status cgks_batch_set_state(cgks_batch* b, int k, const double* src, int is_device, double t);
+cgks_status cgks_batch_get_state(cgks_batch* b, int k, double* dst, int is_device, double* t);
+/* Per-case time and last time step into host arrays of ncase (may be NULL). */
+cgks_status cgks_batch_times(cgks_batch* b, double* t, double* dt_last);
+/* Advance every case nsteps steps.  use_graph = 1: one graph launch (captured
+   on first use for this nsteps; changing the tiles drops the graphs);
+   0: plain launches.  Synchronises once; CGKS_ENONPHYS if any case became
+   non-physical. */
+cgks_status cgks_batch_step(cgks_batch* b, int nsteps, int use_graph);
+cgks_status cgks_batch_get_tiles(const cgks_batch* b, cgks_batch_tiles* out);
+cgks_status cgks_batch_set_tiles(cgks_batch* b, const cgks_batch_tiles* t);
+/* Autotuner: times each phase of a stage (reps repetitions) under every
+   candidate tile shape and grid size on the batch's current data, keeps the
+   fastest per phase and returns it in *chosen (and the sum of the phase times
+   in *ms_best, may be NULL).  The cases' states and times are unchanged. */
+cgks_status cgks_batch_tune(cgks_batch* b, int reps, cgks_batch_tiles* chosen, double* ms_best);
+cgks_status cgks_batch_last_error(const cgks_batch* b, char* msg, size_t cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1150,6 +1150,18 @@ static double mirror_sign(int dim, int v, int k, int mirror, int noslip) {
   return s;
 }
 
+/* rho > 0 and p > 0 at every face Gauss point of one cell's reconstruction */
+static int gp_states_physical(const ref_t* R, double gamma, double ref[MAXV][MAXGP * 4]) {
+  const int dim = R->dim;
+  for (int gp = 0; gp < R->ngp; ++gp) {
+    double rho = ref[0][gp * (1 + dim)], ke = 0;
+    for (int i = 0; i < dim; ++i) { double m = ref[1 + i][gp * (1 + dim)]; ke += m * m; }
+    double p = (gamma - 1.0) * (ref[dim + 1][gp * (1 + dim)] - 0.5 * ke / rho);
+    if (!(rho > 0) || !(p > 0)) return 0;
+  }
+  return 1;
+}
+
 /* reconstruct all variables of one cell at its face Gauss points, physical
    gradients (reverse transform of Sec. 4); positivity fallback forces chi = 0 */
 static void recon_cell(orc_ctx* c, const double* S, long id, int record_chi) {
@@ -1196,17 +1208,20 @@ static void recon_cell(orc_ctx* c, const double* S, long id, int record_chi) {
   double force = c->d.linear ? 1.0 : -1.0;
   for (int v = 0; v < nv; ++v) recon_var(R, dat[v], force, c->d.c_chi, ref[v], &chi[v]);
   /* positivity of the reconstructed Gauss-point states */
-  int bad = 0;
-  for (int gp = 0; gp < R->ngp && !bad; ++gp) {
-    double rho = ref[0][gp * (1 + dim)], ke = 0;
-    for (int i = 0; i < dim; ++i) { double m = ref[1 + i][gp * (1 + dim)]; ke += m * m; }
-    double p = (c->d.gamma - 1.0) * (ref[dim + 1][gp * (1 + dim)] - 0.5 * ke / rho);
-    if (!(rho > 0) || !(p > 0)) bad = 1;
-  }
+  int bad = !gp_states_physical(R, c->d.gamma, ref);
   if (bad) {
 #pragma omp atomic
     c->npos_fallback++;
     for (int v = 0; v < nv; ++v) recon_var(R, dat[v], 0.0, c->d.c_chi, ref[v], &chi[v]);
+    bad = !gp_states_physical(R, c->d.gamma, ref);
+    if (bad) {
+      /* last resort: first order, the cell average with zero gradient */
+      for (int v = 0; v < nv; ++v)
+        for (int gp = 0; gp < R->ngp; ++gp) {
+          ref[v][gp * (1 + dim)] = dat[v][0];
+          for (int k = 0; k < dim; ++k) ref[v][gp * (1 + dim) + 1 + k] = 0.0;
+        }
+    }
   }
   if (record_chi)
     for (int v = 0; v < nv; ++v) c->chi[(long)v * N + id] = chi[v];

@@ -33,10 +33,21 @@ class MeshDesc(C.Structure):
 # boundary kinds of MeshDesc.bc (CGKS_BC_* of include/cgks.h)
 BC_PERIODIC, BC_OUTFLOW, BC_SLIP_WALL, BC_NOSLIP_WALL = 0, 1, 2, 3
 
+class BatchTiles(C.Structure):
+    _fields_ = [("tile_x", C.c_int), ("tile_y", C.c_int), ("recon_blocks", C.c_int), ("flux_blocks", C.c_int),
+                ("update_blocks", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 EXPORTS = ["cgks_create_mesh", "cgks_destroy", "cgks_num_vars", "cgks_num_fields", "cgks_num_cells",
            "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_compute_dt", "cgks_init_points_per_cell",
            "cgks_init_points", "cgks_init_from_prims", "cgks_get_chi", "cgks_profile_enable",
-           "cgks_profile_read", "cgks_last_error", "cgks_compute_dt_noalloc"]
+           "cgks_profile_read", "cgks_last_error", "cgks_compute_dt_noalloc", "cgks_batch_create",
+           "cgks_batch_destroy", "cgks_batch_num_cases", "cgks_batch_num_cells", "cgks_batch_set_state",
+           "cgks_batch_get_state", "cgks_batch_times", "cgks_batch_step", "cgks_batch_get_tiles",
+           "cgks_batch_set_tiles", "cgks_batch_tune", "cgks_batch_last_error"]
 
 _lib = None
 
@@ -72,6 +83,20 @@ def lib(build_if_missing=True):
     L.cgks_profile_read.argtypes = [vp, C.POINTER(C.c_char_p), lp, dp, C.c_int]
     L.cgks_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
     L.cgks_compute_dt_noalloc.argtypes = [C.POINTER(MeshDesc), vp, dp]
+    L.cgks_batch_create.argtypes = [C.POINTER(MeshDesc), C.c_int, vp, C.POINTER(vp)]
+    L.cgks_batch_destroy.argtypes = [vp]
+    L.cgks_batch_destroy.restype = None
+    L.cgks_batch_num_cases.argtypes = [vp]
+    L.cgks_batch_num_cells.argtypes = [vp]
+    L.cgks_batch_num_cells.restype = C.c_long
+    L.cgks_batch_set_state.argtypes = [vp, C.c_int, vp, C.c_int, C.c_double]
+    L.cgks_batch_get_state.argtypes = [vp, C.c_int, vp, C.c_int, dp]
+    L.cgks_batch_times.argtypes = [vp, dp, dp]
+    L.cgks_batch_step.argtypes = [vp, C.c_int, C.c_int]
+    L.cgks_batch_get_tiles.argtypes = [vp, C.POINTER(BatchTiles)]
+    L.cgks_batch_set_tiles.argtypes = [vp, C.POINTER(BatchTiles)]
+    L.cgks_batch_tune.argtypes = [vp, C.c_int, C.POINTER(BatchTiles), dp]
+    L.cgks_batch_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
     _lib = L
     return L
 
@@ -79,6 +104,29 @@ def lib(build_if_missing=True):
 def _torch():
     import torch
     return torch
+
+
+def make_desc(dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=1.4, mu=0.0, prandtl=1.0,
+              tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=0.0, precision=0, bc=None):
+    """A cgks_mesh_desc (and the node array it points to, which the caller
+    keeps alive until the library has copied it)."""
+    d = MeshDesc()
+    d.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    for a in range(3):
+        d.n[a] = int(nn[a])
+        d.lo[a] = float(lo[a]) if a < len(lo) else 0.0
+        d.hi[a] = float(hi[a]) if a < len(hi) else 1.0
+    keep = None
+    if nodes is not None:
+        keep = np.ascontiguousarray(nodes, dtype=np.float64)
+        d.nodes = keep.ctypes.data_as(C.POINTER(C.c_double))
+    d.gamma, d.mu, d.prandtl, d.tau_mode = gamma, mu, prandtl, tau_mode
+    d.cfl, d.dt_fixed, d.linear, d.c_chi = cfl, dt_fixed, int(linear), c_chi
+    for f in range(6):
+        d.bc[f] = int(bc[f]) if bc is not None and f < len(bc) else BC_PERIODIC
+    d.precision = int(precision)
+    return d, keep
 
 
 class Mesh:
@@ -95,22 +143,9 @@ class Mesh:
                  precision=0, bc=None):
         torch = _torch()
         L = lib()
-        d = MeshDesc()
-        d.dim = dim
+        d, self._nodes = make_desc(dim, n, lo, hi, nodes, gamma, mu, prandtl, tau_mode, cfl, dt_fixed, linear, c_chi,
+                                   precision, bc)
         nn = list(n) + [1] * (3 - len(n))
-        for a in range(3):
-            d.n[a] = int(nn[a])
-            d.lo[a] = float(lo[a]) if a < len(lo) else 0.0
-            d.hi[a] = float(hi[a]) if a < len(hi) else 1.0
-        self._nodes = None
-        if nodes is not None:
-            self._nodes = np.ascontiguousarray(nodes, dtype=np.float64)
-            d.nodes = self._nodes.ctypes.data_as(C.POINTER(C.c_double))
-        d.gamma, d.mu, d.prandtl, d.tau_mode = gamma, mu, prandtl, tau_mode
-        d.cfl, d.dt_fixed, d.linear, d.c_chi = cfl, dt_fixed, int(linear), c_chi
-        for f in range(6):
-            d.bc[f] = int(bc[f]) if bc is not None and f < len(bc) else BC_PERIODIC
-        d.precision = int(precision)
         self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         d.stream = C.c_void_p(self.stream.cuda_stream)
@@ -239,3 +274,103 @@ def compute_dt_noalloc(state, dim, n, lo, hi, gamma=1.4, mu=0.0, cfl=0.5, dt_fix
     dt = C.c_double(0.0)
     status = lib().cgks_compute_dt_noalloc(C.byref(d), C.c_void_p(state.data_ptr()), C.byref(dt))
     return status, dt.value
+
+
+class Batch:
+    """Many independent uniform-box meshes (cases) advanced together by the
+    batched kernels: one launch per kernel and phase for all cases, and one
+    CUDA graph launch per call of step().  ``cases`` is a list of dicts of
+    Mesh's keyword arguments (dim, n, lo, hi, bc, gamma, mu, ...); all share
+    dim and ``precision``.  ``stream``: a torch.cuda.Stream (a new one if
+    None: graph capture needs a non-default stream)."""
+
+    def __init__(self, cases, precision=0, stream=None):
+        torch = _torch()
+        L = lib()
+        arr = (MeshDesc * len(cases))()
+        for k, kw in enumerate(cases):
+            kw = dict(kw)
+            if kw.get("nodes") is not None:
+                raise ValueError("batched cases are uniform boxes")
+            d, _ = make_desc(precision=precision, **kw)
+            arr[k] = d
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        self._h = None
+        self._check(L.cgks_batch_create(arr, len(cases), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+        self.ncase = len(cases)
+        self.dims = [(kw["dim"], tuple(int(x) for x in kw["n"][:kw["dim"]])) for kw in cases]
+        self.ncell = L.cgks_batch_num_cells(h)
+        self.precision = int(precision)
+
+    def _check(self, st):
+        if st != 0:
+            msg = ""
+            if self._h:
+                buf = C.create_string_buffer(512)
+                lib().cgks_batch_last_error(self._h, buf, 512)
+                msg = buf.value.decode()
+            raise CgksError(st, msg)
+
+    def close(self):
+        if self._h:
+            lib().cgks_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state_shape(self, k):
+        dim, n = self.dims[k]
+        nf = 1 + dim + dim * (4 if dim == 3 else 2)
+        return (nf, dim + 2) + tuple(reversed(n))
+
+    def set_state(self, k, s, t=0.0):
+        """State of case k: numpy (host) or torch CUDA float64, that case's layout."""
+        torch = _torch()
+        if isinstance(s, torch.Tensor) and s.is_cuda:
+            s = s.contiguous()
+            self._check(lib().cgks_batch_set_state(self._h, int(k), C.c_void_p(s.data_ptr()), 1, float(t)))
+        else:
+            a = np.ascontiguousarray(s, dtype=np.float64)
+            assert a.shape == self.state_shape(k) or a.size == int(np.prod(self.state_shape(k)))
+            self._check(lib().cgks_batch_set_state(self._h, int(k), a.ctypes.data_as(C.c_void_p), 0, float(t)))
+
+    def get_state(self, k):
+        a = np.empty(self.state_shape(k))
+        t = C.c_double(0)
+        self._check(lib().cgks_batch_get_state(self._h, int(k), a.ctypes.data_as(C.c_void_p), 0, C.byref(t)))
+        return a, t.value
+
+    def times(self):
+        t = np.empty(self.ncase)
+        dt = np.empty(self.ncase)
+        self._check(lib().cgks_batch_times(self._h, t.ctypes.data_as(C.POINTER(C.c_double)),
+                                           dt.ctypes.data_as(C.POINTER(C.c_double))))
+        return t, dt
+
+    def step(self, nsteps=1, graph=True):
+        self._check(lib().cgks_batch_step(self._h, int(nsteps), int(bool(graph))))
+
+    def tiles(self):
+        t = BatchTiles()
+        self._check(lib().cgks_batch_get_tiles(self._h, C.byref(t)))
+        return t.as_dict()
+
+    def set_tiles(self, **kw):
+        t = BatchTiles()
+        self._check(lib().cgks_batch_get_tiles(self._h, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        self._check(lib().cgks_batch_set_tiles(self._h, C.byref(t)))
+
+    def tune(self, reps=3):
+        """Run the library's autotuner; returns (chosen tiles, summed phase ms)."""
+        t = BatchTiles()
+        ms = C.c_double(0)
+        self._check(lib().cgks_batch_tune(self._h, int(reps), C.byref(t), C.byref(ms)))
+        return t.as_dict(), ms.value

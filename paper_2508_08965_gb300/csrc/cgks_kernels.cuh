@@ -25,15 +25,43 @@ struct DtState {
    ones keep 2 (they are bound by the FP64 pipe, and spill more when capped) */
 template <typename T> constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
 
+/* first order: every face Gauss-point state of cell c is its cell average
+   with zero gradient (stored where recon_var stores them) */
+template <typename T, int DIM>
+__device__ __noinline__ void first_order_states(const double* __restrict__ avg, const float* __restrict__ avh,
+                                                const float* __restrict__ avl, const DevGeo& g, long c, int i, int j,
+                                                int k, T* __restrict__ gpL, T* __restrict__ gpR) {
+  typedef Sz<DIM> S;
+  const long N = g.ncell;
+  for (int v = 0; v < S::NV; ++v) {
+    T q;
+    if constexpr (sizeof(T) == 4) q = avh[(long)v * N + c] + avl[(long)v * N + c];
+    else q = T(avg[(long)v * N + c]);
+    for (int ax = 0; ax < DIM; ++ax) {
+      int o[3] = {0, 0, 0};
+      o[ax] = -1;
+      const long clo = nbr(g, i, j, k, o[0], o[1], o[2]);
+      for (int side = 0; side < 2; ++side)
+        for (int kq = 0; kq < S::GPF; ++kq) {
+          T* dst = side ? gpL : gpR;
+          const long b = ((long)((ax * S::GPF + kq) * S::NV + v) * (1 + DIM)) * N + (side ? c : clo);
+          dst[b] = q;
+          for (int kk = 0; kk < DIM; ++kk) dst[b + (long)(1 + kk) * N] = T(0);
+        }
+    }
+  }
+}
+
+/* reconstruction of all variables of cell c = (i, j, k), with the
+   positivity fallbacks (shared by the single-case and batched kernels):
+   chi = 0 if a face Gauss-point state has rho <= 0 or p <= 0, then first
+   order if that is not enough either */
 template <typename T, int DIM, bool CURVI, bool WALL>
-__global__ void __launch_bounds__(128, min_blocks<T>())
-    k_recon(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
-            const T* __restrict__ der, DevGeo g, Phys ph, T* __restrict__ gpL, T* __restrict__ gpR,
-            double* __restrict__ chi, int record_chi, int* __restrict__ st) {
-  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
-  int i, j, k;
-  cell_ijk(g, c, i, j, k);
+__device__ __forceinline__ void recon_cell(const double* __restrict__ avg, const float* __restrict__ avh,
+                                           const float* __restrict__ avl, const T* __restrict__ der, const DevGeo& g,
+                                           const Phys& ph, long c, int i, int j, int k, T* __restrict__ gpL,
+                                           T* __restrict__ gpR, double* __restrict__ chi, int record_chi,
+                                           int* __restrict__ st) {
   const int NV = Sz<DIM>::NV;
   const T force = ph.linear ? T(1) : T(-1);
   T cs[NV];
@@ -43,26 +71,37 @@ __global__ void __launch_bounds__(128, min_blocks<T>())
     atomicAdd(&st[ST_FALLBACK], 1);
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, v, T(0), gpL, gpR);
-    if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) atomicOr(&st[ST_NONPHYS], 1);
+    if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) {
+      first_order_states<T, DIM>(avg, avh, avl, g, c, i, j, k, gpL, gpR);
+      if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) atomicOr(&st[ST_NONPHYS], 1);
+    }
   }
   if (record_chi)
     for (int v = 0; v < NV; ++v) chi[(long)v * g.ncell + c] = double(cs[v]);
 }
 
-/* one thread per face slot (the face above cell c along the axis) and
-   Gauss point; slots on a non-periodic high boundary are left to k_flux_bnd */
+template <typename T, int DIM, bool CURVI, bool WALL>
+__global__ void __launch_bounds__(128, min_blocks<T>())
+    k_recon(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
+            const T* __restrict__ der, DevGeo g, Phys ph, T* __restrict__ gpL, T* __restrict__ gpR,
+            double* __restrict__ chi, int record_chi, int* __restrict__ st) {
+  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  int i, j, k;
+  cell_ijk(g, c, i, j, k);
+  recon_cell<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st);
+}
+
+/* face-point item t = (ax * GPF + k) * N + c of a mesh: the face slot above
+   cell c along ax at Gauss point k; slots on a non-periodic high boundary are
+   left to the boundary items */
 template <typename T, int DIM, bool CURVI>
-__global__ void __launch_bounds__(128, min_blocks<T>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
-                                              const T* __restrict__ gpL, const T* __restrict__ gpR,
-                                              T* __restrict__ flux, int* __restrict__ st) {
-  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void flux_item(const DevGeo& g, const Phys& ph, double dt, long t, const T* __restrict__ gpL,
+                                          const T* __restrict__ gpR, T* __restrict__ flux, int* __restrict__ st) {
   const long N = g.ncell;
-  if (t >= (long)DIM * Sz<DIM>::GPF * N) return;
-  long c = t % N;
-  int r = (int)(t / N);
-  int k = r % Sz<DIM>::GPF, ax = r / Sz<DIM>::GPF;
-  const double dt = dts->dt;
-  if (!(dt > 0.0)) return;
+  const long c = t % N;
+  const int r = (int)(t / N);
+  const int k = r % Sz<DIM>::GPF, ax = r / Sz<DIM>::GPF;
   if (geo_bc(g, 2 * ax + 1) != BC_PERIODIC) {
     int ijk[3];
     cell_ijk(g, c, ijk[0], ijk[1], ijk[2]);
@@ -71,19 +110,15 @@ __global__ void __launch_bounds__(128, min_blocks<T>()) k_flux(DevGeo g, Phys ph
   if (!flux_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c, gpL, gpR, flux)) atomicOr(&st[ST_FLUX], 1);
 }
 
-/* the faces on the non-periodic domain boundaries: thread
-   ((side * DIM + ax) * GPF + k) * nplane + plane.  In a plane normal to ax,
-   c0 is the cell on the low boundary and c1 the one on the high boundary;
-   slot c1 holds both c1's high-face state (gpL) and c0's low-face state
-   (gpR).  The high face goes to flux at slot c1, the low face to fxb. */
+/* boundary face-point item t = ((side * DIM + ax) * GPF + k) * nplane + plane.
+   In a plane normal to ax, c0 is the cell on the low boundary and c1 the one
+   on the high boundary; slot c1 holds both c1's high-face state (gpL) and
+   c0's low-face state (gpR).  The high face goes to flux at slot c1, the low
+   face to fxb. */
 template <typename T, int DIM, bool CURVI>
-__global__ void __launch_bounds__(128) k_flux_bnd(DevGeo g, Phys ph, const DtState* __restrict__ dts,
-                                                  const T* __restrict__ gpL, const T* __restrict__ gpR,
-                                                  T* __restrict__ flux, T* __restrict__ fxb, int* __restrict__ st) {
-  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (t >= 2L * DIM * Sz<DIM>::GPF * g.nplane) return;
-  const double dt = dts->dt;
-  if (!(dt > 0.0)) return;
+__device__ __forceinline__ void flux_bnd_item(const DevGeo& g, const Phys& ph, double dt, long t,
+                                              const T* __restrict__ gpL, const T* __restrict__ gpR,
+                                              T* __restrict__ flux, T* __restrict__ fxb, int* __restrict__ st) {
   const long pidx = t % g.nplane;
   int r = (int)(t / g.nplane);
   const int k = r % Sz<DIM>::GPF;
@@ -107,6 +142,31 @@ __global__ void __launch_bounds__(128) k_flux_bnd(DevGeo g, Phys ph, const DtSta
     ok = flux_bnd_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c1, c0, (2 * ax) * Sz<DIM>::GPF + k, 1, bc, gpL, gpR,
                                        fxb, g.nplane, pidx);
   if (!ok) atomicOr(&st[ST_FLUX], 1);
+}
+
+/* one thread per face slot and Gauss point */
+template <typename T, int DIM, bool CURVI>
+__global__ void __launch_bounds__(128, min_blocks<T>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
+                                              const T* __restrict__ gpL, const T* __restrict__ gpR,
+                                              T* __restrict__ flux, int* __restrict__ st) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long N = g.ncell;
+  if (t >= (long)DIM * Sz<DIM>::GPF * N) return;
+  const double dt = dts->dt;
+  if (!(dt > 0.0)) return;
+  flux_item<T, DIM, CURVI>(g, ph, dt, t, gpL, gpR, flux, st);
+}
+
+/* the faces on the non-periodic domain boundaries (flux_bnd_item) */
+template <typename T, int DIM, bool CURVI>
+__global__ void __launch_bounds__(128) k_flux_bnd(DevGeo g, Phys ph, const DtState* __restrict__ dts,
+                                                  const T* __restrict__ gpL, const T* __restrict__ gpR,
+                                                  T* __restrict__ flux, T* __restrict__ fxb, int* __restrict__ st) {
+  long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= 2L * DIM * Sz<DIM>::GPF * g.nplane) return;
+  const double dt = dts->dt;
+  if (!(dt > 0.0)) return;
+  flux_bnd_item<T, DIM, CURVI>(g, ph, dt, t, gpL, gpR, flux, fxb, st);
 }
 
 template <typename T, int DIM, bool CURVI>

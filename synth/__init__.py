@@ -12,3 +12,4 @@ from .fields import (  # noqa: F401
     sod_x, riemann4_2d, riemann4_params, turbulence_velocity_grid,
 )
 from .meshes import uniform_nodes, perturbed_nodes_3d, perturbed_nodes_xy  # noqa: F401
+from .ensemble import ensemble_stream, ensemble_specs, spec_mesh, spec_field  # noqa: F401

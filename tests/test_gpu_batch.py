@@ -1,0 +1,201 @@
+"""The batched ensemble (cgks_batch_*) against the single-case path and the
+oracle.  The batched kernels run the same per-cell and per-face device code
+on per-case slices of concatenated arrays, so each case must reproduce its
+single-case run; one small batch is also checked against the oracle
+directly."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from parity import class_scaled_diff
+
+pytestmark = pytest.mark.gpu
+
+P, OUT, SLIP, NOSLIP = 0, 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_08965_gb300 as p
+    p.lib()
+    return p
+
+
+def s2(x, y):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x + 0.3) * np.cos(2 * np.pi * y)
+    u = 0.3 * np.sin(np.pi * x) + 0.1 * np.cos(2 * np.pi * y + 0.7) * x
+    v = 0.2 * np.cos(2 * np.pi * y) + 0.1 * x
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * x - 0.4)
+    return [rho, u, v, p]
+
+
+def mixed_cases():
+    """(mesh kwargs, field) of uneven 2-D cases covering every boundary kind"""
+    r4 = synth.riemann4_params(3)
+    return [
+        (dict(dim=2, n=(24, 20), lo=(0, 0), hi=(10, 10)), lambda x, y: synth.isentropic_vortex_2d(x, y)),
+        (dict(dim=2, n=(16, 32), lo=(0, 0), hi=(1, 1), bc=[OUT] * 4, tau_mode=1),
+         lambda x, y: synth.riemann4_2d(x, y, r4)),
+        (dict(dim=2, n=(37, 29), lo=(0, 0), hi=(1, 1), bc=[SLIP, SLIP, P, P]), s2),
+        (dict(dim=2, n=(20, 24), lo=(0, 0), hi=(1, 1), bc=[NOSLIP, NOSLIP, OUT, OUT], mu=2e-3, tau_mode=2,
+              prandtl=0.72), s2),
+        (dict(dim=2, n=(64, 8), lo=(0, 0), hi=(10, 10), cfl=0.3),
+         lambda x, y: synth.isentropic_vortex_2d(x, y, eps=2.0, center=(3.0, 6.0))),
+        (dict(dim=2, n=(9, 41), lo=(0, 0), hi=(1, 1), bc=[P, P, NOSLIP, SLIP], tau_mode=1), s2),
+    ]
+
+
+def initial_states(orc, cases):
+    out = []
+    for kw, fn in cases:
+        o = orc.Oracle(**kw)
+        o.init(fn)
+        out.append(o.get_state())
+    return out
+
+
+def singles(cg, cases, states, precision, steps):
+    res = []
+    for (kw, _), s in zip(cases, states):
+        m = cg.Mesh(precision=precision, **kw)
+        m.set_state(s)
+        t, dt = m.step(steps)
+        res.append((m.get_state()[0], t, dt))
+        m.close()
+    return res
+
+
+def batch_of(cg, cases, states, precision):
+    b = cg.Batch([kw for kw, _ in cases], precision=precision)
+    for k, s in enumerate(states):
+        b.set_state(k, s)
+    return b
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_reproduces_single_cases(orc, cg, precision):
+    cases = mixed_cases()
+    states = initial_states(orc, cases)
+    ref = singles(cg, cases, states, precision, 6)
+    b = batch_of(cg, cases, states, precision)
+    b.step(6)
+    t, dt = b.times()
+    tol = 1e-13 if precision == 0 else 1e-5  # FP32: see test_batch_3d
+    for k, (s_ref, t_ref, dt_ref) in enumerate(ref):
+        s, tk = b.get_state(k)
+        h = min(1.0 / x for x in cases[k][0]["n"])
+        assert abs(tk - t_ref) <= 1e-14 * t_ref and abs(dt[k] - dt_ref) <= 1e-14 * dt_ref
+        assert class_scaled_diff(s, s_ref, h) <= tol, k
+    b.close()
+
+
+def test_graph_and_plain_launches_agree(orc, cg):
+    cases = mixed_cases()
+    states = initial_states(orc, cases)
+    b1 = batch_of(cg, cases, states, 1)
+    b2 = batch_of(cg, cases, states, 1)
+    b1.step(3, graph=True)
+    b1.step(3, graph=True)  # replays the captured graph
+    b2.step(6, graph=False)
+    for k in range(len(cases)):
+        assert np.array_equal(b1.get_state(k)[0], b2.get_state(k)[0])
+    b1.close()
+    b2.close()
+
+
+def test_tuner_keeps_state_and_results(orc, cg):
+    cases = mixed_cases()
+    states = initial_states(orc, cases)
+    b = batch_of(cg, cases, states, 1)
+    before = [b.get_state(k) for k in range(len(cases))]
+    tiles, ms = b.tune(reps=2)
+    assert ms > 0 and tiles["tile_x"] * tiles["tile_y"] <= 128
+    for k in range(len(cases)):
+        s, t = b.get_state(k)
+        assert np.array_equal(s, before[k][0]) and t == before[k][1]
+    ref = singles(cg, cases, states, 1, 4)
+    b.step(4)
+    for k, (s_ref, _, _) in enumerate(ref):
+        assert class_scaled_diff(b.get_state(k)[0], s_ref, 0.01) <= 1e-6
+    # every tile shape and grid gives the same result
+    for shape in ((128, 1), (16, 8), (8, 16)):
+        for blocks in (0, 1, 3):
+            bb = batch_of(cg, cases, states, 1)
+            bb.set_tiles(tile_x=shape[0], tile_y=shape[1], recon_blocks=blocks, flux_blocks=blocks,
+                         update_blocks=blocks)
+            bb.step(2)
+            b2 = batch_of(cg, cases, states, 1)
+            b2.step(2)
+            for k in range(len(cases)):
+                assert np.array_equal(bb.get_state(k)[0], b2.get_state(k)[0])
+            bb.close()
+            b2.close()
+    b.close()
+
+
+def test_batch_against_oracle(orc, cg):
+    cases = mixed_cases()[:4]
+    os_ = []
+    for kw, fn in cases:
+        o = orc.Oracle(**kw)
+        o.init(fn)
+        os_.append(o)
+    b = batch_of(cg, cases, [o.get_state() for o in os_], 0)
+    b.step(1)
+    for k, o in enumerate(os_):
+        o.step(1)
+        h = min(1.0 / x for x in cases[k][0]["n"])
+        assert class_scaled_diff(b.get_state(k)[0], o.get_state(), h) <= 1e-12
+    b.close()
+
+
+def test_batch_3d(orc, cg):
+    kw = dict(mu=1 / 1600, prandtl=0.72, tau_mode=2)
+    cases = [(dict(dim=3, n=(8, 8, 8), lo=(0, 0, 0), hi=(2 * math.pi,) * 3, **kw),
+              lambda x, y, z: synth.taylor_green_3d(x, y, z)),
+             (dict(dim=3, n=(6, 7, 9), lo=(0, 0, 0), hi=(2 * math.pi,) * 3, bc=[SLIP, SLIP, P, P, OUT, OUT], **kw),
+              lambda x, y, z: synth.taylor_green_3d(x, y, z))]
+    states = initial_states(orc, cases)
+    for precision in (0, 1):
+        ref = singles(cg, cases, states, precision, 2)
+        b = batch_of(cg, cases, states, precision)
+        b.step(2)
+        for k, (s_ref, _, _) in enumerate(ref):
+            # FP32: two FP32-form runs whose kernels the compiler may contract
+            # differently (FMA or not) differ at FP32 rounding, well inside the
+            # form's error against FP64
+            tol = 1e-13 if precision == 0 else 1e-5
+            assert class_scaled_diff(b.get_state(k)[0], s_ref, 2 * math.pi / 9) <= tol
+        b.close()
+
+
+def test_batch_rejects_bad_input(cg):
+    with pytest.raises(cg.CgksError):
+        cg.Batch([dict(dim=2, n=(8, 8)), dict(dim=3, n=(8, 8, 8))])
+    with pytest.raises(cg.CgksError):
+        cg.Batch([dict(dim=2, n=(8, 8), bc=[SLIP, P, P, P])])
+
+
+def test_ensemble_specs_build(cg):
+    """A slice of the seeded 256-case ensemble initialises and steps."""
+    import torch
+    specs = synth.ensemble_specs(256)[:6]
+    kws = [synth.spec_mesh(s) for s in specs]
+    b = cg.Batch(kws, precision=1)
+    for k, s in enumerate(specs):
+        m = cg.Mesh(precision=1, **kws[k])
+        m.init(synth.spec_field(s))
+        st = torch.empty(b.state_shape(k), dtype=torch.float64, device="cuda")
+        m.get_state(out=st)
+        b.set_state(k, st)
+        m.close()
+    b.tune(reps=1)
+    b.step(2)
+    t, dt = b.times()
+    assert np.all(t > 0) and np.all(np.isfinite(t))
+    b.close()

@@ -175,3 +175,21 @@ def test_bad_boundary_codes_rejected(orc):
         orc.Oracle(2, (4, 4), bc=[7, 7, 0, 0])
     with pytest.raises(RuntimeError):
         orc.Oracle(2, (4, 4), bc=[SLIP, 0, 0, 0])
+
+
+def test_strong_riemann_first_order_fallback(orc):
+    """Four-quadrant data whose jumps defeat even the chi = 0 polynomial in
+    the first step: the first-order fallback keeps every average physical
+    (rho > 0, p > 0) and the domain sums of an outflow box change only
+    through the boundary."""
+    import synth
+    states = synth.riemann4_params(328031897)
+    o = orc.Oracle(2, (32, 32), bc=[OUTFLOW] * 4, tau_mode=1)
+    o.init(lambda x, y: synth.riemann4_2d(x, y, states))
+    for _ in range(20):
+        o.step(1)
+    s = o.get_state()
+    rho, m, E = s[0, 0], s[0, 1:3], s[0, 3]
+    p = 0.4 * (E - 0.5 * (m * m).sum(0) / rho)
+    assert o.positivity_fallbacks() > 0
+    assert rho.min() > 0 and p.min() > 0 and np.all(np.isfinite(s))
