@@ -340,6 +340,71 @@ def ensemble_bench(args, stream, ncase=256):
     }
 
 
+def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
+    """The learned selector (FP32 form): held-out four-quadrant Riemann
+    problems on 1024^2 and the TGV 128^3, each with and without the trained
+    selector from the same initial state: time per step and per
+    reconstruction, skip and low-confidence rates, and the density difference
+    from the plain adaptive method."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2508_08965_gb300 import CgksError, Mesh, selector
+    params, thr, lo = selector.load()
+    out = {"thr_skip": thr, "thr_lo": lo, "cases": []}
+
+    def run(kw, fn, s0, steps, on):
+        m = Mesh(precision=1, stream=stream, **kw)
+        if s0 is None:
+            m.init(fn)
+        else:
+            m.set_state(s0, 0.0)
+        if on:
+            m.set_selector(params, thr, lo)
+        m.step(args.warmup)
+        m.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = m.profile_read()
+        stats = m.selector_stats() if on else (0, 0)
+        s, _ = m.get_state()
+        m.close()
+        return s, e0.elapsed_time(e1) / steps, prof["recon"][1] / prof["recon"][0], stats
+
+    cases = []
+    for seed in (9001, 9002, 9003, 9004):
+        st = synth.riemann4_params(seed)
+        cases.append(("riemann1024 seed %d" % seed,
+                      dict(dim=2, n=(1024, 1024), lo=(0, 0), hi=(1, 1), bc=[1, 1, 1, 1], tau_mode=1),
+                      (lambda st: (lambda x, y: synth.riemann4_2d(x, y, st)))(st), None))
+    cases.append(("tgv128", dict(dim=3, n=(128, 128, 128), **mesh_kwargs("tgv128")), field_fn("tgv128"), s_tgv_init))
+    for name, kw, fn, s0 in cases:
+        try:
+            s_plain, ms0, rc0, _ = run(kw, fn, s0, args.steps, False)
+            s_sel, ms1, rc1, (nskip, nuns) = run(kw, fn, s0, args.steps, True)
+        except CgksError as ex:
+            out["cases"].append({"case": name, "error": str(ex)})
+            continue
+        ncell = int(np.prod(kw["n"]))
+        recons = 2 * (args.warmup + args.steps) * ncell
+        e = s_sel[0, 0] - s_plain[0, 0]
+        rec = {"case": name, "ms_per_step": {"plain": ms0, "selector": ms1}, "speedup": ms0 / ms1,
+               "recon_ms": {"plain": rc0, "selector": rc1},
+               "skip_rate": nskip / recons, "low_confidence_rate": nuns / recons,
+               "density_l2_vs_plain": float(np.sqrt(np.mean(e * e) / np.mean(s_plain[0, 0] ** 2))),
+               "density_linf_vs_plain": float(np.abs(e).max() / np.abs(s_plain[0, 0]).max())}
+        if name == "tgv128" and s_tgv_fp64 is not None:
+            d = s_sel[0, 0] - s_tgv_fp64[0, 0]
+            rec["density_l2_vs_fp64"] = float(np.sqrt(np.mean(d * d)))
+            rec["value"] = ncell / (ms1 / 1e3)
+        out["cases"].append(rec)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,6 +416,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-selector", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -481,6 +547,15 @@ def main():
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
         "forms": forms,
     }
+    if not args.no_selector:
+        line["selector"] = selector_bench(args, stream, s_init, s_fp64)
+        tg = [c for c in line["selector"]["cases"] if c["case"] == "tgv128" and "value" in c]
+        if tg and "fp32" in forms:
+            forms["fp32_learned"] = {"value": tg[0]["value"], "unit": "cell-updates/s",
+                                     "ms_per_step": tg[0]["ms_per_step"]["selector"],
+                                     "speedup_vs_fp64": (ms / args.steps) / tg[0]["ms_per_step"]["selector"],
+                                     "density_l2_vs_fp64": tg[0].get("density_l2_vs_fp64"),
+                                     "skip_rate": tg[0]["skip_rate"]}
     if not args.no_ensemble:
         line["ensemble"] = ensemble_bench(args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -221,6 +221,51 @@ cgks_status cgks_batch_set_tiles(cgks_batch* b, const cgks_batch_tiles* t);
 cgks_status cgks_batch_tune(cgks_batch* b, int reps, cgks_batch_tiles* chosen, double* ms_best);
 cgks_status cgks_batch_last_error(const cgks_batch* b, char* msg, size_t cap);
 
+/* ---- Learned troubled-cell selector ---------------------------------------
+   Not in the paper (its GENO weights, Sec. 3.3, run on every cell).  A small
+   network predicts from 16 normalised stencil features of a cell (face jumps,
+   second-difference ratios, line-derivative spread and mismatch, pooled per
+   variable class) whether the cell can skip the adaptive weights and take the
+   fifth-order polynomial directly (chi = 1 for all its variables).  Inference
+   runs inside the reconstruction kernel in BF16 on the tensor cores (weights
+   and features rounded to BF16, FP32 sums).  A cell whose logit reaches
+   thr_skip skips; below it (low confidence, or a predicted troubled cell) the
+   full GENO weights run as without the selector; the positivity fallbacks
+   apply either way.
+   params (host): CGKS_SEL_NPARAM floats, W1[32][16] b1[32] W2[32][32] b2[32]
+   W3[32][32] b3[32] w4[32] b4, row-major [out][in]; NULL switches the
+   selector off.  thr_lo <= thr_skip (else CGKS_EINVAL) only splits the
+   non-skipped cells into low-confidence (thr_lo < logit) and confident
+   troubled cells for the counters. */
+#define CGKS_SEL_NFEAT 16
+#define CGKS_SEL_NPARAM 2689
+cgks_status cgks_set_selector(cgks_ctx* ctx, const float* params, float thr_skip, float thr_lo);
+/* Cell reconstructions that skipped, and that ran GENO with low confidence,
+   since the selector was set (both stages of every step). */
+cgks_status cgks_selector_stats(cgks_ctx* ctx, unsigned long long* skips, unsigned long long* unsure);
+/* The 16 features of every cell of the current state into dev_out (device,
+   ncell x 16 floats, cell-major): training samples.  Synchronises. */
+cgks_status cgks_selector_features(cgks_ctx* ctx, float* dev_out);
+cgks_status cgks_batch_set_selector(cgks_batch* b, const float* params, float thr_skip, float thr_lo);
+cgks_status cgks_batch_selector_stats(cgks_batch* b, unsigned long long* skips, unsigned long long* unsure);
+
+/* Training arithmetic of the selector network, FP32 on device buffers
+   (stream: cudaStream_t or NULL).  Loss: the weighted binary cross-entropy of
+   the logits, sum_s w_s (softplus(z_s) - y_s z_s) / sum_s w_s.
+   cgks_mlp_loss_grad: X [n][16], labels y and weights w [n] (device); writes
+   the gradient (CGKS_SEL_NPARAM floats, device) and *loss_out (host).
+   Blocked sums in a fixed order (deterministic); allocates its work space
+   stream-ordered and synchronises the stream.
+   cgks_mlp_logits: logits [n] (device), FP32 forward pass.
+   cgks_mlp_adam: one Adam update of params with first/second moments m, v
+   (device, zero before step 1); step counts from 1. */
+cgks_status cgks_mlp_loss_grad(const float* dev_params, const float* dev_X, const float* dev_y, const float* dev_w,
+                               long n, float* dev_grad, float* loss_out, void* stream);
+cgks_status cgks_mlp_logits(const float* dev_params, const float* dev_X, long n, float* dev_out, void* stream);
+cgks_status cgks_mlp_adam(float* dev_params, const float* dev_grad, float* dev_m, float* dev_v, int step, float lr,
+                          float beta1, float beta2, float eps, void* stream);
+
+
 #ifdef __cplusplus
 }
 #endif

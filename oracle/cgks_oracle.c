@@ -14,6 +14,7 @@
 
 #include <math.h>
 #include <stdlib.h>
+#include <stdint.h>
 #include <string.h>
 
 #define NB3 34 /* quartic zero-mean basis size in 3-D (Eq. base, 1 <= |d| <= 4) */
@@ -742,6 +743,9 @@ struct orc_ctx {
   double* fxlo;   /* low boundary faces of non-periodic axes */
   double* L1; double* Lt1; double* D1; double* L2; double* Lt2; double* Dt;
   int err;
+  struct selector* sel; /* learned troubled-cell selector, or NULL */
+  long nskip, nunsure;  /* selector decisions since orc_set_selector */
+  double margin;        /* smallest |logit - threshold| seen */
 };
 
 static long cidx(const orc_ctx* c, int i, int j, int k) {
@@ -929,6 +933,7 @@ orc_ctx* orc_create(const orc_desc* d) {
 void orc_destroy(orc_ctx* c) {
   if (!c) return;
   free(c->nodes); free(c->geo); free(c->U); free(c->chi); free(c->gpv); free(c->fx); free(c->fxlo);
+  free(c->sel);
   free(c->L1); free(c->Lt1); free(c->L2); free(c->Lt2); free(c->D1); free(c->Dt);
   free(c);
 }
@@ -1162,6 +1167,150 @@ static int gp_states_physical(const ref_t* R, double gamma, double ref[MAXV][MAX
   return 1;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Learned troubled-cell selector (not in the paper; test reference for the */
+/* library's fused selector).  Per cell, 16 features from the face-neighbour */
+/* averages and the cell's own line derivatives, computed in float with the */
+/* rounding of each operation fixed; a 16-32-32-32-1 ReLU network evaluated */
+/* with BF16 inputs and weights and float sums; skip (chi = 1 for every      */
+/* variable) when the logit reaches thr_skip.                                */
+/* ------------------------------------------------------------------------ */
+#define SEL_NF 16
+#define SEL_H 32
+#define SEL_NPARAM (SEL_H * SEL_NF + SEL_H + 2 * (SEL_H * SEL_H + SEL_H) + SEL_H + 1)
+
+struct selector {
+  float p[SEL_NPARAM]; /* W1[32][16] b1[32] W2[32][32] b2 W3[32][32] b3 w4[32] b4 */
+  float thr_skip, thr_lo;
+};
+
+/* features of cell id of state S: per variable class (density, momentum,
+   energy) the largest normalised face jump J, corner (edge-neighbour) jump E,
+   second-difference ratio R, spread of the line differences S and their
+   mismatch with the central difference C, and over all variables the largest
+   normalised jump G of a gradient component between the cell and a face
+   neighbour; J, E, S, C, G mapped by x/(1+x).  Normalising by the scale is a
+   multiplication by its float reciprocal (J, E, S, G) or a division (R, C). */
+static void sel_features(const orc_ctx* c, const double* S, long id, float* f) {
+  const int dim = c->dim, nv = c->nv, gpf = c->R->gpf;
+  const long N = c->ncell;
+  const cellgeo_t* G = &c->geo[id];
+  float q0[MAXV];
+  for (int v = 0; v < nv; ++v) q0[v] = (float)S[(long)v * N + id];
+  float fj[3] = {0, 0, 0}, fe[3] = {0, 0, 0}, fr[3] = {0, 0, 0}, fs[3] = {0, 0, 0}, fc[3] = {0, 0, 0};
+  float fg = 0.0f;
+  for (int v = 0; v < nv; ++v) {
+    const int cls = v == 0 ? 0 : (v == nv - 1 ? 2 : 1);
+    float scale = fabsf(q0[v]);
+    if (cls == 1) scale = scale + sqrtf(fabsf(q0[0]) * fabsf(q0[nv - 1]));
+    const float inv = 1.0f / scale;
+    for (int a = 0; a < dim; ++a) {
+      float qn[2];
+      for (int sd = 0; sd < 2; ++sd) {
+        int o[3] = {0, 0, 0};
+        o[a] = sd ? 1 : -1;
+        int mi, ns;
+        const long nb = nbr_bc(c, id, o, &mi, &ns);
+        float q = (float)S[(long)v * N + nb];
+        if (mirror_sign(dim, v, -1, mi, ns) < 0) q = -q;
+        qn[sd] = q;
+        for (int k = 0; k < dim; ++k) {
+          float gm = (float)S[((long)(1 + k) * nv + v) * N + nb];
+          if (mirror_sign(dim, v, k, mi, ns) < 0) gm = -gm;
+          const float g0 = (float)S[((long)(1 + k) * nv + v) * N + id];
+          const float gd = (fabsf(gm - g0) * (float)G->len[k * gpf]) * inv;
+          fg = fmaxf(fg, gd);
+        }
+      }
+      const float dm = q0[v] - qn[0], dp = qn[1] - q0[v];
+      const float adm = fabsf(dm), adp = fabsf(dp);
+      const float J = fmaxf(adm, adp) * inv;
+      const float den = (adm + adp) + 1e-7f * scale;
+      const float Rr = fabsf(dp - dm) / den;
+      float lsum = 0.0f, lmin = 0.0f, lmax = 0.0f;
+      for (int k = 0; k < gpf; ++k) {
+        const int sl = a * gpf + k;
+        const float lh = (float)S[((long)(1 + dim + sl) * nv + v) * N + id] * (float)G->len[sl];
+        lsum = lsum + lh;
+        if (k == 0 || lh < lmin) lmin = lh;
+        if (k == 0 || lh > lmax) lmax = lh;
+      }
+      const float lhm = lsum * (1.0f / (float)gpf);
+      const float sp = (lmax - lmin) * inv;
+      const float cd = (dp + dm) * 0.5f;
+      const float Cm = fabsf(lhm - cd) / den;
+      fj[cls] = fmaxf(fj[cls], J);
+      fr[cls] = fmaxf(fr[cls], Rr);
+      fs[cls] = fmaxf(fs[cls], sp);
+      fc[cls] = fmaxf(fc[cls], Cm);
+      /* edge neighbours across axes a < b */
+      for (int b = a + 1; b < dim; ++b)
+        for (int sg = 0; sg < 4; ++sg) {
+          int o[3] = {0, 0, 0};
+          o[a] = (sg & 1) ? 1 : -1;
+          o[b] = (sg & 2) ? 1 : -1;
+          int mi, ns;
+          const long nb = nbr_bc(c, id, o, &mi, &ns);
+          float q = (float)S[(long)v * N + nb];
+          if (mirror_sign(dim, v, -1, mi, ns) < 0) q = -q;
+          fe[cls] = fmaxf(fe[cls], fabsf(q - q0[v]) * inv);
+        }
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    f[5 * k + 0] = fj[k] / (1.0f + fj[k]);
+    f[5 * k + 1] = fe[k] / (1.0f + fe[k]);
+    f[5 * k + 2] = fr[k];
+    f[5 * k + 3] = fs[k] / (1.0f + fs[k]);
+    f[5 * k + 4] = fc[k] / (1.0f + fc[k]);
+  }
+  f[15] = fg / (1.0f + fg);
+}
+
+/* round a float to the nearest bfloat16 (ties to even), kept as a float */
+static float bf16r(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  memcpy(&x, &u, 4);
+  return x;
+}
+
+static float sel_logit(const struct selector* sl, const float* feat) {
+  const float* W1 = sl->p;
+  const float* b1 = W1 + SEL_H * SEL_NF;
+  const float* W2 = b1 + SEL_H;
+  const float* b2 = W2 + SEL_H * SEL_H;
+  const float* W3 = b2 + SEL_H;
+  const float* b3 = W3 + SEL_H * SEL_H;
+  const float* w4 = b3 + SEL_H;
+  const float b4 = w4[SEL_H];
+  float x[SEL_NF], h1[SEL_H], h2[SEL_H], h3[SEL_H];
+  for (int k = 0; k < SEL_NF; ++k) x[k] = bf16r(feat[k]);
+  for (int o = 0; o < SEL_H; ++o) {
+    float acc = 0.0f;
+    for (int k = 0; k < SEL_NF; ++k) acc = acc + bf16r(W1[o * SEL_NF + k]) * x[k];
+    const float z = acc + b1[o];
+    h1[o] = bf16r(z > 0.0f ? z : 0.0f);
+  }
+  for (int o = 0; o < SEL_H; ++o) {
+    float acc = 0.0f;
+    for (int k = 0; k < SEL_H; ++k) acc = acc + bf16r(W2[o * SEL_H + k]) * h1[k];
+    const float z = acc + b2[o];
+    h2[o] = bf16r(z > 0.0f ? z : 0.0f);
+  }
+  for (int o = 0; o < SEL_H; ++o) {
+    float acc = 0.0f;
+    for (int k = 0; k < SEL_H; ++k) acc = acc + bf16r(W3[o * SEL_H + k]) * h2[k];
+    const float z = acc + b3[o];
+    h3[o] = bf16r(z > 0.0f ? z : 0.0f);
+  }
+  float acc = 0.0f;
+  for (int k = 0; k < SEL_H; ++k) acc = acc + bf16r(w4[k]) * h3[k];
+  return acc + b4;
+}
+
 /* reconstruct all variables of one cell at its face Gauss points, physical
    gradients (reverse transform of Sec. 4); positivity fallback forces chi = 0 */
 static void recon_cell(orc_ctx* c, const double* S, long id, int record_chi) {
@@ -1206,6 +1355,19 @@ static void recon_cell(orc_ctx* c, const double* S, long id, int record_chi) {
   double ref[MAXV][MAXGP * 4];
   double chi[MAXV];
   double force = c->d.linear ? 1.0 : -1.0;
+  if (c->sel && !c->d.linear) {
+    float feat[SEL_NF];
+    sel_features(c, S, id, feat);
+    const float lg = sel_logit(c->sel, feat);
+    const double mg = fmin(fabs((double)lg - c->sel->thr_skip), fabs((double)lg - c->sel->thr_lo));
+#pragma omp critical(orc_selector)
+    {
+      if (lg >= c->sel->thr_skip) c->nskip++;
+      else if (lg > c->sel->thr_lo) c->nunsure++;
+      if (mg < c->margin) c->margin = mg;
+    }
+    if (lg >= c->sel->thr_skip) force = 1.0; /* skip the adaptive weights: P4 alone */
+  }
   for (int v = 0; v < nv; ++v) recon_var(R, dat[v], force, c->d.c_chi, ref[v], &chi[v]);
   /* positivity of the reconstructed Gauss-point states */
   int bad = !gp_states_physical(R, c->d.gamma, ref);
@@ -1467,6 +1629,43 @@ static int step_impl(orc_ctx* c, int nsteps, double dt_given, double* dt_last) {
 
 int orc_step(orc_ctx* c, int nsteps, double* dt_last) { return step_impl(c, nsteps, 0.0, dt_last); }
 int orc_step_dt(orc_ctx* c, double dt) { return step_impl(c, 1, dt, NULL); }
+
+int orc_set_selector(orc_ctx* c, const float* params, float thr_skip, float thr_lo) {
+  free(c->sel);
+  c->sel = NULL;
+  c->nskip = c->nunsure = 0;
+  c->margin = 1e300;
+  if (!params) return 0;
+  c->sel = malloc(sizeof(struct selector));
+  memcpy(c->sel->p, params, sizeof(float) * SEL_NPARAM);
+  c->sel->thr_skip = thr_skip;
+  c->sel->thr_lo = thr_lo;
+  return 0;
+}
+
+int orc_selector_stats(const orc_ctx* c, long* nskip, long* nunsure, double* margin) {
+  *nskip = c->nskip;
+  *nunsure = c->nunsure;
+  *margin = c->margin;
+  return 0;
+}
+
+/* features of every cell of the current state, [cell][16] */
+int orc_selector_features(const orc_ctx* c, float* out) {
+#pragma omp parallel for schedule(static)
+  for (long id = 0; id < c->ncell; ++id) sel_features(c, c->U, id, out + id * SEL_NF);
+  return 0;
+}
+
+/* the emulated BF16 logit of given features (unit-level) */
+int orc_selector_logits(const float* params, const float* feat, long n, float* out) {
+  struct selector sl;
+  memcpy(sl.p, params, sizeof(float) * SEL_NPARAM);
+  for (long i = 0; i < n; ++i) out[i] = sel_logit(&sl, feat + i * SEL_NF);
+  return 0;
+}
+
+int orc_selector_nparam(void) { return SEL_NPARAM; }
 
 int orc_get_chi(const orc_ctx* c, double* chi) {
   memcpy(chi, c->chi, sizeof(double) * c->nv * c->ncell);

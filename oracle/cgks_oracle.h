@@ -58,6 +58,16 @@ int orc_step_dt(orc_ctx* c, double dt);
 /* cell-wise chi of the first stage of the last step, [v][cell] */
 int orc_get_chi(const orc_ctx* c, double* chi);
 long orc_positivity_fallbacks(const orc_ctx* c);
+
+/* learned troubled-cell selector (not in the paper; reference for the
+   library's fused selector): params = SEL_NPARAM floats (W1[32][16] b1
+   W2[32][32] b2 W3[32][32] b3 w4[32] b4), NULL switches it off; a cell whose
+   BF16-emulated logit reaches thr_skip takes chi = 1 for every variable */
+int orc_set_selector(orc_ctx* c, const float* params, float thr_skip, float thr_lo);
+int orc_selector_stats(const orc_ctx* c, long* nskip, long* nunsure, double* margin);
+int orc_selector_features(const orc_ctx* c, float* out);
+int orc_selector_logits(const float* params, const float* feat, long n, float* out);
+int orc_selector_nparam(void);
 /* metric quantities: volume per cell and sum over faces of the area vectors */
 int orc_get_metrics(const orc_ctx* c, double* vol, double* closure /* ncell*dim */);
 

@@ -61,6 +61,11 @@ def lib():
         L.orc_positivity_fallbacks.restype = C.c_long
         L.orc_positivity_fallbacks.argtypes = [C.c_void_p]
         L.orc_get_metrics.argtypes = [C.c_void_p, dp, dp]
+        fp = C.POINTER(C.c_float)
+        L.orc_set_selector.argtypes = [C.c_void_p, fp, C.c_float, C.c_float]
+        L.orc_selector_stats.argtypes = [C.c_void_p, C.POINTER(C.c_long), C.POINTER(C.c_long), dp]
+        L.orc_selector_features.argtypes = [C.c_void_p, fp]
+        L.orc_selector_logits.argtypes = [fp, fp, C.c_long, fp]
         L.orc_basis_size.argtypes = [C.c_int]
         L.orc_data_size.argtypes = [C.c_int]
         L.orc_recon_matrix.argtypes = [C.c_int, dp, ip]
@@ -190,6 +195,26 @@ class Oracle:
     def positivity_fallbacks(self):
         return lib().orc_positivity_fallbacks(self._h)
 
+    def set_selector(self, params=None, thr_skip=0.0, thr_lo=0.0):
+        """Learned selector on (params: SEL_NPARAM floats) or off (None)."""
+        fp = C.POINTER(C.c_float)
+        if params is None:
+            lib().orc_set_selector(self._h, None, 0.0, 0.0)
+            return
+        self._sel = np.ascontiguousarray(params, dtype=np.float32)
+        assert self._sel.size == selector_nparam()
+        lib().orc_set_selector(self._h, self._sel.ctypes.data_as(fp), float(thr_skip), float(thr_lo))
+
+    def selector_stats(self):
+        a, b, m = C.c_long(0), C.c_long(0), C.c_double(0)
+        lib().orc_selector_stats(self._h, C.byref(a), C.byref(b), C.byref(m))
+        return a.value, b.value, m.value
+
+    def selector_features(self):
+        out = np.empty((self.ncell, 16), dtype=np.float32)
+        lib().orc_selector_features(self._h, out.ctypes.data_as(C.POINTER(C.c_float)))
+        return out
+
     def metrics(self):
         vol = np.empty(self.ncell)
         clo = np.empty((self.ncell, self.dim))
@@ -270,3 +295,18 @@ def s2o4(Q, dt, L, Lt, Lt_star=None):
     if Lt_star is None:
         return qs
     return qs, lb.orc_s2o4_stage2(Q, dt, L, Lt, Lt_star)
+
+
+def selector_nparam():
+    return lib().orc_selector_nparam()
+
+
+def selector_logits(params, feat):
+    """BF16-emulated logits of the selector network for features [n][16]."""
+    fp = C.POINTER(C.c_float)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    feat = np.ascontiguousarray(feat, dtype=np.float32)
+    out = np.empty(feat.shape[0], dtype=np.float32)
+    lib().orc_selector_logits(params.ctypes.data_as(fp), feat.ctypes.data_as(fp), feat.shape[0],
+                              out.ctypes.data_as(fp))
+    return out

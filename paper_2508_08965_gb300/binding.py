@@ -33,6 +33,45 @@ class MeshDesc(C.Structure):
 # boundary kinds of MeshDesc.bc (CGKS_BC_* of include/cgks.h)
 BC_PERIODIC, BC_OUTFLOW, BC_SLIP_WALL, BC_NOSLIP_WALL = 0, 1, 2, 3
 
+SEL_NFEAT, SEL_NPARAM = 16, 2689
+
+
+def mlp_loss_grad(params, X, y, w, grad, stream=None):
+    """Weighted BCE loss of the selector network and its gradient (into
+    `grad`), all torch CUDA float32 tensors; returns the loss."""
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    loss = C.c_float(0)
+    status = lib().cgks_mlp_loss_grad(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()),
+                                      C.c_void_p(y.data_ptr()), C.c_void_p(w.data_ptr()), int(X.shape[0]),
+                                      C.c_void_p(grad.data_ptr()), C.byref(loss), C.c_void_p(st.cuda_stream))
+    if status:
+        raise CgksError(status, "cgks_mlp_loss_grad")
+    return loss.value
+
+
+def mlp_logits(params, X, out=None, stream=None):
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    if out is None:
+        out = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    status = lib().cgks_mlp_logits(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()), int(X.shape[0]),
+                                   C.c_void_p(out.data_ptr()), C.c_void_p(st.cuda_stream))
+    if status:
+        raise CgksError(status, "cgks_mlp_logits")
+    return out
+
+
+def mlp_adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    status = lib().cgks_mlp_adam(C.c_void_p(params.data_ptr()), C.c_void_p(grad.data_ptr()), C.c_void_p(m.data_ptr()),
+                                 C.c_void_p(v.data_ptr()), int(step), float(lr), float(beta1), float(beta2),
+                                 float(eps), C.c_void_p(st.cuda_stream))
+    if status:
+        raise CgksError(status, "cgks_mlp_adam")
+
+
 class BatchTiles(C.Structure):
     _fields_ = [("tile_x", C.c_int), ("tile_y", C.c_int), ("recon_blocks", C.c_int), ("flux_blocks", C.c_int),
                 ("update_blocks", C.c_int)]
@@ -47,7 +86,9 @@ EXPORTS = ["cgks_create_mesh", "cgks_destroy", "cgks_num_vars", "cgks_num_fields
            "cgks_profile_read", "cgks_last_error", "cgks_compute_dt_noalloc", "cgks_batch_create",
            "cgks_batch_destroy", "cgks_batch_num_cases", "cgks_batch_num_cells", "cgks_batch_set_state",
            "cgks_batch_get_state", "cgks_batch_times", "cgks_batch_step", "cgks_batch_get_tiles",
-           "cgks_batch_set_tiles", "cgks_batch_tune", "cgks_batch_last_error"]
+           "cgks_batch_set_tiles", "cgks_batch_tune", "cgks_batch_last_error", "cgks_set_selector",
+           "cgks_selector_stats", "cgks_selector_features", "cgks_batch_set_selector", "cgks_batch_selector_stats",
+           "cgks_mlp_loss_grad", "cgks_mlp_logits", "cgks_mlp_adam"]
 
 _lib = None
 
@@ -97,6 +138,16 @@ def lib(build_if_missing=True):
     L.cgks_batch_set_tiles.argtypes = [vp, C.POINTER(BatchTiles)]
     L.cgks_batch_tune.argtypes = [vp, C.c_int, C.POINTER(BatchTiles), dp]
     L.cgks_batch_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
+    fp = C.POINTER(C.c_float)
+    ull = C.POINTER(C.c_ulonglong)
+    L.cgks_set_selector.argtypes = [vp, fp, C.c_float, C.c_float]
+    L.cgks_selector_stats.argtypes = [vp, ull, ull]
+    L.cgks_selector_features.argtypes = [vp, vp]
+    L.cgks_batch_set_selector.argtypes = [vp, fp, C.c_float, C.c_float]
+    L.cgks_batch_selector_stats.argtypes = [vp, ull, ull]
+    L.cgks_mlp_loss_grad.argtypes = [vp, vp, vp, vp, C.c_long, vp, fp, vp]
+    L.cgks_mlp_logits.argtypes = [vp, vp, C.c_long, vp, vp]
+    L.cgks_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, vp]
     _lib = L
     return L
 
@@ -222,10 +273,38 @@ class Mesh:
         self._check(lib().cgks_compute_dt(self._h, C.byref(dt)))
         return dt.value
 
-    def chi(self):
+    def chi(self, out=None):
+        """GENO weights of stage 1 of the last step, [v][cell] (host numpy, or
+        into a torch CUDA float64 tensor `out`)."""
+        if out is not None:
+            self._check(lib().cgks_get_chi(self._h, C.c_void_p(out.data_ptr()), 1))
+            return out
         a = np.empty((self.nv,) + tuple(reversed(self.n)))
         self._check(lib().cgks_get_chi(self._h, a.ctypes.data_as(C.c_void_p), 0))
         return a
+
+    def set_selector(self, params=None, thr_skip=0.0, thr_lo=0.0):
+        """Learned troubled-cell selector on (params: CGKS_SEL_NPARAM floats) or off (None)."""
+        if params is None:
+            self._check(lib().cgks_set_selector(self._h, None, 0.0, 0.0))
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == SEL_NPARAM
+        self._check(lib().cgks_set_selector(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), float(thr_skip),
+                                            float(thr_lo)))
+
+    def selector_stats(self):
+        a, b = C.c_ulonglong(0), C.c_ulonglong(0)
+        self._check(lib().cgks_selector_stats(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def selector_features(self, out=None):
+        """Features of every cell of the current state: torch CUDA float32 [ncell][16]."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.ncell, SEL_NFEAT), dtype=torch.float32, device="cuda")
+        self._check(lib().cgks_selector_features(self._h, C.c_void_p(out.data_ptr())))
+        return out
 
     def init(self, field_fn, chunk_cells=1 << 18):
         """Initial data from a point function field_fn(*coords) -> [rho, U, V[, W], p]
@@ -367,6 +446,19 @@ class Batch:
         for k, v in kw.items():
             setattr(t, k, int(v))
         self._check(lib().cgks_batch_set_tiles(self._h, C.byref(t)))
+
+    def set_selector(self, params=None, thr_skip=0.0, thr_lo=0.0):
+        if params is None:
+            self._check(lib().cgks_batch_set_selector(self._h, None, 0.0, 0.0))
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(lib().cgks_batch_set_selector(self._h, p.ctypes.data_as(C.POINTER(C.c_float)),
+                                                  float(thr_skip), float(thr_lo)))
+
+    def selector_stats(self):
+        a, b = C.c_ulonglong(0), C.c_ulonglong(0)
+        self._check(lib().cgks_batch_selector_stats(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def tune(self, reps=3):
         """Run the library's autotuner; returns (chosen tiles, summed phase ms)."""

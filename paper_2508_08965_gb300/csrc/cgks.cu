@@ -277,6 +277,7 @@ void cgks_destroy(cgks_ctx* ctx) {
   cudaFree(ctx->d_nodes);
   cudaFree(ctx->d_met);
   cudaFree(ctx->d_rmet);
+  cudaFree(ctx->sel_buf);
   for (auto e : ctx->prof.pool) cudaEventDestroy(e);
   delete ctx;
 }
@@ -449,6 +450,118 @@ int cgks_profile_read(cgks_ctx* ctx, const char** names, long* launches, double*
     if (total_ms) total_ms[n] = ctx->prof.ms[k];
   }
   return n;
+}
+
+}  // extern "C"
+
+/* ---- learned selector ---------------------------------------------------- */
+/* float -> bfloat16, round to nearest, ties to even (finite values) */
+static uint16_t to_bf16(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+/* device copy of a selector: BF16 weights then FP32 biases then counters */
+cgks_status selector_upload(void** buf, SelectorDev* sd, const float* params, float thr_skip, float thr_lo,
+                            cudaStream_t stream) {
+  const size_t wbytes = sizeof(uint16_t) * SEL_NW, bbytes = sizeof(float) * SEL_NB;
+  const size_t off_b = (wbytes + 255) & ~size_t(255), off_c = (off_b + bbytes + 255) & ~size_t(255);
+  if (!*buf && cudaMalloc(buf, off_c + 2 * SEL_SLOTS * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return CGKS_ENOMEM;
+  }
+  std::vector<uint16_t> w(SEL_NW);
+  std::vector<float> b(SEL_NB);
+  const float* W1 = params;
+  const float* b1 = W1 + SEL_H * SEL_NF;
+  const float* W2 = b1 + SEL_H;
+  const float* b2 = W2 + SEL_H * SEL_H;
+  const float* W3 = b2 + SEL_H;
+  const float* b3 = W3 + SEL_H * SEL_H;
+  const float* w4 = b3 + SEL_H;
+  int o = 0;
+  for (int i = 0; i < SEL_H * SEL_NF; ++i) w[o++] = to_bf16(W1[i]);
+  for (int i = 0; i < SEL_H * SEL_H; ++i) w[o++] = to_bf16(W2[i]);
+  for (int i = 0; i < SEL_H * SEL_H; ++i) w[o++] = to_bf16(W3[i]);
+  for (int i = 0; i < SEL_H; ++i) w[o++] = to_bf16(w4[i]);
+  for (int i = 0; i < SEL_H; ++i) {
+    b[i] = b1[i];
+    b[SEL_H + i] = b2[i];
+    b[2 * SEL_H + i] = b3[i];
+  }
+  b[3 * SEL_H] = w4[SEL_H];
+  char* base = (char*)*buf;
+  if (cudaMemcpyAsync(base, w.data(), wbytes, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      cudaMemcpyAsync(base + off_b, b.data(), bbytes, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      cudaMemsetAsync(base + off_c, 0, 2 * SEL_SLOTS * sizeof(unsigned long long), stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return CGKS_ECUDA;
+  sd->w = (const __nv_bfloat16*)base;
+  sd->b = (const float*)(base + off_b);
+  sd->counts = (unsigned long long*)(base + off_c);
+  sd->thr_skip = thr_skip;
+  sd->thr_lo = thr_lo;
+  sd->on = 1;
+  return CGKS_OK;
+}
+
+extern "C" {
+
+cgks_status cgks_set_selector(cgks_ctx* ctx, const float* params, float thr_skip, float thr_lo) {
+  if (!ctx) return CGKS_EINVAL;
+  if (!params) {
+    ctx->sel.on = 0;
+    return CGKS_OK;
+  }
+  if (!(thr_lo <= thr_skip)) return CGKS_EINVAL;
+  cgks_status s = selector_upload(&ctx->sel_buf, &ctx->sel, params, thr_skip, thr_lo, ctx->stream);
+  if (s != CGKS_OK) return fail(ctx, s, "selector upload failed");
+  return CGKS_OK;
+}
+
+cgks_status cgks_selector_stats(cgks_ctx* ctx, unsigned long long* skips, unsigned long long* unsure) {
+  if (!ctx) return CGKS_EINVAL;
+  unsigned long long h[2 * SEL_SLOTS] = {0};
+  if (ctx->sel.counts) {
+    CK(cudaMemcpyAsync(h, ctx->sel.counts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  unsigned long long a = 0, u = 0;
+  for (int i = 0; i < SEL_SLOTS; ++i) {
+    a += h[2 * i];
+    u += h[2 * i + 1];
+  }
+  if (skips) *skips = a;
+  if (unsure) *unsure = u;
+  return CGKS_OK;
+}
+
+cgks_status cgks_selector_features(cgks_ctx* ctx, float* dev_out) {
+  if (!ctx || !dev_out) return CGKS_EINVAL;
+  const long N = ctx->ncell;
+  const int nb = (int)cdiv(N, 128);
+  const DevGeo& g = ctx->geo;
+  const bool w = ctx->walls;
+#define SELF(T, D)                                                                                        \
+  do {                                                                                                    \
+    if (w) k_selector_features<T, D, true><<<nb, 128, 0, ctx->stream>>>(ctx->avg[0], ctx->avh[0],         \
+                                                                         (const T*)ctx->der[0], g, dev_out); \
+    else k_selector_features<T, D, false><<<nb, 128, 0, ctx->stream>>>(ctx->avg[0], ctx->avh[0],          \
+                                                                        (const T*)ctx->der[0], g, dev_out); \
+  } while (0)
+  if (ctx->prec == 0) {
+    if (ctx->dim == 3) SELF(double, 3);
+    else SELF(double, 2);
+  } else {
+    if (ctx->dim == 3) SELF(float, 3);
+    else SELF(float, 2);
+  }
+#undef SELF
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CGKS_OK;
 }
 
 cgks_status cgks_last_error(const cgks_ctx* ctx, char* msg, size_t cap) {

@@ -22,6 +22,10 @@
 
 using namespace cgks;
 
+/* defined in cgks.cu */
+cgks_status selector_upload(void** buf, cgks::SelectorDev* sd, const float* params, float thr_skip, float thr_lo,
+                            cudaStream_t stream);
+
 namespace {
 
 struct List {
@@ -68,6 +72,8 @@ struct cgks_batch {
   List l_recon[2], l_flux, l_fbnd, l_upd, l_dt;
   cgks_batch_tiles tiles{};
   std::vector<Graph> graphs;
+  SelectorDev sel{};
+  void* sel_buf = nullptr;
   std::string err;
 };
 
@@ -205,10 +211,10 @@ static void enqueue_stage(cgks_batch* b, int stage, int phase = -1) {
     const int tpb = 128;
     if (b->l_recon[0].ntile)
       kb_recon<T, DIM, false><<<grid_of(b, b->l_recon[0], t.recon_blocks), tpb, 0, b->stream>>>(
-          b->dcase, b->l_recon[0].view(), A, t.tile_x, t.tile_y);
+          b->dcase, b->l_recon[0].view(), A, t.tile_x, t.tile_y, b->sel);
     if (b->l_recon[1].ntile)
       kb_recon<T, DIM, true><<<grid_of(b, b->l_recon[1], t.recon_blocks), tpb, 0, b->stream>>>(
-          b->dcase, b->l_recon[1].view(), A, t.tile_x, t.tile_y);
+          b->dcase, b->l_recon[1].view(), A, t.tile_x, t.tile_y, b->sel);
   }
   if (phase < 0 || phase == 1) {
     kb_flux<T, DIM><<<grid_of(b, b->l_flux, t.flux_blocks), 128, 0, b->stream>>>(b->dcase, b->l_flux.view(), A);
@@ -404,6 +410,7 @@ void cgks_batch_destroy(cgks_batch* b) {
   cudaFree(b->dts);
   cudaFree(b->st);
   cudaFree(b->staging);
+  cudaFree(b->sel_buf);
   delete b;
 }
 
@@ -624,6 +631,36 @@ done:
     if (ms_best) *ms_best = total;
   }
   return s;
+}
+
+cgks_status cgks_batch_set_selector(cgks_batch* b, const float* params, float thr_skip, float thr_lo) {
+  if (!b) return CGKS_EINVAL;
+  drop_graphs(b); /* the graphs hold the selector by value */
+  if (!params) {
+    b->sel.on = 0;
+    return CGKS_OK;
+  }
+  if (!(thr_lo <= thr_skip)) return CGKS_EINVAL;
+  cgks_status s = selector_upload(&b->sel_buf, &b->sel, params, thr_skip, thr_lo, b->stream);
+  if (s != CGKS_OK) return bfail(b, s, "selector upload failed");
+  return CGKS_OK;
+}
+
+cgks_status cgks_batch_selector_stats(cgks_batch* b, unsigned long long* skips, unsigned long long* unsure) {
+  if (!b) return CGKS_EINVAL;
+  unsigned long long h[2 * SEL_SLOTS] = {0};
+  if (b->sel.counts) {
+    BCK(cudaMemcpyAsync(h, b->sel.counts, sizeof h, cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+  }
+  unsigned long long a = 0, u = 0;
+  for (int i = 0; i < SEL_SLOTS; ++i) {
+    a += h[2 * i];
+    u += h[2 * i + 1];
+  }
+  if (skips) *skips = a;
+  if (unsure) *unsure = u;
+  return CGKS_OK;
 }
 
 cgks_status cgks_batch_last_error(const cgks_batch* b, char* msg, size_t cap) {

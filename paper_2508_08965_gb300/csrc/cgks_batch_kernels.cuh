@@ -95,8 +95,8 @@ template <int DIM> __host__ __device__ constexpr int batch_nf() { return 1 + DIM
 
 /* reconstruction: a tile is a tx x ty patch of one (i, j) plane of a case */
 template <typename T, int DIM, bool WALL>
-__global__ void __launch_bounds__(128, min_blocks<T>())
-    kb_recon(const BatchCase* __restrict__ cases, TileList L, BatchArrays<T> A, int tx, int ty) {
+__global__ void __launch_bounds__(128, min_blocks<T, DIM>())
+    kb_recon(const BatchCase* __restrict__ cases, TileList L, BatchArrays<T> A, int tx, int ty, SelectorDev sel) {
   __shared__ BatchCase sc;
   __shared__ TileRef sr;
   constexpr int NV = Sz<DIM>::NV;
@@ -107,22 +107,26 @@ __global__ void __launch_bounds__(128, min_blocks<T>())
     const int i = (ref.lt % ntx) * tx + (int)threadIdx.x % tx;
     const int j = ((ref.lt / ntx) % nty) * ty + (int)threadIdx.x / tx;
     const int k = ref.lt / (ntx * nty);
-    if ((int)threadIdx.x < tx * ty && i < g.n[0] && j < g.n[1]) {
-      const Phys& ph = sc.ph;
-      const long o = sc.cell0;
-      const long c = cell_index(g, i, j, k);
+    const bool active = (int)threadIdx.x < tx * ty && i < g.n[0] && j < g.n[1];
+    const Phys& ph = sc.ph;
+    const long o = sc.cell0;
+    const long c = active ? cell_index(g, i, j, k) : 0;
+    const double* avg = A.avg_in + NV * o;
+    const float* avh = A.avh_in ? A.avh_in + NV * o : nullptr;
+    const T* der = A.der_in + (long)(batch_nf<DIM>() - 1) * NV * o;
+    bool skip = false;
+    if (sel.on && !ph.linear) skip = selector_skip<T, DIM, WALL>(sel, avg, avh, der, g, c, i, j, k, active);
+    if (active) {
       const int ngp = DIM * Sz<DIM>::GPF * NV * (1 + DIM);
-      recon_cell<T, DIM, false, WALL>(A.avg_in + NV * o, A.avh_in ? A.avh_in + NV * o : nullptr,
-                                      A.avl_in ? A.avl_in + NV * o : nullptr,
-                                      A.der_in + (long)(batch_nf<DIM>() - 1) * NV * o, g, ph, c, i, j, k,
-                                      A.gpL + (long)ngp * o, A.gpR + (long)ngp * o, nullptr, 0, A.st);
+      recon_cell<T, DIM, false, WALL>(avg, avh, A.avl_in ? A.avl_in + NV * o : nullptr, der, g, ph, c, i, j, k,
+                                      A.gpL + (long)ngp * o, A.gpR + (long)ngp * o, nullptr, 0, A.st, skip);
     }
   }
 }
 
 /* interface flux: tiles of blockDim.x face-point items (flux_item) */
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128, min_blocks<T>())
+__global__ void __launch_bounds__(128, min_blocks<T, DIM>())
     kb_flux(const BatchCase* __restrict__ cases, TileList L, BatchArrays<T> A) {
   __shared__ BatchCase sc;
   __shared__ TileRef sr;

@@ -68,10 +68,19 @@ struct cgks_ctx {
   double t = 0.0;
   std::string err;
   cgks_host::Prof prof;
+  /* learned selector (cgks_set_selector): device copy of its parameters */
+  cgks::SelectorDev sel{};
+  void* sel_buf = nullptr; /* BF16 weights, FP32 biases, two counters */
 };
 
 
 inline long cdiv(long a, long b) { return (a + b - 1) / b; }
+
+/* device copy of a selector's parameters (packed as cgks_set_selector takes
+   them) in *buf (allocated on first use): BF16 weights, FP32 biases and two
+   zeroed counters; fills *sd and switches it on */
+cgks_status selector_upload(void** buf, cgks::SelectorDev* sd, const float* params, float thr_skip, float thr_lo,
+                            cudaStream_t stream);
 
 /* ---- profiling: CUDA events around each launch on the context stream ---- */
 inline void prof_begin(cgks_ctx* ctx, int kid) {

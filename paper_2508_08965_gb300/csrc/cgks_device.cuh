@@ -420,11 +420,15 @@ CGKS_HD T recon_var(const double* __restrict__ avg, const float* __restrict__ av
     const T alpha = T(2) * ah / (ah + al);
     chi = cg_tanh(ph_cchi<T>(ph) * alpha) / cg_tanh(ph_cchi<T>(ph));
   }
+  /* chi == 1 (forced, or the path function saturated in T): the blend is
+     the fifth-order polynomial alone, bit for bit, and the sub-stencil
+     polynomials are not needed */
+  const bool lin = chi == T(1);
   /* linear sub-stencil polynomials and their WENO weights (d_m = 1/(2 dim)).
      omega_m = (IS_m + eps)^-5 / sum_m' (IS_m' + eps)^-5, evaluated through the
      ratios (IS_min + eps)/(IS_m + eps) <= 1, which stays finite in FP32. */
   T bbar[3] = {T(0), T(0), T(0)};
-  {
+  if (!lin) {
     T lsum[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int s = 0; s < S::NL; ++s) lsum[s / S::GPF] += ld.line(s);
@@ -493,13 +497,19 @@ CGKS_HD T recon_var(const double* __restrict__ avg, const float* __restrict__ av
     for (int i = 0; i < 2 * S::GPF; ++i) {
       const int side = i / S::GPF, k = i % S::GPF;
       const int gp = (2 * ax + side) * S::GPF + k;
-      T v1 = T(0);
+      T rel, gref[3];
+      if (lin) {
+        rel = pv[i] - mean4;
 #pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) v1 += bbar[kk] * gp_delta<DIM, T>(gp, kk);
-      const T rel = chi * (pv[i] - mean4) + (T(1) - chi) * v1;
-      T gref[3];
+        for (int kk = 0; kk < DIM; ++kk) gref[kk] = pg[i][kk];
+      } else {
+        T v1 = T(0);
 #pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) gref[kk] = chi * pg[i][kk] + (T(1) - chi) * bbar[kk];
+        for (int kk = 0; kk < DIM; ++kk) v1 += bbar[kk] * gp_delta<DIM, T>(gp, kk);
+        rel = chi * (pv[i] - mean4) + (T(1) - chi) * v1;
+#pragma unroll
+        for (int kk = 0; kk < DIM; ++kk) gref[kk] = chi * pg[i][kk] + (T(1) - chi) * bbar[kk];
+      }
       T* dst = side ? gpL : gpR;
       const long cell = side ? c : clo;
       const long b = ((long)((ax * S::GPF + k) * NV + v) * (1 + DIM)) * N + cell;

@@ -5,6 +5,7 @@
  */
 #pragma once
 #include "cgks_device.cuh"
+#include "cgks_selector.cuh"
 
 namespace cgks {
 
@@ -21,9 +22,11 @@ struct DtState {
   double dt, t, t_end, dt_fixed;
 };
 
-/* FP32 kernels fit 3 blocks of 128 threads per SM (168 registers); the FP64
-   ones keep 2 (they are bound by the FP64 pipe, and spill more when capped) */
-template <typename T> constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
+/* Blocks of 128 threads per SM: FP32 3-D kernels fit 3 (168 registers), FP32
+   2-D ones 4 (128 registers; the 2-D reconstruction is latency-bound and
+   gains from the extra warps); the FP64 ones keep 2 (they are bound by the
+   FP64 pipe, and spill more when capped) */
+template <typename T, int DIM = 3> constexpr int min_blocks() { return sizeof(T) == 4 ? (DIM == 2 ? 4 : 3) : 2; }
 
 /* first order: every face Gauss-point state of cell c is its cell average
    with zero gradient (stored where recon_var stores them) */
@@ -61,9 +64,10 @@ __device__ __forceinline__ void recon_cell(const double* __restrict__ avg, const
                                            const float* __restrict__ avl, const T* __restrict__ der, const DevGeo& g,
                                            const Phys& ph, long c, int i, int j, int k, T* __restrict__ gpL,
                                            T* __restrict__ gpR, double* __restrict__ chi, int record_chi,
-                                           int* __restrict__ st) {
+                                           int* __restrict__ st, bool skip = false) {
   const int NV = Sz<DIM>::NV;
-  const T force = ph.linear ? T(1) : T(-1);
+  /* skip: the learned selector passed this cell (chi = 1, no adaptive weights) */
+  const T force = (ph.linear || skip) ? T(1) : T(-1);
   T cs[NV];
 #pragma unroll 1
   for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, v, force, gpL, gpR);
@@ -80,16 +84,52 @@ __device__ __forceinline__ void recon_cell(const double* __restrict__ avg, const
     for (int v = 0; v < NV; ++v) chi[(long)v * g.ncell + c] = double(cs[v]);
 }
 
+/* the selector's decision for the calling lane's cell (warp-collective: all
+   lanes call it, inactive ones with active = false); blocks of 128 threads */
+template <typename T, int DIM, bool WALL>
+__device__ __forceinline__ bool selector_skip(const SelectorDev& sel, const double* __restrict__ avg,
+                                              const float* __restrict__ avh, const T* __restrict__ der,
+                                              const DevGeo& g, long c, int i, int j, int k, bool active) {
+  __shared__ uint32_t stage[4][32 * SEL_PITCH];
+  float f[SEL_NF];
+  if (active) {
+    if constexpr (sizeof(T) == 4) selector_features<DIM, WALL>(avh, der, g, c, i, j, k, f);
+    else selector_features<DIM, WALL>(avg, der, g, c, i, j, k, f);
+  } else {
+#pragma unroll
+    for (int q = 0; q < SEL_NF; ++q) f[q] = 0.f;
+  }
+  return selector_decide(sel, f, active, stage[threadIdx.x >> 5]) == SEL_SKIP;
+}
+
 template <typename T, int DIM, bool CURVI, bool WALL>
-__global__ void __launch_bounds__(128, min_blocks<T>())
+__global__ void __launch_bounds__(128, min_blocks<T, DIM>())
     k_recon(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
             const T* __restrict__ der, DevGeo g, Phys ph, T* __restrict__ gpL, T* __restrict__ gpR,
-            double* __restrict__ chi, int record_chi, int* __restrict__ st) {
+            double* __restrict__ chi, int record_chi, int* __restrict__ st, SelectorDev sel) {
+  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const bool active = c < g.ncell;
+  int i = 0, j = 0, k = 0;
+  if (active) cell_ijk(g, c, i, j, k);
+  bool skip = false;
+  if (sel.on && !ph.linear) skip = selector_skip<T, DIM, WALL>(sel, avg, avh, der, g, c, i, j, k, active);
+  if (!active) return;
+  recon_cell<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st, skip);
+}
+
+/* features of every cell of a state, [cell][SEL_NF] (training samples) */
+template <typename T, int DIM, bool WALL>
+__global__ void k_selector_features(const double* __restrict__ avg, const float* __restrict__ avh,
+                                    const T* __restrict__ der, DevGeo g, float* __restrict__ out) {
   long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   int i, j, k;
   cell_ijk(g, c, i, j, k);
-  recon_cell<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st);
+  float f[SEL_NF];
+  if constexpr (sizeof(T) == 4) selector_features<DIM, WALL>(avh, der, g, c, i, j, k, f);
+  else selector_features<DIM, WALL>(avg, der, g, c, i, j, k, f);
+#pragma unroll
+  for (int q = 0; q < SEL_NF; ++q) out[c * SEL_NF + q] = f[q];
 }
 
 /* face-point item t = (ax * GPF + k) * N + c of a mesh: the face slot above
@@ -146,7 +186,7 @@ __device__ __forceinline__ void flux_bnd_item(const DevGeo& g, const Phys& ph, d
 
 /* one thread per face slot and Gauss point */
 template <typename T, int DIM, bool CURVI>
-__global__ void __launch_bounds__(128, min_blocks<T>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
+__global__ void __launch_bounds__(128, min_blocks<T, DIM>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
                                               const T* __restrict__ gpL, const T* __restrict__ gpR,
                                               T* __restrict__ flux, int* __restrict__ st) {
   long t = blockIdx.x * (long)blockDim.x + threadIdx.x;

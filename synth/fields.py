@@ -134,3 +134,29 @@ def turbulence_velocity_grid(n, seed, k0=8.0):
     vel = [np.real(np.fft.ifftn(c)) for c in comps]
     rms = np.sqrt(np.mean(vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2) / 3.0)
     return [v / rms for v in vel]
+
+
+def random_smooth_3d(x, y, z, seed, nmodes=4, mach=0.1, gamma=1.4, length=2.0 * math.pi):
+    """Seeded smooth periodic 3-D flow on [0, length)^3: density, velocity and
+    pressure perturbed by `nmodes` random Fourier modes each (wave numbers
+    1..3 per axis, random phases), velocity amplitude 1, mean density 1 and
+    mean pressure 1/(gamma mach^2)."""
+    xp = _ns(x)
+    rng = np.random.default_rng(seed)
+    two_pi = 2.0 * math.pi / length
+
+    def modes(amp):
+        out = 0.0 * x
+        for _ in range(nmodes):
+            k = rng.integers(-3, 4, 3)
+            if not np.any(k):
+                k[0] = 1
+            ph = rng.uniform(0, 2 * math.pi)
+            a = amp * rng.uniform(0.5, 1.0) / nmodes
+            out = out + a * xp.sin(two_pi * (k[0] * x + k[1] * y + k[2] * z) + ph)
+        return out
+    p0 = 1.0 / (gamma * mach * mach)
+    rho = 1.0 + modes(0.1)
+    u, v, w = modes(1.0), modes(1.0), modes(1.0)
+    p = p0 * (1.0 + modes(0.05))
+    return [rho, u, v, w, p]

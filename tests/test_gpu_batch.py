@@ -86,10 +86,13 @@ def test_batch_reproduces_single_cases(orc, cg, precision):
     b.step(6)
     t, dt = b.times()
     tol = 1e-13 if precision == 0 else 1e-5  # FP32: see test_batch_3d
+    # time steps follow the states: FP32 rounding of the fluxes moves them by
+    # up to FP32 relative precision
+    tol_t = 1e-14 if precision == 0 else 1e-6
     for k, (s_ref, t_ref, dt_ref) in enumerate(ref):
         s, tk = b.get_state(k)
         h = min(1.0 / x for x in cases[k][0]["n"])
-        assert abs(tk - t_ref) <= 1e-14 * t_ref and abs(dt[k] - dt_ref) <= 1e-14 * dt_ref
+        assert abs(tk - t_ref) <= tol_t * t_ref and abs(dt[k] - dt_ref) <= tol_t * dt_ref
         assert class_scaled_diff(s, s_ref, h) <= tol, k
     b.close()
 

@@ -1,0 +1,176 @@
+"""The learned troubled-cell selector on the GPU: the training kernels and
+the features against the oracle's reference arithmetic, the fused BF16
+inference against the oracle's emulation of it (decisions taken on the
+same side of the threshold by construction of the test's thresholds), and
+what a trained network gains over the plain method."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp
+from parity import class_scaled_diff
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2508_08965_gb300 as p
+    p.lib()
+    return p
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def test_mlp_loss_gradient_logits_adam(cg):
+    from paper_2508_08965_gb300 import binding as B
+    rng = np.random.default_rng(2)
+    p = mlp.init_params(4)
+    p[mlp.H * mlp.NF:mlp.H * mlp.NF + mlp.H] = rng.normal(0, 0.2, mlp.H).astype(np.float32)
+    n = 3001
+    X = rng.uniform(0, 1, (n, mlp.NF)).astype(np.float32)
+    X[:, 15] = 0
+    y = (rng.uniform(size=n) > 0.3).astype(np.float32)
+    w = np.where(y > 0.5, 1.0, 8.0).astype(np.float32)
+    L, g = mlp.loss_grad(p.astype(np.float64), X.astype(np.float64), y.astype(np.float64), w.astype(np.float64))
+    dp, dg = _dev(p), _dev(np.zeros(mlp.NPARAM))
+    Lg = B.mlp_loss_grad(dp, _dev(X), _dev(y), _dev(w), dg)
+    gg = dg.cpu().numpy()
+    assert Lg == pytest.approx(L, rel=1e-5)
+    assert np.abs(gg - g).max() <= 2e-5 * np.abs(g).max()
+    z, _ = mlp.forward(p.astype(np.float64), X.astype(np.float64))
+    zg = B.mlp_logits(dp, _dev(X)).cpu().numpy()
+    assert np.abs(zg - z).max() <= 1e-5 * max(1.0, np.abs(z).max())
+    # one Adam step from zero moments moves every parameter by lr g / (|g| + eps)
+    dm, dv = _dev(np.zeros(mlp.NPARAM)), _dev(np.zeros(mlp.NPARAM))
+    B.mlp_adam(dp, dg, dm, dv, 1, 1e-3)
+    want = p - 1e-3 * gg / (np.abs(gg) + 1e-8)
+    assert np.abs(dp.cpu().numpy() - want).max() <= 1e-6
+
+
+def _walls(x, y):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x + 0.3) * np.cos(2 * np.pi * y)
+    return [rho, 0.3 * np.sin(np.pi * x), 0.2 * np.cos(2 * np.pi * y), 1.0 + 0.1 * np.cos(2 * np.pi * x)]
+
+
+FEATURE_CASES = [
+    ("vortex", dict(dim=2, n=(40, 33), lo=(0, 0), hi=(10, 10)), lambda x, y: synth.isentropic_vortex_2d(x, y)),
+    ("riemann-outflow", dict(dim=2, n=(32, 32), lo=(0, 0), hi=(1, 1), bc=[1, 1, 1, 1], tau_mode=1),
+     lambda x, y: synth.riemann4_2d(x, y, synth.riemann4_params(9))),
+    ("walls", dict(dim=2, n=(24, 20), lo=(0, 0), hi=(1, 1), bc=[3, 3, 2, 2]), _walls),
+    ("tgv3d", dict(dim=3, n=(10, 9, 8), lo=(0, 0, 0), hi=(2 * math.pi,) * 3),
+     lambda x, y, z: synth.taylor_green_3d(x, y, z)),
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", FEATURE_CASES, ids=[c[0] for c in FEATURE_CASES])
+def test_features_match_oracle(orc, cg, case, precision):
+    name, kw, fn = case
+    o = orc.Oracle(**kw)
+    o.init(fn)
+    fo = o.selector_features()
+    m = cg.Mesh(precision=precision, **kw)
+    m.set_state(o.get_state())
+    fg = m.selector_features().cpu().numpy()
+    assert np.abs(fg - fo).max() <= 2e-6
+    m.close()
+
+
+def _gap_threshold(z, lo_q, hi_q):
+    """A threshold in the widest gap between neighbouring sorted logits of the
+    quantile range [lo_q, hi_q]: the mid-point, so every logit is at least
+    half the gap away from it."""
+    zs = np.sort(z)
+    a, b = int(lo_q * len(zs)), int(hi_q * len(zs))
+    gaps = zs[a + 1:b] - zs[a:b - 1]
+    i = a + int(np.argmax(gaps))
+    return 0.5 * (zs[i] + zs[i + 1])
+
+
+@pytest.mark.parametrize("case", FEATURE_CASES, ids=[c[0] for c in FEATURE_CASES])
+def test_fused_selector_matches_oracle(orc, cg, case):
+    """Seeded parameters; thresholds in gaps of the oracle's own logits of
+    the initial state, and a short step (1e-3 of the CFL step) so that the
+    second stage's logits stay in those gaps: both sides decide alike unless
+    a logit moves by more than the checked margin."""
+    name, kw, fn = case
+    p = mlp.init_params(7 + len(name))
+    o = orc.Oracle(**kw)
+    o.init(fn)
+    dt = 1e-3 * o.dt()
+    z = orc.selector_logits(p, o.selector_features()).astype(np.float64)
+    thr = _gap_threshold(z, 0.1, 0.9)
+    lo = _gap_threshold(z, 0.02, 0.1)
+    o.set_selector(p, thr, lo)
+    m = cg.Mesh(dt_fixed=dt, **kw)
+    m.set_state(o.get_state())
+    m.set_selector(p, thr, lo)
+    o.step_dt(dt)
+    m.step(1)
+    nskip, nuns, margin = o.selector_stats()
+    assert margin >= 1e-4, "thresholds too close to a logit for a parity check"
+    assert nskip > 0 and nskip < 2 * o.ncell
+    assert m.selector_stats() == (nskip, nuns)
+    h = min((kw["hi"][a] - kw["lo"][a]) / kw["n"][a] for a in range(kw["dim"]))
+    assert class_scaled_diff(m.get_state()[0], o.get_state(), h) <= 1e-12
+    m.close()
+
+
+def test_training_reduces_loss(cg):
+    from paper_2508_08965_gb300 import selector
+    m = selector.riemann_mesh(3, 64)
+    X, y = selector.trajectory_samples(m, 6)
+    m.close()
+    assert 0.0 < float(y.mean()) < 1.0
+    params, hist = selector.train(X, y, epochs=12, batch=2048, lr=3e-3)
+    assert hist[-1] < 0.6 * hist[0]
+    thr, lo = selector.thresholds(params, X, y)
+    assert lo < thr
+
+
+TRAINED = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2508_08965_gb300",
+                       "selector_params.npz")
+
+
+@pytest.mark.skipif(not os.path.exists(TRAINED), reason="no trained selector parameters")
+@pytest.mark.parametrize("precision", [0, 1])
+def test_trained_selector_ablation(cg, precision):
+    """A held-out Riemann problem and the 3-D TGV: the trained selector skips
+    most cells and the result stays close to the plain method's."""
+    import torch
+    from paper_2508_08965_gb300 import selector
+    params, thr, lo = selector.load(TRAINED)
+    states = synth.riemann4_params(777777)
+    cases = [
+        ("riemann", dict(dim=2, n=(256, 256), lo=(0, 0), hi=(1, 1), bc=[1, 1, 1, 1], tau_mode=1),
+         lambda x, y: synth.riemann4_2d(x, y, states), 20, 0.5, 1e-6),
+        ("tgv", dict(dim=3, n=(64, 64, 64), lo=(0, 0, 0), hi=(2 * math.pi,) * 3, mu=1 / 1600, prandtl=0.72,
+                     tau_mode=2), lambda x, y, z: synth.taylor_green_3d(x, y, z), 10, 0.2, 1e-5),
+    ]
+    for name, kw, fn, steps, min_skip, tol in cases:
+        res = {}
+        for on in (False, True):
+            m = cg.Mesh(precision=precision, **kw)
+            m.init(fn)
+            if on:
+                m.set_selector(params, thr, lo)
+            m.step(steps)
+            res[on] = (m.get_state()[0], m.selector_stats() if on else None)
+            m.close()
+        s0, (s1, stats) = res[False][0], res[True]
+        skip_rate = stats[0] / (2 * steps * np.prod(kw["n"]))
+        e = s1[0, 0] - s0[0, 0]
+        l2 = math.sqrt(np.mean(e * e) / np.mean(s0[0, 0] ** 2))
+        print("%s precision %d: skip rate %.3f, unsure %.3f, density L2 vs plain %.2e" % (
+            name, precision, skip_rate, stats[1] / (2 * steps * np.prod(kw["n"])), l2))
+        assert skip_rate >= min_skip and l2 <= tol
