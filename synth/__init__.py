@@ -9,7 +9,7 @@ the CUDA path.  Every function works on numpy arrays and on torch tensors
 """
 from .fields import (  # noqa: F401
     isentropic_vortex_2d, taylor_green_3d, density_sine_3d, uniform_state,
-    sod_x, riemann4_2d, riemann4_params, turbulence_velocity_grid, random_smooth_3d,
+    sod_x, riemann4_2d, riemann4_params, turbulence_velocity_grid, random_smooth_3d, turbulence_field,
 )
 from .meshes import uniform_nodes, perturbed_nodes_3d, perturbed_nodes_xy  # noqa: F401
 from .ensemble import ensemble_stream, ensemble_specs, spec_mesh, spec_field  # noqa: F401

@@ -160,3 +160,53 @@ def random_smooth_3d(x, y, z, seed, nmodes=4, mach=0.1, gamma=1.4, length=2.0 * 
     u, v, w = modes(1.0), modes(1.0), modes(1.0)
     p = p0 * (1.0 + modes(0.05))
     return [rho, u, v, w, p]
+
+
+def turbulence_field(seed, n=128, k0=8.0, mach_t=0.5, re_lambda=72.0, gamma=1.4):
+    """Decaying isotropic turbulence initial data on the periodic [0, 2 pi)^3:
+    the seeded solenoidal velocity of turbulence_velocity_grid (spectrum
+    E(k) ~ k^4 exp(-2 (k/k0)^2)) on an n^3 grid, scaled so that
+    Ma_t = sqrt(<|u|^2>) / c = mach_t with rho = 1, p = 1/gamma (c = 1), and
+    evaluated anywhere by periodic trilinear interpolation.  Returns
+    (field(x, y, z) -> [rho, u, v, w, p], mu) with mu from
+    Re_lambda = rho u_rms lambda / mu, u_rms = sqrt(<|u|^2>/3) and
+    lambda = u_rms / (du/dx)_rms, the derivative taken spectrally on the
+    grid."""
+    vel = turbulence_velocity_grid(n, seed, k0)
+    scale = mach_t / math.sqrt(np.mean(vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2))
+    vel = [v * scale for v in vel]
+    u_rms = math.sqrt(np.mean(vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2) / 3.0)
+    k1 = np.fft.fftfreq(n, d=1.0 / n)
+    dudx = np.real(np.fft.ifftn(1j * k1[:, None, None] * np.fft.fftn(vel[0])))
+    lam = u_rms / math.sqrt(np.mean(dudx ** 2))
+    mu = u_rms * lam / re_lambda
+    h = 2.0 * math.pi / n
+    grids = {}
+
+    def field(x, y, z):
+        xp = _ns(x)
+        key = id(xp)
+        if key not in grids:
+            if xp is np:
+                grids[key] = [np.asarray(v) for v in vel]
+            else:
+                grids[key] = [xp.as_tensor(v, dtype=x.dtype, device=x.device) for v in vel]
+        g = grids[key]
+        fx, fy, fz = x / h, y / h, z / h
+        i0, j0, k0_ = xp.floor(fx), xp.floor(fy), xp.floor(fz)
+        tx, ty, tz = fx - i0, fy - j0, fz - k0_
+        out = []
+        for comp in g:
+            acc = 0.0 * x
+            for dx in (0, 1):
+                for dy in (0, 1):
+                    for dz in (0, 1):
+                        ii = ((i0 + dx) % n).long() if xp is not np else ((i0 + dx) % n).astype(np.int64)
+                        jj = ((j0 + dy) % n).long() if xp is not np else ((j0 + dy) % n).astype(np.int64)
+                        kk = ((k0_ + dz) % n).long() if xp is not np else ((k0_ + dz) % n).astype(np.int64)
+                        w = (tx if dx else 1 - tx) * (ty if dy else 1 - ty) * (tz if dz else 1 - tz)
+                        acc = acc + w * comp[ii, jj, kk]
+            out.append(acc)
+        return [1.0 + 0.0 * x, out[0], out[1], out[2], 1.0 / gamma + 0.0 * x]
+
+    return field, mu
