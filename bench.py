@@ -429,7 +429,7 @@ def main():
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2508_08965_gb300 import Mesh
+    from paper_2508_08965_gb300 import Mesh, replicas
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -470,14 +470,11 @@ def main():
         ms = e0.elapsed_time(e1)
         prof = mesh.profile_read()
         mesh.profile(False)
-        ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        return mesh, s0, float(ms_t.item()), prof, clk
+        return mesh, s0, replicas.job_time_ms(ms, device="cuda"), prof, clk
 
     mesh, s_init, ms, prof, clk = timed_form(0)
     ncell = mesh.ncell
-    value = world * ncell * args.steps / (ms / 1e3)
+    value = replicas.whole_job_rate(ncell, args.steps, ms, world)
 
     # end to end through the C-ABI with host buffers: every step copies the
     # state in from pinned host memory, steps, and copies the new state out
@@ -494,11 +491,7 @@ def main():
         mesh.step(1)
         mesh.get_state(h_out.numpy())
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
+    e2e_s = replicas.job_time_ms(1e3 * (time.perf_counter() - t0), device="cuda") / 1e3
     state_bytes = int(np.prod(shape)) * 8
     mesh.close()
     kernels = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)}
