@@ -167,6 +167,16 @@ int cgks_profile_read(cgks_ctx* ctx, const char** names, long* launches, double*
 #define CGKS_DT_NOALLOC_MAX_CELLS 16777216
 cgks_status cgks_compute_dt_noalloc(const cgks_mesh_desc* desc, const double* dev_state, double* dt_out);
 
+/* The volume averages of the TGV diagnostics (Sec. 6.2) for the current
+   state: *ek = (1/(rho0 |Omega|)) sum_cells (1/2) |m|^2/rho |cell| and
+   *enstrophy = (1/(rho0 |Omega|)) sum_cells mu |curl U|^2 |cell|, with rho0
+   the mean density and the velocity gradient from the cell averages and the
+   cell-averaged gradients, d_k U_i = (d_k m_i - U_i d_k rho)/rho (cell-centred
+   quadrature, second order; the paper integrates reconstruction
+   derivatives).  mu is the mesh's constant viscosity.  Either output may be
+   NULL.  Synchronises. */
+cgks_status cgks_diagnostics(cgks_ctx* ctx, double* ek, double* enstrophy);
+
 /* Copy the last error message (NUL-terminated, truncated to cap). */
 cgks_status cgks_last_error(const cgks_ctx* ctx, char* msg, size_t cap);
 

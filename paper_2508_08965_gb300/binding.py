@@ -88,7 +88,7 @@ EXPORTS = ["cgks_create_mesh", "cgks_destroy", "cgks_num_vars", "cgks_num_fields
            "cgks_batch_get_state", "cgks_batch_times", "cgks_batch_step", "cgks_batch_get_tiles",
            "cgks_batch_set_tiles", "cgks_batch_tune", "cgks_batch_last_error", "cgks_set_selector",
            "cgks_selector_stats", "cgks_selector_features", "cgks_batch_set_selector", "cgks_batch_selector_stats",
-           "cgks_mlp_loss_grad", "cgks_mlp_logits", "cgks_mlp_adam"]
+           "cgks_mlp_loss_grad", "cgks_mlp_logits", "cgks_mlp_adam", "cgks_diagnostics"]
 
 _lib = None
 
@@ -140,6 +140,7 @@ def lib(build_if_missing=True):
     L.cgks_batch_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
     fp = C.POINTER(C.c_float)
     ull = C.POINTER(C.c_ulonglong)
+    L.cgks_diagnostics.argtypes = [vp, dp, dp]
     L.cgks_set_selector.argtypes = [vp, fp, C.c_float, C.c_float]
     L.cgks_selector_stats.argtypes = [vp, ull, ull]
     L.cgks_selector_features.argtypes = [vp, vp]
@@ -282,6 +283,12 @@ class Mesh:
         a = np.empty((self.nv,) + tuple(reversed(self.n)))
         self._check(lib().cgks_get_chi(self._h, a.ctypes.data_as(C.c_void_p), 0))
         return a
+
+    def diagnostics(self):
+        """(kinetic energy, enstrophy) volume averages of the current state."""
+        ek, es = C.c_double(0), C.c_double(0)
+        self._check(lib().cgks_diagnostics(self._h, C.byref(ek), C.byref(es)))
+        return ek.value, es.value
 
     def set_selector(self, params=None, thr_skip=0.0, thr_lo=0.0):
         """Learned troubled-cell selector on (params: CGKS_SEL_NPARAM floats) or off (None)."""

@@ -564,6 +564,38 @@ cgks_status cgks_selector_features(cgks_ctx* ctx, float* dev_out) {
   return CGKS_OK;
 }
 
+cgks_status cgks_diagnostics(cgks_ctx* ctx, double* ek, double* enstrophy) {
+  if (!ctx) return CGKS_EINVAL;
+  const int nblk = 304;
+  double* part = nullptr;
+  if (cudaMallocAsync((void**)&part, sizeof(double) * 4 * nblk, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, CGKS_ENOMEM, "diagnostics work space");
+  }
+  const DevGeo& g = ctx->geo;
+  const double mu = ctx->ph.mu;
+  if (ctx->prec == 0) {
+    if (ctx->dim == 3) k_diagnostics<double, 3><<<nblk, 256, 0, ctx->stream>>>(g, ctx->avg[0], (const double*)ctx->der[0], mu, part);
+    else k_diagnostics<double, 2><<<nblk, 256, 0, ctx->stream>>>(g, ctx->avg[0], (const double*)ctx->der[0], mu, part);
+  } else {
+    if (ctx->dim == 3) k_diagnostics<float, 3><<<nblk, 256, 0, ctx->stream>>>(g, ctx->avg[0], (const float*)ctx->der[0], mu, part);
+    else k_diagnostics<float, 2><<<nblk, 256, 0, ctx->stream>>>(g, ctx->avg[0], (const float*)ctx->der[0], mu, part);
+  }
+  std::vector<double> h(4 * nblk);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, sizeof(double) * 4 * nblk, cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(part, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, CGKS_ECUDA, "diagnostics: %s", cudaGetErrorString(e));
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < nblk; ++b)
+    for (int q = 0; q < 4; ++q) s[q] += h[4 * b + q];
+  const double rho0 = s[2] / s[3];
+  if (ek) *ek = s[0] / (rho0 * s[3]);
+  if (enstrophy) *enstrophy = s[1] / (rho0 * s[3]);
+  return CGKS_OK;
+}
+
 cgks_status cgks_last_error(const cgks_ctx* ctx, char* msg, size_t cap) {
   if (!ctx || !msg || cap == 0) return CGKS_EINVAL;
   snprintf(msg, cap, "%s", ctx->err.c_str());

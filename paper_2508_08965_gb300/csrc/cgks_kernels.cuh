@@ -514,6 +514,55 @@ CGKS_HD double g5w(int q) {
   return (q == 0 || q == 4) ? 0.23692688505618908751 : (q == 1 || q == 3) ? 0.47862867049936646804
                                                                           : 0.56888888888888888889;
 }
+/* Volume sums of the TGV diagnostics (Sec. 6.2): kinetic energy 1/2 |m|^2/rho,
+   mu |curl U|^2 (the velocity gradient from the conservative averages and
+   cell-averaged gradients: d_k U_i = (d_k m_i - U_i d_k rho) / rho), mass and
+   volume; block partials [block][4], summed in a fixed order by the host */
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_diagnostics(DevGeo g, const double* __restrict__ avg,
+                                                     const T* __restrict__ der, double mu,
+                                                     double* __restrict__ part) {
+  const long N = g.ncell;
+  constexpr int NV = DIM + 2;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < N; c += (long)gridDim.x * blockDim.x) {
+    const double vol = g.curvi ? met_vol<DIM>(g, c) : (DIM == 3 ? g.h[0] * g.h[1] * g.h[2] : g.h[0] * g.h[1]);
+    const double rho = avg[c];
+    double U[3] = {0.0, 0.0, 0.0}, ke = 0.0;
+    for (int i = 0; i < DIM; ++i) {
+      U[i] = avg[(long)(1 + i) * N + c] / rho;
+      ke += 0.5 * rho * U[i] * U[i];
+    }
+    double G[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}; /* G[i][k] = d_k U_i */
+    for (int k = 0; k < DIM; ++k) {
+      const double dr = (double)der[((long)k * NV + 0) * N + c];
+      for (int i = 0; i < DIM; ++i) G[i][k] = ((double)der[((long)k * NV + 1 + i) * N + c] - U[i] * dr) / rho;
+    }
+    double w2;
+    if (DIM == 3) {
+      const double w0 = G[2][1] - G[1][2], w1 = G[0][2] - G[2][0], wz = G[1][0] - G[0][1];
+      w2 = w0 * w0 + w1 * w1 + wz * wz;
+    } else {
+      const double wz = G[1][0] - G[0][1];
+      w2 = wz * wz;
+    }
+    acc[0] += ke * vol;
+    acc[1] += mu * w2 * vol;
+    acc[2] += rho * vol;
+    acc[3] += vol;
+  }
+  __shared__ double sh[256][4];
+  for (int q = 0; q < 4; ++q) sh[threadIdx.x][q] = acc[q];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int q = 0; q < 4; ++q) sh[threadIdx.x][q] += sh[threadIdx.x + o][q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 4; ++q) part[blockIdx.x * 4 + q] = sh[0][q];
+}
+
 /* FP32 CFL metric of each curvilinear cell (RateMet<DIM>) from the FP64
    metrics, by the same formulas as the curvilinear branch of cell_rate */
 template <int DIM>

@@ -208,3 +208,27 @@ def test_time_step_equals_fp64_maximum(orc, cg, precision, dim, n, curvi, mu):
         dg, do = m.compute_dt(), o.dt()
         assert abs(dg - do) <= 1e-14 * do, (seed, dg, do)
         m.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_diagnostics_match_oracle(orc, cg, precision):
+    """Kinetic energy and enstrophy averages of a TGV state after a few steps
+    (curvilinear and Cartesian) against the oracle's sums of the same
+    state."""
+    from oracle.diagnostics import tgv_diagnostics
+    for nodes in (None, "perturbed"):
+        n = (12, 12, 12)
+        nd = synth.perturbed_nodes_3d(n) if nodes else None
+        kw = dict(lo=(0, 0, 0), hi=(2 * math.pi,) * 3, nodes=nd, mu=1 / 1600, prandtl=0.72, tau_mode=2)
+        o = orc.Oracle(3, n, **kw)
+        o.init(tgv)
+        o.step(3)
+        s = o.get_state()
+        vol, _ = o.metrics()
+        ek, es = tgv_diagnostics(s, 3, vol, 1 / 1600)
+        m = cg.Mesh(3, n, precision=precision, **kw)
+        m.set_state(s)
+        gk, gs = m.diagnostics()
+        tol = 1e-12 if precision == 0 else 1e-6
+        assert abs(gk - ek) <= tol * ek and abs(gs - es) <= tol * es
+        m.close()
