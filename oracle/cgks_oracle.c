@@ -886,14 +886,15 @@ static void build_geo(orc_ctx* c) {
 /* 6. Context, state and initial data.                                      */
 /* ------------------------------------------------------------------------ */
 /* boundary kinds of orc_desc.bc */
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_SLIP = 2, BC_NOSLIP = 3 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_SLIP = 2, BC_NOSLIP = 3, BC_INFLOW = 4 };
 
 orc_ctx* orc_create(const orc_desc* d) {
   const ref_t* R = get_ref(d->dim);
   if (!R) return NULL;
   for (int f = 0; f < 2 * d->dim; ++f) {
-    if (d->bc[f] < BC_PERIODIC || d->bc[f] > BC_NOSLIP) return NULL;
-    if (d->bc[f] >= BC_SLIP && d->nodes) return NULL; /* a mirror is a reflection only on a box */
+    if (d->bc[f] < BC_PERIODIC || d->bc[f] > BC_INFLOW) return NULL;
+    /* a mirror is a reflection only on a box; inflow faces likewise on boxes */
+    if ((d->bc[f] == BC_SLIP || d->bc[f] == BC_NOSLIP || d->bc[f] == BC_INFLOW) && d->nodes) return NULL;
     if ((d->bc[f] == BC_PERIODIC) != (d->bc[f ^ 1] == BC_PERIODIC)) return NULL;
   }
   orc_ctx* c = calloc(1, sizeof(orc_ctx));
@@ -1114,19 +1115,26 @@ double orc_compute_dt(orc_ctx* c) {
    boundary cell); beyond a wall it is mirrored and the ghost carries the
    mirror image of the cell's data: reflecting axis a negates the normal
    momentum (slip) or every momentum component (no-slip), and negates
-   derivatives along a. */
-static long nbr_bc(const orc_ctx* c, long id, const int* o, int* mirror, int* noslip) {
+   derivatives along a.  Beyond an inflow face the ghost holds the face's
+   fixed state with zero gradients (*inflow = 1 + that face; the index is
+   clamped and unused for values). */
+static long nbr_bc3(const orc_ctx* c, long id, const int* o, int* mirror, int* noslip, int* inflow) {
   int ii[3] = {(int)(id % c->n[0]), (int)((id / c->n[0]) % c->n[1]),
                c->dim == 3 ? (int)(id / ((long)c->n[0] * c->n[1])) : 0};
   *mirror = 0;
   *noslip = 0;
+  *inflow = 0;
   for (int a = 0; a < c->dim; ++a) {
     int x = ii[a] + o[a];
     if (x < 0 || x >= c->n[a]) {
-      int bc = c->d.bc[2 * a + (x < 0 ? 0 : 1)];
+      const int f = 2 * a + (x < 0 ? 0 : 1);
+      int bc = c->d.bc[f];
       if (bc == BC_PERIODIC) x = (x + c->n[a]) % c->n[a];
       else if (bc == BC_OUTFLOW) x = x < 0 ? 0 : c->n[a] - 1;
-      else {
+      else if (bc == BC_INFLOW) {
+        x = x < 0 ? 0 : c->n[a] - 1;
+        if (!*inflow) *inflow = 1 + f;
+      } else {
         x = x < 0 ? -1 - x : 2 * c->n[a] - 1 - x;
         *mirror |= 1 << a;
         if (bc == BC_NOSLIP) *noslip |= 1 << a;
@@ -1137,9 +1145,28 @@ static long nbr_bc(const orc_ctx* c, long id, const int* o, int* mirror, int* no
   return cidx(c, ii[0], ii[1], ii[2]);
 }
 
+static long nbr_bc(const orc_ctx* c, long id, const int* o, int* mirror, int* noslip) {
+  int inf;
+  return nbr_bc3(c, id, o, mirror, noslip, &inf);
+}
+
 static long nbr(const orc_ctx* c, long id, const int* o) {
   int m, ns;
   return nbr_bc(c, id, o, &m, &ns);
+}
+
+static double mirror_sign(int dim, int v, int k, int mirror, int noslip);
+#define mirror_sign_fwd mirror_sign
+
+/* value (k < 0) or physical gradient component k of variable v at the
+   neighbour of cell id at offset o, through the boundaries */
+static double nbr_field(const orc_ctx* c, const double* S, long id, const int* o, int v, int k) {
+  int mi, ns, inf;
+  const long nb = nbr_bc3(c, id, o, &mi, &ns, &inf);
+  if (inf) return k < 0 ? c->d.bc_state[inf - 1][v] : 0.0;
+  const long N = c->ncell;
+  const double x = S[((long)(k < 0 ? 0 : 1 + k) * c->nv + v) * N + nb];
+  return mirror_sign_fwd(c->dim, v, k, mi, ns) * x;
 }
 
 /* sign of variable v (and of its derivative along axis k, k < 0: the value)
@@ -1209,14 +1236,9 @@ static void sel_features(const orc_ctx* c, const double* S, long id, float* f) {
       for (int sd = 0; sd < 2; ++sd) {
         int o[3] = {0, 0, 0};
         o[a] = sd ? 1 : -1;
-        int mi, ns;
-        const long nb = nbr_bc(c, id, o, &mi, &ns);
-        float q = (float)S[(long)v * N + nb];
-        if (mirror_sign(dim, v, -1, mi, ns) < 0) q = -q;
-        qn[sd] = q;
+        qn[sd] = (float)nbr_field(c, S, id, o, v, -1);
         for (int k = 0; k < dim; ++k) {
-          float gm = (float)S[((long)(1 + k) * nv + v) * N + nb];
-          if (mirror_sign(dim, v, k, mi, ns) < 0) gm = -gm;
+          const float gm = (float)nbr_field(c, S, id, o, v, k);
           const float g0 = (float)S[((long)(1 + k) * nv + v) * N + id];
           const float gd = (fabsf(gm - g0) * (float)G->len[k * gpf]) * inv;
           fg = fmaxf(fg, gd);
@@ -1249,10 +1271,7 @@ static void sel_features(const orc_ctx* c, const double* S, long id, float* f) {
           int o[3] = {0, 0, 0};
           o[a] = (sg & 1) ? 1 : -1;
           o[b] = (sg & 2) ? 1 : -1;
-          int mi, ns;
-          const long nb = nbr_bc(c, id, o, &mi, &ns);
-          float q = (float)S[(long)v * N + nb];
-          if (mirror_sign(dim, v, -1, mi, ns) < 0) q = -q;
+          const float q = (float)nbr_field(c, S, id, o, v, -1);
           fe[cls] = fmaxf(fe[cls], fabsf(q - q0[v]) * inv);
         }
     }
@@ -1323,24 +1342,20 @@ static void recon_cell(orc_ctx* c, const double* S, long id, int record_chi) {
     double* d = dat[v];
     d[0] = S[(0 * nv + v) * N + id];
     for (int m = 0; m < 2 * dim; ++m) {
-      int mi, ns;
-      long nb = nbr_bc(c, id, R->face_off[m], &mi, &ns);
-      d[R->d_face + m] = mirror_sign(dim, v, -1, mi, ns) * S[(0 * nv + v) * N + nb];
+      d[R->d_face + m] = nbr_field(c, S, id, R->face_off[m], v, -1);
       /* reference-frame gradient J0^T (grad Q)_{1,m} with the target's J0 */
       for (int k = 0; k < dim; ++k) {
         double s = 0;
-        for (int r = 0; r < dim; ++r) s += G->J0[r][k] * mirror_sign(dim, v, r, mi, ns) * S[((1 + r) * nv + v) * N + nb];
+        for (int r = 0; r < dim; ++r) s += G->J0[r][k] * nbr_field(c, S, id, R->face_off[m], v, r);
         d[R->d_fgrad + m * dim + k] = s;
       }
     }
     for (int n = 0; n < R->ne; ++n) {
-      int mi, ns;
-      long nb = nbr_bc(c, id, R->edge_off[n], &mi, &ns);
-      d[R->d_edge + n] = mirror_sign(dim, v, -1, mi, ns) * S[(0 * nv + v) * N + nb];
+      d[R->d_edge + n] = nbr_field(c, S, id, R->edge_off[n], v, -1);
       double g[3];
       for (int k = 0; k < dim; ++k) {
         double s = 0;
-        for (int r = 0; r < dim; ++r) s += G->J0[r][k] * mirror_sign(dim, v, r, mi, ns) * S[((1 + r) * nv + v) * N + nb];
+        for (int r = 0; r < dim; ++r) s += G->J0[r][k] * nbr_field(c, S, id, R->edge_off[n], v, r);
         g[k] = s;
       }
       for (int t = 0; t < R->ntau; ++t) {
@@ -1499,7 +1514,11 @@ static int stage(orc_ctx* c, const double* S, double dt, double* Lout, double* L
           const double* own = c->gpv + id * stride + gown * nv * (1 + dim);
           const int bnd = pass == 0 ? hi_bnd : 1;
           const int bc = c->d.bc[2 * ax + (pass == 0 ? 1 : 0)];
-          if (bnd) {
+          if (bnd && bc == BC_INFLOW) {
+            const int f = 2 * ax + (pass == 0 ? 1 : 0);
+            for (int v = 0; v < nv; ++v)
+              for (int k = -1; k < dim; ++k) st_bc[v * (1 + dim) + 1 + k] = k < 0 ? c->d.bc_state[f][v] : 0.0;
+          } else if (bnd) {
             int mi = bc == BC_OUTFLOW ? 0 : 1 << ax, ns = bc == BC_NOSLIP ? 1 << ax : 0;
             for (int v = 0; v < nv; ++v)
               for (int k = -1; k < dim; ++k)
@@ -1515,7 +1534,7 @@ static int stage(orc_ctx* c, const double* S, double dt, double* Lout, double* L
           int st = gks_point(dim, c->d.gamma, c->d.mu, c->d.prandtl, c->d.tau_mode, dt, WL, dWL, WR, dWR, out);
           if (st) err |= 1;
           for (int p = 0; p < 6; ++p) rotate_out(dim, Rm, out + p * nv);
-          if (bnd && bc >= BC_SLIP) wall_face(dim, ax, bc, nv, out);
+          if (bnd && (bc == BC_SLIP || bc == BC_NOSLIP)) wall_face(dim, ax, bc, nv, out);
         }
       }
     }

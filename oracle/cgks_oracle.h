@@ -36,7 +36,9 @@ typedef struct {
   int linear;         /* 1: force chi = 1 (linear CGKS-5) */
   double c_chi;       /* path-function constant C in chi = tanh(C alpha)/tanh(C) */
   int bc[6];          /* per domain face -x,+x,-y,+y,-z,+z: 0 periodic, 1 outflow,
-                         2 slip wall, 3 no-slip wall (walls: axis-aligned meshes) */
+                         2 slip wall, 3 no-slip wall (walls: axis-aligned meshes),
+                         4 inflow (a fixed state) */
+  double bc_state[6][5]; /* inflow faces: conservative state (rho, m..., rho E) */
 } orc_desc;
 
 typedef struct orc_ctx orc_ctx;

@@ -28,7 +28,7 @@ class _Desc(C.Structure):
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("gamma", C.c_double),
                 ("mu", C.c_double), ("prandtl", C.c_double), ("tau_mode", C.c_int),
                 ("cfl", C.c_double), ("dt_fixed", C.c_double), ("linear", C.c_int),
-                ("c_chi", C.c_double), ("bc", C.c_int * 6)]
+                ("c_chi", C.c_double), ("bc", C.c_int * 6), ("bc_state", (C.c_double * 5) * 6)]
 
 
 _lib = None
@@ -93,7 +93,8 @@ class Oracle:
     """One oracle mesh + state.  Arguments mirror the library's mesh descriptor."""
 
     def __init__(self, dim, n, lo=(0, 0, 0), hi=(1, 1, 1), nodes=None, gamma=1.4, mu=0.0,
-                 prandtl=1.0, tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=100.0, bc=None):
+                 prandtl=1.0, tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=100.0, bc=None,
+                 bc_state=None):
         L = lib()
         d = _Desc()
         d.dim = dim
@@ -110,6 +111,9 @@ class Oracle:
         d.cfl, d.dt_fixed, d.linear, d.c_chi = cfl, dt_fixed, int(linear), c_chi
         for f in range(6):
             d.bc[f] = int(bc[f]) if bc is not None and f < len(bc) else 0
+            if bc_state is not None and f < len(bc_state) and bc_state[f] is not None:
+                for v, q in enumerate(bc_state[f]):
+                    d.bc_state[f][v] = float(q)
         self._h = L.orc_create(C.byref(d))
         if not self._h:
             raise RuntimeError("orc_create failed")

@@ -8,6 +8,7 @@ the CUDA path.  Every function works on numpy arrays and on torch tensors
 (the array namespace is taken from the arguments).
 """
 from .fields import (  # noqa: F401
+    shock_vortex_params, shock_vortex_upstream, shock_vortex_2d, shock_vortex_inflow,
     isentropic_vortex_2d, taylor_green_3d, density_sine_3d, uniform_state,
     sod_x, riemann4_2d, riemann4_params, turbulence_velocity_grid, random_smooth_3d, turbulence_field,
 )

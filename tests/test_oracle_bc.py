@@ -1,5 +1,8 @@
 """Boundary pins of the oracle (not GPU).
 
+B5  Inflow: a matching uniform state stays uniform; a stationary normal shock
+    between supersonic inflow and outflow stays in place.
+
 B1  Slip wall = mirror symmetry: a walled box evolves exactly like the upper
     half of the periodic box of twice the length holding the state and its
     mirror image (reflection symmetry of the Euler equations), in 2-D and 3-D,
@@ -10,6 +13,8 @@ B3  A closed box of walls conserves mass and energy.
 B4  Outflow: a uniform moving state stays uniform; Sod's problem in a box with
     outflow ends against the exact Riemann solution.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -193,3 +198,94 @@ def test_strong_riemann_first_order_fallback(orc):
     p = 0.4 * (E - 0.5 * (m * m).sum(0) / rho)
     assert o.positivity_fallbacks() > 0
     assert rho.min() > 0 and p.min() > 0 and np.all(np.isfinite(s))
+
+
+INFLOW = 4
+
+
+def _cons(rho, u, v, p, gamma=1.4):
+    return (rho, rho * u, rho * v, p / (gamma - 1) + 0.5 * rho * (u * u + v * v))
+
+
+def test_inflow_keeps_matching_uniform_state(orc):
+    q = (1.1, 0.6, -0.2, 0.9)
+    o = orc.Oracle(2, (10, 6), bc=[INFLOW, OUTFLOW, 0, 0], bc_state=[_cons(*q)])
+    o.init(lambda x, y: [q[0] + 0 * x, q[1] + 0 * x, q[2] + 0 * x, q[3] + 0 * x])
+    s0 = o.get_state()
+    o.step(5)
+    assert np.abs(o.get_state() - s0).max() < 1e-13
+
+
+def rankine_hugoniot(mach, rho1=1.0, p1=1.0, gamma=1.4):
+    """post-shock state of a stationary normal shock with upstream Mach number `mach`"""
+    c1 = (gamma * p1 / rho1) ** 0.5
+    u1 = mach * c1
+    r = (gamma + 1) * mach ** 2 / ((gamma - 1) * mach ** 2 + 2)
+    p2 = p1 * (1 + 2 * gamma * (mach ** 2 - 1) / (gamma + 1))
+    return (rho1, u1, p1), (rho1 * r, u1 / r, p2)
+
+
+def test_stationary_shock_between_inflow_and_outflow(orc):
+    """A Mach-2 normal shock between supersonic inflow and outflow stays
+    where it is: the upstream state exactly, the Rankine-Hugoniot downstream
+    state within the start-up waves, the shock within 1.5 cells of x = 0.5
+    after 100 steps."""
+    (r1, u1, p1), (r2, u2, p2) = rankine_hugoniot(2.0)
+    nx = 40
+    o = orc.Oracle(2, (nx, 2), lo=(0, 0), hi=(1, 2.0 / nx), tau_mode=1,
+                   bc=[INFLOW, OUTFLOW, 0, 0], bc_state=[_cons(r1, u1, 0.0, p1)])
+    o.init(lambda x, y: [np.where(x < 0.5, r1, r2), np.where(x < 0.5, u1, u2), 0 * x, np.where(x < 0.5, p1, p2)])
+    o.step(100)
+    rho = o.get_state()[0, 0, 0, :]
+    xc = (np.arange(nx) + 0.5) / nx
+    assert np.all(np.abs(rho[xc < 0.4] - r1) < 1e-6 * r1)
+    # the start-up of a captured steady shock leaves waves of about 1% behind it
+    assert np.all(np.abs(rho[xc > 0.6] - r2) < 2e-2 * r2)
+    mid = 0.5 * (r1 + r2)
+    i = int(np.argmax(rho > mid))
+    xs = xc[i - 1] + (mid - rho[i - 1]) / (rho[i] - rho[i - 1]) / nx
+    assert abs(xs - 0.5) < 1.5 / nx
+
+
+def test_shock_vortex_field_satisfies_rankine_hugoniot():
+    """The shock-vortex initial field: mass, momentum and energy fluxes agree
+    across the shock (vortex strength 0), the upstream Mach number is the one
+    asked for, and the vortex is isentropic."""
+    import synth
+    g = 1.4
+    for mach in (1.1, 2.0, 3.0):
+        x = np.array([0.49, 0.51])
+        y = np.array([0.5, 0.5])
+        r, u, v, p = synth.shock_vortex_2d(x, y, mach, eps=0.0)
+        e = p / (g - 1) + 0.5 * r * u * u
+        for a in (r * u, r * u * u + p, (e + p) * u):
+            assert abs(a[0] - a[1]) <= 1e-13 * abs(a[0])
+        assert r[1] > r[0] and p[1] > p[0]
+        assert abs(u[0] / math.sqrt(g * p[0] / r[0]) - mach) < 1e-12
+        xv = 0.25 + 0.03 * np.cos(np.linspace(0, 6, 7))
+        yv = 0.5 + 0.03 * np.sin(np.linspace(0, 6, 7))
+        rv, uv, vv, pv = synth.shock_vortex_2d(xv, yv, mach)
+        assert np.allclose(pv / rv ** g, 1.0, rtol=0, atol=1e-13)
+        assert np.all(rv < 1.0)
+
+
+def test_shock_vortex_oracle_keeps_shock_and_upstream(orc):
+    """Mach-1.5 shock-vortex on a coarse 48 x 24 mesh of [0, 2] x [0, 1]
+    (inflow, outflow, slip walls): upstream of the vortex the inflow state is
+    kept, and far from the vortex (y < 0.15) the shock stays within two
+    cells of x = 0.5."""
+    import synth
+    mach = 1.5
+    nx, ny = 48, 24
+    o = orc.Oracle(2, (nx, ny), lo=(0, 0), hi=(2, 1), tau_mode=1, bc=[INFLOW, OUTFLOW, 2, 2],
+                   bc_state=[synth.shock_vortex_inflow(mach)])
+    o.init(lambda x, y: synth.shock_vortex_2d(x, y, mach))
+    o.step(30)
+    rho = o.get_state()[0, 0]
+    assert np.all(np.isfinite(rho))
+    assert np.abs(rho[:, 0] - 1.0).max() < 2e-2
+    xc = (np.arange(nx) + 0.5) * 2 / nx
+    for j in range(3):
+        row = rho[j]
+        i = int(np.argmax(np.abs(np.diff(row))))
+        assert abs(0.5 * (xc[i] + xc[i + 1]) - 0.5) <= 2 * 2 / nx
