@@ -342,10 +342,11 @@ def ensemble_bench(args, stream, ncase=256):
 
 def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
     """The learned selector (FP32 form): held-out four-quadrant Riemann
-    problems on 1024^2 and the TGV 128^3, each with and without the trained
+    problems on 1024^2, held-out shock-vortex interactions on 1024^2 cells of
+    [0, 2] x [0, 1], and the TGV 128^3, each with and without the trained
     selector from the same initial state: time per step and per
-    reconstruction, skip and low-confidence rates, and the density difference
-    from the plain adaptive method."""
+    reconstruction, skip, fallback (full GENO) and low-confidence rates, and
+    the density difference from the plain adaptive method."""
     import numpy as np
     import torch
     import synth
@@ -381,6 +382,12 @@ def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
         cases.append(("riemann1024 seed %d" % seed,
                       dict(dim=2, n=(1024, 1024), lo=(0, 0), hi=(1, 1), bc=[1, 1, 1, 1], tau_mode=1),
                       (lambda st: (lambda x, y: synth.riemann4_2d(x, y, st)))(st), None))
+    for seed in (9101, 9102):
+        mach = synth.shock_vortex_params(seed)
+        cases.append(("shockvortex1024 mach %.2f" % mach,
+                      dict(dim=2, n=(1024, 1024), lo=(0, 0), hi=(2, 1), bc=[4, 1, 2, 2], tau_mode=1,
+                           bc_state=[synth.shock_vortex_inflow(mach)]),
+                      (lambda mach: (lambda x, y: synth.shock_vortex_2d(x, y, mach)))(mach), None))
     cases.append(("tgv128", dict(dim=3, n=(128, 128, 128), **mesh_kwargs("tgv128")), field_fn("tgv128"), s_tgv_init))
     for name, kw, fn, s0 in cases:
         try:
@@ -394,7 +401,8 @@ def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
         e = s_sel[0, 0] - s_plain[0, 0]
         rec = {"case": name, "ms_per_step": {"plain": ms0, "selector": ms1}, "speedup": ms0 / ms1,
                "recon_ms": {"plain": rc0, "selector": rc1},
-               "skip_rate": nskip / recons, "low_confidence_rate": nuns / recons,
+               "skip_rate": nskip / recons, "fallback_rate": 1.0 - nskip / recons,
+               "low_confidence_rate": nuns / recons,
                "density_l2_vs_plain": float(np.sqrt(np.mean(e * e) / np.mean(s_plain[0, 0] ** 2))),
                "density_linf_vs_plain": float(np.abs(e).max() / np.abs(s_plain[0, 0]).max())}
         if name == "tgv128" and s_tgv_fp64 is not None:

@@ -66,12 +66,17 @@ typedef enum {
      normal change sign; the face solves the GKS problem against the mirror
      image of the interior Gauss-point state, then passes no mass and no energy
      (adiabatic) and its interface values carry no normal (no-slip: no)
-     momentum. */
+     momentum.
+   INFLOW (uniform boxes only): a fixed state, bc_state[face] (conservative:
+     rho, rho U, rho V[, rho W], rho E); ghosts hold it with zero gradients and
+     the face solves the GKS problem against it (supersonic inflow, or any
+     prescribed far state). */
 enum {
   CGKS_BC_PERIODIC = 0,
   CGKS_BC_OUTFLOW = 1,
   CGKS_BC_SLIP_WALL = 2,
-  CGKS_BC_NOSLIP_WALL = 3
+  CGKS_BC_NOSLIP_WALL = 3,
+  CGKS_BC_INFLOW = 4
 };
 
 /* Mesh and physics description.  Uniform box when nodes == NULL. */
@@ -83,7 +88,9 @@ typedef struct {
   double lo[3], hi[3];
   int bc[6];            /* CGKS_BC_* per face (-x,+x,-y,+y,-z,+z); a code outside the
                            list or a periodic face opposite a non-periodic one:
-                           CGKS_EINVAL; a wall with nodes != NULL: CGKS_EUNSUPPORTED */
+                           CGKS_EINVAL; a wall or inflow with nodes != NULL:
+                           CGKS_EUNSUPPORTED */
+  double bc_state[6][5]; /* CGKS_BC_INFLOW faces: their fixed conservative state */
   double gamma;         /* specific heat ratio */
   double mu;            /* dynamic viscosity; 0 = inviscid */
   double prandtl;       /* Prandtl number for the heat-flux correction (used when mu > 0) */

@@ -24,6 +24,7 @@ class CgksError(RuntimeError):
 class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("nodes", C.POINTER(C.c_double)),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("bc", C.c_int * 6),
+                ("bc_state", (C.c_double * 5) * 6),
                 ("gamma", C.c_double), ("mu", C.c_double), ("prandtl", C.c_double),
                 ("tau_mode", C.c_int), ("cfl", C.c_double), ("dt_fixed", C.c_double),
                 ("linear", C.c_int), ("c_chi", C.c_double), ("precision", C.c_int),
@@ -31,7 +32,7 @@ class MeshDesc(C.Structure):
 
 
 # boundary kinds of MeshDesc.bc (CGKS_BC_* of include/cgks.h)
-BC_PERIODIC, BC_OUTFLOW, BC_SLIP_WALL, BC_NOSLIP_WALL = 0, 1, 2, 3
+BC_PERIODIC, BC_OUTFLOW, BC_SLIP_WALL, BC_NOSLIP_WALL, BC_INFLOW = 0, 1, 2, 3, 4
 
 SEL_NFEAT, SEL_NPARAM = 16, 2689
 
@@ -159,7 +160,7 @@ def _torch():
 
 
 def make_desc(dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=1.4, mu=0.0, prandtl=1.0,
-              tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=0.0, precision=0, bc=None):
+              tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=0.0, precision=0, bc=None, bc_state=None):
     """A cgks_mesh_desc (and the node array it points to, which the caller
     keeps alive until the library has copied it)."""
     d = MeshDesc()
@@ -177,6 +178,9 @@ def make_desc(dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=
     d.cfl, d.dt_fixed, d.linear, d.c_chi = cfl, dt_fixed, int(linear), c_chi
     for f in range(6):
         d.bc[f] = int(bc[f]) if bc is not None and f < len(bc) else BC_PERIODIC
+        if bc_state is not None and f < len(bc_state) and bc_state[f] is not None:
+            for v, q in enumerate(bc_state[f]):
+                d.bc_state[f][v] = float(q)
     d.precision = int(precision)
     return d, keep
 
@@ -192,11 +196,11 @@ class Mesh:
 
     def __init__(self, dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=1.4, mu=0.0,
                  prandtl=1.0, tau_mode=0, cfl=0.5, dt_fixed=0.0, linear=False, c_chi=0.0, stream=None,
-                 precision=0, bc=None):
+                 precision=0, bc=None, bc_state=None):
         torch = _torch()
         L = lib()
         d, self._nodes = make_desc(dim, n, lo, hi, nodes, gamma, mu, prandtl, tau_mode, cfl, dt_fixed, linear, c_chi,
-                                   precision, bc)
+                                   precision, bc, bc_state)
         nn = list(n) + [1] * (3 - len(n))
         self.precision = int(precision)
         self.stream = stream if stream is not None else torch.cuda.current_stream()

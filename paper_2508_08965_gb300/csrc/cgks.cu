@@ -125,7 +125,7 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
     if (d->n[a] < 3) return CGKS_EINVAL;
   if (d->precision != 0 && d->precision != 1) return CGKS_EUNSUPPORTED;
   for (int f = 0; f < 2 * d->dim; ++f) {
-    if (d->bc[f] < CGKS_BC_PERIODIC || d->bc[f] > CGKS_BC_NOSLIP_WALL) return CGKS_EINVAL;
+    if (d->bc[f] < CGKS_BC_PERIODIC || d->bc[f] > CGKS_BC_INFLOW) return CGKS_EINVAL;
     if ((d->bc[f] == CGKS_BC_PERIODIC) != (d->bc[f ^ 1] == CGKS_BC_PERIODIC)) return CGKS_EINVAL;
     if (d->bc[f] >= CGKS_BC_SLIP_WALL && d->nodes) return CGKS_EUNSUPPORTED;
   }
@@ -167,11 +167,12 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   g.curvi = d->nodes ? 1 : 0;
   g.met = nullptr;
   g.rmet = nullptr;
+  g.bcq = nullptr;
   g.nplane = 0;
   g.bcm = 0;
   ctx->walls = false;
   for (int f = 0; f < 2 * d->dim; ++f) {
-    g.bcm |= d->bc[f] << (2 * f);
+    g.bcm |= d->bc[f] << (3 * f);
     if (d->bc[f] >= CGKS_BC_SLIP_WALL) ctx->walls = true;
     if (d->bc[f] != CGKS_BC_PERIODIC) g.nplane = std::max(g.nplane, ctx->ncell / ctx->n[f / 2]);
   }
@@ -221,6 +222,13 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   ALLOC(ctx->gpR, gp_sz);
   ALLOC(ctx->flux, fx_sz);
   if (g.nplane > 0) ALLOC(ctx->fxb, rsz * (size_t)dim * gpf * 6 * nv * g.nplane);
+  g.bcq = nullptr;
+  for (int f = 0; f < 2 * dim; ++f)
+    if (d->bc[f] == CGKS_BC_INFLOW && !ctx->d_bcq) {
+      ALLOC(ctx->d_bcq, sizeof(double) * 30);
+      CK(cudaMemcpyAsync(ctx->d_bcq, &d->bc_state[0][0], sizeof(double) * 30, cudaMemcpyHostToDevice, ctx->stream));
+      g.bcq = ctx->d_bcq;
+    }
   ALLOC(ctx->chi, sizeof(double) * (size_t)nv * N);
   ALLOC(ctx->dts, sizeof(DtState));
   ALLOC(ctx->st, sizeof(int) * ST_N);
@@ -277,6 +285,7 @@ void cgks_destroy(cgks_ctx* ctx) {
   cudaFree(ctx->d_nodes);
   cudaFree(ctx->d_met);
   cudaFree(ctx->d_rmet);
+  cudaFree(ctx->d_bcq);
   cudaFree(ctx->sel_buf);
   for (auto e : ctx->prof.pool) cudaEventDestroy(e);
   delete ctx;

@@ -69,6 +69,7 @@ struct cgks_batch {
   DtState* dts = nullptr;
   int* st = nullptr;
   double* staging = nullptr; /* public layout of the largest case */
+  double* bcq = nullptr;     /* inflow states [case][face][5] */
   List l_recon[2], l_flux, l_fbnd, l_upd, l_dt;
   cgks_batch_tiles tiles{};
   std::vector<Graph> graphs;
@@ -280,7 +281,7 @@ cgks_status cgks_batch_create(const cgks_mesh_desc* descs, int ncase, void* stre
     for (int a = 0; a < dim; ++a)
       if (d.n[a] < 3) return CGKS_EINVAL;
     for (int f = 0; f < 2 * dim; ++f) {
-      if (d.bc[f] < CGKS_BC_PERIODIC || d.bc[f] > CGKS_BC_NOSLIP_WALL) return CGKS_EINVAL;
+      if (d.bc[f] < CGKS_BC_PERIODIC || d.bc[f] > CGKS_BC_INFLOW) return CGKS_EINVAL;
       if ((d.bc[f] == CGKS_BC_PERIODIC) != (d.bc[f ^ 1] == CGKS_BC_PERIODIC)) return CGKS_EINVAL;
     }
     if (!(d.gamma > 1.0) || d.mu < 0.0 || !(d.cfl > 0.0) || d.tau_mode < 0 || d.tau_mode > 2) return CGKS_EINVAL;
@@ -317,7 +318,7 @@ cgks_status cgks_batch_create(const cgks_mesh_desc* descs, int ncase, void* stre
     g.bcm = 0;
     g.nplane = 0;
     for (int f = 0; f < 2 * dim; ++f) {
-      g.bcm |= d.bc[f] << (2 * f);
+      g.bcm |= d.bc[f] << (3 * f);
       if (d.bc[f] != CGKS_BC_PERIODIC) g.nplane = std::max(g.nplane, g.ncell / g.n[f / 2]);
     }
     if (case_has_wall(d)) b->wall = true;
@@ -361,7 +362,20 @@ cgks_status cgks_batch_create(const cgks_mesh_desc* descs, int ncase, void* stre
   BALLOC(b->dts, sizeof(DtState) * ncase);
   BALLOC(b->st, sizeof(int) * ST_N);
   BALLOC(b->staging, sizeof(double) * (nd + nv) * maxcell);
+  BALLOC(b->bcq, sizeof(double) * 30 * ncase);
 #undef BALLOC
+  {
+    std::vector<double> hq(30 * (size_t)ncase);
+    for (int k = 0; k < ncase; ++k) {
+      memcpy(&hq[30 * (size_t)k], &descs[k].bc_state[0][0], sizeof(double) * 30);
+      b->hcase[k].g.bcq = b->bcq + 30 * (size_t)k;
+    }
+    if (cudaMemcpyAsync(b->bcq, hq.data(), sizeof(double) * hq.size(), cudaMemcpyHostToDevice, b->stream) !=
+        cudaSuccess) {
+      cgks_batch_destroy(b);
+      return CGKS_ECUDA;
+    }
+  }
   std::vector<DtState> d0(ncase);
   for (int k = 0; k < ncase; ++k) {
     memset(&d0[k], 0, sizeof(DtState));
@@ -410,6 +424,7 @@ void cgks_batch_destroy(cgks_batch* b) {
   cudaFree(b->dts);
   cudaFree(b->st);
   cudaFree(b->staging);
+  cudaFree(b->bcq);
   cudaFree(b->sel_buf);
   delete b;
 }

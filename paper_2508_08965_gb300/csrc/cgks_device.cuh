@@ -86,15 +86,17 @@ struct DevGeo {
   const double* met;  /* curvilinear metrics (Met<DIM>), or null */
   const float* rmet;  /* curvilinear: FP32 CFL metric per cell (RateMet<DIM>), or null */
   int bcm;            /* boundary kind (BcKind) of domain face f = -x,+x,-y,+y,-z,+z in bits
-                         2f..2f+1: shifts, not an array, so that no copy of DevGeo is
+                         3f..3f+2: shifts, not an array, so that no copy of DevGeo is
                          indexed at run time (which would put it in local memory) */
+  const double* bcq;  /* inflow faces: conservative states [face][5] (device), or null */
   long nplane;        /* slots of the low-boundary face array per (axis, Gauss point):
                          the largest ncell / n[axis] over non-periodic axes, else 0 */
 };
 
 /* boundary kinds (the values of the public CGKS_BC_* codes) */
-enum BcKind { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_SLIP = 2, BC_NOSLIP = 3 };
-CGKS_HD int geo_bc(const DevGeo& g, int f) { return (g.bcm >> (2 * f)) & 3; }
+enum BcKind { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_SLIP = 2, BC_NOSLIP = 3, BC_INFLOW = 4 };
+CGKS_HD int geo_bc(const DevGeo& g, int f) { return (g.bcm >> (3 * f)) & 7; }
+CGKS_HD bool bc_wall(int bc) { return bc == BC_SLIP || bc == BC_NOSLIP; }
 
 /* FP32 CFL metric of a curvilinear cell, [k * ncell + cell]: per axis the
    direction w = n/(|n| h) and 1/h (n the mean face normal, h = vol / mean
@@ -153,7 +155,7 @@ CGKS_HD long nbr_bc(const DevGeo& g, int i, int j, int k, int ox, int oy, int oz
       const int hi = x[a] >= g.n[a] ? 1 : 0;
       const int bc = geo_bc(g, 2 * a + hi);
       if (bc == BC_PERIODIC) x[a] += hi ? -g.n[a] : g.n[a];
-      else if (bc == BC_OUTFLOW) x[a] = hi ? g.n[a] - 1 : 0;
+      else if (bc == BC_OUTFLOW || bc == BC_INFLOW) x[a] = hi ? g.n[a] - 1 : 0;
       else {
         x[a] = hi ? 2 * g.n[a] - 1 - x[a] : -1 - x[a];
         m |= (1 << a) | (bc == BC_NOSLIP ? (8 << a) : 0);
@@ -167,10 +169,13 @@ CGKS_HD long nbr_bc(const DevGeo& g, int i, int j, int k, int ox, int oy, int oz
 /* The stencil neighbours of one cell, resolved once: the linear-index
    offsets of the -1 and +1 neighbours along each axis (through the
    boundaries as nbr_bc resolves them) and their mirror bits, so that a
-   neighbour (ox, oy, oz) in {-1, 0, 1}^DIM costs additions only. */
+   neighbour (ox, oy, oz) in {-1, 0, 1}^DIM costs additions only.  Beyond an
+   inflow face the neighbour is the face's fixed state: bit 6 + axis of mm
+   (the index is clamped and not read for values). */
+constexpr int MM_INFLOW = 0x1C0;
 template <int DIM> struct NbrOff {
   int lo[3], hi[3];
-  int mlo, mhi; /* nbr_bc's mm format; the bits of different axes are disjoint */
+  int mlo, mhi; /* nbr_bc's mm format plus inflow bits; the bits of different axes are disjoint */
   CGKS_HD void setup(const DevGeo& g, int ci, int cj, int ck) {
     const int x[3] = {ci, cj, ck};
     int stride = 1;
@@ -183,13 +188,15 @@ template <int DIM> struct NbrOff {
       else {
         const int bc = geo_bc(g, 2 * a);
         lo[a] = bc == BC_PERIODIC ? (n - 1) * stride : 0;
-        if (bc >= BC_SLIP) mlo |= bits | (bc == BC_NOSLIP ? bits << 3 : 0);
+        if (bc_wall(bc)) mlo |= bits | (bc == BC_NOSLIP ? bits << 3 : 0);
+        if (bc == BC_INFLOW) mlo |= bits << 6;
       }
       if (x[a] < n - 1) hi[a] = stride;
       else {
         const int bc = geo_bc(g, 2 * a + 1);
         hi[a] = bc == BC_PERIODIC ? -(n - 1) * stride : 0;
-        if (bc >= BC_SLIP) mhi |= bits | (bc == BC_NOSLIP ? bits << 3 : 0);
+        if (bc_wall(bc)) mhi |= bits | (bc == BC_NOSLIP ? bits << 3 : 0);
+        if (bc == BC_INFLOW) mhi |= bits << 6;
       }
       stride *= n;
     }
@@ -198,13 +205,20 @@ template <int DIM> struct NbrOff {
   template <bool WALL> CGKS_HD long at(long c, int ox, int oy, int oz, int* mm) const {
     long i = c;
     int m = 0;
-    if (ox < 0) { i += lo[0]; m |= mlo & 0x9; } else if (ox > 0) { i += hi[0]; m |= mhi & 0x9; }
-    if (oy < 0) { i += lo[1]; m |= mlo & 0x12; } else if (oy > 0) { i += hi[1]; m |= mhi & 0x12; }
+    if (ox < 0) { i += lo[0]; m |= mlo & 0x49; } else if (ox > 0) { i += hi[0]; m |= mhi & 0x49; }
+    if (oy < 0) { i += lo[1]; m |= mlo & 0x92; } else if (oy > 0) { i += hi[1]; m |= mhi & 0x92; }
     if (DIM == 3) {
-      if (oz < 0) { i += lo[2]; m |= mlo & 0x24; } else if (oz > 0) { i += hi[2]; m |= mhi & 0x24; }
+      if (oz < 0) { i += lo[2]; m |= mlo & 0x124; } else if (oz > 0) { i += hi[2]; m |= mhi & 0x124; }
     }
     *mm = WALL ? m : 0;
     return i;
+  }
+  /* the inflow face a neighbour with inflow bits in mm lies beyond: the
+     first such axis, on the side of the offset */
+  CGKS_HD static int inflow_face(int mm, int ox, int oy, int oz) {
+    if (mm & 0x40) return ox < 0 ? 0 : 1;
+    if (mm & 0x80) return oy < 0 ? 2 : 3;
+    return oz < 0 ? 4 : 5;
   }
 };
 
@@ -319,6 +333,11 @@ template <typename T, int DIM, bool CURVI, bool WALL> struct ReconLd {
   CGKS_HD T avg(int ox, int oy, int oz) const {
     int mm;
     const long i = (long)v * g.ncell + nb.template at<WALL>(c, ox, oy, oz, &mm);
+    if (WALL && (mm & MM_INFLOW)) {
+      const double q = g.bcq[NbrOff<DIM>::inflow_face(mm, ox, oy, oz) * 5 + v];
+      if constexpr (sizeof(T) == 4) return T(q - (double(q0h) + double(q0l)));
+      else return T(q - q0d);
+    }
     if (WALL && mirror_odd<DIM>(v, mm)) {
       if constexpr (sizeof(T) == 4) return (-avh[i] - q0h) + (-avl[i] - q0l);
       else return T(-avgp[i] - q0d);
@@ -337,7 +356,10 @@ template <typename T, int DIM, bool CURVI, bool WALL> struct ReconLd {
     T gp[3];
 #pragma unroll
     for (int r = 0; r < DIM; ++r) gp[r] = der[((long)r * (DIM + 2) + v) * g.ncell + ni];
-    if (WALL && mm) {
+    if (WALL && (mm & MM_INFLOW)) {
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) gp[r] = T(0);
+    } else if (WALL && mm) {
       const int f = mirror_odd<DIM>(v, mm);
 #pragma unroll
       for (int r = 0; r < DIM; ++r)
@@ -1174,6 +1196,11 @@ template <typename T, int DIM> struct BndLd {
   CartLd<T, DIM> cl;
   int real, kind;
   CGKS_HD void grad(int side, int j, T* o) const {
+    if (side != real && kind == BC_INFLOW) {
+#pragma unroll
+      for (int v = 0; v < DIM + 2; ++v) o[v] = T(0);
+      return;
+    }
     cl.grad(real, j, o);
     if (side != real) {
 #pragma unroll
@@ -1234,12 +1261,13 @@ CGKS_HD bool flux_bnd_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k
       int vg = v, sv = 1;
       if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = sg[v - 1]; }
       const T w = T(sv) * src[(base + vg * (1 + DIM)) * N + c];
-      const T wi = image_odd<DIM>(kind, v, -1) ? -w : w;
+      const int face = 2 * ax + (real ? 0 : 1);
+      const T wi = kind == BC_INFLOW ? T(sv) * T(g.bcq[face * 5 + vg]) : (image_odd<DIM>(kind, v, -1) ? -w : w);
       WL[v] = real ? wi : w;
       WR[v] = real ? w : wi;
     }
     bool ok = gks_point_ld<T, DIM>(ph, dt, WL, WR, ld, out);
-    if (kind >= BC_SLIP) wall_face_local<T, DIM>(kind, out);
+    if (bc_wall(kind)) wall_face_local<T, DIM>(kind, out);
 #pragma unroll
     for (int part = 0; part < 6; ++part) {
 #pragma unroll
@@ -1262,8 +1290,21 @@ CGKS_HD bool flux_bnd_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k
     double R[3][3];
     face_frame<DIM>(A, Tt, R);
     to_local<T, DIM>(R, st, WL, dW);
-    for (int v = 0; v < NV; ++v) WR[v] = WL[v];
-    bool ok = gks_point<T, DIM>(ph, dt, WL, dW, WR, dW, out);
+    bool ok;
+    if (kind == BC_INFLOW) {
+      /* the fixed state, zero derivatives, on the image side */
+      const int face = 2 * ax + (real ? 0 : 1);
+      T sq[NV * (1 + DIM)], Wq[NV], dq[DIM * NV];
+      for (int v = 0; v < NV; ++v) {
+        sq[v * (1 + DIM)] = T(g.bcq[face * 5 + v]);
+        for (int k2 = 0; k2 < DIM; ++k2) sq[v * (1 + DIM) + 1 + k2] = T(0);
+      }
+      to_local<T, DIM>(R, sq, Wq, dq);
+      ok = real ? gks_point<T, DIM>(ph, dt, Wq, dq, WL, dW, out) : gks_point<T, DIM>(ph, dt, WL, dW, Wq, dq, out);
+    } else {
+      for (int v = 0; v < NV; ++v) WR[v] = WL[v];
+      ok = gks_point<T, DIM>(ph, dt, WL, dW, WR, dW, out);
+    }
     for (int part = 0; part < 6; ++part) to_global<T, DIM>(R, out + part * NV);
     for (int q = 0; q < 6 * NV; ++q) out_arr[(fb + q) * ns + oidx] = out[q];
     return ok;

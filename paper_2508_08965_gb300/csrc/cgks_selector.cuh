@@ -70,13 +70,15 @@ __device__ __forceinline__ void selector_var(const S* __restrict__ avg, const D*
       o[a] = sd ? 1 : -1;
       int mm;
       const long i = nb.template at<WALL>(c, o[0], o[1], o[2], &mm);
+      const bool inflow = WALL && (mm & MM_INFLOW);
       const int odd = WALL ? mirror_odd<DIM>(v, mm) : 0;
-      const float q = (float)avg[(long)v * N + i];
-      qn[sd] = odd ? -q : q;
+      const float q = inflow ? (float)g.bcq[NbrOff<DIM>::inflow_face(mm, o[0], o[1], o[2]) * 5 + v]
+                             : (float)avg[(long)v * N + i];
+      qn[sd] = (odd && !inflow) ? -q : q;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
-        float gm = (float)der[((long)k * NV + v) * N + i];
-        if (WALL && (odd ^ ((mm >> k) & 1))) gm = -gm;
+        float gm = inflow ? 0.f : (float)der[((long)k * NV + v) * N + i];
+        if (WALL && !inflow && (odd ^ ((mm >> k) & 1))) gm = -gm;
         const float g0 = (float)der[((long)k * NV + v) * N + c];
         const float len = g.curvi ? (float)met_len<DIM>(g, c, k * GPF) : g.hf[k];
         fg = fmaxf(fg, __fmul_rn(__fmul_rn(fabsf(__fsub_rn(gm, g0)), len), inv));
@@ -114,8 +116,12 @@ __device__ __forceinline__ void selector_var(const S* __restrict__ avg, const D*
         o[b] = (sg & 2) ? 1 : -1;
         int mm;
         const long i = nb.template at<WALL>(c, o[0], o[1], o[2], &mm);
-        float q = (float)avg[(long)v * N + i];
-        if (WALL && mirror_odd<DIM>(v, mm)) q = -q;
+        float q;
+        if (WALL && (mm & MM_INFLOW)) q = (float)g.bcq[NbrOff<DIM>::inflow_face(mm, o[0], o[1], o[2]) * 5 + v];
+        else {
+          q = (float)avg[(long)v * N + i];
+          if (WALL && mirror_odd<DIM>(v, mm)) q = -q;
+        }
         fe = fmaxf(fe, __fmul_rn(fabsf(__fsub_rn(q, q0v)), inv));
       }
   }

@@ -10,9 +10,10 @@ cell's stencil varies by less than 1e-6 of its scale (every feature below
 that.  (GENO's absolute epsilon turns variations of order 1e-7, invisible in
 FP32 features, into weights below 1; such cells would otherwise be troubled
 cells with all-zero features.)  Trajectories are seeded four-quadrant
-Riemann problems (outflow boundaries), isentropic vortices and smooth
-random 3-D periodic flows (synth.random_smooth_3d), advanced by the plain
-method (FP64, no selector).
+Riemann problems (outflow boundaries), isentropic vortices, shock-vortex
+interactions (Mach 1.1-3, inflow / outflow / slip walls) and smooth random
+3-D periodic flows (synth.random_smooth_3d), advanced by the plain method
+(FP64, no selector).
 
     python -m paper_2508_08965_gb300.selector --out selector_params.npz
 """
@@ -73,6 +74,17 @@ def vortex_mesh(seed, n):
     return m
 
 
+def shock_vortex_mesh(seed, n):
+    """[0, 2] x [0, 1] at 2n x n cells (square cells), shock Mach number
+    drawn from [1.1, 3] by seed."""
+    import synth
+    mach = synth.shock_vortex_params(seed)
+    m = Mesh(2, (2 * n, n), lo=(0.0, 0.0), hi=(2.0, 1.0), bc=[4, 1, 2, 2],
+             bc_state=[synth.shock_vortex_inflow(mach)], tau_mode=1)
+    m.init(lambda x, y: synth.shock_vortex_2d(x, y, mach))
+    return m
+
+
 def smooth3d_mesh(seed, n):
     import synth
     m = Mesh(3, (n, n, n), lo=(0.0, 0.0, 0.0), hi=(2 * np.pi,) * 3, mu=1e-3, prandtl=0.72, tau_mode=2)
@@ -80,22 +92,31 @@ def smooth3d_mesh(seed, n):
     return m
 
 
-def build_dataset(riemann_seeds, vortex_seeds, n=256, steps=24, stride=1, smooth3d_seeds=(), n3=32):
+def build_dataset(riemann_seeds, vortex_seeds, n=256, steps=24, stride=1, smooth3d_seeds=(), n3=32,
+                  shock_vortex_seeds=(), shock_vortex_steps=None):
     """Samples of the trajectories; Riemann draws the plain method cannot
-    advance are left out (returned as `failed`)."""
+    advance are left out (returned as `failed`).  Shock-vortex meshes are
+    n x n/2 (the cell size of an n^2 Riemann mesh) and run for
+    shock_vortex_steps (default: steps), long enough for the vortex to
+    cross the shock."""
     import torch
     from .binding import CgksError
     X, Y, failed = [], [], []
-    for kind, seeds in (("riemann", riemann_seeds), ("vortex", vortex_seeds), ("smooth3d", smooth3d_seeds)):
+    for kind, seeds in (("riemann", riemann_seeds), ("vortex", vortex_seeds), ("smooth3d", smooth3d_seeds),
+                        ("shockvortex", shock_vortex_seeds)):
         for s in seeds:
+            nst = steps
             if kind == "riemann":
                 m = riemann_mesh(s, n)
             elif kind == "vortex":
                 m = vortex_mesh(s, n)
+            elif kind == "shockvortex":
+                m = shock_vortex_mesh(s, n // 2)
+                nst = shock_vortex_steps or steps
             else:
                 m = smooth3d_mesh(s, n3)
             try:
-                x, y = trajectory_samples(m, steps)
+                x, y = trajectory_samples(m, nst)
             except CgksError:
                 failed.append((kind, s))
                 continue
@@ -168,13 +189,18 @@ def main():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--stride", type=int, default=4)
     ap.add_argument("--smooth3d", type=int, default=8)
+    ap.add_argument("--shock-vortex", type=int, default=8)
+    ap.add_argument("--shock-vortex-steps", type=int, default=192)
     args = ap.parse_args()
     train_r = list(range(0, args.riemann))
     train_v = list(range(1000, 1000 + args.vortex))
     train_s = list(range(2000, 2000 + args.smooth3d))
-    X, y, failed = build_dataset(train_r, train_v, args.n, args.steps, args.stride, train_s)
+    train_k = list(range(3000, 3000 + args.shock_vortex))
+    X, y, failed = build_dataset(train_r, train_v, args.n, args.steps, args.stride, train_s,
+                                 shock_vortex_seeds=train_k, shock_vortex_steps=args.shock_vortex_steps)
     Xv, yv, failed_v = build_dataset(list(range(5000, 5000 + args.riemann // 4)), [6000, 6001], args.n, args.steps,
-                                     args.stride, [7000, 7001])
+                                     args.stride, [7000, 7001], shock_vortex_seeds=[8000, 8001],
+                                     shock_vortex_steps=args.shock_vortex_steps)
     params, hist = train(X, y, epochs=args.epochs)
     thr, lo = thresholds(params, Xv, yv)
     z = mlp_logits(torch.tensor(params, device="cuda"), Xv)

@@ -170,3 +170,128 @@ def test_strong_riemann_fallbacks(orc, cg):
             e = sg[0, 0] - so[0, 0]
             assert np.sqrt(np.mean(e * e) / np.mean(so[0, 0] ** 2)) <= tol
         m.close()
+
+
+INFLOW = 4
+
+
+def cons2(r, u, v, p, g=1.4):
+    return [r, r * u, r * v, p / (g - 1) + 0.5 * r * (u * u + v * v)]
+
+
+def cons3(r, u, v, w, p, g=1.4):
+    return [r, r * u, r * v, r * w, p / (g - 1) + 0.5 * r * (u * u + v * v + w * w)]
+
+
+INFLOW_CASES = [
+    ("inflow-x-2d", 2, (40, 33), [INFLOW, OUT, SLIP, SLIP], [cons2(1.2, 2.0, 0.1, 1.0)], {"tau_mode": 1}),
+    ("inflow-both-2d-visc", 2, (37, 29), [INFLOW, INFLOW, NOSLIP, OUT],
+     [cons2(1.2, 2.0, 0.1, 1.0), cons2(0.9, -0.5, 0.0, 1.1)], VISC),
+    ("inflow-y-2d", 2, (29, 37), [OUT, OUT, INFLOW, SLIP], [None, None, cons2(1.0, 0.1, 0.8, 1.0)], {}),
+    ("inflow-3d", 3, (9, 10, 11), [INFLOW, OUT, SLIP, NOSLIP, P, P], [cons3(1.2, 2.0, 0.1, -0.2, 1.0)], VISC),
+    ("inflow-z-3d", 3, (8, 7, 12), [OUT, OUT, P, P, INFLOW, INFLOW],
+     [None, None, None, None, cons3(1.2, 0.0, 0.1, 0.5, 1.0), cons3(0.8, 0.0, 0.0, 0.3, 0.9)], VISC),
+]
+
+
+def pair_in(orc, cg, dim, n, bc, bcs, kw, fn=None, precision=0):
+    lo, hi = (0.0,) * dim, (1.0,) * dim
+    o = orc.Oracle(dim, n, lo=lo, hi=hi, bc=bc, bc_state=bcs, **kw)
+    o.init(fn or (s2 if dim == 2 else s3))
+    m = cg.Mesh(dim, n, lo=lo, hi=hi, bc=bc, bc_state=bcs, precision=precision, **kw)
+    m.set_state(o.get_state())
+    return o, m
+
+
+@pytest.mark.parametrize("case", INFLOW_CASES, ids=[c[0] for c in INFLOW_CASES])
+def test_inflow_one_step(orc, cg, case):
+    name, dim, n, bc, bcs, kw = case
+    o, m = pair_in(orc, cg, dim, n, bc, bcs, kw)
+    assert abs(m.compute_dt() - o.dt()) <= 1e-14 * o.dt()
+    o.step(1)
+    m.step(1)
+    sg, _ = m.get_state()
+    assert class_scaled_diff(sg, o.get_state(), hmin(n)) <= 1e-12
+    m.close()
+
+
+@pytest.mark.parametrize("case", INFLOW_CASES[:2] + INFLOW_CASES[3:4],
+                         ids=[INFLOW_CASES[i][0] for i in (0, 1, 3)])
+def test_inflow_many_steps(orc, cg, case):
+    name, dim, n, bc, bcs, kw = case
+    o, m = pair_in(orc, cg, dim, n, bc, bcs, kw)
+    steps = 40 if dim == 3 else 100
+    o.step(steps)
+    m.step(steps)
+    sg, tg = m.get_state()
+    assert abs(tg - o.time()) <= 1e-12 * o.time()
+    assert class_scaled_diff(sg, o.get_state(), hmin(n)) <= 1e-9
+    m.close()
+
+
+def test_inflow_fp32_form(orc, cg):
+    name, dim, n, bc, bcs, kw = INFLOW_CASES[1]
+    o, m = pair_in(orc, cg, dim, n, bc, bcs, kw, precision=1)
+    o.step(10)
+    m.step(10)
+    sg, _ = m.get_state()
+    so = o.get_state()
+    rho_l2 = np.sqrt(np.mean((sg[0, 0] - so[0, 0]) ** 2)) / np.sqrt(np.mean(so[0, 0] ** 2))
+    assert rho_l2 < 1e-6
+    m.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_stationary_shock_stays(orc, cg, precision):
+    """A Mach-2 normal shock (Rankine-Hugoniot states, gamma = 1.4) between
+    supersonic inflow and outflow: the post-shock state is kept and the shock
+    stays in its cell layer, on the GPU as in the oracle."""
+    g, m1 = 1.4, 2.0
+    r1, u1, p1 = 1.0, m1 * math.sqrt(1.4), 1.0
+    r2 = r1 * (g + 1) * m1 ** 2 / ((g - 1) * m1 ** 2 + 2)
+    p2 = p1 * (2 * g * m1 ** 2 - (g - 1)) / (g + 1)
+    u2 = r1 * u1 / r2
+    fn = lambda x, y: [np.where(x < 0.5, r1, r2) + 0 * y, np.where(x < 0.5, u1, u2) + 0 * y,  # noqa: E731
+                       0 * x, np.where(x < 0.5, p1, p2) + 0 * y]
+    n = (64, 4)
+    box = {"lo": (0.0, 0.0), "hi": (1.0, 4.0 / 64)}
+    m = cg.Mesh(2, n, bc=[INFLOW, OUT, P, P], bc_state=[cons2(r1, u1, 0.0, p1)], tau_mode=1,
+                precision=precision, **box)
+    o = orc.Oracle(2, n, bc=[INFLOW, OUT, P, P], bc_state=[cons2(r1, u1, 0.0, p1)], tau_mode=1, **box)
+    o.init(fn)
+    m.set_state(o.get_state())
+    m.step(200)
+    sg, _ = m.get_state()
+    rho = sg[0, 0].reshape(-1, n[0])[0]
+    assert abs(rho[0] - r1) <= 1e-6 and abs(rho[-1] - r2) <= 0.02 * r2
+    jump = np.argmax(np.abs(np.diff(rho)))
+    assert abs(jump - (n[0] // 2 - 1)) <= 2
+    m.close()
+
+
+def test_inflow_rejected_on_curvilinear(cg):
+    nodes = synth.perturbed_nodes_3d((6, 6, 6))
+    with pytest.raises(cg.CgksError):
+        cg.Mesh(3, (6, 6, 6), nodes=nodes, bc=[INFLOW, OUT, P, P, P, P], bc_state=[cons3(1, 1, 0, 0, 1)])
+
+
+@pytest.mark.parametrize("mach", [1.1, 3.0])
+def test_shock_vortex_parity(orc, cg, mach):
+    """The shock-vortex interaction (inflow, outflow, slip walls, non-square
+    box) against the oracle: 1e-12 after one step, 1e-9 after 60."""
+    n = (64, 32)
+    kw = dict(lo=(0.0, 0.0), hi=(2.0, 1.0), bc=[INFLOW, OUT, SLIP, SLIP], bc_state=[synth.shock_vortex_inflow(mach)],
+              tau_mode=1)
+    fn = lambda x, y: synth.shock_vortex_2d(x, y, mach)  # noqa: E731
+    o = orc.Oracle(2, n, **kw)
+    o.init(fn)
+    m = cg.Mesh(2, n, **kw)
+    m.set_state(o.get_state())
+    h = 1.0 / 32
+    for steps, tol in ((1, 1e-12), (59, 1e-9)):
+        o.step(steps)
+        m.step(steps)
+        sg, tg = m.get_state()
+        assert abs(tg - o.time()) <= 1e-12 * o.time()
+        assert class_scaled_diff(sg, o.get_state(), h) <= tol
+    m.close()
