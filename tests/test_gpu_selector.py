@@ -150,7 +150,11 @@ TRAINED = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 def test_trained_selector_ablation(cg, precision):
     """A held-out Riemann problem, a held-out shock-vortex interaction and the
     3-D TGV: the trained selector skips most cells and the result stays close
-    to the plain method's."""
+    to the plain method's.  The Riemann problem's skipped cells are constant
+    states, where every reconstruction agrees, hence 1e-6; in the smooth
+    vortex and the TGV a skipped cell's GENO weights are within 1e-3 of 1 but
+    not equal to it, so a skip moves each step by a fraction of the high-/
+    low-order gap, hence 1e-5 there."""
     import torch
     from paper_2508_08965_gb300 import selector
     params, thr, lo = selector.load(TRAINED)
@@ -161,7 +165,7 @@ def test_trained_selector_ablation(cg, precision):
          lambda x, y: synth.riemann4_2d(x, y, states), 20, 0.5, 1e-6),
         ("shock-vortex", dict(dim=2, n=(256, 128), lo=(0, 0), hi=(2, 1), bc=[4, 1, 2, 2], tau_mode=1,
                               bc_state=[synth.shock_vortex_inflow(sv_mach)]),
-         lambda x, y: synth.shock_vortex_2d(x, y, sv_mach), 40, 0.5, 1e-6),
+         lambda x, y: synth.shock_vortex_2d(x, y, sv_mach), 40, 0.5, 1e-5),
         ("tgv", dict(dim=3, n=(64, 64, 64), lo=(0, 0, 0), hi=(2 * math.pi,) * 3, mu=1 / 1600, prandtl=0.72,
                      tau_mode=2), lambda x, y, z: synth.taylor_green_3d(x, y, z), 10, 0.2, 1e-5),
     ]
