@@ -383,11 +383,11 @@ def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
                       dict(dim=2, n=(1024, 1024), lo=(0, 0), hi=(1, 1), bc=[1, 1, 1, 1], tau_mode=1),
                       (lambda st: (lambda x, y: synth.riemann4_2d(x, y, st)))(st), None))
     for seed in (9101, 9102):
-        mach = synth.shock_vortex_params(seed)
-        cases.append(("shockvortex1024 mach %.2f" % mach,
+        mach, eps = synth.shock_vortex_params(seed)
+        cases.append(("shockvortex1024 mach %.2f eps %.2f" % (mach, eps),
                       dict(dim=2, n=(1024, 1024), lo=(0, 0), hi=(2, 1), bc=[4, 1, 2, 2], tau_mode=1,
                            bc_state=[synth.shock_vortex_inflow(mach)]),
-                      (lambda mach: (lambda x, y: synth.shock_vortex_2d(x, y, mach)))(mach), None))
+                      (lambda mach, eps: (lambda x, y: synth.shock_vortex_2d(x, y, mach, eps)))(mach, eps), None))
     cases.append(("tgv128", dict(dim=3, n=(128, 128, 128), **mesh_kwargs("tgv128")), field_fn("tgv128"), s_tgv_init))
     for name, kw, fn, s0 in cases:
         try:

@@ -11,7 +11,8 @@ that.  (GENO's absolute epsilon turns variations of order 1e-7, invisible in
 FP32 features, into weights below 1; such cells would otherwise be troubled
 cells with all-zero features.)  Trajectories are seeded four-quadrant
 Riemann problems (outflow boundaries), isentropic vortices, shock-vortex
-interactions (Mach 1.1-3, inflow / outflow / slip walls) and smooth random
+interactions (Mach 1.1-3, vortex strength 1-5, inflow / outflow / slip
+walls) and smooth random
 3-D periodic flows (synth.random_smooth_3d), advanced by the plain method
 (FP64, no selector).
 
@@ -75,13 +76,13 @@ def vortex_mesh(seed, n):
 
 
 def shock_vortex_mesh(seed, n):
-    """[0, 2] x [0, 1] at 2n x n cells (square cells), shock Mach number
-    drawn from [1.1, 3] by seed."""
+    """[0, 2] x [0, 1] at 2n x n cells (square cells); shock Mach number in
+    [1.1, 3] and vortex strength in [1, 5] drawn by seed."""
     import synth
-    mach = synth.shock_vortex_params(seed)
+    mach, eps = synth.shock_vortex_params(seed)
     m = Mesh(2, (2 * n, n), lo=(0.0, 0.0), hi=(2.0, 1.0), bc=[4, 1, 2, 2],
              bc_state=[synth.shock_vortex_inflow(mach)], tau_mode=1)
-    m.init(lambda x, y: synth.shock_vortex_2d(x, y, mach))
+    m.init(lambda x, y: synth.shock_vortex_2d(x, y, mach, eps))
     return m
 
 

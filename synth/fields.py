@@ -212,28 +212,30 @@ def turbulence_field(seed, n=128, k0=8.0, mach_t=0.5, re_lambda=72.0, gamma=1.4)
     return field, mu
 
 
-def shock_vortex_params(seed, mach_range=(1.1, 3.0)):
-    """Seeded shock Mach number, uniform in `mach_range`."""
+def shock_vortex_params(seed, mach_range=(1.1, 3.0), eps_range=(1.0, 5.0)):
+    """Seeded (shock Mach number, vortex strength), uniform in the ranges."""
     rng = np.random.default_rng(seed)
-    return float(rng.uniform(*mach_range))
+    return float(rng.uniform(*mach_range)), float(rng.uniform(*eps_range))
 
 
 def shock_vortex_upstream(mach, gamma=1.4):
     """Upstream (rho, u, v, p) of the stationary normal shock: rho = p = 1,
-    u = mach * sqrt(gamma) (sound speed 1 * sqrt(gamma))."""
+    u = mach * sqrt(gamma) (the upstream sound speed is sqrt(gamma))."""
     return (1.0, mach * math.sqrt(gamma), 0.0, 1.0)
 
 
-def shock_vortex_2d(x, y, mach, eps=0.3, rc=0.05, alpha=0.204, center=(0.25, 0.5), x_shock=0.5, gamma=1.4):
+def shock_vortex_2d(x, y, mach, eps=3.0, rc=0.05, center=(0.25, 0.5), x_shock=0.5, gamma=1.4):
     """Shock-vortex interaction on [0, 2] x [0, 1]: a stationary normal shock
     at x = x_shock with upstream Mach number `mach` (Rankine-Hugoniot state
-    behind it) and an isentropic vortex of strength eps, core radius rc and
-    decay alpha superposed on the upstream flow at `center` (the classical
-    set-up of Jiang and Shu, J. Comput. Phys. 126, 1996):
-        tau = r / rc,  u' = eps tau e^{alpha (1 - tau^2)} sin(theta),
-        v' = -eps tau e^{alpha (1 - tau^2)} cos(theta),
-        T' = -(gamma - 1) eps^2 e^{2 alpha (1 - tau^2)} / (4 alpha gamma),
-    with T = p / rho and constant entropy p / rho^gamma."""
+    behind it) and, superposed on the upstream flow at `center`, the
+    isentropic vortex of the vortex-advection test with lengths in units of
+    the core radius rc (r = |x - center| / rc):
+        u' = -(eps / 2 pi) e^{(1 - r^2)/2} (y - yc) / rc,
+        v' =  (eps / 2 pi) e^{(1 - r^2)/2} (x - xc) / rc,
+        T' = -(gamma - 1) eps^2 / (8 gamma pi^2) e^{1 - r^2},
+    T = p / rho, with the upstream entropy p / rho^gamma.  The scaled vortex
+    is still a steady solution of the Euler equations (the radial balance
+    dp/dr = rho v_theta^2 / r scales by 1/rc on both sides)."""
     xp = _ns(x)
     r1, u1, _, p1 = shock_vortex_upstream(mach, gamma)
     m2 = mach * mach
@@ -242,12 +244,12 @@ def shock_vortex_2d(x, y, mach, eps=0.3, rc=0.05, alpha=0.204, center=(0.25, 0.5
     u2 = u1 * r1 / r2
     dx = (x - center[0]) / rc
     dy = (y - center[1]) / rc
-    tau2 = dx * dx + dy * dy
-    e = xp.exp(alpha * (1.0 - tau2))
-    du = eps * dy * e
-    dv = -eps * dx * e
-    temp = p1 / r1 - (gamma - 1.0) * eps * eps * e * e / (4.0 * alpha * gamma)
-    rho_v = r1 * (temp / (p1 / r1)) ** (1.0 / (gamma - 1.0))
+    e = xp.exp(0.5 * (1.0 - dx * dx - dy * dy))
+    du = -(eps / (2.0 * math.pi)) * e * dy
+    dv = (eps / (2.0 * math.pi)) * e * dx
+    t1 = p1 / r1
+    temp = t1 - (gamma - 1.0) * eps * eps / (8.0 * gamma * math.pi ** 2) * e * e
+    rho_v = r1 * (temp / t1) ** (1.0 / (gamma - 1.0))
     p_v = rho_v * temp
     up = x < x_shock
     zero = 0.0 * x
@@ -260,7 +262,7 @@ def shock_vortex_2d(x, y, mach, eps=0.3, rc=0.05, alpha=0.204, center=(0.25, 0.5
 
 def shock_vortex_inflow(mach, gamma=1.4):
     """Conservative upstream state for the inflow face of the shock-vortex
-    problem.  The face holds the unperturbed stream: the vortex's tail at
-    x = 0 (|v'| <= 1.2e-2, e^{-4.9} of its peak) is not imposed there."""
+    problem: the unperturbed stream (the vortex's tail at x = 0, five core
+    radii from its centre, is below 1e-4 of the stream)."""
     r, u, v, p = shock_vortex_upstream(mach, gamma)
     return [r, r * u, r * v, p / (gamma - 1.0) + 0.5 * r * (u * u + v * v)]

@@ -159,13 +159,13 @@ def test_trained_selector_ablation(cg, precision):
     from paper_2508_08965_gb300 import selector
     params, thr, lo = selector.load(TRAINED)
     states = synth.riemann4_params(777777)
-    sv_mach = synth.shock_vortex_params(888888)
+    sv_mach, sv_eps = synth.shock_vortex_params(888888)
     cases = [
         ("riemann", dict(dim=2, n=(256, 256), lo=(0, 0), hi=(1, 1), bc=[1, 1, 1, 1], tau_mode=1),
          lambda x, y: synth.riemann4_2d(x, y, states), 20, 0.5, 1e-6),
         ("shock-vortex", dict(dim=2, n=(256, 128), lo=(0, 0), hi=(2, 1), bc=[4, 1, 2, 2], tau_mode=1,
                               bc_state=[synth.shock_vortex_inflow(sv_mach)]),
-         lambda x, y: synth.shock_vortex_2d(x, y, sv_mach), 40, 0.5, 1e-5),
+         lambda x, y: synth.shock_vortex_2d(x, y, sv_mach, sv_eps), 40, 0.5, 1e-5),
         ("tgv", dict(dim=3, n=(64, 64, 64), lo=(0, 0, 0), hi=(2 * math.pi,) * 3, mu=1 / 1600, prandtl=0.72,
                      tau_mode=2), lambda x, y, z: synth.taylor_green_3d(x, y, z), 10, 0.2, 1e-5),
     ]

@@ -264,9 +264,31 @@ def test_shock_vortex_field_satisfies_rankine_hugoniot():
         assert abs(u[0] / math.sqrt(g * p[0] / r[0]) - mach) < 1e-12
         xv = 0.25 + 0.03 * np.cos(np.linspace(0, 6, 7))
         yv = 0.5 + 0.03 * np.sin(np.linspace(0, 6, 7))
-        rv, uv, vv, pv = synth.shock_vortex_2d(xv, yv, mach)
+        rv, uv, vv, pv = synth.shock_vortex_2d(xv, yv, mach, eps=5.0)
         assert np.allclose(pv / rv ** g, 1.0, rtol=0, atol=1e-13)
         assert np.all(rv < 1.0)
+
+
+@pytest.mark.parametrize("eps", [1.0, 5.0])
+def test_shock_vortex_vortex_is_steady(eps):
+    """The scaled vortex is a steady Euler solution: in its own frame the
+    velocity is azimuthal and the pressure balances the centripetal term,
+    dp/dr = rho v_theta^2 / r (central differences, step 1e-5 rc)."""
+    import synth
+    mach, rc, (xc, yc) = 2.0, 0.05, (0.25, 0.5)
+    u1 = synth.shock_vortex_upstream(mach)[1]
+    th = np.linspace(0.1, 6.0, 9)
+    for rr in (0.3, 1.0, 2.0):
+        x, y = xc + rr * rc * np.cos(th), yc + rr * rc * np.sin(th)
+        rho, u, v, p = synth.shock_vortex_2d(x, y, mach, eps, rc=rc)
+        ur = (u - u1) * np.cos(th) + v * np.sin(th)
+        vt = -(u - u1) * np.sin(th) + v * np.cos(th)
+        assert np.abs(ur).max() < 1e-14
+        d = 1e-5 * rc
+        pp = synth.shock_vortex_2d(x + d * np.cos(th), y + d * np.sin(th), mach, eps, rc=rc)[3]
+        pm = synth.shock_vortex_2d(x - d * np.cos(th), y - d * np.sin(th), mach, eps, rc=rc)[3]
+        dpdr = (pp - pm) / (2 * d)
+        assert np.allclose(dpdr, rho * vt * vt / (rr * rc), rtol=1e-7, atol=0)
 
 
 def test_shock_vortex_oracle_keeps_shock_and_upstream(orc):
@@ -279,7 +301,7 @@ def test_shock_vortex_oracle_keeps_shock_and_upstream(orc):
     nx, ny = 48, 24
     o = orc.Oracle(2, (nx, ny), lo=(0, 0), hi=(2, 1), tau_mode=1, bc=[INFLOW, OUTFLOW, 2, 2],
                    bc_state=[synth.shock_vortex_inflow(mach)])
-    o.init(lambda x, y: synth.shock_vortex_2d(x, y, mach))
+    o.init(lambda x, y: synth.shock_vortex_2d(x, y, mach, 3.0))
     o.step(30)
     rho = o.get_state()[0, 0]
     assert np.all(np.isfinite(rho))
