@@ -69,7 +69,7 @@ FEATURE_CASES = [
     ("walls", dict(dim=2, n=(24, 20), lo=(0, 0), hi=(1, 1), bc=[3, 3, 2, 2]), _walls),
     ("shock-vortex", dict(dim=2, n=(48, 24), lo=(0, 0), hi=(2, 1), bc=[4, 1, 2, 2], tau_mode=1,
                           bc_state=[synth.shock_vortex_inflow(1.7)]),
-     lambda x, y: synth.shock_vortex_2d(x, y, 1.7)),
+     lambda x, y: synth.shock_vortex_2d(x, y, 1.7, rc=0.15)),
     ("tgv3d", dict(dim=3, n=(10, 9, 8), lo=(0, 0, 0), hi=(2 * math.pi,) * 3),
      lambda x, y, z: synth.taylor_green_3d(x, y, z)),
 ]
