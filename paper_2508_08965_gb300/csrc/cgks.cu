@@ -225,8 +225,10 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   g.bcq = nullptr;
   for (int f = 0; f < 2 * dim; ++f)
     if (d->bc[f] == CGKS_BC_INFLOW && !ctx->d_bcq) {
-      ALLOC(ctx->d_bcq, sizeof(double) * 30);
-      CK(cudaMemcpyAsync(ctx->d_bcq, &d->bc_state[0][0], sizeof(double) * 30, cudaMemcpyHostToDevice, ctx->stream));
+      double hq[cgks::BCQ_DOUBLES];
+      cgks::pack_bcq(d->bc_state, hq);
+      ALLOC(ctx->d_bcq, sizeof(hq));
+      CK(cudaMemcpy(ctx->d_bcq, hq, sizeof(hq), cudaMemcpyHostToDevice));
       g.bcq = ctx->d_bcq;
     }
   ALLOC(ctx->chi, sizeof(double) * (size_t)nv * N);

@@ -69,7 +69,7 @@ struct cgks_batch {
   DtState* dts = nullptr;
   int* st = nullptr;
   double* staging = nullptr; /* public layout of the largest case */
-  double* bcq = nullptr;     /* inflow states [case][face][5] */
+  double* bcq = nullptr;     /* inflow states per case (cgks::BCQ_DOUBLES each) */
   List l_recon[2], l_flux, l_fbnd, l_upd, l_dt;
   cgks_batch_tiles tiles{};
   std::vector<Graph> graphs;
@@ -362,16 +362,15 @@ cgks_status cgks_batch_create(const cgks_mesh_desc* descs, int ncase, void* stre
   BALLOC(b->dts, sizeof(DtState) * ncase);
   BALLOC(b->st, sizeof(int) * ST_N);
   BALLOC(b->staging, sizeof(double) * (nd + nv) * maxcell);
-  BALLOC(b->bcq, sizeof(double) * 30 * ncase);
+  BALLOC(b->bcq, sizeof(double) * cgks::BCQ_DOUBLES * ncase);
 #undef BALLOC
   {
-    std::vector<double> hq(30 * (size_t)ncase);
+    std::vector<double> hq(cgks::BCQ_DOUBLES * (size_t)ncase);
     for (int k = 0; k < ncase; ++k) {
-      memcpy(&hq[30 * (size_t)k], &descs[k].bc_state[0][0], sizeof(double) * 30);
-      b->hcase[k].g.bcq = b->bcq + 30 * (size_t)k;
+      cgks::pack_bcq(descs[k].bc_state, &hq[cgks::BCQ_DOUBLES * (size_t)k]);
+      b->hcase[k].g.bcq = b->bcq + cgks::BCQ_DOUBLES * (size_t)k;
     }
-    if (cudaMemcpyAsync(b->bcq, hq.data(), sizeof(double) * hq.size(), cudaMemcpyHostToDevice, b->stream) !=
-        cudaSuccess) {
+    if (cudaMemcpy(b->bcq, hq.data(), sizeof(double) * hq.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
       cgks_batch_destroy(b);
       return CGKS_ECUDA;
     }

@@ -114,12 +114,16 @@ __global__ void __launch_bounds__(128, min_blocks<T, DIM>())
     const double* avg = A.avg_in + NV * o;
     const float* avh = A.avh_in ? A.avh_in + NV * o : nullptr;
     const T* der = A.der_in + (long)(batch_nf<DIM>() - 1) * NV * o;
+    const bool wall = wall_warp<WALL, DIM>(g, active, i, j, k);
     bool skip = false;
-    if (sel.on && !ph.linear) skip = selector_skip<T, DIM, WALL>(sel, avg, avh, der, g, c, i, j, k, active);
+    if (sel.on && !ph.linear) skip = selector_skip<T, DIM, WALL>(sel, avg, avh, der, g, c, i, j, k, active, wall);
     if (active) {
       const int ngp = DIM * Sz<DIM>::GPF * NV * (1 + DIM);
-      recon_cell<T, DIM, false, WALL>(avg, avh, A.avl_in ? A.avl_in + NV * o : nullptr, der, g, ph, c, i, j, k,
-                                      A.gpL + (long)ngp * o, A.gpR + (long)ngp * o, nullptr, 0, A.st, skip);
+      const float* avl = A.avl_in ? A.avl_in + NV * o : nullptr;
+      T* gl = A.gpL + (long)ngp * o;
+      T* gr = A.gpR + (long)ngp * o;
+      if (wall) recon_cell<T, DIM, false, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, gl, gr, nullptr, 0, A.st, skip);
+      else recon_cell<T, DIM, false, false>(avg, avh, avl, der, g, ph, c, i, j, k, gl, gr, nullptr, 0, A.st, skip);
     }
   }
 }

@@ -42,7 +42,7 @@ struct cgks_ctx {
   double* d_nodes = nullptr;
   double* d_met = nullptr;
   float* d_rmet = nullptr;
-  double* d_bcq = nullptr;  /* inflow states [face][5] */
+  double* d_bcq = nullptr;  /* inflow states [face][5], then their FP32 hi and lo parts */
   double* d_lo = nullptr;
   /* state buffers.  FP64: full public-layout arrays U (current), Us
      (intermediate) and a stash, with the derivative fields right after the

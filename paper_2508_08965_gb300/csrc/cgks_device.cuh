@@ -88,7 +88,9 @@ struct DevGeo {
   int bcm;            /* boundary kind (BcKind) of domain face f = -x,+x,-y,+y,-z,+z in bits
                          3f..3f+2: shifts, not an array, so that no copy of DevGeo is
                          indexed at run time (which would put it in local memory) */
-  const double* bcq;  /* inflow faces: conservative states [face][5] (device), or null */
+  const double* bcq;  /* inflow faces: conservative states [face][5] (device), followed by
+                         their exact FP32 hi and lo parts [face][5] each (bcq_hi, bcq_lo);
+                         or null when no face is an inflow */
   long nplane;        /* slots of the low-boundary face array per (axis, Gauss point):
                          the largest ncell / n[axis] over non-periodic axes, else 0 */
 };
@@ -96,6 +98,22 @@ struct DevGeo {
 /* boundary kinds (the values of the public CGKS_BC_* codes) */
 enum BcKind { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_SLIP = 2, BC_NOSLIP = 3, BC_INFLOW = 4 };
 CGKS_HD int geo_bc(const DevGeo& g, int f) { return (g.bcm >> (3 * f)) & 7; }
+constexpr int BCQ_DOUBLES = 60; /* size of one inflow-state block in doubles: 30 + 2 x 30 floats */
+CGKS_HD const float* bcq_hi(const DevGeo& g) { return reinterpret_cast<const float*>(g.bcq + 30); }
+CGKS_HD const float* bcq_lo(const DevGeo& g) { return reinterpret_cast<const float*>(g.bcq + 30) + 30; }
+/* host: one block of inflow states (BCQ_DOUBLES doubles) from the
+   descriptor's [face][5] states: the FP64 values, then their exact FP32 hi
+   and lo parts */
+inline void pack_bcq(const double (&st)[6][5], double* out) {
+  float* h = reinterpret_cast<float*>(out + 30);
+  float* l = h + 30;
+  for (int q = 0; q < 30; ++q) {
+    const double x = st[q / 5][q % 5];
+    out[q] = x;
+    h[q] = (float)x;
+    l[q] = (float)(x - (double)h[q]);
+  }
+}
 CGKS_HD bool bc_wall(int bc) { return bc == BC_SLIP || bc == BC_NOSLIP; }
 
 /* FP32 CFL metric of a curvilinear cell, [k * ncell + cell]: per axis the
@@ -222,6 +240,19 @@ template <int DIM> struct NbrOff {
   }
 };
 
+/* true if a neighbour of cell (ci, cj, ck) lies beyond a wall or inflow face
+   (the cell touches such a face); elsewhere the plain neighbour path applies */
+template <int DIM> CGKS_HD bool touches_wall(const DevGeo& g, int ci, int cj, int ck) {
+  const int x[3] = {ci, cj, ck};
+  bool t = false;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    t |= x[a] == 0 && geo_bc(g, 2 * a) >= BC_SLIP;
+    t |= x[a] == g.n[a] - 1 && geo_bc(g, 2 * a + 1) >= BC_SLIP;
+  }
+  return t;
+}
+
 /* 1 if variable v changes sign in the mirror image across the axes of mm:
    the momentum component along a mirrored axis, and every momentum
    component at a no-slip mirror; a derivative along a mirrored axis changes
@@ -330,20 +361,29 @@ template <typename T, int DIM, bool CURVI, bool WALL> struct ReconLd {
     }
   }
   CGKS_HD T q0() const { return T(0); }
+  /* branch-free: beyond an inflow face the (base, index) of the one load
+     switch to the face's state, a mirror image flips the loaded value, so a
+     stencil's loads issue together */
   CGKS_HD T avg(int ox, int oy, int oz) const {
     int mm;
-    const long i = (long)v * g.ncell + nb.template at<WALL>(c, ox, oy, oz, &mm);
-    if (WALL && (mm & MM_INFLOW)) {
-      const double q = g.bcq[NbrOff<DIM>::inflow_face(mm, ox, oy, oz) * 5 + v];
-      if constexpr (sizeof(T) == 4) return T(q - (double(q0h) + double(q0l)));
-      else return T(q - q0d);
+    long i = (long)v * g.ncell + nb.template at<WALL>(c, ox, oy, oz, &mm);
+    const bool inflow = WALL && (mm & MM_INFLOW);
+    const bool odd = WALL && !inflow && mirror_odd<DIM>(v, mm);
+    if (inflow) i = NbrOff<DIM>::inflow_face(mm, ox, oy, oz) * 5 + v;
+    if constexpr (sizeof(T) == 4) {
+      const float* ph = inflow ? bcq_hi(g) : avh;
+      const float* pl = inflow ? bcq_lo(g) : avl;
+      float h = ph[i], l = pl[i];
+      if (odd) {
+        h = -h;
+        l = -l;
+      }
+      return (h - q0h) + (l - q0l);
+    } else {
+      double a = (inflow ? g.bcq : avgp)[i];
+      if (odd) a = -a;
+      return T(a - q0d);
     }
-    if (WALL && mirror_odd<DIM>(v, mm)) {
-      if constexpr (sizeof(T) == 4) return (-avh[i] - q0h) + (-avl[i] - q0l);
-      else return T(-avgp[i] - q0d);
-    }
-    if constexpr (sizeof(T) == 4) return (avh[i] - q0h) + (avl[i] - q0l);
-    else return T(avgp[i] - q0d);
   }
   /* the full value q0 + rel at a Gauss point, stored in T */
   CGKS_HD T full(T rel) const {

@@ -84,17 +84,37 @@ __device__ __forceinline__ void recon_cell(const double* __restrict__ avg, const
     for (int v = 0; v < NV; ++v) chi[(long)v * g.ncell + c] = double(cs[v]);
 }
 
+/* whether the calling warp reconstructs with the boundary selects of the
+   WALL path (warp-collective).  2-D: only warps with a cell next to a wall or
+   inflow face do (the selects cost the latency-bound FP32 form about 40%;
+   measured 0.33 -> 0.24 ms on a 1024^2 shock-vortex mesh).  3-D: every warp
+   of a WALL mesh: warps run along x, so at 128 cells per row half of them
+   touch an x-wall, and a second inlined copy of the 3-D reconstruction cost
+   more than it saved (2.67 -> 3.44 ms at 128^3). */
+template <bool WALL, int DIM>
+__device__ __forceinline__ bool wall_warp(const DevGeo& g, bool active, int i, int j, int k) {
+  if constexpr (WALL && DIM == 2) return __any_sync(0xffffffffu, active && touches_wall<DIM>(g, i, j, k));
+  else return WALL;
+}
+
 /* the selector's decision for the calling lane's cell (warp-collective: all
-   lanes call it, inactive ones with active = false); blocks of 128 threads */
+   lanes call it, inactive ones with active = false); blocks of 128 threads.
+   wall: the warp has a cell next to a wall or inflow face (warp-uniform) */
 template <typename T, int DIM, bool WALL>
 __device__ __forceinline__ bool selector_skip(const SelectorDev& sel, const double* __restrict__ avg,
                                               const float* __restrict__ avh, const T* __restrict__ der,
-                                              const DevGeo& g, long c, int i, int j, int k, bool active) {
+                                              const DevGeo& g, long c, int i, int j, int k, bool active,
+                                              bool wall = WALL) {
   __shared__ uint32_t stage[4][32 * SEL_PITCH];
   float f[SEL_NF];
   if (active) {
-    if constexpr (sizeof(T) == 4) selector_features<DIM, WALL>(avh, der, g, c, i, j, k, f);
-    else selector_features<DIM, WALL>(avg, der, g, c, i, j, k, f);
+    if (WALL && wall) {
+      if constexpr (sizeof(T) == 4) selector_features<DIM, WALL>(avh, der, g, c, i, j, k, f);
+      else selector_features<DIM, WALL>(avg, der, g, c, i, j, k, f);
+    } else {
+      if constexpr (sizeof(T) == 4) selector_features<DIM, false>(avh, der, g, c, i, j, k, f);
+      else selector_features<DIM, false>(avg, der, g, c, i, j, k, f);
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < SEL_NF; ++q) f[q] = 0.f;
@@ -111,10 +131,12 @@ __global__ void __launch_bounds__(128, min_blocks<T, DIM>())
   const bool active = c < g.ncell;
   int i = 0, j = 0, k = 0;
   if (active) cell_ijk(g, c, i, j, k);
+  const bool wall = wall_warp<WALL, DIM>(g, active, i, j, k);
   bool skip = false;
-  if (sel.on && !ph.linear) skip = selector_skip<T, DIM, WALL>(sel, avg, avh, der, g, c, i, j, k, active);
+  if (sel.on && !ph.linear) skip = selector_skip<T, DIM, WALL>(sel, avg, avh, der, g, c, i, j, k, active, wall);
   if (!active) return;
-  recon_cell<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st, skip);
+  if (wall) recon_cell<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st, skip);
+  else recon_cell<T, DIM, CURVI, false>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st, skip);
 }
 
 /* features of every cell of a state, [cell][SEL_NF] (training samples) */

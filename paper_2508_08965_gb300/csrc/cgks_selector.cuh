@@ -50,6 +50,15 @@ struct SelectorDev {
 
 enum { SEL_GENO = 0, SEL_SKIP = 1 };
 
+/* an average (index i of avg) or an inflow state (index i of the face
+   states, in the averages' type: FP64, or the FP32 form's hi parts) */
+__device__ __forceinline__ double sel_avg(const double* avg, const DevGeo& g, bool inflow, long i) {
+  return (inflow ? g.bcq : avg)[i];
+}
+__device__ __forceinline__ float sel_avg(const float* avg, const DevGeo& g, bool inflow, long i) {
+  return (inflow ? bcq_hi(g) : avg)[i];
+}
+
 /* features of cell c; S: the averages' type (double or the FP32 form's hi
    parts), D: the derivative fields' type */
 /* per-variable maxima over the axes (J, E, R, S, C) and the running G */
@@ -70,15 +79,19 @@ __device__ __forceinline__ void selector_var(const S* __restrict__ avg, const D*
       o[a] = sd ? 1 : -1;
       int mm;
       const long i = nb.template at<WALL>(c, o[0], o[1], o[2], &mm);
+      /* branch-free loads: an inflow neighbour switches the load's base and
+         index to the face's state (FP32 form: its hi part, = its float) */
       const bool inflow = WALL && (mm & MM_INFLOW);
       const int odd = WALL ? mirror_odd<DIM>(v, mm) : 0;
-      const float q = inflow ? (float)g.bcq[NbrOff<DIM>::inflow_face(mm, o[0], o[1], o[2]) * 5 + v]
-                             : (float)avg[(long)v * N + i];
-      qn[sd] = (odd && !inflow) ? -q : q;
+      float q = (float)sel_avg(avg, g, inflow, inflow ? NbrOff<DIM>::inflow_face(mm, o[0], o[1], o[2]) * 5 + v
+                                                      : (long)v * N + i);
+      if (odd && !inflow) q = -q;
+      qn[sd] = q;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
-        float gm = inflow ? 0.f : (float)der[((long)k * NV + v) * N + i];
-        if (WALL && !inflow && (odd ^ ((mm >> k) & 1))) gm = -gm;
+        float gm = (float)der[((long)k * NV + v) * N + i];
+        if (WALL && (odd ^ ((mm >> k) & 1))) gm = -gm;
+        if (inflow) gm = 0.f;
         const float g0 = (float)der[((long)k * NV + v) * N + c];
         const float len = g.curvi ? (float)met_len<DIM>(g, c, k * GPF) : g.hf[k];
         fg = fmaxf(fg, __fmul_rn(__fmul_rn(fabsf(__fsub_rn(gm, g0)), len), inv));
@@ -116,12 +129,10 @@ __device__ __forceinline__ void selector_var(const S* __restrict__ avg, const D*
         o[b] = (sg & 2) ? 1 : -1;
         int mm;
         const long i = nb.template at<WALL>(c, o[0], o[1], o[2], &mm);
-        float q;
-        if (WALL && (mm & MM_INFLOW)) q = (float)g.bcq[NbrOff<DIM>::inflow_face(mm, o[0], o[1], o[2]) * 5 + v];
-        else {
-          q = (float)avg[(long)v * N + i];
-          if (WALL && mirror_odd<DIM>(v, mm)) q = -q;
-        }
+        const bool inflow = WALL && (mm & MM_INFLOW);
+        float q = (float)sel_avg(avg, g, inflow, inflow ? NbrOff<DIM>::inflow_face(mm, o[0], o[1], o[2]) * 5 + v
+                                                        : (long)v * N + i);
+        if (WALL && !inflow && mirror_odd<DIM>(v, mm)) q = -q;
         fe = fmaxf(fe, __fmul_rn(fabsf(__fsub_rn(q, q0v)), inv));
       }
   }
