@@ -796,16 +796,14 @@ CGKS_HD void euler_jvp(const MxS<T, DIM>& g, T gam, const T* W, int j, const T* 
   out[DIM + 1] = uj * (dW[DIM + 1] + dp) + H * (dmj - uj * dW[0]);
 }
 
-/* time integrals over [0, dl] of the six coefficient functions of Eq. (flux) */
+/* time integrals over [0, dl] of the six coefficient functions of Eq. (flux),
+   given em = 1 - e^{-dl/tau} and ex = e^{-dl/tau} */
 template <typename T>
-CGKS_HD void tcoef(T tau, T dl, T* c) {
+CGKS_HD void tcoef(T tau, T dl, T em, T ex, T* c) {
   if (tau <= T(0)) {
     c[0] = dl; c[1] = T(0); c[2] = T(0.5) * dl * dl; c[3] = T(0); c[4] = T(0); c[5] = T(0);
     return;
   }
-  const T x = dl / tau;
-  const T em = -cg_expm1(-x);
-  const T ex = cg_exp(-x);
   c[0] = dl - tau * em;
   c[1] = T(2) * tau * tau - tau * (dl + T(2) * tau) * ex - tau * dl;
   c[2] = T(0.5) * dl * dl - tau * dl + tau * tau * em;
@@ -850,11 +848,9 @@ CGKS_HD void side_dir(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, c
 }
 
 template <typename T, int DIM, class Ld>
-CGKS_HD void side_all(const MxS<T, DIM>& s, T gam, T D, T iD, const T* W, const Ld& ld, int side, const T* cn,
-                      const T* ct, bool prfix, T* Fn, T* Ft, T* Qn, T* Qt, T* bs, T* dW0) {
+CGKS_HD void side_all(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, const T* W, const Ld& ld, int side,
+                      const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, T* Qn, T* Qt, T* bs, T* dW0) {
   constexpr int NV = DIM + 2;
-  MxT<T> t;
-  mx_tables<T, DIM>(s, t);
 #pragma unroll
   for (int i = 0; i < NV; ++i) bs[i] = T(0);
   T dWj[NV];
@@ -925,11 +921,13 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   constexpr int NV = DIM + 2;
   const T gam = ph_gamma<T>(ph);
   const T D = T(2) / (gam - T(1));
-  const T iD = T(1) / D;
+  const T iD = T(0.5) * (gam - T(1));
   const T K = D - T(DIM);
   MxS<T, DIM> l, r, z;
   if (!mx_init<T, DIM>(WL, gam, K, REG_POS, l) || !mx_init<T, DIM>(WR, gam, K, REG_NEG, r)) return false;
-  /* equilibrium state W0 and flux part 3 from the two half Maxwellians */
+  /* equilibrium state W0 and flux part 3 from the two half Maxwellians (the
+     moment tables are rebuilt for the slope parts below: keeping both sides'
+     tables live would cost more in register spills than they take to build) */
   T W0[NV], H3[NV], t1[NV], t2[NV];
   {
     MxT<T> t;
@@ -958,9 +956,13 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   else if (ph.tau_mode == 2) tau = ph_mu<T>(ph) / z.p + T(5) * jump * dt;
   T cn[6], ct[6];
   {
+    /* one expm1 serves both intervals: with eh = 1 - e^{-dt/(2 tau)},
+       1 - e^{-dt/tau} = eh (2 - eh) and e^{-dt/tau} = (1 - eh)^2 */
     T cf[6], chf[6];
-    tcoef<T>(tau, dt, cf);
-    tcoef<T>(tau, T(0.5) * dt, chf);
+    const T eh = tau > T(0) ? -cg_expm1(T(-0.5) * dt / tau) : T(0);
+    const T xh = T(1) - eh;
+    tcoef<T>(tau, dt, eh * (T(2) - eh), xh * xh, cf);
+    tcoef<T>(tau, T(0.5) * dt, eh, xh, chf);
     const T idt = T(1) / dt;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -981,8 +983,13 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   }
 #pragma unroll
   for (int i = 0; i < DIM * NV; ++i) dW0[i] = T(0);
-  side_all<T, DIM>(l, gam, D, iD, WL, ld, 0, cn, ct, prfix, Fn, Ft, Qn, Qt, bl, dW0);
-  side_all<T, DIM>(r, gam, D, iD, WR, ld, 1, cn, ct, prfix, Fn, Ft, Qn, Qt, br, dW0);
+  {
+    MxT<T> t;
+    mx_tables<T, DIM>(l, t);
+    side_all<T, DIM>(l, t, gam, D, iD, WL, ld, 0, cn, ct, prfix, Fn, Ft, Qn, Qt, bl, dW0);
+    mx_tables<T, DIM>(r, t);
+    side_all<T, DIM>(r, t, gam, D, iD, WR, ld, 1, cn, ct, prfix, Fn, Ft, Qn, Qt, br, dW0);
+  }
   {
     MxT<T> t;
     mx_tables<T, DIM>(z, t);
@@ -1054,8 +1061,11 @@ CGKS_HD bool gks_point(const Phys& ph, T dt, const T* WL, const T* dWL, const T*
 }
 
 /* derivative loader of the Cartesian path: reads the local-frame derivative of
-   side 0 (left, gpL) or 1 (right, gpR) along local axis j from global memory,
-   through the signed-permutation frame */
+   side 0 (left, gl) or 1 (right, gr) along local axis j, through the
+   signed-permutation frame.  Component q of a side's Gauss-point state is at
+   [(base + q) * N + c]: the global face-major arrays (base of the face, N =
+   cells, c = slot), or a thread's staged copy in shared memory (base 0, N =
+   the block size, c = the thread) */
 template <typename T, int DIM> struct CartLd {
   const T* gl;
   const T* gr;
@@ -1071,6 +1081,22 @@ template <typename T, int DIM> struct CartLd {
     }
   }
 };
+
+/* asynchronous copy of one element global -> shared (cp.async, sm_80 on):
+   the copies of a thread stay in flight together until async_wait_all */
+template <typename T> __device__ __forceinline__ void async_copy(T* dst_smem, const T* src) {
+#if defined(__CUDA_ARCH__)
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(sizeof(T)) : "memory");
+#else
+  *dst_smem = *src;
+#endif
+}
+__device__ __forceinline__ void async_wait_all() {
+#if defined(__CUDA_ARCH__)
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+#endif
+}
 
 /* local orthonormal frame rows (n, t1, t2): n along the area vector, t1 from
    the face tangent (3-D); t = (-n_y, n_x) in 2-D */
@@ -1154,10 +1180,14 @@ CGKS_HD void to_global(const double R[3][3], T* F) {
 
 /* one face Gauss point: gather, rotate, solve, rotate back, store.
    CURVI selects at compile time between the Cartesian signed-permutation
-   frames and general face frames. */
+   frames and general face frames.  Cartesian: with sm (this thread's slot of
+   a [2][NV (1+DIM)][ns] shared array, ns = the block size) the point's two
+   Gauss-point states are first copied there asynchronously, all 2 NV (1+DIM)
+   loads in flight at once, and the solve reads them from shared memory. */
 template <typename T, int DIM, bool CURVI>
 CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, long c,
-                        const T* __restrict__ gpL, const T* __restrict__ gpR, T* __restrict__ flux) {
+                        const T* __restrict__ gpL, const T* __restrict__ gpR, T* __restrict__ flux,
+                        T* sm = nullptr, int ns = 0) {
   typedef Sz<DIM> S;
   constexpr int NV = S::NV;
   const long N = g.ncell;
@@ -1166,12 +1196,27 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
   if constexpr (!CURVI) {
     /* value and momentum: W_loc[1+i] = s_i m_{p_i}; derivative along local j:
        s_j d/dx_{p_j} of the local variable (loaded when its side needs it) */
+    constexpr int NQ = NV * (1 + DIM);
     CartLd<T, DIM> ld;
-    ld.gl = gpL;
-    ld.gr = gpR;
-    ld.base = base;
-    ld.N = N;
-    ld.c = c;
+    if (sm) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        async_copy(sm + (long)q * ns, gpL + (base + q) * N + c);
+        async_copy(sm + (long)(NQ + q) * ns, gpR + (base + q) * N + c);
+      }
+      async_wait_all();
+      ld.gl = sm;
+      ld.gr = sm + (long)NQ * ns;
+      ld.base = 0;
+      ld.N = ns;
+      ld.c = 0;
+    } else {
+      ld.gl = gpL;
+      ld.gr = gpR;
+      ld.base = base;
+      ld.N = N;
+      ld.c = c;
+    }
     cart_frame<DIM>(ax, ld.p, ld.s);
     const int* p = ld.p;
     const int* s = ld.s;
@@ -1179,9 +1224,9 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
     for (int v = 0; v < NV; ++v) {
       int vg = v, sv = 1;
       if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
-      const long b = (base + vg * (1 + DIM)) * N + c;
-      WL[v] = T(sv) * gpL[b];
-      WR[v] = T(sv) * gpR[b];
+      const long b = (ld.base + vg * (1 + DIM)) * ld.N + ld.c;
+      WL[v] = T(sv) * ld.gl[b];
+      WR[v] = T(sv) * ld.gr[b];
     }
     bool ok = gks_point_ld<T, DIM>(ph, dt, WL, WR, ld, out);
     const long fb = (long)((ax * S::GPF + k) * 6) * NV;

@@ -159,7 +159,8 @@ __global__ void k_selector_features(const double* __restrict__ avg, const float*
    left to the boundary items */
 template <typename T, int DIM, bool CURVI>
 __device__ __forceinline__ void flux_item(const DevGeo& g, const Phys& ph, double dt, long t, const T* __restrict__ gpL,
-                                          const T* __restrict__ gpR, T* __restrict__ flux, int* __restrict__ st) {
+                                          const T* __restrict__ gpR, T* __restrict__ flux, int* __restrict__ st,
+                                          T* sm = nullptr, int ns = 0) {
   const long N = g.ncell;
   const long c = t % N;
   const int r = (int)(t / N);
@@ -169,7 +170,7 @@ __device__ __forceinline__ void flux_item(const DevGeo& g, const Phys& ph, doubl
     cell_ijk(g, c, ijk[0], ijk[1], ijk[2]);
     if (ijk[ax] == g.n[ax] - 1) return;
   }
-  if (!flux_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c, gpL, gpR, flux)) atomicOr(&st[ST_FLUX], 1);
+  if (!flux_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c, gpL, gpR, flux, sm, ns)) atomicOr(&st[ST_FLUX], 1);
 }
 
 /* boundary face-point item t = ((side * DIM + ax) * GPF + k) * nplane + plane.
@@ -206,7 +207,8 @@ __device__ __forceinline__ void flux_bnd_item(const DevGeo& g, const Phys& ph, d
   if (!ok) atomicOr(&st[ST_FLUX], 1);
 }
 
-/* one thread per face slot and Gauss point */
+/* one thread per face slot and Gauss point (blocks of 128); the Cartesian
+   path stages each point's Gauss-point states in shared memory */
 template <typename T, int DIM, bool CURVI>
 __global__ void __launch_bounds__(128, min_blocks<T, DIM>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
                                               const T* __restrict__ gpL, const T* __restrict__ gpR,
@@ -216,7 +218,12 @@ __global__ void __launch_bounds__(128, min_blocks<T, DIM>()) k_flux(DevGeo g, Ph
   if (t >= (long)DIM * Sz<DIM>::GPF * N) return;
   const double dt = dts->dt;
   if (!(dt > 0.0)) return;
-  flux_item<T, DIM, CURVI>(g, ph, dt, t, gpL, gpR, flux, st);
+  if constexpr (!CURVI) {
+    __shared__ T stage[2 * Sz<DIM>::NV * (1 + DIM) * 128];
+    flux_item<T, DIM, CURVI>(g, ph, dt, t, gpL, gpR, flux, st, stage + threadIdx.x, 128);
+  } else {
+    flux_item<T, DIM, CURVI>(g, ph, dt, t, gpL, gpR, flux, st);
+  }
 }
 
 /* the faces on the non-periodic domain boundaries (flux_bnd_item) */
