@@ -128,13 +128,15 @@ __global__ void __launch_bounds__(128, min_blocks<T, DIM>())
   }
 }
 
-/* interface flux: tiles of blockDim.x face-point items (flux_item) */
+/* interface flux: tiles of blockDim.x = 128 face-point items (flux_item),
+   each point's Gauss-point states staged in shared memory */
 template <typename T, int DIM>
 __global__ void __launch_bounds__(128, min_blocks<T, DIM>())
     kb_flux(const BatchCase* __restrict__ cases, TileList L, BatchArrays<T> A) {
   __shared__ BatchCase sc;
   __shared__ TileRef sr;
   constexpr int NV = Sz<DIM>::NV;
+  __shared__ T stage[2 * NV * (1 + DIM) * 128];
   for (int tile = blockIdx.x; tile < L.ntile; tile += gridDim.x) {
     const TileRef ref = stage_tile(L, cases, tile, &sc, &sr);
     const long t = (long)ref.lt * blockDim.x + threadIdx.x;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(128, min_blocks<T, DIM>())
       const int ngp = DIM * Sz<DIM>::GPF * NV * (1 + DIM);
       const int nfx = DIM * Sz<DIM>::GPF * 6 * NV;
       flux_item<T, DIM, false>(g, sc.ph, dt, t, A.gpL + (long)ngp * o, A.gpR + (long)ngp * o,
-                               A.flux + (long)nfx * o, A.st);
+                               A.flux + (long)nfx * o, A.st, stage + threadIdx.x, 128);
     }
   }
 }

@@ -13,7 +13,7 @@ from parity import class_scaled_diff
 
 pytestmark = pytest.mark.gpu
 
-P, OUT, SLIP, NOSLIP = 0, 1, 2, 3
+P, OUT, SLIP, NOSLIP, INFLOW = 0, 1, 2, 3, 4
 
 
 @pytest.fixture(scope="module")
@@ -47,6 +47,11 @@ def mixed_cases():
         (dict(dim=2, n=(64, 8), lo=(0, 0), hi=(10, 10), cfl=0.3),
          lambda x, y: synth.isentropic_vortex_2d(x, y, eps=2.0, center=(3.0, 6.0))),
         (dict(dim=2, n=(9, 41), lo=(0, 0), hi=(1, 1), bc=[P, P, NOSLIP, SLIP], tau_mode=1), s2),
+        (dict(dim=2, n=(32, 16), lo=(0, 0), hi=(2, 1), bc=[INFLOW, OUT, SLIP, SLIP], tau_mode=1,
+              bc_state=[synth.shock_vortex_inflow(2.0)]),
+         lambda x, y: synth.shock_vortex_2d(x, y, 2.0, 3.0, rc=0.15)),
+        (dict(dim=2, n=(20, 28), lo=(0, 0), hi=(1, 1), bc=[OUT, OUT, INFLOW, OUT], tau_mode=1,
+              bc_state=[None, None, [1.0, 0.1, 0.8, 2.5 + 0.5 * 0.65]]), s2),
     ]
 
 
