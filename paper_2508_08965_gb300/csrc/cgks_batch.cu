@@ -451,7 +451,7 @@ cgks_status cgks_batch_set_state(cgks_batch* b, int k, const double* src, int is
   BCK(cudaMemcpyAsync(&h, b->dts + k, sizeof h, cudaMemcpyDeviceToHost, b->stream));
   BCK(cudaStreamSynchronize(b->stream));
   h.t = t;
-  h.dt = 0.0;
+  cgks::set_dt(h, 0.0);
   h.t_end = 0.0;
   BCK(cudaMemcpyAsync(b->dts + k, &h, sizeof h, cudaMemcpyHostToDevice, b->stream));
   BCK(cudaStreamSynchronize(b->stream));

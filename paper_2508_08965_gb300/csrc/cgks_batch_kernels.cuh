@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(128)
     const TileRef ref = stage_tile(L, cases, tile, &sc, &sr);
     const long t = (long)ref.lt * blockDim.x + threadIdx.x;
     const DevGeo& g = sc.g;
-    const double dt = A.dts[ref.ci].dt;
+    const StageCoef kc = A.dts[ref.ci].k;
+    const double dt = kc.dt;
     if (t < (long)NV * g.ncell && dt > 0.0) {
       const long o = sc.cell0;
       const long c = t % g.ncell;
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(128)
       cell_ijk(g, c, i, j, k);
       const long nd = (long)(batch_nf<DIM>() - 1) * NV;
       const int nfx = DIM * Sz<DIM>::GPF * 6 * NV;
-      update_var<T, DIM, false>(g, dt, stage, c, i, j, k, v, A.avg_in + NV * o, A.flux + (long)nfx * o,
+      update_var<T, DIM, false>(g, kc, stage, c, i, j, k, v, A.avg_in + NV * o, A.flux + (long)nfx * o,
                                 A.fxb + (long)nfx * sc.plane0, A.savg + NV * o, A.sder + nd * o,
                                 A.avg_out + NV * o, A.der_out + nd * o, A.avh_out ? A.avh_out + NV * o : nullptr,
                                 A.avl_out ? A.avl_out + NV * o : nullptr);
@@ -262,7 +263,7 @@ static __global__ void kb_dt_final(const BatchCase* __restrict__ cases, DtState*
     const double rem = d.t_end - d.t;
     if (rem < dt) dt = rem > 0.0 ? rem : 0.0;
   }
-  d.dt = dt;
+  set_dt(d, dt);
 }
 
 static __global__ void kb_time_advance(DtState* dts, int ncase) {

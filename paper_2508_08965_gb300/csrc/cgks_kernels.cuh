@@ -20,7 +20,12 @@ struct DtState {
   unsigned int lo_bits;         /* FP32 screening: largest lower bound of a cell's rate */
   unsigned int pad;
   double dt, t, t_end, dt_fixed;
+  StageCoef k; /* stage_coef(dt), set with dt */
 };
+CGKS_HD void set_dt(DtState& d, double dt) {
+  d.dt = dt;
+  d.k = stage_coef(dt);
+}
 
 /* Blocks of 128 threads per SM: FP32 3-D kernels fit 3 (168 registers), FP32
    2-D ones 4 (128 registers; the 2-D reconstruction is latency-bound and
@@ -248,13 +253,13 @@ __global__ void __launch_bounds__(128) k_update(DevGeo g, const DtState* __restr
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long N = g.ncell;
   if (t >= (long)Sz<DIM>::NV * N) return;
-  const double dt = dts->dt;
-  if (!(dt > 0.0)) return;
+  const StageCoef kc = dts->k;
+  if (!(kc.dt > 0.0)) return;
   const long c = t % N;
   const int v = (int)(t / N);
   int i, j, k;
   cell_ijk(g, c, i, j, k);
-  update_var<T, DIM, CURVI>(g, dt, stage, c, i, j, k, v, avg_in, flux, fxb, stash_avg, stash_der, avg_out, der_out,
+  update_var<T, DIM, CURVI>(g, kc, stage, c, i, j, k, v, avg_in, flux, fxb, stash_avg, stash_der, avg_out, der_out,
                             avh_out, avl_out);
 }
 
@@ -375,7 +380,7 @@ static __global__ void k_dt_final(Phys ph, DtState* dts, int* st) {
     double rem = dts->t_end - dts->t;
     if (rem < dt) dt = rem > 0.0 ? rem : 0.0;
   }
-  dts->dt = dt;
+  set_dt(*dts, dt);
 }
 
 static __global__ void k_time_advance(DtState* dts) { dts->t += dts->dt; }
