@@ -101,3 +101,32 @@ def test_turbulence192_perturbed_sampled_cells(orc, cg):
         i, j, k = cell
         g = st[:, :, k:k + 1, j:j + 1, i:i + 1].cpu().numpy()
         assert class_scaled_diff(g, centre(o.get_state()), h) <= 1e-12, cell
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tgv256_sampled_cells(orc, cg, precision):
+    """The largest configuration (TGV 256^3, ~150 GB of device memory in
+    FP64), cells in the interior and next to the periodic wrap."""
+    import torch
+    n, lo, hi = (256,) * 3, (0.0,) * 3, (2 * math.pi,) * 3
+    kw = dict(mu=1 / 1600, prandtl=0.72, tau_mode=2)
+    h = 2 * math.pi / 256
+    dt = 0.5 / (3 * (1.0 + 10.02) / h)
+    m = cg.Mesh(3, n, lo=lo, hi=hi, dt_fixed=dt, precision=precision, **kw)
+    m.init(lambda x, y, z: synth.taylor_green_3d(x, y, z))
+    m.step(1)
+    st = torch.empty((m.nf, m.nv) + n, dtype=torch.float64, device="cuda")
+    m.get_state(out=st)
+    m.close()
+    tol = 1e-12 if precision == 0 else 1e-5
+    for cell in [(0, 255, 128), (255, 0, 3), (77, 190, 250), (128, 128, 128)]:
+        o = patch_oracle(orc, n, lo, hi, None, cell, dt_fixed=dt, **kw)
+        o.init(lambda x, y, z: synth.taylor_green_3d(x, y, z))
+        o.step(1)
+        i, j, k = cell
+        g = st[:, :, k:k + 1, j:j + 1, i:i + 1].cpu().numpy()
+        d = class_scaled_diff(g, centre(o.get_state()), h)
+        print("TGV 256^3 precision %d cell %s: %.2e" % (precision, cell, d))
+        assert d <= tol, cell
+    del st
+    torch.cuda.empty_cache()
