@@ -108,6 +108,7 @@ def test_tgv256_sampled_cells(orc, cg, precision):
     """The largest configuration (TGV 256^3, ~150 GB of device memory in
     FP64), cells in the interior and next to the periodic wrap."""
     import torch
+    torch.cuda.empty_cache()  # earlier tests' cached blocks: the library allocates with cudaMalloc
     n, lo, hi = (256,) * 3, (0.0,) * 3, (2 * math.pi,) * 3
     kw = dict(mu=1 / 1600, prandtl=0.72, tau_mode=2)
     h = 2 * math.pi / 256
