@@ -341,10 +341,11 @@ def ensemble_bench(args, stream, ncase=256):
 
 
 def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
-    """The learned selector (FP32 form): held-out four-quadrant Riemann
-    problems on 1024^2, held-out shock-vortex interactions on 1024^2 cells of
-    [0, 2] x [0, 1], and the TGV 128^3, each with and without the trained
-    selector from the same initial state: time per step and per
+    """The learned selector: held-out four-quadrant Riemann problems on
+    1024^2, held-out shock-vortex interactions on 1024^2 cells of [0, 2] x
+    [0, 1], and the TGV 128^3, each with and without the trained selector
+    from the same initial state, in the FP32 form, and for one Riemann and
+    the shock-vortex cases also in the plain FP64 form: time per step and per
     reconstruction, skip, fallback (full GENO) and low-confidence rates, and
     the density difference from the plain adaptive method."""
     import numpy as np
@@ -354,8 +355,8 @@ def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
     params, thr, lo = selector.load()
     out = {"thr_skip": thr, "thr_lo": lo, "cases": []}
 
-    def run(kw, fn, s0, steps, on):
-        m = Mesh(precision=1, stream=stream, **kw)
+    def run(kw, fn, s0, steps, on, precision):
+        m = Mesh(precision=precision, stream=stream, **kw)
         if s0 is None:
             m.init(fn)
         else:
@@ -381,25 +382,30 @@ def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
         st = synth.riemann4_params(seed)
         cases.append(("riemann1024 seed %d" % seed,
                       dict(dim=2, n=(1024, 1024), lo=(0, 0), hi=(1, 1), bc=[1, 1, 1, 1], tau_mode=1),
-                      (lambda st: (lambda x, y: synth.riemann4_2d(x, y, st)))(st), None))
+                      (lambda st: (lambda x, y: synth.riemann4_2d(x, y, st)))(st), None,
+                      (1, 0) if seed == 9001 else (1,)))
     for seed in (9101, 9102):
         mach, eps = synth.shock_vortex_params(seed)
         cases.append(("shockvortex1024 mach %.2f eps %.2f" % (mach, eps),
                       dict(dim=2, n=(1024, 1024), lo=(0, 0), hi=(2, 1), bc=[4, 1, 2, 2], tau_mode=1,
                            bc_state=[synth.shock_vortex_inflow(mach)]),
-                      (lambda mach, eps: (lambda x, y: synth.shock_vortex_2d(x, y, mach, eps)))(mach, eps), None))
-    cases.append(("tgv128", dict(dim=3, n=(128, 128, 128), **mesh_kwargs("tgv128")), field_fn("tgv128"), s_tgv_init))
-    for name, kw, fn, s0 in cases:
+                      (lambda mach, eps: (lambda x, y: synth.shock_vortex_2d(x, y, mach, eps)))(mach, eps), None,
+                      (1, 0)))
+    cases.append(("tgv128", dict(dim=3, n=(128, 128, 128), **mesh_kwargs("tgv128")), field_fn("tgv128"), s_tgv_init,
+                  (1,)))
+    runs = [(name if p == 1 else name + " fp64", kw, fn, s0, p) for name, kw, fn, s0, precs in cases for p in precs]
+    for name, kw, fn, s0, precision in runs:
         try:
-            s_plain, ms0, rc0, _ = run(kw, fn, s0, args.steps, False)
-            s_sel, ms1, rc1, (nskip, nuns) = run(kw, fn, s0, args.steps, True)
+            s_plain, ms0, rc0, _ = run(kw, fn, s0, args.steps, False, precision)
+            s_sel, ms1, rc1, (nskip, nuns) = run(kw, fn, s0, args.steps, True, precision)
         except CgksError as ex:
             out["cases"].append({"case": name, "error": str(ex)})
             continue
         ncell = int(np.prod(kw["n"]))
         recons = 2 * (args.warmup + args.steps) * ncell
         e = s_sel[0, 0] - s_plain[0, 0]
-        rec = {"case": name, "ms_per_step": {"plain": ms0, "selector": ms1}, "speedup": ms0 / ms1,
+        rec = {"case": name, "form": "fp32" if precision == 1 else "fp64",
+               "ms_per_step": {"plain": ms0, "selector": ms1}, "speedup": ms0 / ms1,
                "recon_ms": {"plain": rc0, "selector": rc1},
                "skip_rate": nskip / recons, "fallback_rate": 1.0 - nskip / recons,
                "low_confidence_rate": nuns / recons,
