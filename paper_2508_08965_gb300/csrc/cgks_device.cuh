@@ -692,41 +692,60 @@ CGKS_HD void mx_tables(const MxS<T, DIM>& m, MxT<T>& t) {
   }
 }
 
-/* out_i = < (al . psi) u^A v^B w^C psi_i >, psi = (1, u, v[, w], (u^2+v^2[+w^2]+xi^2)/2) */
+/* out_i = < (al . psi) u^A v^B w^C psi_i >, psi = (1, u, v[, w], (u^2+v^2[+w^2]+xi^2)/2).
+   Factorised over the three velocity directions: with P = al . psi and
+   G(p, q, r) = < P u^p v^q w^r >,
+     G(p,q,r) = u_p T(q,r) + (a1 u_{p+1} + ae/2 u_{p+2}) v_q w_r,
+     T(q,r)   = v_q S(r) + (a2 v_{q+1} + ae/2 v_{q+2}) w_r,
+     S(r)     = (a0 + ae/2 <xi^2>) w_r + a3 w_{r+1} + ae/2 w_{r+2},
+   out_0..DIM are G at (A,B,C) and its unit shifts, and
+   out_{DIM+1} = (G(A+2,B,C) + G(A,B+2,C) + G(A,B,C+2) + <xi^2> G(A,B,C)
+                 + ae/2 (<xi^4> - <xi^2>^2) u_A v_B w_C) / 2.
+   The same slope's moments at several (A, B, C) share their S, T and G
+   terms once inlined into one scope, which is how the callers use it. */
+template <typename T, int DIM> struct PolyMom {
+  const MxT<T>& t;
+  T a0x, a1, a2, a3, ah, xi2, xi4;
+  CGKS_HD PolyMom(const MxS<T, DIM>& s, const MxT<T>& m, const T* al) : t(m) {
+    ah = T(0.5) * al[DIM + 1];
+    a0x = al[0] + ah * s.xi2;
+    a1 = al[1];
+    a2 = al[2];
+    a3 = DIM == 3 ? al[DIM == 3 ? 3 : 0] : T(0);
+    xi2 = s.xi2;
+    xi4 = s.xi4;
+  }
+  template <int R> CGKS_HD T S() const {
+    if constexpr (DIM == 3) return a0x * t.w[R] + a3 * t.w[R + 1] + ah * t.w[R + 2];
+    else return R == 0 ? a0x : T(0);
+  }
+  template <int R> CGKS_HD T W() const {
+    if constexpr (DIM == 3) return t.w[R];
+    else return R == 0 ? T(1) : T(0);
+  }
+  template <int Q, int R> CGKS_HD T Tq() const {
+    return t.v[Q] * S<R>() + (a2 * t.v[Q + 1] + ah * t.v[Q + 2]) * W<R>();
+  }
+  template <int P, int Q, int R> CGKS_HD T G() const {
+    return t.u[P] * Tq<Q, R>() + (a1 * t.u[P + 1] + ah * t.u[P + 2]) * (t.v[Q] * W<R>());
+  }
+  template <int A, int B, int C> CGKS_HD void out(T* o) const {
+    const T g0 = G<A, B, C>();
+    o[0] = g0;
+    o[1] = G<A + 1, B, C>();
+    o[2] = G<A, B + 1, C>();
+    T e = G<A + 2, B, C>() + G<A, B + 2, C>() + xi2 * g0 + ah * (xi4 - xi2 * xi2) * (t.u[A] * t.v[B] * W<C>());
+    if constexpr (DIM == 3) {
+      o[3] = G<A, B, C + 1>();
+      e += G<A, B, C + 2>();
+    }
+    o[DIM + 1] = T(0.5) * e;
+  }
+};
+
 template <typename T, int DIM, int A, int B, int C>
 CGKS_HD void mvec(const MxS<T, DIM>& s, const MxT<T>& m, const T* al, T* out) {
-#define CG_M(i, j, k) (m.u[(i)] * m.v[(j)] * m.w[(k)])
-  const T M0 = CG_M(A, B, C), Ma1 = CG_M(A + 1, B, C), Mb1 = CG_M(A, B + 1, C);
-  const T Ma2 = CG_M(A + 2, B, C), Mb2 = CG_M(A, B + 2, C), Mab = CG_M(A + 1, B + 1, C);
-  T Mc1 = T(0), Mc2 = T(0), Mac = T(0), Mbc = T(0), Ec = T(0);
-  T E0 = Ma2 + Mb2 + s.xi2 * M0;
-  T Ea = CG_M(A + 3, B, C) + CG_M(A + 1, B + 2, C) + s.xi2 * Ma1;
-  T Eb = CG_M(A + 2, B + 1, C) + CG_M(A, B + 3, C) + s.xi2 * Mb1;
-  T EE = CG_M(A + 4, B, C) + CG_M(A, B + 4, C) + T(2) * CG_M(A + 2, B + 2, C) + T(2) * s.xi2 * (Ma2 + Mb2) +
-         s.xi4 * M0;
-  if constexpr (DIM == 3) {
-    Mc1 = CG_M(A, B, C + 1);
-    Mc2 = CG_M(A, B, C + 2);
-    Mac = CG_M(A + 1, B, C + 1);
-    Mbc = CG_M(A, B + 1, C + 1);
-    E0 += Mc2;
-    Ea += CG_M(A + 1, B, C + 2);
-    Eb += CG_M(A, B + 1, C + 2);
-    Ec = T(0.5) * (CG_M(A + 2, B, C + 1) + CG_M(A, B + 2, C + 1) + CG_M(A, B, C + 3) + s.xi2 * Mc1);
-    EE += CG_M(A, B, C + 4) + T(2) * CG_M(A + 2, B, C + 2) + T(2) * CG_M(A, B + 2, C + 2) + T(2) * s.xi2 * Mc2;
-  }
-#undef CG_M
-  E0 *= T(0.5);
-  Ea *= T(0.5);
-  Eb *= T(0.5);
-  EE *= T(0.25);
-  const T a0 = al[0], a1 = al[1], a2 = al[2], ae = al[DIM + 1];
-  const T a3 = DIM == 3 ? al[DIM == 3 ? 3 : 0] : T(0);
-  out[0] = a0 * M0 + a1 * Ma1 + a2 * Mb1 + a3 * Mc1 + ae * E0;
-  out[1] = a0 * Ma1 + a1 * Ma2 + a2 * Mab + a3 * Mac + ae * Ea;
-  out[2] = a0 * Mb1 + a1 * Mab + a2 * Mb2 + a3 * Mbc + ae * Eb;
-  if constexpr (DIM == 3) out[3] = a0 * Mc1 + a1 * Mac + a2 * Mbc + a3 * Mc2 + ae * Ec;
-  out[DIM + 1] = a0 * E0 + a1 * Ea + a2 * Eb + a3 * Ec + ae * EE;
+  PolyMom<T, DIM>(s, m, al).template out<A, B, C>(out);
 }
 
 /* <u^A psi> */
