@@ -11,32 +11,25 @@ CGKS_HD void gen_coeffs_2d(const Ld& ld, T* __restrict__ a) {
 #pragma unroll
   for (int b = 0; b < 14; ++b) a[b] = T(0);
   {
-    { const T f = T(4)*ld.q0();
-      a[0] = cg_fma(T(-1.2171052631578947), f, a[0]);
-      a[1] = cg_fma(T(-1.2171052631578947), f, a[1]);
-      a[2] = cg_fma(T(5.684210526315789), f, a[2]);
-      a[3] = cg_fma(T(0.15789473684210525), f, a[3]);
-      a[4] = cg_fma(T(5.684210526315789), f, a[4]);
+    { const T f = ld.line(0) +ld.line(1);
+      a[8] = cg_fma(T(0.17031568228105906), f, a[8]);
+      a[9] = cg_fma(T(-0.824847250509165), f, a[9]);
+      a[10] = cg_fma(T(0.03665987780040733), f, a[10]);
     }
-    { const T f = T(2)*ld.line(0) +T(2)*ld.line(1);
-      a[8] = cg_fma(T(0.08515784114052953), f, a[8]);
-      a[9] = cg_fma(T(-0.4124236252545825), f, a[9]);
-      a[10] = cg_fma(T(0.018329938900203666), f, a[10]);
+    { const T f = ld.line(0) -ld.line(1);
+      a[11] = cg_fma(T(-0.2755883921729478), f, a[11]);
+      a[12] = cg_fma(T(0.3408698035031975), f, a[12]);
+      a[13] = cg_fma(T(0.6639466380756306), f, a[13]);
     }
-    { const T f = T(2)*ld.line(0) -T(2)*ld.line(1);
-      a[11] = cg_fma(T(-0.1377941960864739), f, a[11]);
-      a[12] = cg_fma(T(0.17043490175159876), f, a[12]);
-      a[13] = cg_fma(T(0.3319733190378153), f, a[13]);
+    { const T f = ld.line(2) +ld.line(3);
+      a[5] = cg_fma(T(0.17031568228105906), f, a[5]);
+      a[6] = cg_fma(T(0.03665987780040733), f, a[6]);
+      a[7] = cg_fma(T(-0.824847250509165), f, a[7]);
     }
-    { const T f = T(2)*ld.line(2) +T(2)*ld.line(3);
-      a[5] = cg_fma(T(0.08515784114052953), f, a[5]);
-      a[6] = cg_fma(T(0.018329938900203666), f, a[6]);
-      a[7] = cg_fma(T(-0.4124236252545825), f, a[7]);
-    }
-    { const T f = T(2)*ld.line(2) -T(2)*ld.line(3);
-      a[11] = cg_fma(T(-0.1377941960864739), f, a[11]);
-      a[12] = cg_fma(T(0.3319733190378153), f, a[12]);
-      a[13] = cg_fma(T(0.17043490175159876), f, a[13]);
+    { const T f = ld.line(2) -ld.line(3);
+      a[11] = cg_fma(T(-0.2755883921729478), f, a[11]);
+      a[12] = cg_fma(T(0.6639466380756306), f, a[12]);
+      a[13] = cg_fma(T(0.3408698035031975), f, a[13]);
     }
   }
   {
@@ -46,39 +39,39 @@ CGKS_HD void gen_coeffs_2d(const Ld& ld, T* __restrict__ a) {
     const T npzQ = ld.avg(1, 0, 0);
     T npzG[2];
     ld.grefv(1, 0, 0, npzG);
-    { const T f = T(2)*nmzQ +T(2)*npzQ;
-      a[0] = cg_fma(T(1.2171052631578947), f, a[0]);
-      a[1] = cg_fma(T(-0.03289473684210526), f, a[1]);
-      a[2] = cg_fma(T(-5.684210526315789), f, a[2]);
-      a[3] = cg_fma(T(-0.15789473684210525), f, a[3]);
-      a[4] = cg_fma(T(0.3157894736842105), f, a[4]);
+    { const T f = nmzQ +npzQ;
+      a[0] = cg_fma(T(2.4342105263157894), f, a[0]);
+      a[1] = cg_fma(T(-0.06578947368421052), f, a[1]);
+      a[2] = cg_fma(T(-11.368421052631579), f, a[2]);
+      a[3] = cg_fma(T(-0.3157894736842105), f, a[3]);
+      a[4] = cg_fma(T(0.631578947368421), f, a[4]);
     }
-    { const T f = T(2)*nmzQ -T(2)*npzQ;
-      a[8] = cg_fma(T(-0.22275967413441955), f, a[8]);
-      a[9] = cg_fma(T(-0.1924643584521385), f, a[9]);
-      a[10] = cg_fma(T(0.3085539714867617), f, a[10]);
+    { const T f = nmzQ -npzQ;
+      a[8] = cg_fma(T(-0.4455193482688391), f, a[8]);
+      a[9] = cg_fma(T(-0.384928716904277), f, a[9]);
+      a[10] = cg_fma(T(0.6171079429735234), f, a[10]);
     }
-    { const T f = T(2)*nmzG[0] -T(2)*npzG[0];
-      a[0] = cg_fma(T(0.35635964912280704), f, a[0]);
-      a[1] = cg_fma(T(-0.01864035087719298), f, a[1]);
-      a[2] = cg_fma(T(-2.9210526315789473), f, a[2]);
-      a[3] = cg_fma(T(0.21052631578947367), f, a[3]);
-      a[4] = cg_fma(T(0.07894736842105263), f, a[4]);
+    { const T f = nmzG[0] -npzG[0];
+      a[0] = cg_fma(T(0.7127192982456141), f, a[0]);
+      a[1] = cg_fma(T(-0.03728070175438596), f, a[1]);
+      a[2] = cg_fma(T(-5.842105263157895), f, a[2]);
+      a[3] = cg_fma(T(0.42105263157894735), f, a[3]);
+      a[4] = cg_fma(T(0.15789473684210525), f, a[4]);
     }
-    { const T f = T(2)*nmzG[0] +T(2)*npzG[0];
-      a[8] = cg_fma(T(-0.0756958587915818), f, a[8]);
-      a[9] = cg_fma(T(0.3665987780040733), f, a[9]);
-      a[10] = cg_fma(T(-0.016293279022403257), f, a[10]);
+    { const T f = nmzG[0] +npzG[0];
+      a[8] = cg_fma(T(-0.1513917175831636), f, a[8]);
+      a[9] = cg_fma(T(0.7331975560081466), f, a[9]);
+      a[10] = cg_fma(T(-0.032586558044806514), f, a[10]);
     }
-    { const T f = T(2)*nmzG[1] +T(2)*npzG[1];
-      a[5] = cg_fma(T(0.0373387644263408), f, a[5]);
-      a[6] = cg_fma(T(0.1425661914460285), f, a[6]);
-      a[7] = cg_fma(T(-0.20773930753564154), f, a[7]);
+    { const T f = nmzG[1] +npzG[1];
+      a[5] = cg_fma(T(0.0746775288526816), f, a[5]);
+      a[6] = cg_fma(T(0.285132382892057), f, a[6]);
+      a[7] = cg_fma(T(-0.4154786150712831), f, a[7]);
     }
-    { const T f = T(2)*nmzG[1] -T(2)*npzG[1];
-      a[11] = cg_fma(T(-0.12413670975739331), f, a[11]);
-      a[12] = cg_fma(T(-0.5899248626672331), f, a[12]);
-      a[13] = cg_fma(T(0.9023031166073783), f, a[13]);
+    { const T f = nmzG[1] -npzG[1];
+      a[11] = cg_fma(T(-0.24827341951478663), f, a[11]);
+      a[12] = cg_fma(T(-1.1798497253344662), f, a[12]);
+      a[13] = cg_fma(T(1.8046062332147565), f, a[13]);
     }
   }
   {
@@ -88,39 +81,39 @@ CGKS_HD void gen_coeffs_2d(const Ld& ld, T* __restrict__ a) {
     const T nzpQ = ld.avg(0, 1, 0);
     T nzpG[2];
     ld.grefv(0, 1, 0, nzpG);
-    { const T f = T(2)*nzmQ +T(2)*nzpQ;
-      a[0] = cg_fma(T(-0.03289473684210526), f, a[0]);
-      a[1] = cg_fma(T(1.2171052631578947), f, a[1]);
-      a[2] = cg_fma(T(0.3157894736842105), f, a[2]);
-      a[3] = cg_fma(T(-0.15789473684210525), f, a[3]);
-      a[4] = cg_fma(T(-5.684210526315789), f, a[4]);
+    { const T f = nzmQ +nzpQ;
+      a[0] = cg_fma(T(-0.06578947368421052), f, a[0]);
+      a[1] = cg_fma(T(2.4342105263157894), f, a[1]);
+      a[2] = cg_fma(T(0.631578947368421), f, a[2]);
+      a[3] = cg_fma(T(-0.3157894736842105), f, a[3]);
+      a[4] = cg_fma(T(-11.368421052631579), f, a[4]);
     }
-    { const T f = T(2)*nzmQ -T(2)*nzpQ;
-      a[5] = cg_fma(T(-0.22275967413441955), f, a[5]);
-      a[6] = cg_fma(T(0.3085539714867617), f, a[6]);
-      a[7] = cg_fma(T(-0.1924643584521385), f, a[7]);
+    { const T f = nzmQ -nzpQ;
+      a[5] = cg_fma(T(-0.4455193482688391), f, a[5]);
+      a[6] = cg_fma(T(0.6171079429735234), f, a[6]);
+      a[7] = cg_fma(T(-0.384928716904277), f, a[7]);
     }
-    { const T f = T(2)*nzmG[0] +T(2)*nzpG[0];
-      a[8] = cg_fma(T(0.0373387644263408), f, a[8]);
-      a[9] = cg_fma(T(-0.20773930753564154), f, a[9]);
-      a[10] = cg_fma(T(0.1425661914460285), f, a[10]);
+    { const T f = nzmG[0] +nzpG[0];
+      a[8] = cg_fma(T(0.0746775288526816), f, a[8]);
+      a[9] = cg_fma(T(-0.4154786150712831), f, a[9]);
+      a[10] = cg_fma(T(0.285132382892057), f, a[10]);
     }
-    { const T f = T(2)*nzmG[0] -T(2)*nzpG[0];
-      a[11] = cg_fma(T(-0.12413670975739331), f, a[11]);
-      a[12] = cg_fma(T(0.9023031166073783), f, a[12]);
-      a[13] = cg_fma(T(-0.5899248626672331), f, a[13]);
+    { const T f = nzmG[0] -nzpG[0];
+      a[11] = cg_fma(T(-0.24827341951478663), f, a[11]);
+      a[12] = cg_fma(T(1.8046062332147565), f, a[12]);
+      a[13] = cg_fma(T(-1.1798497253344662), f, a[13]);
     }
-    { const T f = T(2)*nzmG[1] -T(2)*nzpG[1];
-      a[0] = cg_fma(T(-0.01864035087719298), f, a[0]);
-      a[1] = cg_fma(T(0.35635964912280704), f, a[1]);
-      a[2] = cg_fma(T(0.07894736842105263), f, a[2]);
-      a[3] = cg_fma(T(0.21052631578947367), f, a[3]);
-      a[4] = cg_fma(T(-2.9210526315789473), f, a[4]);
+    { const T f = nzmG[1] -nzpG[1];
+      a[0] = cg_fma(T(-0.03728070175438596), f, a[0]);
+      a[1] = cg_fma(T(0.7127192982456141), f, a[1]);
+      a[2] = cg_fma(T(0.15789473684210525), f, a[2]);
+      a[3] = cg_fma(T(0.42105263157894735), f, a[3]);
+      a[4] = cg_fma(T(-5.842105263157895), f, a[4]);
     }
-    { const T f = T(2)*nzmG[1] +T(2)*nzpG[1];
-      a[5] = cg_fma(T(-0.0756958587915818), f, a[5]);
-      a[6] = cg_fma(T(-0.016293279022403257), f, a[6]);
-      a[7] = cg_fma(T(0.3665987780040733), f, a[7]);
+    { const T f = nzmG[1] +nzpG[1];
+      a[5] = cg_fma(T(-0.1513917175831636), f, a[5]);
+      a[6] = cg_fma(T(-0.032586558044806514), f, a[6]);
+      a[7] = cg_fma(T(0.7331975560081466), f, a[7]);
     }
   }
   {
@@ -451,73 +444,62 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
 #pragma unroll
   for (int b = 0; b < 34; ++b) a[b] = T(0);
   {
-    { const T f = T(8)*ld.q0();
-      a[0] = cg_fma(T(-0.5958333333333333), f, a[0]);
-      a[1] = cg_fma(T(-0.5958333333333333), f, a[1]);
-      a[2] = cg_fma(T(-0.5958333333333333), f, a[2]);
-      a[3] = cg_fma(T(2.7), f, a[3]);
-      a[4] = cg_fma(T(0.1), f, a[4]);
-      a[5] = cg_fma(T(0.1), f, a[5]);
-      a[6] = cg_fma(T(2.7), f, a[6]);
-      a[7] = cg_fma(T(0.1), f, a[7]);
-      a[8] = cg_fma(T(2.7), f, a[8]);
+    { const T f = ld.line(0) +ld.line(1) +ld.line(2) +ld.line(3);
+      a[21] = cg_fma(T(0.10817307692307693), f, a[21]);
+      a[22] = cg_fma(T(-0.5192307692307693), f, a[22]);
     }
-    { const T f = T(2)*ld.line(0) +T(2)*ld.line(1) +T(2)*ld.line(2) +T(2)*ld.line(3);
-      a[21] = cg_fma(T(0.054086538461538464), f, a[21]);
-      a[22] = cg_fma(T(-0.25961538461538464), f, a[22]);
+    { const T f = ld.line(0) +ld.line(1) -ld.line(2) -ld.line(3);
+      a[25] = cg_fma(T(-0.22401937772088515), f, a[25]);
+      a[26] = cg_fma(T(0.28317079043922294), f, a[26]);
+      a[27] = cg_fma(T(0.23326159319779152), f, a[27]);
+      a[28] = cg_fma(T(0.4981839941374284), f, a[28]);
     }
-    { const T f = T(2)*ld.line(0) +T(2)*ld.line(1) -T(2)*ld.line(2) -T(2)*ld.line(3);
-      a[25] = cg_fma(T(-0.11200968886044257), f, a[25]);
-      a[26] = cg_fma(T(0.14158539521961147), f, a[26]);
-      a[27] = cg_fma(T(0.11663079659889576), f, a[27]);
-      a[28] = cg_fma(T(0.2490919970687142), f, a[28]);
+    { const T f = ld.line(0) -ld.line(1) +ld.line(2) -ld.line(3);
+      a[29] = cg_fma(T(-0.22401937772088515), f, a[29]);
+      a[30] = cg_fma(T(0.28317079043922294), f, a[30]);
+      a[31] = cg_fma(T(0.4981839941374284), f, a[31]);
+      a[32] = cg_fma(T(0.23326159319779152), f, a[32]);
     }
-    { const T f = T(2)*ld.line(0) -T(2)*ld.line(1) +T(2)*ld.line(2) -T(2)*ld.line(3);
-      a[29] = cg_fma(T(-0.11200968886044257), f, a[29]);
-      a[30] = cg_fma(T(0.14158539521961147), f, a[30]);
-      a[31] = cg_fma(T(0.2490919970687142), f, a[31]);
-      a[32] = cg_fma(T(0.11663079659889576), f, a[32]);
+    { const T f = ld.line(0) -ld.line(1) -ld.line(2) +ld.line(3);
+      a[33] = cg_fma(T(0.058823529411764705), f, a[33]);
     }
-    { const T f = T(2)*ld.line(0) -T(2)*ld.line(1) -T(2)*ld.line(2) +T(2)*ld.line(3);
-      a[33] = cg_fma(T(0.029411764705882353), f, a[33]);
+    { const T f = ld.line(4) +ld.line(5) +ld.line(6) +ld.line(7);
+      a[13] = cg_fma(T(0.10817307692307693), f, a[13]);
+      a[15] = cg_fma(T(-0.5192307692307693), f, a[15]);
     }
-    { const T f = T(2)*ld.line(4) +T(2)*ld.line(5) +T(2)*ld.line(6) +T(2)*ld.line(7);
-      a[13] = cg_fma(T(0.054086538461538464), f, a[13]);
-      a[15] = cg_fma(T(-0.25961538461538464), f, a[15]);
+    { const T f = ld.line(4) +ld.line(5) -ld.line(6) -ld.line(7);
+      a[17] = cg_fma(T(-0.22401937772088515), f, a[17]);
+      a[18] = cg_fma(T(0.23326159319779152), f, a[18]);
+      a[19] = cg_fma(T(0.28317079043922294), f, a[19]);
+      a[20] = cg_fma(T(0.4981839941374284), f, a[20]);
     }
-    { const T f = T(2)*ld.line(4) +T(2)*ld.line(5) -T(2)*ld.line(6) -T(2)*ld.line(7);
-      a[17] = cg_fma(T(-0.11200968886044257), f, a[17]);
-      a[18] = cg_fma(T(0.11663079659889576), f, a[18]);
-      a[19] = cg_fma(T(0.14158539521961147), f, a[19]);
-      a[20] = cg_fma(T(0.2490919970687142), f, a[20]);
+    { const T f = ld.line(4) -ld.line(5) +ld.line(6) -ld.line(7);
+      a[29] = cg_fma(T(-0.22401937772088515), f, a[29]);
+      a[30] = cg_fma(T(0.4981839941374284), f, a[30]);
+      a[31] = cg_fma(T(0.28317079043922294), f, a[31]);
+      a[32] = cg_fma(T(0.23326159319779152), f, a[32]);
     }
-    { const T f = T(2)*ld.line(4) -T(2)*ld.line(5) +T(2)*ld.line(6) -T(2)*ld.line(7);
-      a[29] = cg_fma(T(-0.11200968886044257), f, a[29]);
-      a[30] = cg_fma(T(0.2490919970687142), f, a[30]);
-      a[31] = cg_fma(T(0.14158539521961147), f, a[31]);
-      a[32] = cg_fma(T(0.11663079659889576), f, a[32]);
+    { const T f = ld.line(4) -ld.line(5) -ld.line(6) +ld.line(7);
+      a[33] = cg_fma(T(0.058823529411764705), f, a[33]);
     }
-    { const T f = T(2)*ld.line(4) -T(2)*ld.line(5) -T(2)*ld.line(6) +T(2)*ld.line(7);
-      a[33] = cg_fma(T(0.029411764705882353), f, a[33]);
+    { const T f = ld.line(8) +ld.line(9) +ld.line(10) +ld.line(11);
+      a[9] = cg_fma(T(0.10817307692307693), f, a[9]);
+      a[12] = cg_fma(T(-0.5192307692307693), f, a[12]);
     }
-    { const T f = T(2)*ld.line(8) +T(2)*ld.line(9) +T(2)*ld.line(10) +T(2)*ld.line(11);
-      a[9] = cg_fma(T(0.054086538461538464), f, a[9]);
-      a[12] = cg_fma(T(-0.25961538461538464), f, a[12]);
+    { const T f = ld.line(8) +ld.line(9) -ld.line(10) -ld.line(11);
+      a[17] = cg_fma(T(-0.22401937772088515), f, a[17]);
+      a[18] = cg_fma(T(0.23326159319779152), f, a[18]);
+      a[19] = cg_fma(T(0.4981839941374284), f, a[19]);
+      a[20] = cg_fma(T(0.28317079043922294), f, a[20]);
     }
-    { const T f = T(2)*ld.line(8) +T(2)*ld.line(9) -T(2)*ld.line(10) -T(2)*ld.line(11);
-      a[17] = cg_fma(T(-0.11200968886044257), f, a[17]);
-      a[18] = cg_fma(T(0.11663079659889576), f, a[18]);
-      a[19] = cg_fma(T(0.2490919970687142), f, a[19]);
-      a[20] = cg_fma(T(0.14158539521961147), f, a[20]);
+    { const T f = ld.line(8) -ld.line(9) +ld.line(10) -ld.line(11);
+      a[25] = cg_fma(T(-0.22401937772088515), f, a[25]);
+      a[26] = cg_fma(T(0.4981839941374284), f, a[26]);
+      a[27] = cg_fma(T(0.23326159319779152), f, a[27]);
+      a[28] = cg_fma(T(0.28317079043922294), f, a[28]);
     }
-    { const T f = T(2)*ld.line(8) -T(2)*ld.line(9) +T(2)*ld.line(10) -T(2)*ld.line(11);
-      a[25] = cg_fma(T(-0.11200968886044257), f, a[25]);
-      a[26] = cg_fma(T(0.2490919970687142), f, a[26]);
-      a[27] = cg_fma(T(0.11663079659889576), f, a[27]);
-      a[28] = cg_fma(T(0.14158539521961147), f, a[28]);
-    }
-    { const T f = T(2)*ld.line(8) -T(2)*ld.line(9) -T(2)*ld.line(10) +T(2)*ld.line(11);
-      a[33] = cg_fma(T(0.029411764705882353), f, a[33]);
+    { const T f = ld.line(8) -ld.line(9) -ld.line(10) +ld.line(11);
+      a[33] = cg_fma(T(0.058823529411764705), f, a[33]);
     }
   }
   {
@@ -527,61 +509,61 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T npzzQ = ld.avg(1, 0, 0);
     T npzzG[3];
     ld.grefv(1, 0, 0, npzzG);
-    { const T f = T(4)*nmzzQ +T(4)*npzzQ;
-      a[0] = cg_fma(T(0.5939189189189189), f, a[0]);
-      a[1] = cg_fma(T(-0.013626126126126126), f, a[1]);
-      a[2] = cg_fma(T(-0.013626126126126126), f, a[2]);
-      a[3] = cg_fma(T(-2.691891891891892), f, a[3]);
-      a[4] = cg_fma(T(-0.0891891891891892), f, a[4]);
-      a[5] = cg_fma(T(-0.0891891891891892), f, a[5]);
+    { const T f = nmzzQ +npzzQ;
+      a[0] = cg_fma(T(2.3756756756756756), f, a[0]);
+      a[1] = cg_fma(T(-0.0545045045045045), f, a[1]);
+      a[2] = cg_fma(T(-0.0545045045045045), f, a[2]);
+      a[3] = cg_fma(T(-10.767567567567568), f, a[3]);
+      a[4] = cg_fma(T(-0.3567567567567568), f, a[4]);
+      a[5] = cg_fma(T(-0.3567567567567568), f, a[5]);
+      a[6] = cg_fma(T(0.5837837837837838), f, a[6]);
+      a[7] = cg_fma(T(-0.08648648648648649), f, a[7]);
+      a[8] = cg_fma(T(0.5837837837837838), f, a[8]);
+    }
+    { const T f = nmzzQ -npzzQ;
+      a[21] = cg_fma(T(-0.3559379217273954), f, a[21]);
+      a[22] = cg_fma(T(-0.9230769230769231), f, a[22]);
+      a[23] = cg_fma(T(0.5789473684210527), f, a[23]);
+      a[24] = cg_fma(T(0.5789473684210527), f, a[24]);
+    }
+    { const T f = nmzzG[0] -npzzG[0];
+      a[0] = cg_fma(T(0.6772522522522523), f, a[0]);
+      a[1] = cg_fma(T(-0.03445945945945946), f, a[1]);
+      a[2] = cg_fma(T(-0.03445945945945946), f, a[2]);
+      a[3] = cg_fma(T(-5.691891891891892), f, a[3]);
+      a[4] = cg_fma(T(0.41081081081081083), f, a[4]);
+      a[5] = cg_fma(T(0.41081081081081083), f, a[5]);
       a[6] = cg_fma(T(0.14594594594594595), f, a[6]);
       a[7] = cg_fma(T(-0.021621621621621623), f, a[7]);
       a[8] = cg_fma(T(0.14594594594594595), f, a[8]);
     }
-    { const T f = T(4)*nmzzQ -T(4)*npzzQ;
-      a[21] = cg_fma(T(-0.08898448043184885), f, a[21]);
-      a[22] = cg_fma(T(-0.23076923076923078), f, a[22]);
-      a[23] = cg_fma(T(0.14473684210526316), f, a[23]);
-      a[24] = cg_fma(T(0.14473684210526316), f, a[24]);
+    { const T f = nmzzG[0] +npzzG[0];
+      a[21] = cg_fma(T(-0.09615384615384616), f, a[21]);
+      a[22] = cg_fma(T(0.46153846153846156), f, a[22]);
     }
-    { const T f = T(4)*nmzzG[0] -T(4)*npzzG[0];
-      a[0] = cg_fma(T(0.16931306306306307), f, a[0]);
-      a[1] = cg_fma(T(-0.008614864864864865), f, a[1]);
-      a[2] = cg_fma(T(-0.008614864864864865), f, a[2]);
-      a[3] = cg_fma(T(-1.422972972972973), f, a[3]);
-      a[4] = cg_fma(T(0.10270270270270271), f, a[4]);
-      a[5] = cg_fma(T(0.10270270270270271), f, a[5]);
-      a[6] = cg_fma(T(0.03648648648648649), f, a[6]);
-      a[7] = cg_fma(T(-0.005405405405405406), f, a[7]);
-      a[8] = cg_fma(T(0.03648648648648649), f, a[8]);
+    { const T f = nmzzG[1] +npzzG[1];
+      a[13] = cg_fma(T(0.03930499325236168), f, a[13]);
+      a[14] = cg_fma(T(0.23859649122807017), f, a[14]);
+      a[15] = cg_fma(T(-0.23076923076923078), f, a[15]);
+      a[16] = cg_fma(T(-0.028070175438596492), f, a[16]);
     }
-    { const T f = T(4)*nmzzG[0] +T(4)*npzzG[0];
-      a[21] = cg_fma(T(-0.02403846153846154), f, a[21]);
-      a[22] = cg_fma(T(0.11538461538461539), f, a[22]);
+    { const T f = nmzzG[1] -npzzG[1];
+      a[29] = cg_fma(T(-0.20272193151565226), f, a[29]);
+      a[30] = cg_fma(T(-0.7848963427952782), f, a[30]);
+      a[31] = cg_fma(T(1.201310553756446), f, a[31]);
+      a[32] = cg_fma(T(0.27816028642247315), f, a[32]);
     }
-    { const T f = T(4)*nmzzG[1] +T(4)*npzzG[1];
-      a[13] = cg_fma(T(0.00982624831309042), f, a[13]);
-      a[14] = cg_fma(T(0.05964912280701754), f, a[14]);
-      a[15] = cg_fma(T(-0.057692307692307696), f, a[15]);
-      a[16] = cg_fma(T(-0.007017543859649123), f, a[16]);
+    { const T f = nmzzG[2] +npzzG[2];
+      a[9] = cg_fma(T(0.03930499325236168), f, a[9]);
+      a[10] = cg_fma(T(0.23859649122807017), f, a[10]);
+      a[11] = cg_fma(T(-0.028070175438596492), f, a[11]);
+      a[12] = cg_fma(T(-0.23076923076923078), f, a[12]);
     }
-    { const T f = T(4)*nmzzG[1] -T(4)*npzzG[1];
-      a[29] = cg_fma(T(-0.050680482878913066), f, a[29]);
-      a[30] = cg_fma(T(-0.19622408569881955), f, a[30]);
-      a[31] = cg_fma(T(0.3003276384391115), f, a[31]);
-      a[32] = cg_fma(T(0.06954007160561829), f, a[32]);
-    }
-    { const T f = T(4)*nmzzG[2] +T(4)*npzzG[2];
-      a[9] = cg_fma(T(0.00982624831309042), f, a[9]);
-      a[10] = cg_fma(T(0.05964912280701754), f, a[10]);
-      a[11] = cg_fma(T(-0.007017543859649123), f, a[11]);
-      a[12] = cg_fma(T(-0.057692307692307696), f, a[12]);
-    }
-    { const T f = T(4)*nmzzG[2] -T(4)*npzzG[2];
-      a[25] = cg_fma(T(-0.050680482878913066), f, a[25]);
-      a[26] = cg_fma(T(-0.19622408569881955), f, a[26]);
-      a[27] = cg_fma(T(0.06954007160561829), f, a[27]);
-      a[28] = cg_fma(T(0.3003276384391115), f, a[28]);
+    { const T f = nmzzG[2] -npzzG[2];
+      a[25] = cg_fma(T(-0.20272193151565226), f, a[25]);
+      a[26] = cg_fma(T(-0.7848963427952782), f, a[26]);
+      a[27] = cg_fma(T(0.27816028642247315), f, a[27]);
+      a[28] = cg_fma(T(1.201310553756446), f, a[28]);
     }
   }
   {
@@ -591,61 +573,61 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T nzpzQ = ld.avg(0, 1, 0);
     T nzpzG[3];
     ld.grefv(0, 1, 0, nzpzG);
-    { const T f = T(4)*nzmzQ +T(4)*nzpzQ;
-      a[0] = cg_fma(T(-0.013626126126126126), f, a[0]);
-      a[1] = cg_fma(T(0.5939189189189189), f, a[1]);
-      a[2] = cg_fma(T(-0.013626126126126126), f, a[2]);
+    { const T f = nzmzQ +nzpzQ;
+      a[0] = cg_fma(T(-0.0545045045045045), f, a[0]);
+      a[1] = cg_fma(T(2.3756756756756756), f, a[1]);
+      a[2] = cg_fma(T(-0.0545045045045045), f, a[2]);
+      a[3] = cg_fma(T(0.5837837837837838), f, a[3]);
+      a[4] = cg_fma(T(-0.3567567567567568), f, a[4]);
+      a[5] = cg_fma(T(-0.08648648648648649), f, a[5]);
+      a[6] = cg_fma(T(-10.767567567567568), f, a[6]);
+      a[7] = cg_fma(T(-0.3567567567567568), f, a[7]);
+      a[8] = cg_fma(T(0.5837837837837838), f, a[8]);
+    }
+    { const T f = nzmzQ -nzpzQ;
+      a[13] = cg_fma(T(-0.3559379217273954), f, a[13]);
+      a[14] = cg_fma(T(0.5789473684210527), f, a[14]);
+      a[15] = cg_fma(T(-0.9230769230769231), f, a[15]);
+      a[16] = cg_fma(T(0.5789473684210527), f, a[16]);
+    }
+    { const T f = nzmzG[0] +nzpzG[0];
+      a[21] = cg_fma(T(0.03930499325236168), f, a[21]);
+      a[22] = cg_fma(T(-0.23076923076923078), f, a[22]);
+      a[23] = cg_fma(T(0.23859649122807017), f, a[23]);
+      a[24] = cg_fma(T(-0.028070175438596492), f, a[24]);
+    }
+    { const T f = nzmzG[0] -nzpzG[0];
+      a[29] = cg_fma(T(-0.20272193151565226), f, a[29]);
+      a[30] = cg_fma(T(1.201310553756446), f, a[30]);
+      a[31] = cg_fma(T(-0.7848963427952782), f, a[31]);
+      a[32] = cg_fma(T(0.27816028642247315), f, a[32]);
+    }
+    { const T f = nzmzG[1] -nzpzG[1];
+      a[0] = cg_fma(T(-0.03445945945945946), f, a[0]);
+      a[1] = cg_fma(T(0.6772522522522523), f, a[1]);
+      a[2] = cg_fma(T(-0.03445945945945946), f, a[2]);
       a[3] = cg_fma(T(0.14594594594594595), f, a[3]);
-      a[4] = cg_fma(T(-0.0891891891891892), f, a[4]);
+      a[4] = cg_fma(T(0.41081081081081083), f, a[4]);
       a[5] = cg_fma(T(-0.021621621621621623), f, a[5]);
-      a[6] = cg_fma(T(-2.691891891891892), f, a[6]);
-      a[7] = cg_fma(T(-0.0891891891891892), f, a[7]);
+      a[6] = cg_fma(T(-5.691891891891892), f, a[6]);
+      a[7] = cg_fma(T(0.41081081081081083), f, a[7]);
       a[8] = cg_fma(T(0.14594594594594595), f, a[8]);
     }
-    { const T f = T(4)*nzmzQ -T(4)*nzpzQ;
-      a[13] = cg_fma(T(-0.08898448043184885), f, a[13]);
-      a[14] = cg_fma(T(0.14473684210526316), f, a[14]);
-      a[15] = cg_fma(T(-0.23076923076923078), f, a[15]);
-      a[16] = cg_fma(T(0.14473684210526316), f, a[16]);
+    { const T f = nzmzG[1] +nzpzG[1];
+      a[13] = cg_fma(T(-0.09615384615384616), f, a[13]);
+      a[15] = cg_fma(T(0.46153846153846156), f, a[15]);
     }
-    { const T f = T(4)*nzmzG[0] +T(4)*nzpzG[0];
-      a[21] = cg_fma(T(0.00982624831309042), f, a[21]);
-      a[22] = cg_fma(T(-0.057692307692307696), f, a[22]);
-      a[23] = cg_fma(T(0.05964912280701754), f, a[23]);
-      a[24] = cg_fma(T(-0.007017543859649123), f, a[24]);
+    { const T f = nzmzG[2] +nzpzG[2];
+      a[9] = cg_fma(T(0.03930499325236168), f, a[9]);
+      a[10] = cg_fma(T(-0.028070175438596492), f, a[10]);
+      a[11] = cg_fma(T(0.23859649122807017), f, a[11]);
+      a[12] = cg_fma(T(-0.23076923076923078), f, a[12]);
     }
-    { const T f = T(4)*nzmzG[0] -T(4)*nzpzG[0];
-      a[29] = cg_fma(T(-0.050680482878913066), f, a[29]);
-      a[30] = cg_fma(T(0.3003276384391115), f, a[30]);
-      a[31] = cg_fma(T(-0.19622408569881955), f, a[31]);
-      a[32] = cg_fma(T(0.06954007160561829), f, a[32]);
-    }
-    { const T f = T(4)*nzmzG[1] -T(4)*nzpzG[1];
-      a[0] = cg_fma(T(-0.008614864864864865), f, a[0]);
-      a[1] = cg_fma(T(0.16931306306306307), f, a[1]);
-      a[2] = cg_fma(T(-0.008614864864864865), f, a[2]);
-      a[3] = cg_fma(T(0.03648648648648649), f, a[3]);
-      a[4] = cg_fma(T(0.10270270270270271), f, a[4]);
-      a[5] = cg_fma(T(-0.005405405405405406), f, a[5]);
-      a[6] = cg_fma(T(-1.422972972972973), f, a[6]);
-      a[7] = cg_fma(T(0.10270270270270271), f, a[7]);
-      a[8] = cg_fma(T(0.03648648648648649), f, a[8]);
-    }
-    { const T f = T(4)*nzmzG[1] +T(4)*nzpzG[1];
-      a[13] = cg_fma(T(-0.02403846153846154), f, a[13]);
-      a[15] = cg_fma(T(0.11538461538461539), f, a[15]);
-    }
-    { const T f = T(4)*nzmzG[2] +T(4)*nzpzG[2];
-      a[9] = cg_fma(T(0.00982624831309042), f, a[9]);
-      a[10] = cg_fma(T(-0.007017543859649123), f, a[10]);
-      a[11] = cg_fma(T(0.05964912280701754), f, a[11]);
-      a[12] = cg_fma(T(-0.057692307692307696), f, a[12]);
-    }
-    { const T f = T(4)*nzmzG[2] -T(4)*nzpzG[2];
-      a[17] = cg_fma(T(-0.050680482878913066), f, a[17]);
-      a[18] = cg_fma(T(0.06954007160561829), f, a[18]);
-      a[19] = cg_fma(T(-0.19622408569881955), f, a[19]);
-      a[20] = cg_fma(T(0.3003276384391115), f, a[20]);
+    { const T f = nzmzG[2] -nzpzG[2];
+      a[17] = cg_fma(T(-0.20272193151565226), f, a[17]);
+      a[18] = cg_fma(T(0.27816028642247315), f, a[18]);
+      a[19] = cg_fma(T(-0.7848963427952782), f, a[19]);
+      a[20] = cg_fma(T(1.201310553756446), f, a[20]);
     }
   }
   {
@@ -655,61 +637,61 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T nzzpQ = ld.avg(0, 0, 1);
     T nzzpG[3];
     ld.grefv(0, 0, 1, nzzpG);
-    { const T f = T(4)*nzzmQ +T(4)*nzzpQ;
-      a[0] = cg_fma(T(-0.013626126126126126), f, a[0]);
-      a[1] = cg_fma(T(-0.013626126126126126), f, a[1]);
-      a[2] = cg_fma(T(0.5939189189189189), f, a[2]);
+    { const T f = nzzmQ +nzzpQ;
+      a[0] = cg_fma(T(-0.0545045045045045), f, a[0]);
+      a[1] = cg_fma(T(-0.0545045045045045), f, a[1]);
+      a[2] = cg_fma(T(2.3756756756756756), f, a[2]);
+      a[3] = cg_fma(T(0.5837837837837838), f, a[3]);
+      a[4] = cg_fma(T(-0.08648648648648649), f, a[4]);
+      a[5] = cg_fma(T(-0.3567567567567568), f, a[5]);
+      a[6] = cg_fma(T(0.5837837837837838), f, a[6]);
+      a[7] = cg_fma(T(-0.3567567567567568), f, a[7]);
+      a[8] = cg_fma(T(-10.767567567567568), f, a[8]);
+    }
+    { const T f = nzzmQ -nzzpQ;
+      a[9] = cg_fma(T(-0.3559379217273954), f, a[9]);
+      a[10] = cg_fma(T(0.5789473684210527), f, a[10]);
+      a[11] = cg_fma(T(0.5789473684210527), f, a[11]);
+      a[12] = cg_fma(T(-0.9230769230769231), f, a[12]);
+    }
+    { const T f = nzzmG[0] +nzzpG[0];
+      a[21] = cg_fma(T(0.03930499325236168), f, a[21]);
+      a[22] = cg_fma(T(-0.23076923076923078), f, a[22]);
+      a[23] = cg_fma(T(-0.028070175438596492), f, a[23]);
+      a[24] = cg_fma(T(0.23859649122807017), f, a[24]);
+    }
+    { const T f = nzzmG[0] -nzzpG[0];
+      a[25] = cg_fma(T(-0.20272193151565226), f, a[25]);
+      a[26] = cg_fma(T(1.201310553756446), f, a[26]);
+      a[27] = cg_fma(T(0.27816028642247315), f, a[27]);
+      a[28] = cg_fma(T(-0.7848963427952782), f, a[28]);
+    }
+    { const T f = nzzmG[1] +nzzpG[1];
+      a[13] = cg_fma(T(0.03930499325236168), f, a[13]);
+      a[14] = cg_fma(T(-0.028070175438596492), f, a[14]);
+      a[15] = cg_fma(T(-0.23076923076923078), f, a[15]);
+      a[16] = cg_fma(T(0.23859649122807017), f, a[16]);
+    }
+    { const T f = nzzmG[1] -nzzpG[1];
+      a[17] = cg_fma(T(-0.20272193151565226), f, a[17]);
+      a[18] = cg_fma(T(0.27816028642247315), f, a[18]);
+      a[19] = cg_fma(T(1.201310553756446), f, a[19]);
+      a[20] = cg_fma(T(-0.7848963427952782), f, a[20]);
+    }
+    { const T f = nzzmG[2] -nzzpG[2];
+      a[0] = cg_fma(T(-0.03445945945945946), f, a[0]);
+      a[1] = cg_fma(T(-0.03445945945945946), f, a[1]);
+      a[2] = cg_fma(T(0.6772522522522523), f, a[2]);
       a[3] = cg_fma(T(0.14594594594594595), f, a[3]);
       a[4] = cg_fma(T(-0.021621621621621623), f, a[4]);
-      a[5] = cg_fma(T(-0.0891891891891892), f, a[5]);
+      a[5] = cg_fma(T(0.41081081081081083), f, a[5]);
       a[6] = cg_fma(T(0.14594594594594595), f, a[6]);
-      a[7] = cg_fma(T(-0.0891891891891892), f, a[7]);
-      a[8] = cg_fma(T(-2.691891891891892), f, a[8]);
+      a[7] = cg_fma(T(0.41081081081081083), f, a[7]);
+      a[8] = cg_fma(T(-5.691891891891892), f, a[8]);
     }
-    { const T f = T(4)*nzzmQ -T(4)*nzzpQ;
-      a[9] = cg_fma(T(-0.08898448043184885), f, a[9]);
-      a[10] = cg_fma(T(0.14473684210526316), f, a[10]);
-      a[11] = cg_fma(T(0.14473684210526316), f, a[11]);
-      a[12] = cg_fma(T(-0.23076923076923078), f, a[12]);
-    }
-    { const T f = T(4)*nzzmG[0] +T(4)*nzzpG[0];
-      a[21] = cg_fma(T(0.00982624831309042), f, a[21]);
-      a[22] = cg_fma(T(-0.057692307692307696), f, a[22]);
-      a[23] = cg_fma(T(-0.007017543859649123), f, a[23]);
-      a[24] = cg_fma(T(0.05964912280701754), f, a[24]);
-    }
-    { const T f = T(4)*nzzmG[0] -T(4)*nzzpG[0];
-      a[25] = cg_fma(T(-0.050680482878913066), f, a[25]);
-      a[26] = cg_fma(T(0.3003276384391115), f, a[26]);
-      a[27] = cg_fma(T(0.06954007160561829), f, a[27]);
-      a[28] = cg_fma(T(-0.19622408569881955), f, a[28]);
-    }
-    { const T f = T(4)*nzzmG[1] +T(4)*nzzpG[1];
-      a[13] = cg_fma(T(0.00982624831309042), f, a[13]);
-      a[14] = cg_fma(T(-0.007017543859649123), f, a[14]);
-      a[15] = cg_fma(T(-0.057692307692307696), f, a[15]);
-      a[16] = cg_fma(T(0.05964912280701754), f, a[16]);
-    }
-    { const T f = T(4)*nzzmG[1] -T(4)*nzzpG[1];
-      a[17] = cg_fma(T(-0.050680482878913066), f, a[17]);
-      a[18] = cg_fma(T(0.06954007160561829), f, a[18]);
-      a[19] = cg_fma(T(0.3003276384391115), f, a[19]);
-      a[20] = cg_fma(T(-0.19622408569881955), f, a[20]);
-    }
-    { const T f = T(4)*nzzmG[2] -T(4)*nzzpG[2];
-      a[0] = cg_fma(T(-0.008614864864864865), f, a[0]);
-      a[1] = cg_fma(T(-0.008614864864864865), f, a[1]);
-      a[2] = cg_fma(T(0.16931306306306307), f, a[2]);
-      a[3] = cg_fma(T(0.03648648648648649), f, a[3]);
-      a[4] = cg_fma(T(-0.005405405405405406), f, a[4]);
-      a[5] = cg_fma(T(0.10270270270270271), f, a[5]);
-      a[6] = cg_fma(T(0.03648648648648649), f, a[6]);
-      a[7] = cg_fma(T(0.10270270270270271), f, a[7]);
-      a[8] = cg_fma(T(-1.422972972972973), f, a[8]);
-    }
-    { const T f = T(4)*nzzmG[2] +T(4)*nzzpG[2];
-      a[9] = cg_fma(T(-0.02403846153846154), f, a[9]);
-      a[12] = cg_fma(T(0.11538461538461539), f, a[12]);
+    { const T f = nzzmG[2] +nzzpG[2];
+      a[9] = cg_fma(T(-0.09615384615384616), f, a[9]);
+      a[12] = cg_fma(T(0.46153846153846156), f, a[12]);
     }
   }
   {
@@ -725,82 +707,82 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T nzppQ = ld.avg(0, 1, 1);
     T nzppG[3];
     ld.grefv(0, 1, 1, nzppG);
-    { const T f = T(2)*nzmmQ +T(2)*nzpmQ +T(2)*nzmpQ +T(2)*nzppQ;
-      a[0] = cg_fma(T(-0.0019144144144144144), f, a[0]);
-      a[1] = cg_fma(T(0.015540540540540541), f, a[1]);
-      a[2] = cg_fma(T(0.015540540540540541), f, a[2]);
-      a[3] = cg_fma(T(0.008108108108108109), f, a[3]);
-      a[4] = cg_fma(T(0.010810810810810811), f, a[4]);
-      a[5] = cg_fma(T(0.010810810810810811), f, a[5]);
-      a[6] = cg_fma(T(-0.15405405405405406), f, a[6]);
-      a[7] = cg_fma(T(0.07837837837837838), f, a[7]);
-      a[8] = cg_fma(T(-0.15405405405405406), f, a[8]);
+    { const T f = nzmmQ +nzpmQ +nzmpQ +nzppQ;
+      a[0] = cg_fma(T(-0.0038288288288288288), f, a[0]);
+      a[1] = cg_fma(T(0.031081081081081083), f, a[1]);
+      a[2] = cg_fma(T(0.031081081081081083), f, a[2]);
+      a[3] = cg_fma(T(0.016216216216216217), f, a[3]);
+      a[4] = cg_fma(T(0.021621621621621623), f, a[4]);
+      a[5] = cg_fma(T(0.021621621621621623), f, a[5]);
+      a[6] = cg_fma(T(-0.3081081081081081), f, a[6]);
+      a[7] = cg_fma(T(0.15675675675675677), f, a[7]);
+      a[8] = cg_fma(T(-0.3081081081081081), f, a[8]);
     }
-    { const T f = T(2)*nzmmQ +T(2)*nzpmQ -T(2)*nzmpQ -T(2)*nzppQ;
-      a[9] = cg_fma(T(0.0010964912280701754), f, a[9]);
-      a[10] = cg_fma(T(0.0035087719298245615), f, a[10]);
-      a[11] = cg_fma(T(-0.02982456140350877), f, a[11]);
+    { const T f = nzmmQ +nzpmQ -nzmpQ -nzppQ;
+      a[9] = cg_fma(T(0.0021929824561403508), f, a[9]);
+      a[10] = cg_fma(T(0.007017543859649123), f, a[10]);
+      a[11] = cg_fma(T(-0.05964912280701754), f, a[11]);
     }
-    { const T f = T(2)*nzmmQ -T(2)*nzpmQ +T(2)*nzmpQ -T(2)*nzppQ;
-      a[13] = cg_fma(T(0.0010964912280701754), f, a[13]);
-      a[14] = cg_fma(T(0.0035087719298245615), f, a[14]);
-      a[16] = cg_fma(T(-0.02982456140350877), f, a[16]);
+    { const T f = nzmmQ -nzpmQ +nzmpQ -nzppQ;
+      a[13] = cg_fma(T(0.0021929824561403508), f, a[13]);
+      a[14] = cg_fma(T(0.007017543859649123), f, a[14]);
+      a[16] = cg_fma(T(-0.05964912280701754), f, a[16]);
     }
-    { const T f = T(2)*nzmmQ -T(2)*nzpmQ -T(2)*nzmpQ +T(2)*nzppQ;
-      a[17] = cg_fma(T(0.010106834664463417), f, a[17]);
-      a[18] = cg_fma(T(-0.026094739741118148), f, a[18]);
-      a[19] = cg_fma(T(0.01611126411456899), f, a[19]);
-      a[20] = cg_fma(T(0.01611126411456899), f, a[20]);
+    { const T f = nzmmQ -nzpmQ -nzmpQ +nzppQ;
+      a[17] = cg_fma(T(0.020213669328926834), f, a[17]);
+      a[18] = cg_fma(T(-0.052189479482236296), f, a[18]);
+      a[19] = cg_fma(T(0.03222252822913798), f, a[19]);
+      a[20] = cg_fma(T(0.03222252822913798), f, a[20]);
     }
-    { const T f = T(2)*nzmmG[0] +T(2)*nzpmG[0] +T(2)*nzmpG[0] +T(2)*nzppG[0];
-      a[21] = cg_fma(T(0.0038166329284750338), f, a[21]);
-      a[22] = cg_fma(T(-0.028846153846153848), f, a[22]);
-      a[23] = cg_fma(T(0.02631578947368421), f, a[23]);
-      a[24] = cg_fma(T(0.02631578947368421), f, a[24]);
+    { const T f = nzmmG[0] +nzpmG[0] +nzmpG[0] +nzppG[0];
+      a[21] = cg_fma(T(0.0076332658569500675), f, a[21]);
+      a[22] = cg_fma(T(-0.057692307692307696), f, a[22]);
+      a[23] = cg_fma(T(0.05263157894736842), f, a[23]);
+      a[24] = cg_fma(T(0.05263157894736842), f, a[24]);
     }
-    { const T f = T(2)*nzmmG[0] +T(2)*nzpmG[0] -T(2)*nzmpG[0] -T(2)*nzppG[0];
-      a[25] = cg_fma(T(0.005208333333333333), f, a[25]);
-      a[26] = cg_fma(T(0.12413793103448276), f, a[26]);
-      a[27] = cg_fma(T(-0.125), f, a[27]);
-      a[28] = cg_fma(T(-0.12413793103448276), f, a[28]);
+    { const T f = nzmmG[0] +nzpmG[0] -nzmpG[0] -nzppG[0];
+      a[25] = cg_fma(T(0.010416666666666666), f, a[25]);
+      a[26] = cg_fma(T(0.2482758620689655), f, a[26]);
+      a[27] = cg_fma(T(-0.25), f, a[27]);
+      a[28] = cg_fma(T(-0.2482758620689655), f, a[28]);
     }
-    { const T f = T(2)*nzmmG[0] -T(2)*nzpmG[0] +T(2)*nzmpG[0] -T(2)*nzppG[0];
-      a[29] = cg_fma(T(0.005208333333333333), f, a[29]);
-      a[30] = cg_fma(T(0.12413793103448276), f, a[30]);
-      a[31] = cg_fma(T(-0.12413793103448276), f, a[31]);
-      a[32] = cg_fma(T(-0.125), f, a[32]);
+    { const T f = nzmmG[0] -nzpmG[0] +nzmpG[0] -nzppG[0];
+      a[29] = cg_fma(T(0.010416666666666666), f, a[29]);
+      a[30] = cg_fma(T(0.2482758620689655), f, a[30]);
+      a[31] = cg_fma(T(-0.2482758620689655), f, a[31]);
+      a[32] = cg_fma(T(-0.25), f, a[32]);
     }
-    { const T f = T(2)*nzmmG[0] -T(2)*nzpmG[0] -T(2)*nzmpG[0] +T(2)*nzppG[0];
-      a[33] = cg_fma(T(0.0392156862745098), f, a[33]);
+    { const T f = nzmmG[0] -nzpmG[0] -nzmpG[0] +nzppG[0];
+      a[33] = cg_fma(T(0.0784313725490196), f, a[33]);
     }
-    { const T f = T(2)*(-nzmmG[1] -nzmmG[2]) +T(2)*(nzpmG[1] -nzpmG[2]) +T(2)*(-nzmpG[1] +nzmpG[2]) +T(2)*(nzppG[1] +nzppG[2]);
-      a[0] = cg_fma(T(0.0004786036036036036), f, a[0]);
-      a[1] = cg_fma(T(-0.00909346846846847), f, a[1]);
-      a[2] = cg_fma(T(-0.00909346846846847), f, a[2]);
-      a[3] = cg_fma(T(-0.002027027027027027), f, a[3]);
-      a[4] = cg_fma(T(-0.002702702702702703), f, a[4]);
-      a[5] = cg_fma(T(-0.002702702702702703), f, a[5]);
-      a[6] = cg_fma(T(0.038513513513513516), f, a[6]);
-      a[7] = cg_fma(T(0.10540540540540541), f, a[7]);
-      a[8] = cg_fma(T(0.038513513513513516), f, a[8]);
+    { const T f = (-nzmmG[1] -nzmmG[2]) +(nzpmG[1] -nzpmG[2]) +(-nzmpG[1] +nzmpG[2]) +(nzppG[1] +nzppG[2]);
+      a[0] = cg_fma(T(0.0009572072072072072), f, a[0]);
+      a[1] = cg_fma(T(-0.01818693693693694), f, a[1]);
+      a[2] = cg_fma(T(-0.01818693693693694), f, a[2]);
+      a[3] = cg_fma(T(-0.004054054054054054), f, a[3]);
+      a[4] = cg_fma(T(-0.005405405405405406), f, a[4]);
+      a[5] = cg_fma(T(-0.005405405405405406), f, a[5]);
+      a[6] = cg_fma(T(0.07702702702702703), f, a[6]);
+      a[7] = cg_fma(T(0.21081081081081082), f, a[7]);
+      a[8] = cg_fma(T(0.07702702702702703), f, a[8]);
     }
-    { const T f = T(2)*(-nzmmG[1] -nzmmG[2]) +T(2)*(nzpmG[1] -nzpmG[2]) -T(2)*(-nzmpG[1] +nzmpG[2]) -T(2)*(nzppG[1] +nzppG[2]);
-      a[9] = cg_fma(T(0.007654352226720648), f, a[9]);
-      a[10] = cg_fma(T(0.005263157894736842), f, a[10]);
-      a[11] = cg_fma(T(-0.04473684210526316), f, a[11]);
-      a[12] = cg_fma(T(-0.028846153846153848), f, a[12]);
+    { const T f = (-nzmmG[1] -nzmmG[2]) +(nzpmG[1] -nzpmG[2]) -(-nzmpG[1] +nzmpG[2]) -(nzppG[1] +nzppG[2]);
+      a[9] = cg_fma(T(0.015308704453441296), f, a[9]);
+      a[10] = cg_fma(T(0.010526315789473684), f, a[10]);
+      a[11] = cg_fma(T(-0.08947368421052632), f, a[11]);
+      a[12] = cg_fma(T(-0.057692307692307696), f, a[12]);
     }
-    { const T f = T(2)*(-nzmmG[1] -nzmmG[2]) -T(2)*(nzpmG[1] -nzpmG[2]) +T(2)*(-nzmpG[1] +nzmpG[2]) -T(2)*(nzppG[1] +nzppG[2]);
-      a[13] = cg_fma(T(0.007654352226720648), f, a[13]);
-      a[14] = cg_fma(T(0.005263157894736842), f, a[14]);
-      a[15] = cg_fma(T(-0.028846153846153848), f, a[15]);
-      a[16] = cg_fma(T(-0.04473684210526316), f, a[16]);
+    { const T f = (-nzmmG[1] -nzmmG[2]) -(nzpmG[1] -nzpmG[2]) +(-nzmpG[1] +nzmpG[2]) -(nzppG[1] +nzppG[2]);
+      a[13] = cg_fma(T(0.015308704453441296), f, a[13]);
+      a[14] = cg_fma(T(0.010526315789473684), f, a[14]);
+      a[15] = cg_fma(T(-0.057692307692307696), f, a[15]);
+      a[16] = cg_fma(T(-0.08947368421052632), f, a[16]);
     }
-    { const T f = T(2)*(-nzmmG[1] -nzmmG[2]) -T(2)*(nzpmG[1] -nzpmG[2]) -T(2)*(-nzmpG[1] +nzmpG[2]) +T(2)*(nzppG[1] +nzppG[2]);
-      a[17] = cg_fma(T(-0.020359978885522812), f, a[17]);
-      a[18] = cg_fma(T(-0.008744147617736162), f, a[18]);
-      a[19] = cg_fma(T(0.10038556871385293), f, a[19]);
-      a[20] = cg_fma(T(0.10038556871385293), f, a[20]);
+    { const T f = (-nzmmG[1] -nzmmG[2]) -(nzpmG[1] -nzpmG[2]) -(-nzmpG[1] +nzmpG[2]) +(nzppG[1] +nzppG[2]);
+      a[17] = cg_fma(T(-0.040719957771045624), f, a[17]);
+      a[18] = cg_fma(T(-0.017488295235472323), f, a[18]);
+      a[19] = cg_fma(T(0.20077113742770586), f, a[19]);
+      a[20] = cg_fma(T(0.20077113742770586), f, a[20]);
     }
   }
   {
@@ -816,82 +798,82 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T npzpQ = ld.avg(1, 0, 1);
     T npzpG[3];
     ld.grefv(1, 0, 1, npzpG);
-    { const T f = T(2)*nmzmQ +T(2)*npzmQ +T(2)*nmzpQ +T(2)*npzpQ;
-      a[0] = cg_fma(T(0.015540540540540541), f, a[0]);
-      a[1] = cg_fma(T(-0.0019144144144144144), f, a[1]);
-      a[2] = cg_fma(T(0.015540540540540541), f, a[2]);
-      a[3] = cg_fma(T(-0.15405405405405406), f, a[3]);
-      a[4] = cg_fma(T(0.010810810810810811), f, a[4]);
-      a[5] = cg_fma(T(0.07837837837837838), f, a[5]);
-      a[6] = cg_fma(T(0.008108108108108109), f, a[6]);
-      a[7] = cg_fma(T(0.010810810810810811), f, a[7]);
-      a[8] = cg_fma(T(-0.15405405405405406), f, a[8]);
+    { const T f = nmzmQ +npzmQ +nmzpQ +npzpQ;
+      a[0] = cg_fma(T(0.031081081081081083), f, a[0]);
+      a[1] = cg_fma(T(-0.0038288288288288288), f, a[1]);
+      a[2] = cg_fma(T(0.031081081081081083), f, a[2]);
+      a[3] = cg_fma(T(-0.3081081081081081), f, a[3]);
+      a[4] = cg_fma(T(0.021621621621621623), f, a[4]);
+      a[5] = cg_fma(T(0.15675675675675677), f, a[5]);
+      a[6] = cg_fma(T(0.016216216216216217), f, a[6]);
+      a[7] = cg_fma(T(0.021621621621621623), f, a[7]);
+      a[8] = cg_fma(T(-0.3081081081081081), f, a[8]);
     }
-    { const T f = T(2)*nmzmQ +T(2)*npzmQ -T(2)*nmzpQ -T(2)*npzpQ;
-      a[9] = cg_fma(T(0.0010964912280701754), f, a[9]);
-      a[10] = cg_fma(T(-0.02982456140350877), f, a[10]);
-      a[11] = cg_fma(T(0.0035087719298245615), f, a[11]);
+    { const T f = nmzmQ +npzmQ -nmzpQ -npzpQ;
+      a[9] = cg_fma(T(0.0021929824561403508), f, a[9]);
+      a[10] = cg_fma(T(-0.05964912280701754), f, a[10]);
+      a[11] = cg_fma(T(0.007017543859649123), f, a[11]);
     }
-    { const T f = T(2)*nmzmQ -T(2)*npzmQ +T(2)*nmzpQ -T(2)*npzpQ;
-      a[21] = cg_fma(T(0.0010964912280701754), f, a[21]);
-      a[23] = cg_fma(T(0.0035087719298245615), f, a[23]);
-      a[24] = cg_fma(T(-0.02982456140350877), f, a[24]);
+    { const T f = nmzmQ -npzmQ +nmzpQ -npzpQ;
+      a[21] = cg_fma(T(0.0021929824561403508), f, a[21]);
+      a[23] = cg_fma(T(0.007017543859649123), f, a[23]);
+      a[24] = cg_fma(T(-0.05964912280701754), f, a[24]);
     }
-    { const T f = T(2)*nmzmQ -T(2)*npzmQ -T(2)*nmzpQ +T(2)*npzpQ;
-      a[25] = cg_fma(T(0.010106834664463417), f, a[25]);
-      a[26] = cg_fma(T(0.01611126411456899), f, a[26]);
-      a[27] = cg_fma(T(-0.026094739741118148), f, a[27]);
-      a[28] = cg_fma(T(0.01611126411456899), f, a[28]);
+    { const T f = nmzmQ -npzmQ -nmzpQ +npzpQ;
+      a[25] = cg_fma(T(0.020213669328926834), f, a[25]);
+      a[26] = cg_fma(T(0.03222252822913798), f, a[26]);
+      a[27] = cg_fma(T(-0.052189479482236296), f, a[27]);
+      a[28] = cg_fma(T(0.03222252822913798), f, a[28]);
     }
-    { const T f = T(2)*nmzmG[1] +T(2)*npzmG[1] +T(2)*nmzpG[1] +T(2)*npzpG[1];
-      a[13] = cg_fma(T(0.0038166329284750338), f, a[13]);
-      a[14] = cg_fma(T(0.02631578947368421), f, a[14]);
-      a[15] = cg_fma(T(-0.028846153846153848), f, a[15]);
-      a[16] = cg_fma(T(0.02631578947368421), f, a[16]);
+    { const T f = nmzmG[1] +npzmG[1] +nmzpG[1] +npzpG[1];
+      a[13] = cg_fma(T(0.0076332658569500675), f, a[13]);
+      a[14] = cg_fma(T(0.05263157894736842), f, a[14]);
+      a[15] = cg_fma(T(-0.057692307692307696), f, a[15]);
+      a[16] = cg_fma(T(0.05263157894736842), f, a[16]);
     }
-    { const T f = T(2)*nmzmG[1] +T(2)*npzmG[1] -T(2)*nmzpG[1] -T(2)*npzpG[1];
-      a[17] = cg_fma(T(0.005208333333333333), f, a[17]);
-      a[18] = cg_fma(T(-0.125), f, a[18]);
-      a[19] = cg_fma(T(0.12413793103448276), f, a[19]);
-      a[20] = cg_fma(T(-0.12413793103448276), f, a[20]);
+    { const T f = nmzmG[1] +npzmG[1] -nmzpG[1] -npzpG[1];
+      a[17] = cg_fma(T(0.010416666666666666), f, a[17]);
+      a[18] = cg_fma(T(-0.25), f, a[18]);
+      a[19] = cg_fma(T(0.2482758620689655), f, a[19]);
+      a[20] = cg_fma(T(-0.2482758620689655), f, a[20]);
     }
-    { const T f = T(2)*nmzmG[1] -T(2)*npzmG[1] +T(2)*nmzpG[1] -T(2)*npzpG[1];
-      a[29] = cg_fma(T(0.005208333333333333), f, a[29]);
-      a[30] = cg_fma(T(-0.12413793103448276), f, a[30]);
-      a[31] = cg_fma(T(0.12413793103448276), f, a[31]);
-      a[32] = cg_fma(T(-0.125), f, a[32]);
+    { const T f = nmzmG[1] -npzmG[1] +nmzpG[1] -npzpG[1];
+      a[29] = cg_fma(T(0.010416666666666666), f, a[29]);
+      a[30] = cg_fma(T(-0.2482758620689655), f, a[30]);
+      a[31] = cg_fma(T(0.2482758620689655), f, a[31]);
+      a[32] = cg_fma(T(-0.25), f, a[32]);
     }
-    { const T f = T(2)*nmzmG[1] -T(2)*npzmG[1] -T(2)*nmzpG[1] +T(2)*npzpG[1];
-      a[33] = cg_fma(T(0.0392156862745098), f, a[33]);
+    { const T f = nmzmG[1] -npzmG[1] -nmzpG[1] +npzpG[1];
+      a[33] = cg_fma(T(0.0784313725490196), f, a[33]);
     }
-    { const T f = T(2)*(-nmzmG[0] -nmzmG[2]) +T(2)*(npzmG[0] -npzmG[2]) +T(2)*(-nmzpG[0] +nmzpG[2]) +T(2)*(npzpG[0] +npzpG[2]);
-      a[0] = cg_fma(T(-0.00909346846846847), f, a[0]);
-      a[1] = cg_fma(T(0.0004786036036036036), f, a[1]);
-      a[2] = cg_fma(T(-0.00909346846846847), f, a[2]);
-      a[3] = cg_fma(T(0.038513513513513516), f, a[3]);
-      a[4] = cg_fma(T(-0.002702702702702703), f, a[4]);
-      a[5] = cg_fma(T(0.10540540540540541), f, a[5]);
-      a[6] = cg_fma(T(-0.002027027027027027), f, a[6]);
-      a[7] = cg_fma(T(-0.002702702702702703), f, a[7]);
-      a[8] = cg_fma(T(0.038513513513513516), f, a[8]);
+    { const T f = (-nmzmG[0] -nmzmG[2]) +(npzmG[0] -npzmG[2]) +(-nmzpG[0] +nmzpG[2]) +(npzpG[0] +npzpG[2]);
+      a[0] = cg_fma(T(-0.01818693693693694), f, a[0]);
+      a[1] = cg_fma(T(0.0009572072072072072), f, a[1]);
+      a[2] = cg_fma(T(-0.01818693693693694), f, a[2]);
+      a[3] = cg_fma(T(0.07702702702702703), f, a[3]);
+      a[4] = cg_fma(T(-0.005405405405405406), f, a[4]);
+      a[5] = cg_fma(T(0.21081081081081082), f, a[5]);
+      a[6] = cg_fma(T(-0.004054054054054054), f, a[6]);
+      a[7] = cg_fma(T(-0.005405405405405406), f, a[7]);
+      a[8] = cg_fma(T(0.07702702702702703), f, a[8]);
     }
-    { const T f = T(2)*(-nmzmG[0] -nmzmG[2]) +T(2)*(npzmG[0] -npzmG[2]) -T(2)*(-nmzpG[0] +nmzpG[2]) -T(2)*(npzpG[0] +npzpG[2]);
-      a[9] = cg_fma(T(0.007654352226720648), f, a[9]);
-      a[10] = cg_fma(T(-0.04473684210526316), f, a[10]);
-      a[11] = cg_fma(T(0.005263157894736842), f, a[11]);
-      a[12] = cg_fma(T(-0.028846153846153848), f, a[12]);
+    { const T f = (-nmzmG[0] -nmzmG[2]) +(npzmG[0] -npzmG[2]) -(-nmzpG[0] +nmzpG[2]) -(npzpG[0] +npzpG[2]);
+      a[9] = cg_fma(T(0.015308704453441296), f, a[9]);
+      a[10] = cg_fma(T(-0.08947368421052632), f, a[10]);
+      a[11] = cg_fma(T(0.010526315789473684), f, a[11]);
+      a[12] = cg_fma(T(-0.057692307692307696), f, a[12]);
     }
-    { const T f = T(2)*(-nmzmG[0] -nmzmG[2]) -T(2)*(npzmG[0] -npzmG[2]) +T(2)*(-nmzpG[0] +nmzpG[2]) -T(2)*(npzpG[0] +npzpG[2]);
-      a[21] = cg_fma(T(0.007654352226720648), f, a[21]);
-      a[22] = cg_fma(T(-0.028846153846153848), f, a[22]);
-      a[23] = cg_fma(T(0.005263157894736842), f, a[23]);
-      a[24] = cg_fma(T(-0.04473684210526316), f, a[24]);
+    { const T f = (-nmzmG[0] -nmzmG[2]) -(npzmG[0] -npzmG[2]) +(-nmzpG[0] +nmzpG[2]) -(npzpG[0] +npzpG[2]);
+      a[21] = cg_fma(T(0.015308704453441296), f, a[21]);
+      a[22] = cg_fma(T(-0.057692307692307696), f, a[22]);
+      a[23] = cg_fma(T(0.010526315789473684), f, a[23]);
+      a[24] = cg_fma(T(-0.08947368421052632), f, a[24]);
     }
-    { const T f = T(2)*(-nmzmG[0] -nmzmG[2]) -T(2)*(npzmG[0] -npzmG[2]) -T(2)*(-nmzpG[0] +nmzpG[2]) +T(2)*(npzpG[0] +npzpG[2]);
-      a[25] = cg_fma(T(-0.020359978885522812), f, a[25]);
-      a[26] = cg_fma(T(0.10038556871385293), f, a[26]);
-      a[27] = cg_fma(T(-0.008744147617736162), f, a[27]);
-      a[28] = cg_fma(T(0.10038556871385293), f, a[28]);
+    { const T f = (-nmzmG[0] -nmzmG[2]) -(npzmG[0] -npzmG[2]) -(-nmzpG[0] +nmzpG[2]) +(npzpG[0] +npzpG[2]);
+      a[25] = cg_fma(T(-0.040719957771045624), f, a[25]);
+      a[26] = cg_fma(T(0.20077113742770586), f, a[26]);
+      a[27] = cg_fma(T(-0.017488295235472323), f, a[27]);
+      a[28] = cg_fma(T(0.20077113742770586), f, a[28]);
     }
   }
   {
@@ -907,82 +889,82 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T nppzQ = ld.avg(1, 1, 0);
     T nppzG[3];
     ld.grefv(1, 1, 0, nppzG);
-    { const T f = T(2)*nmmzQ +T(2)*npmzQ +T(2)*nmpzQ +T(2)*nppzQ;
-      a[0] = cg_fma(T(0.015540540540540541), f, a[0]);
-      a[1] = cg_fma(T(0.015540540540540541), f, a[1]);
-      a[2] = cg_fma(T(-0.0019144144144144144), f, a[2]);
-      a[3] = cg_fma(T(-0.15405405405405406), f, a[3]);
-      a[4] = cg_fma(T(0.07837837837837838), f, a[4]);
-      a[5] = cg_fma(T(0.010810810810810811), f, a[5]);
-      a[6] = cg_fma(T(-0.15405405405405406), f, a[6]);
-      a[7] = cg_fma(T(0.010810810810810811), f, a[7]);
-      a[8] = cg_fma(T(0.008108108108108109), f, a[8]);
+    { const T f = nmmzQ +npmzQ +nmpzQ +nppzQ;
+      a[0] = cg_fma(T(0.031081081081081083), f, a[0]);
+      a[1] = cg_fma(T(0.031081081081081083), f, a[1]);
+      a[2] = cg_fma(T(-0.0038288288288288288), f, a[2]);
+      a[3] = cg_fma(T(-0.3081081081081081), f, a[3]);
+      a[4] = cg_fma(T(0.15675675675675677), f, a[4]);
+      a[5] = cg_fma(T(0.021621621621621623), f, a[5]);
+      a[6] = cg_fma(T(-0.3081081081081081), f, a[6]);
+      a[7] = cg_fma(T(0.021621621621621623), f, a[7]);
+      a[8] = cg_fma(T(0.016216216216216217), f, a[8]);
     }
-    { const T f = T(2)*nmmzQ +T(2)*npmzQ -T(2)*nmpzQ -T(2)*nppzQ;
-      a[13] = cg_fma(T(0.0010964912280701754), f, a[13]);
-      a[14] = cg_fma(T(-0.02982456140350877), f, a[14]);
-      a[16] = cg_fma(T(0.0035087719298245615), f, a[16]);
+    { const T f = nmmzQ +npmzQ -nmpzQ -nppzQ;
+      a[13] = cg_fma(T(0.0021929824561403508), f, a[13]);
+      a[14] = cg_fma(T(-0.05964912280701754), f, a[14]);
+      a[16] = cg_fma(T(0.007017543859649123), f, a[16]);
     }
-    { const T f = T(2)*nmmzQ -T(2)*npmzQ +T(2)*nmpzQ -T(2)*nppzQ;
-      a[21] = cg_fma(T(0.0010964912280701754), f, a[21]);
-      a[23] = cg_fma(T(-0.02982456140350877), f, a[23]);
-      a[24] = cg_fma(T(0.0035087719298245615), f, a[24]);
+    { const T f = nmmzQ -npmzQ +nmpzQ -nppzQ;
+      a[21] = cg_fma(T(0.0021929824561403508), f, a[21]);
+      a[23] = cg_fma(T(-0.05964912280701754), f, a[23]);
+      a[24] = cg_fma(T(0.007017543859649123), f, a[24]);
     }
-    { const T f = T(2)*nmmzQ -T(2)*npmzQ -T(2)*nmpzQ +T(2)*nppzQ;
-      a[29] = cg_fma(T(0.010106834664463417), f, a[29]);
-      a[30] = cg_fma(T(0.01611126411456899), f, a[30]);
-      a[31] = cg_fma(T(0.01611126411456899), f, a[31]);
-      a[32] = cg_fma(T(-0.026094739741118148), f, a[32]);
+    { const T f = nmmzQ -npmzQ -nmpzQ +nppzQ;
+      a[29] = cg_fma(T(0.020213669328926834), f, a[29]);
+      a[30] = cg_fma(T(0.03222252822913798), f, a[30]);
+      a[31] = cg_fma(T(0.03222252822913798), f, a[31]);
+      a[32] = cg_fma(T(-0.052189479482236296), f, a[32]);
     }
-    { const T f = T(2)*nmmzG[2] +T(2)*npmzG[2] +T(2)*nmpzG[2] +T(2)*nppzG[2];
-      a[9] = cg_fma(T(0.0038166329284750338), f, a[9]);
-      a[10] = cg_fma(T(0.02631578947368421), f, a[10]);
-      a[11] = cg_fma(T(0.02631578947368421), f, a[11]);
-      a[12] = cg_fma(T(-0.028846153846153848), f, a[12]);
+    { const T f = nmmzG[2] +npmzG[2] +nmpzG[2] +nppzG[2];
+      a[9] = cg_fma(T(0.0076332658569500675), f, a[9]);
+      a[10] = cg_fma(T(0.05263157894736842), f, a[10]);
+      a[11] = cg_fma(T(0.05263157894736842), f, a[11]);
+      a[12] = cg_fma(T(-0.057692307692307696), f, a[12]);
     }
-    { const T f = T(2)*nmmzG[2] +T(2)*npmzG[2] -T(2)*nmpzG[2] -T(2)*nppzG[2];
-      a[17] = cg_fma(T(0.005208333333333333), f, a[17]);
-      a[18] = cg_fma(T(-0.125), f, a[18]);
-      a[19] = cg_fma(T(-0.12413793103448276), f, a[19]);
-      a[20] = cg_fma(T(0.12413793103448276), f, a[20]);
+    { const T f = nmmzG[2] +npmzG[2] -nmpzG[2] -nppzG[2];
+      a[17] = cg_fma(T(0.010416666666666666), f, a[17]);
+      a[18] = cg_fma(T(-0.25), f, a[18]);
+      a[19] = cg_fma(T(-0.2482758620689655), f, a[19]);
+      a[20] = cg_fma(T(0.2482758620689655), f, a[20]);
     }
-    { const T f = T(2)*nmmzG[2] -T(2)*npmzG[2] +T(2)*nmpzG[2] -T(2)*nppzG[2];
-      a[25] = cg_fma(T(0.005208333333333333), f, a[25]);
-      a[26] = cg_fma(T(-0.12413793103448276), f, a[26]);
-      a[27] = cg_fma(T(-0.125), f, a[27]);
-      a[28] = cg_fma(T(0.12413793103448276), f, a[28]);
+    { const T f = nmmzG[2] -npmzG[2] +nmpzG[2] -nppzG[2];
+      a[25] = cg_fma(T(0.010416666666666666), f, a[25]);
+      a[26] = cg_fma(T(-0.2482758620689655), f, a[26]);
+      a[27] = cg_fma(T(-0.25), f, a[27]);
+      a[28] = cg_fma(T(0.2482758620689655), f, a[28]);
     }
-    { const T f = T(2)*nmmzG[2] -T(2)*npmzG[2] -T(2)*nmpzG[2] +T(2)*nppzG[2];
-      a[33] = cg_fma(T(0.0392156862745098), f, a[33]);
+    { const T f = nmmzG[2] -npmzG[2] -nmpzG[2] +nppzG[2];
+      a[33] = cg_fma(T(0.0784313725490196), f, a[33]);
     }
-    { const T f = T(2)*(-nmmzG[0] -nmmzG[1]) +T(2)*(npmzG[0] -npmzG[1]) +T(2)*(-nmpzG[0] +nmpzG[1]) +T(2)*(nppzG[0] +nppzG[1]);
-      a[0] = cg_fma(T(-0.00909346846846847), f, a[0]);
-      a[1] = cg_fma(T(-0.00909346846846847), f, a[1]);
-      a[2] = cg_fma(T(0.0004786036036036036), f, a[2]);
-      a[3] = cg_fma(T(0.038513513513513516), f, a[3]);
-      a[4] = cg_fma(T(0.10540540540540541), f, a[4]);
-      a[5] = cg_fma(T(-0.002702702702702703), f, a[5]);
-      a[6] = cg_fma(T(0.038513513513513516), f, a[6]);
-      a[7] = cg_fma(T(-0.002702702702702703), f, a[7]);
-      a[8] = cg_fma(T(-0.002027027027027027), f, a[8]);
+    { const T f = (-nmmzG[0] -nmmzG[1]) +(npmzG[0] -npmzG[1]) +(-nmpzG[0] +nmpzG[1]) +(nppzG[0] +nppzG[1]);
+      a[0] = cg_fma(T(-0.01818693693693694), f, a[0]);
+      a[1] = cg_fma(T(-0.01818693693693694), f, a[1]);
+      a[2] = cg_fma(T(0.0009572072072072072), f, a[2]);
+      a[3] = cg_fma(T(0.07702702702702703), f, a[3]);
+      a[4] = cg_fma(T(0.21081081081081082), f, a[4]);
+      a[5] = cg_fma(T(-0.005405405405405406), f, a[5]);
+      a[6] = cg_fma(T(0.07702702702702703), f, a[6]);
+      a[7] = cg_fma(T(-0.005405405405405406), f, a[7]);
+      a[8] = cg_fma(T(-0.004054054054054054), f, a[8]);
     }
-    { const T f = T(2)*(-nmmzG[0] -nmmzG[1]) +T(2)*(npmzG[0] -npmzG[1]) -T(2)*(-nmpzG[0] +nmpzG[1]) -T(2)*(nppzG[0] +nppzG[1]);
-      a[13] = cg_fma(T(0.007654352226720648), f, a[13]);
-      a[14] = cg_fma(T(-0.04473684210526316), f, a[14]);
-      a[15] = cg_fma(T(-0.028846153846153848), f, a[15]);
-      a[16] = cg_fma(T(0.005263157894736842), f, a[16]);
+    { const T f = (-nmmzG[0] -nmmzG[1]) +(npmzG[0] -npmzG[1]) -(-nmpzG[0] +nmpzG[1]) -(nppzG[0] +nppzG[1]);
+      a[13] = cg_fma(T(0.015308704453441296), f, a[13]);
+      a[14] = cg_fma(T(-0.08947368421052632), f, a[14]);
+      a[15] = cg_fma(T(-0.057692307692307696), f, a[15]);
+      a[16] = cg_fma(T(0.010526315789473684), f, a[16]);
     }
-    { const T f = T(2)*(-nmmzG[0] -nmmzG[1]) -T(2)*(npmzG[0] -npmzG[1]) +T(2)*(-nmpzG[0] +nmpzG[1]) -T(2)*(nppzG[0] +nppzG[1]);
-      a[21] = cg_fma(T(0.007654352226720648), f, a[21]);
-      a[22] = cg_fma(T(-0.028846153846153848), f, a[22]);
-      a[23] = cg_fma(T(-0.04473684210526316), f, a[23]);
-      a[24] = cg_fma(T(0.005263157894736842), f, a[24]);
+    { const T f = (-nmmzG[0] -nmmzG[1]) -(npmzG[0] -npmzG[1]) +(-nmpzG[0] +nmpzG[1]) -(nppzG[0] +nppzG[1]);
+      a[21] = cg_fma(T(0.015308704453441296), f, a[21]);
+      a[22] = cg_fma(T(-0.057692307692307696), f, a[22]);
+      a[23] = cg_fma(T(-0.08947368421052632), f, a[23]);
+      a[24] = cg_fma(T(0.010526315789473684), f, a[24]);
     }
-    { const T f = T(2)*(-nmmzG[0] -nmmzG[1]) -T(2)*(npmzG[0] -npmzG[1]) -T(2)*(-nmpzG[0] +nmpzG[1]) +T(2)*(nppzG[0] +nppzG[1]);
-      a[29] = cg_fma(T(-0.020359978885522812), f, a[29]);
-      a[30] = cg_fma(T(0.10038556871385293), f, a[30]);
-      a[31] = cg_fma(T(0.10038556871385293), f, a[31]);
-      a[32] = cg_fma(T(-0.008744147617736162), f, a[32]);
+    { const T f = (-nmmzG[0] -nmmzG[1]) -(npmzG[0] -npmzG[1]) -(-nmpzG[0] +nmpzG[1]) +(nppzG[0] +nppzG[1]);
+      a[29] = cg_fma(T(-0.040719957771045624), f, a[29]);
+      a[30] = cg_fma(T(0.20077113742770586), f, a[30]);
+      a[31] = cg_fma(T(0.20077113742770586), f, a[31]);
+      a[32] = cg_fma(T(-0.017488295235472323), f, a[32]);
     }
   }
 }

@@ -35,6 +35,7 @@ Data vector order used by the kernels (per variable):
 Edge neighbours are taken in increasing offset order (o_z, o_y, o_x
 lexicographic, -1 < +1) among offsets with exactly two non-zero entries.
 """
+import math
 import itertools
 import os
 from decimal import Decimal, getcontext
@@ -584,15 +585,27 @@ def emit_recon_code(path):
 
             for rep, orb, stab, feats in orbs:
                 for c, coef in feats.items():
-                    expr = " ".join("%s%s" % ("+" if cf > 0 else "-", item_expr(it)) if abs(cf) == 1 else
-                                    "%sT(%d)*%s" % ("+" if cf > 0 else "-", abs(cf), item_expr(it))
+                    # the loader hands averages over relative to q0, so q0
+                    # itself is zero: its terms add nothing
+                    if all(it[0] == "Q0" for it in coef):
+                        continue
+                    # a power-of-two factor common to the integer weights
+                    # moves into the coefficients (exact scaling: the same
+                    # values, without the multiplications)
+                    g = 0
+                    for cf in coef.values():
+                        g = math.gcd(g, abs(cf))
+                    if g & (g - 1):
+                        g = 1
+                    expr = " ".join("%s%s" % ("+" if cf > 0 else "-", item_expr(it)) if abs(cf) == g else
+                                    "%sT(%d)*%s" % ("+" if cf > 0 else "-", abs(cf) // g, item_expr(it))
                                     for it, cf in coef.items()).lstrip("+")
                     rows = [b for b in range(nb) if cls[b] == c and M[b][pos[rep]] != 0.0]
                     if not rows:
                         continue
                     fn.append("    { const T f = %s;" % expr)
                     for b in rows:
-                        fn.append("      a[%d] = cg_fma(%s, f, a[%d]);" % (b, _lit(M[b][pos[rep]] / stab), b))
+                        fn.append("      a[%d] = cg_fma(%s, f, a[%d]);" % (b, _lit(M[b][pos[rep]] / stab * g), b))
                     fn.append("    }")
             fn.append("  }")
         fn.append("}")
