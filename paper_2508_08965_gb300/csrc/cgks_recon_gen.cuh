@@ -362,18 +362,30 @@ CGKS_HD void gen_gp_2d_ax0(const T* __restrict__ a, T* __restrict__ out_v, T (* 
   D3_1 = cg_fma(T(0.5), a[11], D3_1);
   D3_1 = cg_fma(T(0.020833333333333332), a[12], D3_1);
   D3_1 = cg_fma(T(0.020833333333333332), a[13], D3_1);
-  out_v[0] = S0 -S1 -S2 +S3;
-  out_g[0][0] = -D0_0 +D1_0 +D2_0 -D3_0;
-  out_g[0][1] = -D0_1 +D1_1 +D2_1 -D3_1;
-  out_v[1] = S0 +S1 -S2 -S3;
-  out_g[1][0] = -D0_0 -D1_0 +D2_0 +D3_0;
-  out_g[1][1] = D0_1 +D1_1 -D2_1 -D3_1;
-  out_v[2] = S0 -S1 +S2 -S3;
-  out_g[2][0] = D0_0 -D1_0 +D2_0 -D3_0;
-  out_g[2][1] = -D0_1 +D1_1 -D2_1 +D3_1;
-  out_v[3] = S0 +S1 +S2 +S3;
-  out_g[3][0] = D0_0 +D1_0 +D2_0 +D3_0;
-  out_g[3][1] = D0_1 +D1_1 +D2_1 +D3_1;
+  const T wv0_0 = S0 + S2, wv0_1 = S0 - S2;
+  const T wv0_2 = S1 + S3, wv0_3 = S1 - S3;
+  const T wv1_0 = wv0_0 + wv0_2, wv1_2 = wv0_0 - wv0_2;
+  const T wv1_1 = wv0_1 + wv0_3, wv1_3 = wv0_1 - wv0_3;
+  const T wg0_0_0 = D0_0 + D2_0, wg0_0_1 = D0_0 - D2_0;
+  const T wg0_0_2 = D1_0 + D3_0, wg0_0_3 = D1_0 - D3_0;
+  const T wg0_1_0 = wg0_0_0 + wg0_0_2, wg0_1_2 = wg0_0_0 - wg0_0_2;
+  const T wg0_1_1 = wg0_0_1 + wg0_0_3, wg0_1_3 = wg0_0_1 - wg0_0_3;
+  const T wg1_0_0 = D0_1 + D2_1, wg1_0_1 = D0_1 - D2_1;
+  const T wg1_0_2 = D1_1 + D3_1, wg1_0_3 = D1_1 - D3_1;
+  const T wg1_1_0 = wg1_0_0 + wg1_0_2, wg1_1_2 = wg1_0_0 - wg1_0_2;
+  const T wg1_1_1 = wg1_0_1 + wg1_0_3, wg1_1_3 = wg1_0_1 - wg1_0_3;
+  out_v[0] = wv1_3;
+  out_g[0][0] = -wg0_1_3;
+  out_g[0][1] = -wg1_1_3;
+  out_v[1] = wv1_1;
+  out_g[1][0] = -wg0_1_1;
+  out_g[1][1] = wg1_1_1;
+  out_v[2] = wv1_2;
+  out_g[2][0] = wg0_1_2;
+  out_g[2][1] = -wg1_1_2;
+  out_v[3] = wv1_0;
+  out_g[3][0] = wg0_1_0;
+  out_g[3][1] = wg1_1_0;
 }
 
 /* axis 1: out_v[i], out_g[i][k] for the 4 Gauss points i = side*2 + k */
@@ -425,18 +437,30 @@ CGKS_HD void gen_gp_2d_ax1(const T* __restrict__ a, T* __restrict__ out_v, T (* 
   D3_1 = cg_fma(T(0.28867513459481287), a[11], D3_1);
   D3_1 = cg_fma(T(0.004009376869372401), a[12], D3_1);
   D3_1 = cg_fma(T(0.03608439182435161), a[13], D3_1);
-  out_v[0] = S0 -S1 -S2 +S3;
-  out_g[0][0] = -D0_0 +D1_0 +D2_0 -D3_0;
-  out_g[0][1] = -D0_1 +D1_1 +D2_1 -D3_1;
-  out_v[1] = S0 -S1 +S2 -S3;
-  out_g[1][0] = D0_0 -D1_0 +D2_0 -D3_0;
-  out_g[1][1] = -D0_1 +D1_1 -D2_1 +D3_1;
-  out_v[2] = S0 +S1 -S2 -S3;
-  out_g[2][0] = -D0_0 -D1_0 +D2_0 +D3_0;
-  out_g[2][1] = D0_1 +D1_1 -D2_1 -D3_1;
-  out_v[3] = S0 +S1 +S2 +S3;
-  out_g[3][0] = D0_0 +D1_0 +D2_0 +D3_0;
-  out_g[3][1] = D0_1 +D1_1 +D2_1 +D3_1;
+  const T wv0_0 = S0 + S2, wv0_1 = S0 - S2;
+  const T wv0_2 = S1 + S3, wv0_3 = S1 - S3;
+  const T wv1_0 = wv0_0 + wv0_2, wv1_2 = wv0_0 - wv0_2;
+  const T wv1_1 = wv0_1 + wv0_3, wv1_3 = wv0_1 - wv0_3;
+  const T wg0_0_0 = D0_0 + D2_0, wg0_0_1 = D0_0 - D2_0;
+  const T wg0_0_2 = D1_0 + D3_0, wg0_0_3 = D1_0 - D3_0;
+  const T wg0_1_0 = wg0_0_0 + wg0_0_2, wg0_1_2 = wg0_0_0 - wg0_0_2;
+  const T wg0_1_1 = wg0_0_1 + wg0_0_3, wg0_1_3 = wg0_0_1 - wg0_0_3;
+  const T wg1_0_0 = D0_1 + D2_1, wg1_0_1 = D0_1 - D2_1;
+  const T wg1_0_2 = D1_1 + D3_1, wg1_0_3 = D1_1 - D3_1;
+  const T wg1_1_0 = wg1_0_0 + wg1_0_2, wg1_1_2 = wg1_0_0 - wg1_0_2;
+  const T wg1_1_1 = wg1_0_1 + wg1_0_3, wg1_1_3 = wg1_0_1 - wg1_0_3;
+  out_v[0] = wv1_3;
+  out_g[0][0] = -wg0_1_3;
+  out_g[0][1] = -wg1_1_3;
+  out_v[1] = wv1_2;
+  out_g[1][0] = wg0_1_2;
+  out_g[1][1] = -wg1_1_2;
+  out_v[2] = wv1_1;
+  out_g[2][0] = -wg0_1_1;
+  out_g[2][1] = wg1_1_1;
+  out_v[3] = wv1_0;
+  out_g[3][0] = wg0_1_0;
+  out_g[3][1] = wg1_1_0;
 }
 
 template <typename T, class Ld>
@@ -1437,38 +1461,86 @@ CGKS_HD void gen_gp_3d_ax0(const T* __restrict__ a, T* __restrict__ out_v, T (* 
   D7_1 = cg_fma(T(0.14433756729740643), a[33], D7_1);
   T D7_2 = T(0);
   D7_2 = cg_fma(T(0.14433756729740643), a[33], D7_2);
-  out_v[0] = S0 -S1 -S2 +S3 -S4 +S5 +S6 -S7;
-  out_g[0][0] = -D0_0 +D1_0 +D2_0 -D3_0 +D4_0 -D5_0 -D6_0 +D7_0;
-  out_g[0][1] = -D0_1 +D1_1 +D2_1 -D3_1 +D4_1 -D5_1 -D6_1 +D7_1;
-  out_g[0][2] = -D0_2 +D1_2 +D2_2 -D3_2 +D4_2 -D5_2 -D6_2 +D7_2;
-  out_v[1] = S0 -S1 +S2 -S3 -S4 +S5 -S6 +S7;
-  out_g[1][0] = -D0_0 +D1_0 -D2_0 +D3_0 +D4_0 -D5_0 +D6_0 -D7_0;
-  out_g[1][1] = D0_1 -D1_1 +D2_1 -D3_1 -D4_1 +D5_1 -D6_1 +D7_1;
-  out_g[1][2] = -D0_2 +D1_2 -D2_2 +D3_2 +D4_2 -D5_2 +D6_2 -D7_2;
-  out_v[2] = S0 +S1 -S2 -S3 -S4 -S5 +S6 +S7;
-  out_g[2][0] = -D0_0 -D1_0 +D2_0 +D3_0 +D4_0 +D5_0 -D6_0 -D7_0;
-  out_g[2][1] = -D0_1 -D1_1 +D2_1 +D3_1 +D4_1 +D5_1 -D6_1 -D7_1;
-  out_g[2][2] = D0_2 +D1_2 -D2_2 -D3_2 -D4_2 -D5_2 +D6_2 +D7_2;
-  out_v[3] = S0 +S1 +S2 +S3 -S4 -S5 -S6 -S7;
-  out_g[3][0] = -D0_0 -D1_0 -D2_0 -D3_0 +D4_0 +D5_0 +D6_0 +D7_0;
-  out_g[3][1] = D0_1 +D1_1 +D2_1 +D3_1 -D4_1 -D5_1 -D6_1 -D7_1;
-  out_g[3][2] = D0_2 +D1_2 +D2_2 +D3_2 -D4_2 -D5_2 -D6_2 -D7_2;
-  out_v[4] = S0 -S1 -S2 +S3 +S4 -S5 -S6 +S7;
-  out_g[4][0] = D0_0 -D1_0 -D2_0 +D3_0 +D4_0 -D5_0 -D6_0 +D7_0;
-  out_g[4][1] = -D0_1 +D1_1 +D2_1 -D3_1 -D4_1 +D5_1 +D6_1 -D7_1;
-  out_g[4][2] = -D0_2 +D1_2 +D2_2 -D3_2 -D4_2 +D5_2 +D6_2 -D7_2;
-  out_v[5] = S0 -S1 +S2 -S3 +S4 -S5 +S6 -S7;
-  out_g[5][0] = D0_0 -D1_0 +D2_0 -D3_0 +D4_0 -D5_0 +D6_0 -D7_0;
-  out_g[5][1] = D0_1 -D1_1 +D2_1 -D3_1 +D4_1 -D5_1 +D6_1 -D7_1;
-  out_g[5][2] = -D0_2 +D1_2 -D2_2 +D3_2 -D4_2 +D5_2 -D6_2 +D7_2;
-  out_v[6] = S0 +S1 -S2 -S3 +S4 +S5 -S6 -S7;
-  out_g[6][0] = D0_0 +D1_0 -D2_0 -D3_0 +D4_0 +D5_0 -D6_0 -D7_0;
-  out_g[6][1] = -D0_1 -D1_1 +D2_1 +D3_1 -D4_1 -D5_1 +D6_1 +D7_1;
-  out_g[6][2] = D0_2 +D1_2 -D2_2 -D3_2 +D4_2 +D5_2 -D6_2 -D7_2;
-  out_v[7] = S0 +S1 +S2 +S3 +S4 +S5 +S6 +S7;
-  out_g[7][0] = D0_0 +D1_0 +D2_0 +D3_0 +D4_0 +D5_0 +D6_0 +D7_0;
-  out_g[7][1] = D0_1 +D1_1 +D2_1 +D3_1 +D4_1 +D5_1 +D6_1 +D7_1;
-  out_g[7][2] = D0_2 +D1_2 +D2_2 +D3_2 +D4_2 +D5_2 +D6_2 +D7_2;
+  const T wv0_0 = S0 + S4, wv0_1 = S0 - S4;
+  const T wv0_2 = S2 + S6, wv0_3 = S2 - S6;
+  const T wv0_4 = S1 + S5, wv0_5 = S1 - S5;
+  const T wv0_6 = S3 + S7, wv0_7 = S3 - S7;
+  const T wv1_0 = wv0_0 + wv0_2, wv1_2 = wv0_0 - wv0_2;
+  const T wv1_1 = wv0_1 + wv0_3, wv1_3 = wv0_1 - wv0_3;
+  const T wv1_4 = wv0_4 + wv0_6, wv1_6 = wv0_4 - wv0_6;
+  const T wv1_5 = wv0_5 + wv0_7, wv1_7 = wv0_5 - wv0_7;
+  const T wv2_0 = wv1_0 + wv1_4, wv2_4 = wv1_0 - wv1_4;
+  const T wv2_1 = wv1_1 + wv1_5, wv2_5 = wv1_1 - wv1_5;
+  const T wv2_2 = wv1_2 + wv1_6, wv2_6 = wv1_2 - wv1_6;
+  const T wv2_3 = wv1_3 + wv1_7, wv2_7 = wv1_3 - wv1_7;
+  const T wg0_0_0 = D0_0 + D4_0, wg0_0_1 = D0_0 - D4_0;
+  const T wg0_0_2 = D2_0 + D6_0, wg0_0_3 = D2_0 - D6_0;
+  const T wg0_0_4 = D1_0 + D5_0, wg0_0_5 = D1_0 - D5_0;
+  const T wg0_0_6 = D3_0 + D7_0, wg0_0_7 = D3_0 - D7_0;
+  const T wg0_1_0 = wg0_0_0 + wg0_0_2, wg0_1_2 = wg0_0_0 - wg0_0_2;
+  const T wg0_1_1 = wg0_0_1 + wg0_0_3, wg0_1_3 = wg0_0_1 - wg0_0_3;
+  const T wg0_1_4 = wg0_0_4 + wg0_0_6, wg0_1_6 = wg0_0_4 - wg0_0_6;
+  const T wg0_1_5 = wg0_0_5 + wg0_0_7, wg0_1_7 = wg0_0_5 - wg0_0_7;
+  const T wg0_2_0 = wg0_1_0 + wg0_1_4, wg0_2_4 = wg0_1_0 - wg0_1_4;
+  const T wg0_2_1 = wg0_1_1 + wg0_1_5, wg0_2_5 = wg0_1_1 - wg0_1_5;
+  const T wg0_2_2 = wg0_1_2 + wg0_1_6, wg0_2_6 = wg0_1_2 - wg0_1_6;
+  const T wg0_2_3 = wg0_1_3 + wg0_1_7, wg0_2_7 = wg0_1_3 - wg0_1_7;
+  const T wg1_0_0 = D0_1 + D4_1, wg1_0_1 = D0_1 - D4_1;
+  const T wg1_0_2 = D2_1 + D6_1, wg1_0_3 = D2_1 - D6_1;
+  const T wg1_0_4 = D1_1 + D5_1, wg1_0_5 = D1_1 - D5_1;
+  const T wg1_0_6 = D3_1 + D7_1, wg1_0_7 = D3_1 - D7_1;
+  const T wg1_1_0 = wg1_0_0 + wg1_0_2, wg1_1_2 = wg1_0_0 - wg1_0_2;
+  const T wg1_1_1 = wg1_0_1 + wg1_0_3, wg1_1_3 = wg1_0_1 - wg1_0_3;
+  const T wg1_1_4 = wg1_0_4 + wg1_0_6, wg1_1_6 = wg1_0_4 - wg1_0_6;
+  const T wg1_1_5 = wg1_0_5 + wg1_0_7, wg1_1_7 = wg1_0_5 - wg1_0_7;
+  const T wg1_2_0 = wg1_1_0 + wg1_1_4, wg1_2_4 = wg1_1_0 - wg1_1_4;
+  const T wg1_2_1 = wg1_1_1 + wg1_1_5, wg1_2_5 = wg1_1_1 - wg1_1_5;
+  const T wg1_2_2 = wg1_1_2 + wg1_1_6, wg1_2_6 = wg1_1_2 - wg1_1_6;
+  const T wg1_2_3 = wg1_1_3 + wg1_1_7, wg1_2_7 = wg1_1_3 - wg1_1_7;
+  const T wg2_0_0 = D0_2 + D4_2, wg2_0_1 = D0_2 - D4_2;
+  const T wg2_0_2 = D2_2 + D6_2, wg2_0_3 = D2_2 - D6_2;
+  const T wg2_0_4 = D1_2 + D5_2, wg2_0_5 = D1_2 - D5_2;
+  const T wg2_0_6 = D3_2 + D7_2, wg2_0_7 = D3_2 - D7_2;
+  const T wg2_1_0 = wg2_0_0 + wg2_0_2, wg2_1_2 = wg2_0_0 - wg2_0_2;
+  const T wg2_1_1 = wg2_0_1 + wg2_0_3, wg2_1_3 = wg2_0_1 - wg2_0_3;
+  const T wg2_1_4 = wg2_0_4 + wg2_0_6, wg2_1_6 = wg2_0_4 - wg2_0_6;
+  const T wg2_1_5 = wg2_0_5 + wg2_0_7, wg2_1_7 = wg2_0_5 - wg2_0_7;
+  const T wg2_2_0 = wg2_1_0 + wg2_1_4, wg2_2_4 = wg2_1_0 - wg2_1_4;
+  const T wg2_2_1 = wg2_1_1 + wg2_1_5, wg2_2_5 = wg2_1_1 - wg2_1_5;
+  const T wg2_2_2 = wg2_1_2 + wg2_1_6, wg2_2_6 = wg2_1_2 - wg2_1_6;
+  const T wg2_2_3 = wg2_1_3 + wg2_1_7, wg2_2_7 = wg2_1_3 - wg2_1_7;
+  out_v[0] = wv2_7;
+  out_g[0][0] = -wg0_2_7;
+  out_g[0][1] = -wg1_2_7;
+  out_g[0][2] = -wg2_2_7;
+  out_v[1] = wv2_5;
+  out_g[1][0] = -wg0_2_5;
+  out_g[1][1] = wg1_2_5;
+  out_g[1][2] = -wg2_2_5;
+  out_v[2] = wv2_3;
+  out_g[2][0] = -wg0_2_3;
+  out_g[2][1] = -wg1_2_3;
+  out_g[2][2] = wg2_2_3;
+  out_v[3] = wv2_1;
+  out_g[3][0] = -wg0_2_1;
+  out_g[3][1] = wg1_2_1;
+  out_g[3][2] = wg2_2_1;
+  out_v[4] = wv2_6;
+  out_g[4][0] = wg0_2_6;
+  out_g[4][1] = -wg1_2_6;
+  out_g[4][2] = -wg2_2_6;
+  out_v[5] = wv2_4;
+  out_g[5][0] = wg0_2_4;
+  out_g[5][1] = wg1_2_4;
+  out_g[5][2] = -wg2_2_4;
+  out_v[6] = wv2_2;
+  out_g[6][0] = wg0_2_2;
+  out_g[6][1] = -wg1_2_2;
+  out_g[6][2] = wg2_2_2;
+  out_v[7] = wv2_0;
+  out_g[7][0] = wg0_2_0;
+  out_g[7][1] = wg1_2_0;
+  out_g[7][2] = wg2_2_0;
 }
 
 /* axis 1: out_v[i], out_g[i][k] for the 8 Gauss points i = side*4 + k */
@@ -1600,38 +1672,86 @@ CGKS_HD void gen_gp_3d_ax1(const T* __restrict__ a, T* __restrict__ out_v, T (* 
   D7_1 = cg_fma(T(0.08333333333333333), a[33], D7_1);
   T D7_2 = T(0);
   D7_2 = cg_fma(T(0.14433756729740643), a[33], D7_2);
-  out_v[0] = S0 -S1 -S2 +S3 -S4 +S5 +S6 -S7;
-  out_g[0][0] = -D0_0 +D1_0 +D2_0 -D3_0 +D4_0 -D5_0 -D6_0 +D7_0;
-  out_g[0][1] = -D0_1 +D1_1 +D2_1 -D3_1 +D4_1 -D5_1 -D6_1 +D7_1;
-  out_g[0][2] = -D0_2 +D1_2 +D2_2 -D3_2 +D4_2 -D5_2 -D6_2 +D7_2;
-  out_v[1] = S0 -S1 -S2 +S3 +S4 -S5 -S6 +S7;
-  out_g[1][0] = D0_0 -D1_0 -D2_0 +D3_0 +D4_0 -D5_0 -D6_0 +D7_0;
-  out_g[1][1] = -D0_1 +D1_1 +D2_1 -D3_1 -D4_1 +D5_1 +D6_1 -D7_1;
-  out_g[1][2] = -D0_2 +D1_2 +D2_2 -D3_2 -D4_2 +D5_2 +D6_2 -D7_2;
-  out_v[2] = S0 +S1 -S2 -S3 -S4 -S5 +S6 +S7;
-  out_g[2][0] = -D0_0 -D1_0 +D2_0 +D3_0 +D4_0 +D5_0 -D6_0 -D7_0;
-  out_g[2][1] = -D0_1 -D1_1 +D2_1 +D3_1 +D4_1 +D5_1 -D6_1 -D7_1;
-  out_g[2][2] = D0_2 +D1_2 -D2_2 -D3_2 -D4_2 -D5_2 +D6_2 +D7_2;
-  out_v[3] = S0 +S1 -S2 -S3 +S4 +S5 -S6 -S7;
-  out_g[3][0] = D0_0 +D1_0 -D2_0 -D3_0 +D4_0 +D5_0 -D6_0 -D7_0;
-  out_g[3][1] = -D0_1 -D1_1 +D2_1 +D3_1 -D4_1 -D5_1 +D6_1 +D7_1;
-  out_g[3][2] = D0_2 +D1_2 -D2_2 -D3_2 +D4_2 +D5_2 -D6_2 -D7_2;
-  out_v[4] = S0 -S1 +S2 -S3 -S4 +S5 -S6 +S7;
-  out_g[4][0] = -D0_0 +D1_0 -D2_0 +D3_0 +D4_0 -D5_0 +D6_0 -D7_0;
-  out_g[4][1] = D0_1 -D1_1 +D2_1 -D3_1 -D4_1 +D5_1 -D6_1 +D7_1;
-  out_g[4][2] = -D0_2 +D1_2 -D2_2 +D3_2 +D4_2 -D5_2 +D6_2 -D7_2;
-  out_v[5] = S0 -S1 +S2 -S3 +S4 -S5 +S6 -S7;
-  out_g[5][0] = D0_0 -D1_0 +D2_0 -D3_0 +D4_0 -D5_0 +D6_0 -D7_0;
-  out_g[5][1] = D0_1 -D1_1 +D2_1 -D3_1 +D4_1 -D5_1 +D6_1 -D7_1;
-  out_g[5][2] = -D0_2 +D1_2 -D2_2 +D3_2 -D4_2 +D5_2 -D6_2 +D7_2;
-  out_v[6] = S0 +S1 +S2 +S3 -S4 -S5 -S6 -S7;
-  out_g[6][0] = -D0_0 -D1_0 -D2_0 -D3_0 +D4_0 +D5_0 +D6_0 +D7_0;
-  out_g[6][1] = D0_1 +D1_1 +D2_1 +D3_1 -D4_1 -D5_1 -D6_1 -D7_1;
-  out_g[6][2] = D0_2 +D1_2 +D2_2 +D3_2 -D4_2 -D5_2 -D6_2 -D7_2;
-  out_v[7] = S0 +S1 +S2 +S3 +S4 +S5 +S6 +S7;
-  out_g[7][0] = D0_0 +D1_0 +D2_0 +D3_0 +D4_0 +D5_0 +D6_0 +D7_0;
-  out_g[7][1] = D0_1 +D1_1 +D2_1 +D3_1 +D4_1 +D5_1 +D6_1 +D7_1;
-  out_g[7][2] = D0_2 +D1_2 +D2_2 +D3_2 +D4_2 +D5_2 +D6_2 +D7_2;
+  const T wv0_0 = S0 + S4, wv0_1 = S0 - S4;
+  const T wv0_2 = S2 + S6, wv0_3 = S2 - S6;
+  const T wv0_4 = S1 + S5, wv0_5 = S1 - S5;
+  const T wv0_6 = S3 + S7, wv0_7 = S3 - S7;
+  const T wv1_0 = wv0_0 + wv0_2, wv1_2 = wv0_0 - wv0_2;
+  const T wv1_1 = wv0_1 + wv0_3, wv1_3 = wv0_1 - wv0_3;
+  const T wv1_4 = wv0_4 + wv0_6, wv1_6 = wv0_4 - wv0_6;
+  const T wv1_5 = wv0_5 + wv0_7, wv1_7 = wv0_5 - wv0_7;
+  const T wv2_0 = wv1_0 + wv1_4, wv2_4 = wv1_0 - wv1_4;
+  const T wv2_1 = wv1_1 + wv1_5, wv2_5 = wv1_1 - wv1_5;
+  const T wv2_2 = wv1_2 + wv1_6, wv2_6 = wv1_2 - wv1_6;
+  const T wv2_3 = wv1_3 + wv1_7, wv2_7 = wv1_3 - wv1_7;
+  const T wg0_0_0 = D0_0 + D4_0, wg0_0_1 = D0_0 - D4_0;
+  const T wg0_0_2 = D2_0 + D6_0, wg0_0_3 = D2_0 - D6_0;
+  const T wg0_0_4 = D1_0 + D5_0, wg0_0_5 = D1_0 - D5_0;
+  const T wg0_0_6 = D3_0 + D7_0, wg0_0_7 = D3_0 - D7_0;
+  const T wg0_1_0 = wg0_0_0 + wg0_0_2, wg0_1_2 = wg0_0_0 - wg0_0_2;
+  const T wg0_1_1 = wg0_0_1 + wg0_0_3, wg0_1_3 = wg0_0_1 - wg0_0_3;
+  const T wg0_1_4 = wg0_0_4 + wg0_0_6, wg0_1_6 = wg0_0_4 - wg0_0_6;
+  const T wg0_1_5 = wg0_0_5 + wg0_0_7, wg0_1_7 = wg0_0_5 - wg0_0_7;
+  const T wg0_2_0 = wg0_1_0 + wg0_1_4, wg0_2_4 = wg0_1_0 - wg0_1_4;
+  const T wg0_2_1 = wg0_1_1 + wg0_1_5, wg0_2_5 = wg0_1_1 - wg0_1_5;
+  const T wg0_2_2 = wg0_1_2 + wg0_1_6, wg0_2_6 = wg0_1_2 - wg0_1_6;
+  const T wg0_2_3 = wg0_1_3 + wg0_1_7, wg0_2_7 = wg0_1_3 - wg0_1_7;
+  const T wg1_0_0 = D0_1 + D4_1, wg1_0_1 = D0_1 - D4_1;
+  const T wg1_0_2 = D2_1 + D6_1, wg1_0_3 = D2_1 - D6_1;
+  const T wg1_0_4 = D1_1 + D5_1, wg1_0_5 = D1_1 - D5_1;
+  const T wg1_0_6 = D3_1 + D7_1, wg1_0_7 = D3_1 - D7_1;
+  const T wg1_1_0 = wg1_0_0 + wg1_0_2, wg1_1_2 = wg1_0_0 - wg1_0_2;
+  const T wg1_1_1 = wg1_0_1 + wg1_0_3, wg1_1_3 = wg1_0_1 - wg1_0_3;
+  const T wg1_1_4 = wg1_0_4 + wg1_0_6, wg1_1_6 = wg1_0_4 - wg1_0_6;
+  const T wg1_1_5 = wg1_0_5 + wg1_0_7, wg1_1_7 = wg1_0_5 - wg1_0_7;
+  const T wg1_2_0 = wg1_1_0 + wg1_1_4, wg1_2_4 = wg1_1_0 - wg1_1_4;
+  const T wg1_2_1 = wg1_1_1 + wg1_1_5, wg1_2_5 = wg1_1_1 - wg1_1_5;
+  const T wg1_2_2 = wg1_1_2 + wg1_1_6, wg1_2_6 = wg1_1_2 - wg1_1_6;
+  const T wg1_2_3 = wg1_1_3 + wg1_1_7, wg1_2_7 = wg1_1_3 - wg1_1_7;
+  const T wg2_0_0 = D0_2 + D4_2, wg2_0_1 = D0_2 - D4_2;
+  const T wg2_0_2 = D2_2 + D6_2, wg2_0_3 = D2_2 - D6_2;
+  const T wg2_0_4 = D1_2 + D5_2, wg2_0_5 = D1_2 - D5_2;
+  const T wg2_0_6 = D3_2 + D7_2, wg2_0_7 = D3_2 - D7_2;
+  const T wg2_1_0 = wg2_0_0 + wg2_0_2, wg2_1_2 = wg2_0_0 - wg2_0_2;
+  const T wg2_1_1 = wg2_0_1 + wg2_0_3, wg2_1_3 = wg2_0_1 - wg2_0_3;
+  const T wg2_1_4 = wg2_0_4 + wg2_0_6, wg2_1_6 = wg2_0_4 - wg2_0_6;
+  const T wg2_1_5 = wg2_0_5 + wg2_0_7, wg2_1_7 = wg2_0_5 - wg2_0_7;
+  const T wg2_2_0 = wg2_1_0 + wg2_1_4, wg2_2_4 = wg2_1_0 - wg2_1_4;
+  const T wg2_2_1 = wg2_1_1 + wg2_1_5, wg2_2_5 = wg2_1_1 - wg2_1_5;
+  const T wg2_2_2 = wg2_1_2 + wg2_1_6, wg2_2_6 = wg2_1_2 - wg2_1_6;
+  const T wg2_2_3 = wg2_1_3 + wg2_1_7, wg2_2_7 = wg2_1_3 - wg2_1_7;
+  out_v[0] = wv2_7;
+  out_g[0][0] = -wg0_2_7;
+  out_g[0][1] = -wg1_2_7;
+  out_g[0][2] = -wg2_2_7;
+  out_v[1] = wv2_6;
+  out_g[1][0] = wg0_2_6;
+  out_g[1][1] = -wg1_2_6;
+  out_g[1][2] = -wg2_2_6;
+  out_v[2] = wv2_3;
+  out_g[2][0] = -wg0_2_3;
+  out_g[2][1] = -wg1_2_3;
+  out_g[2][2] = wg2_2_3;
+  out_v[3] = wv2_2;
+  out_g[3][0] = wg0_2_2;
+  out_g[3][1] = -wg1_2_2;
+  out_g[3][2] = wg2_2_2;
+  out_v[4] = wv2_5;
+  out_g[4][0] = -wg0_2_5;
+  out_g[4][1] = wg1_2_5;
+  out_g[4][2] = -wg2_2_5;
+  out_v[5] = wv2_4;
+  out_g[5][0] = wg0_2_4;
+  out_g[5][1] = wg1_2_4;
+  out_g[5][2] = -wg2_2_4;
+  out_v[6] = wv2_1;
+  out_g[6][0] = -wg0_2_1;
+  out_g[6][1] = wg1_2_1;
+  out_g[6][2] = wg2_2_1;
+  out_v[7] = wv2_0;
+  out_g[7][0] = wg0_2_0;
+  out_g[7][1] = wg1_2_0;
+  out_g[7][2] = wg2_2_0;
 }
 
 /* axis 2: out_v[i], out_g[i][k] for the 8 Gauss points i = side*4 + k */
@@ -1763,37 +1883,85 @@ CGKS_HD void gen_gp_3d_ax2(const T* __restrict__ a, T* __restrict__ out_v, T (* 
   D7_1 = cg_fma(T(0.14433756729740643), a[33], D7_1);
   T D7_2 = T(0);
   D7_2 = cg_fma(T(0.08333333333333333), a[33], D7_2);
-  out_v[0] = S0 -S1 -S2 +S3 -S4 +S5 +S6 -S7;
-  out_g[0][0] = -D0_0 +D1_0 +D2_0 -D3_0 +D4_0 -D5_0 -D6_0 +D7_0;
-  out_g[0][1] = -D0_1 +D1_1 +D2_1 -D3_1 +D4_1 -D5_1 -D6_1 +D7_1;
-  out_g[0][2] = -D0_2 +D1_2 +D2_2 -D3_2 +D4_2 -D5_2 -D6_2 +D7_2;
-  out_v[1] = S0 -S1 -S2 +S3 +S4 -S5 -S6 +S7;
-  out_g[1][0] = D0_0 -D1_0 -D2_0 +D3_0 +D4_0 -D5_0 -D6_0 +D7_0;
-  out_g[1][1] = -D0_1 +D1_1 +D2_1 -D3_1 -D4_1 +D5_1 +D6_1 -D7_1;
-  out_g[1][2] = -D0_2 +D1_2 +D2_2 -D3_2 -D4_2 +D5_2 +D6_2 -D7_2;
-  out_v[2] = S0 -S1 +S2 -S3 -S4 +S5 -S6 +S7;
-  out_g[2][0] = -D0_0 +D1_0 -D2_0 +D3_0 +D4_0 -D5_0 +D6_0 -D7_0;
-  out_g[2][1] = D0_1 -D1_1 +D2_1 -D3_1 -D4_1 +D5_1 -D6_1 +D7_1;
-  out_g[2][2] = -D0_2 +D1_2 -D2_2 +D3_2 +D4_2 -D5_2 +D6_2 -D7_2;
-  out_v[3] = S0 -S1 +S2 -S3 +S4 -S5 +S6 -S7;
-  out_g[3][0] = D0_0 -D1_0 +D2_0 -D3_0 +D4_0 -D5_0 +D6_0 -D7_0;
-  out_g[3][1] = D0_1 -D1_1 +D2_1 -D3_1 +D4_1 -D5_1 +D6_1 -D7_1;
-  out_g[3][2] = -D0_2 +D1_2 -D2_2 +D3_2 -D4_2 +D5_2 -D6_2 +D7_2;
-  out_v[4] = S0 +S1 -S2 -S3 -S4 -S5 +S6 +S7;
-  out_g[4][0] = -D0_0 -D1_0 +D2_0 +D3_0 +D4_0 +D5_0 -D6_0 -D7_0;
-  out_g[4][1] = -D0_1 -D1_1 +D2_1 +D3_1 +D4_1 +D5_1 -D6_1 -D7_1;
-  out_g[4][2] = D0_2 +D1_2 -D2_2 -D3_2 -D4_2 -D5_2 +D6_2 +D7_2;
-  out_v[5] = S0 +S1 -S2 -S3 +S4 +S5 -S6 -S7;
-  out_g[5][0] = D0_0 +D1_0 -D2_0 -D3_0 +D4_0 +D5_0 -D6_0 -D7_0;
-  out_g[5][1] = -D0_1 -D1_1 +D2_1 +D3_1 -D4_1 -D5_1 +D6_1 +D7_1;
-  out_g[5][2] = D0_2 +D1_2 -D2_2 -D3_2 +D4_2 +D5_2 -D6_2 -D7_2;
-  out_v[6] = S0 +S1 +S2 +S3 -S4 -S5 -S6 -S7;
-  out_g[6][0] = -D0_0 -D1_0 -D2_0 -D3_0 +D4_0 +D5_0 +D6_0 +D7_0;
-  out_g[6][1] = D0_1 +D1_1 +D2_1 +D3_1 -D4_1 -D5_1 -D6_1 -D7_1;
-  out_g[6][2] = D0_2 +D1_2 +D2_2 +D3_2 -D4_2 -D5_2 -D6_2 -D7_2;
-  out_v[7] = S0 +S1 +S2 +S3 +S4 +S5 +S6 +S7;
-  out_g[7][0] = D0_0 +D1_0 +D2_0 +D3_0 +D4_0 +D5_0 +D6_0 +D7_0;
-  out_g[7][1] = D0_1 +D1_1 +D2_1 +D3_1 +D4_1 +D5_1 +D6_1 +D7_1;
-  out_g[7][2] = D0_2 +D1_2 +D2_2 +D3_2 +D4_2 +D5_2 +D6_2 +D7_2;
+  const T wv0_0 = S0 + S4, wv0_1 = S0 - S4;
+  const T wv0_2 = S2 + S6, wv0_3 = S2 - S6;
+  const T wv0_4 = S1 + S5, wv0_5 = S1 - S5;
+  const T wv0_6 = S3 + S7, wv0_7 = S3 - S7;
+  const T wv1_0 = wv0_0 + wv0_2, wv1_2 = wv0_0 - wv0_2;
+  const T wv1_1 = wv0_1 + wv0_3, wv1_3 = wv0_1 - wv0_3;
+  const T wv1_4 = wv0_4 + wv0_6, wv1_6 = wv0_4 - wv0_6;
+  const T wv1_5 = wv0_5 + wv0_7, wv1_7 = wv0_5 - wv0_7;
+  const T wv2_0 = wv1_0 + wv1_4, wv2_4 = wv1_0 - wv1_4;
+  const T wv2_1 = wv1_1 + wv1_5, wv2_5 = wv1_1 - wv1_5;
+  const T wv2_2 = wv1_2 + wv1_6, wv2_6 = wv1_2 - wv1_6;
+  const T wv2_3 = wv1_3 + wv1_7, wv2_7 = wv1_3 - wv1_7;
+  const T wg0_0_0 = D0_0 + D4_0, wg0_0_1 = D0_0 - D4_0;
+  const T wg0_0_2 = D2_0 + D6_0, wg0_0_3 = D2_0 - D6_0;
+  const T wg0_0_4 = D1_0 + D5_0, wg0_0_5 = D1_0 - D5_0;
+  const T wg0_0_6 = D3_0 + D7_0, wg0_0_7 = D3_0 - D7_0;
+  const T wg0_1_0 = wg0_0_0 + wg0_0_2, wg0_1_2 = wg0_0_0 - wg0_0_2;
+  const T wg0_1_1 = wg0_0_1 + wg0_0_3, wg0_1_3 = wg0_0_1 - wg0_0_3;
+  const T wg0_1_4 = wg0_0_4 + wg0_0_6, wg0_1_6 = wg0_0_4 - wg0_0_6;
+  const T wg0_1_5 = wg0_0_5 + wg0_0_7, wg0_1_7 = wg0_0_5 - wg0_0_7;
+  const T wg0_2_0 = wg0_1_0 + wg0_1_4, wg0_2_4 = wg0_1_0 - wg0_1_4;
+  const T wg0_2_1 = wg0_1_1 + wg0_1_5, wg0_2_5 = wg0_1_1 - wg0_1_5;
+  const T wg0_2_2 = wg0_1_2 + wg0_1_6, wg0_2_6 = wg0_1_2 - wg0_1_6;
+  const T wg0_2_3 = wg0_1_3 + wg0_1_7, wg0_2_7 = wg0_1_3 - wg0_1_7;
+  const T wg1_0_0 = D0_1 + D4_1, wg1_0_1 = D0_1 - D4_1;
+  const T wg1_0_2 = D2_1 + D6_1, wg1_0_3 = D2_1 - D6_1;
+  const T wg1_0_4 = D1_1 + D5_1, wg1_0_5 = D1_1 - D5_1;
+  const T wg1_0_6 = D3_1 + D7_1, wg1_0_7 = D3_1 - D7_1;
+  const T wg1_1_0 = wg1_0_0 + wg1_0_2, wg1_1_2 = wg1_0_0 - wg1_0_2;
+  const T wg1_1_1 = wg1_0_1 + wg1_0_3, wg1_1_3 = wg1_0_1 - wg1_0_3;
+  const T wg1_1_4 = wg1_0_4 + wg1_0_6, wg1_1_6 = wg1_0_4 - wg1_0_6;
+  const T wg1_1_5 = wg1_0_5 + wg1_0_7, wg1_1_7 = wg1_0_5 - wg1_0_7;
+  const T wg1_2_0 = wg1_1_0 + wg1_1_4, wg1_2_4 = wg1_1_0 - wg1_1_4;
+  const T wg1_2_1 = wg1_1_1 + wg1_1_5, wg1_2_5 = wg1_1_1 - wg1_1_5;
+  const T wg1_2_2 = wg1_1_2 + wg1_1_6, wg1_2_6 = wg1_1_2 - wg1_1_6;
+  const T wg1_2_3 = wg1_1_3 + wg1_1_7, wg1_2_7 = wg1_1_3 - wg1_1_7;
+  const T wg2_0_0 = D0_2 + D4_2, wg2_0_1 = D0_2 - D4_2;
+  const T wg2_0_2 = D2_2 + D6_2, wg2_0_3 = D2_2 - D6_2;
+  const T wg2_0_4 = D1_2 + D5_2, wg2_0_5 = D1_2 - D5_2;
+  const T wg2_0_6 = D3_2 + D7_2, wg2_0_7 = D3_2 - D7_2;
+  const T wg2_1_0 = wg2_0_0 + wg2_0_2, wg2_1_2 = wg2_0_0 - wg2_0_2;
+  const T wg2_1_1 = wg2_0_1 + wg2_0_3, wg2_1_3 = wg2_0_1 - wg2_0_3;
+  const T wg2_1_4 = wg2_0_4 + wg2_0_6, wg2_1_6 = wg2_0_4 - wg2_0_6;
+  const T wg2_1_5 = wg2_0_5 + wg2_0_7, wg2_1_7 = wg2_0_5 - wg2_0_7;
+  const T wg2_2_0 = wg2_1_0 + wg2_1_4, wg2_2_4 = wg2_1_0 - wg2_1_4;
+  const T wg2_2_1 = wg2_1_1 + wg2_1_5, wg2_2_5 = wg2_1_1 - wg2_1_5;
+  const T wg2_2_2 = wg2_1_2 + wg2_1_6, wg2_2_6 = wg2_1_2 - wg2_1_6;
+  const T wg2_2_3 = wg2_1_3 + wg2_1_7, wg2_2_7 = wg2_1_3 - wg2_1_7;
+  out_v[0] = wv2_7;
+  out_g[0][0] = -wg0_2_7;
+  out_g[0][1] = -wg1_2_7;
+  out_g[0][2] = -wg2_2_7;
+  out_v[1] = wv2_6;
+  out_g[1][0] = wg0_2_6;
+  out_g[1][1] = -wg1_2_6;
+  out_g[1][2] = -wg2_2_6;
+  out_v[2] = wv2_5;
+  out_g[2][0] = -wg0_2_5;
+  out_g[2][1] = wg1_2_5;
+  out_g[2][2] = -wg2_2_5;
+  out_v[3] = wv2_4;
+  out_g[3][0] = wg0_2_4;
+  out_g[3][1] = wg1_2_4;
+  out_g[3][2] = -wg2_2_4;
+  out_v[4] = wv2_3;
+  out_g[4][0] = -wg0_2_3;
+  out_g[4][1] = -wg1_2_3;
+  out_g[4][2] = wg2_2_3;
+  out_v[5] = wv2_2;
+  out_g[5][0] = wg0_2_2;
+  out_g[5][1] = -wg1_2_2;
+  out_g[5][2] = wg2_2_2;
+  out_v[6] = wv2_1;
+  out_g[6][0] = -wg0_2_1;
+  out_g[6][1] = wg1_2_1;
+  out_g[6][2] = wg2_2_1;
+  out_v[7] = wv2_0;
+  out_g[7][0] = wg0_2_0;
+  out_g[7][1] = wg1_2_0;
+  out_g[7][2] = wg2_2_0;
 }
 

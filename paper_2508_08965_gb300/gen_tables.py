@@ -684,7 +684,34 @@ def emit_recon_code(path):
                             ee = e[i2] - (1 if i2 == k else 0)
                             v = v * ipow(x0[i2], ee) * Fr(1, fact(ee))
                         fn.append("  D%d_%d = cg_fma(%s, a[%d], D%d_%d);" % (ci, k, _lit(v.to_float()), b, ci, k))
-            # each Gauss point is R_S x0 for the set S of negated axes
+            # Each Gauss point is R_S x0 for the set S of negated axes, and
+            #   value(S)         = sum_c chi_c(S) S_c,
+            #   d/dx_kk value(S) = sum_c chi_{c xor e_kk}(S) D_c,kk
+            #                    = (-1)^[kk in S] sum_c chi_c(S) D_c,kk,
+            # chi_c(S) = (-1)^(c . S): a Walsh-Hadamard transform over the class
+            # bits, evaluated by butterflies (dim 2^(dim-1) of them) instead of
+            # one 2^dim-term sum per point.
+            def wht(prefix, names):
+                """emit butterflies over the class bits; returns the output
+                variable of each mask of negated axes"""
+                cur = {}
+                for ci, c in enumerate(C):
+                    m = sum(bit << a for a, bit in enumerate(c))
+                    cur[m] = names[ci]
+                for a in range(dim):
+                    nxt = {}
+                    for m in range(1 << dim):
+                        if m & (1 << a):
+                            continue
+                        m2 = m | (1 << a)
+                        n0, n1 = "%s%d_%d" % (prefix, a, m), "%s%d_%d" % (prefix, a, m2)
+                        fn.append("  const T %s = %s + %s, %s = %s - %s;" % (n0, cur[m], cur[m2], n1, cur[m],
+                                                                          cur[m2]))
+                        nxt[m], nxt[m2] = n0, n1
+                    cur = nxt
+                return cur
+            yv = wht("wv", ["S%d" % ci for ci in range(len(C))])
+            yg = [wht("wg%d_" % kk, ["D%d_%d" % (ci, kk) for ci in range(len(C))]) for kk in range(dim)]
             for side in (0, 1):
                 for k in range(g):
                     S = []
@@ -695,16 +722,10 @@ def emit_recon_code(path):
                     if dim == 3 and not (k & 2):
                         S.append(ta[1])
                     i = side * g + k
-                    ve = " ".join("%sS%d" % ("+" if _chi(c, S) > 0 else "-", ci) for ci, c in enumerate(C)).lstrip("+")
-                    fn.append("  out_v[%d] = %s;" % (i, ve))
+                    m = sum(1 << a for a in S)
+                    fn.append("  out_v[%d] = %s;" % (i, yv[m]))
                     for kk in range(dim):
-                        # derivative along kk at R_S x0: sum_c chi_{c xor e_kk}(S) D_c,kk
-                        te = []
-                        for ci, c in enumerate(C):
-                            c2 = list(c)
-                            c2[kk] ^= 1
-                            te.append("%sD%d_%d" % ("+" if _chi(tuple(c2), S) > 0 else "-", ci, kk))
-                        fn.append("  out_g[%d][%d] = %s;" % (i, kk, " ".join(te).lstrip("+")))
+                        fn.append("  out_g[%d][%d] = %s%s;" % (i, kk, "-" if kk in S else "", yg[kk][m]))
             fn.append("}")
             fn.append("")
         out += fn
