@@ -317,6 +317,13 @@ CGKS_HD double cg_expm1(double x) { return expm1(x); }
 CGKS_HD float cg_expm1(float x) { return expm1f(x); }
 CGKS_HD double cg_sqrt(double x) { return sqrt(x); }
 CGKS_HD float cg_sqrt(float x) { return sqrtf(x); }
+#if defined(__CUDA_ARCH__)
+CGKS_HD double cg_rsqrt(double x) { return rsqrt(x); }
+CGKS_HD float cg_rsqrt(float x) { return rsqrtf(x); }
+#else
+CGKS_HD double cg_rsqrt(double x) { return 1.0 / sqrt(x); }
+CGKS_HD float cg_rsqrt(float x) { return 1.0f / sqrtf(x); }
+#endif
 CGKS_HD double cg_fabs(double x) { return fabs(x); }
 CGKS_HD float cg_fabs(float x) { return fabsf(x); }
 CGKS_HD double cg_fma(double a, double b, double c) { return fma(a, b, c); }
@@ -660,8 +667,10 @@ CGKS_HD bool mx_init(const T* W, T gam, T K, int region, MxS<T, DIM>& m) {
     m.u0 = T(1);
     m.u1 = m.U[0];
   } else {
-    const T sl = cg_sqrt(m.lam);
-    const T e = T(0.5) * cg_exp(-m.lam * m.U[0] * m.U[0]) / cg_sqrt(T(3.14159265358979323846) * m.lam);
+    /* sqrt(lam) and 1/sqrt(pi lam) from one reciprocal square root */
+    const T isl = cg_rsqrt(m.lam);
+    const T sl = m.lam * isl;
+    const T e = T(0.28209479177387814347) * cg_exp(-m.lam * m.U[0] * m.U[0]) * isl; /* 1/(2 sqrt(pi)) */
     if (region == REG_POS) {
       m.u0 = T(0.5) * cg_erfc(-sl * m.U[0]);
       m.u1 = m.U[0] * m.u0 + e;
