@@ -114,7 +114,11 @@ __global__ void __launch_bounds__(128, min_blocks<T, DIM>())
     const double* avg = A.avg_in + NV * o;
     const float* avh = A.avh_in ? A.avh_in + NV * o : nullptr;
     const T* der = A.der_in + (long)(batch_nf<DIM>() - 1) * NV * o;
-    const bool wall = wall_warp<WALL, DIM>(g, active, i, j, k);
+    /* every cell of a batch with walls takes the boundary path: which cells
+       share a warp depends on the tile shape the tuner picks, and the two
+       compiled paths may round differently, so a per-warp choice would make
+       the results depend on the tiles */
+    const bool wall = WALL;
     bool skip = false;
     if (sel.on && !ph.linear) skip = selector_skip<T, DIM, WALL>(sel, avg, avh, der, g, c, i, j, k, active, wall);
     if (active) {
