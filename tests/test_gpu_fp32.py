@@ -1,7 +1,7 @@
 """The FP32 form (precision 1): reconstruction, interface flux, weights and
 derivative fields in FP32; cell averages, their S2O4 accumulation and the
 metrics in FP64.  Its error is stated against the FP64 CPU oracle on the
-Taylor-Green vortex (BASELINE bound: density L2 <= 1e-5); conservation holds
+Taylor-Green vortex (the bound asked of the FP32 form: density L2 <= 1e-5); conservation holds
 to FP64 rounding because the averages accumulate in FP64."""
 import math
 
