@@ -32,9 +32,16 @@ CGKS_HD void set_dt(DtState& d, double dt) {
    gains from the extra warps); the FP64 ones keep 2 (they are bound by the
    FP64 pipe, and spill more when capped) */
 template <typename T, int DIM = 3> constexpr int min_blocks() { return sizeof(T) == 4 ? (DIM == 2 ? 4 : 3) : 2; }
-/* the interface flux: FP32 fits 4 blocks in 3-D as well (128 registers, 8 B
-   spilled) since its Maxwellian moments are factorised */
-template <typename T, int DIM = 3> constexpr int flux_min_blocks() { return sizeof(T) == 4 ? 4 : 2; }
+/* the single-case Cartesian kernels: FP32 fits 4 blocks in 3-D as well (128
+   registers: the flux spills 8 B since its Maxwellian moments are
+   factorised, the reconstruction 196 B and still gains 4% from the extra
+   warps); the curvilinear ones, which spill more, keep 3 */
+template <typename T, int DIM, bool CURVI> constexpr int recon_min_blocks() {
+  return sizeof(T) == 4 && DIM == 3 && !CURVI ? 4 : min_blocks<T, DIM>();
+}
+template <typename T, int DIM, bool CURVI> constexpr int flux_min_blocks() {
+  return sizeof(T) == 4 && !CURVI ? 4 : min_blocks<T, DIM>();
+}
 
 /* first order: every face Gauss-point state of cell c is its cell average
    with zero gradient (stored where recon_var stores them) */
@@ -131,7 +138,7 @@ __device__ __forceinline__ bool selector_skip(const SelectorDev& sel, const doub
 }
 
 template <typename T, int DIM, bool CURVI, bool WALL>
-__global__ void __launch_bounds__(128, min_blocks<T, DIM>())
+__global__ void __launch_bounds__(128, recon_min_blocks<T, DIM, CURVI>())
     k_recon(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
             const T* __restrict__ der, DevGeo g, Phys ph, T* __restrict__ gpL, T* __restrict__ gpR,
             double* __restrict__ chi, int record_chi, int* __restrict__ st, SelectorDev sel) {
@@ -218,7 +225,7 @@ __device__ __forceinline__ void flux_bnd_item(const DevGeo& g, const Phys& ph, d
 /* one thread per face slot and Gauss point (blocks of 128); the Cartesian
    path stages each point's Gauss-point states in shared memory */
 template <typename T, int DIM, bool CURVI>
-__global__ void __launch_bounds__(128, flux_min_blocks<T, DIM>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
+__global__ void __launch_bounds__(128, flux_min_blocks<T, DIM, CURVI>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
                                               const T* __restrict__ gpL, const T* __restrict__ gpR,
                                               T* __restrict__ flux, int* __restrict__ st) {
   long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
