@@ -840,13 +840,24 @@ CGKS_HD void tcoef(T tau, T dl, T em, T ex, T* c) {
   c[5] = -tau * tau * em;
 }
 
+/* qw . o: the psi-moment vector o of a distribution part weighted into its
+   moment of the peculiar energy about the interface velocity U,
+   qw = (|U|^2/2, -U, 1), which is all the heat-flux fix needs of it */
+template <typename T, int DIM> CGKS_HD T qdot(const T* qw, const T* o) {
+  T q = qw[DIM + 1] * o[DIM + 1];
+#pragma unroll
+  for (int i = 0; i <= DIM; ++i) q += qw[i] * o[i];
+  return q;
+}
+
 /* one side (the left half Maxwellian for u > 0 or the right one for u < 0):
    its slopes along each local axis, its share of the g0 slopes dW0, its
    compatibility right-hand side and time slope, and its flux parts 4 and 5
    (and their psi-moments for the heat-flux fix) */
 template <typename T, int DIM, int J>
 CGKS_HD void side_dir(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, const T* W, const T* dWj,
-                      const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, T* Qn, T* Qt, T* bs, T* dW0j) {
+                      const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, const T* qw, T& qn, T& qt, T* bs,
+                      T* dW0j) {
   constexpr int NV = DIM + 2;
   constexpr int E0 = J == 0, E1 = J == 1, E2 = J == 2;
   T b[NV], a[NV], t1[NV];
@@ -867,28 +878,27 @@ CGKS_HD void side_dir(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, c
   }
   if (prfix) {
     mvec<T, DIM, E0, E1, E2>(s, t, a, t1);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      Qn[i] += cn[4] * s.rho * t1[i];
-      Qt[i] += ct[4] * s.rho * t1[i];
-    }
+    const T q = qdot<T, DIM>(qw, t1);
+    qn += cn[4] * s.rho * q;
+    qt += ct[4] * s.rho * q;
   }
 }
 
 template <typename T, int DIM, class Ld>
 CGKS_HD void side_all(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, const T* W, const Ld& ld, int side,
-                      const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, T* Qn, T* Qt, T* bs, T* dW0) {
+                      const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, const T* qw, T& qn, T& qt, T* bs,
+                      T* dW0) {
   constexpr int NV = DIM + 2;
 #pragma unroll
   for (int i = 0; i < NV; ++i) bs[i] = T(0);
   T dWj[NV];
   ld.grad(side, 0, dWj);
-  side_dir<T, DIM, 0>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, Qn, Qt, bs, dW0);
+  side_dir<T, DIM, 0>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, qw, qn, qt, bs, dW0);
   ld.grad(side, 1, dWj);
-  side_dir<T, DIM, 1>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, Qn, Qt, bs, dW0 + NV);
+  side_dir<T, DIM, 1>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, qw, qn, qt, bs, dW0 + NV);
   if constexpr (DIM == 3) {
     ld.grad(side, 2, dWj);
-    side_dir<T, DIM, 2>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, Qn, Qt, bs, dW0 + 2 * NV);
+    side_dir<T, DIM, 2>(s, t, gam, D, iD, W, dWj, cn, ct, prfix, Fn, Ft, qw, qn, qt, bs, dW0 + 2 * NV);
   }
   T A[NV], t1[NV];
   slope_solve<T, DIM>(s, D, iD, bs, A);
@@ -900,11 +910,9 @@ CGKS_HD void side_all(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, c
   }
   if (prfix) {
     mvec<T, DIM, 0, 0, 0>(s, t, A, t1);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      Qn[i] += cn[5] * s.rho * t1[i];
-      Qt[i] += ct[5] * s.rho * t1[i];
-    }
+    const T q = qdot<T, DIM>(qw, t1);
+    qn += cn[5] * s.rho * q;
+    qt += ct[5] * s.rho * q;
   }
 }
 
@@ -912,7 +920,7 @@ CGKS_HD void side_all(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, c
    right-hand side (whose psi-moment is the Euler Jacobian product) */
 template <typename T, int DIM, int J>
 CGKS_HD void g0_dir(const MxS<T, DIM>& z, const MxT<T>& t, T gam, T D, T iD, const T* W0, const T* dW0j,
-                    const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, T* Qn, T* Qt, T* b0) {
+                    const T* cn, const T* ct, bool prfix, T* Fn, T* Ft, const T* qw, T& qn, T& qt, T* b0) {
   constexpr int NV = DIM + 2;
   constexpr int E0 = J == 0, E1 = J == 1, E2 = J == 2;
   T b[NV], a[NV], t1[NV];
@@ -929,11 +937,9 @@ CGKS_HD void g0_dir(const MxS<T, DIM>& z, const MxT<T>& t, T gam, T D, T iD, con
 #pragma unroll
   for (int i = 0; i < NV; ++i) b0[i] -= t1[i] * z.irho;
   if (prfix) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      Qn[i] += cn[1] * t1[i];
-      Qt[i] += ct[1] * t1[i];
-    }
+    const T q = qdot<T, DIM>(qw, t1);
+    qn += cn[1] * q;
+    qt += ct[1] * q;
   }
 }
 
@@ -999,31 +1005,48 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
     }
   }
   const bool prfix = ph.prfix != 0;
-  T Fn[NV], Ft[NV], Qn[NV], Qt[NV], bl[NV], br[NV], b0[NV], dW0[DIM * NV];
+  T Fn[NV], Ft[NV], bl[NV], br[NV], b0[NV], dW0[DIM * NV];
+  /* the heat-flux fix needs of the psi-moments Q of f^n and f_t^n only their
+     peculiar-energy moment about the interface velocity, qw . Q */
+  T qw[NV];
+  {
+    T u2 = T(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      qw[1 + i] = -z.U[i];
+      u2 += z.U[i] * z.U[i];
+    }
+    qw[0] = T(0.5) * u2;
+    qw[DIM + 1] = T(1);
+  }
   euler_flux<T, DIM>(z, W0, 0, t1); /* part 0: rho0 <u psi> of g0 */
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     Fn[i] = cn[0] * t1[i] + cn[3] * H3[i];
     Ft[i] = ct[0] * t1[i] + ct[3] * H3[i];
-    Qn[i] = (cn[0] + cn[3]) * W0[i];
-    Qt[i] = (ct[0] + ct[3]) * W0[i];
     b0[i] = T(0);
+  }
+  T qn = T(0), qt = T(0);
+  if (prfix) {
+    const T q = qdot<T, DIM>(qw, W0);
+    qn = (cn[0] + cn[3]) * q;
+    qt = (ct[0] + ct[3]) * q;
   }
 #pragma unroll
   for (int i = 0; i < DIM * NV; ++i) dW0[i] = T(0);
   {
     MxT<T> t;
     mx_tables<T, DIM>(l, t);
-    side_all<T, DIM>(l, t, gam, D, iD, WL, ld, 0, cn, ct, prfix, Fn, Ft, Qn, Qt, bl, dW0);
+    side_all<T, DIM>(l, t, gam, D, iD, WL, ld, 0, cn, ct, prfix, Fn, Ft, qw, qn, qt, bl, dW0);
     mx_tables<T, DIM>(r, t);
-    side_all<T, DIM>(r, t, gam, D, iD, WR, ld, 1, cn, ct, prfix, Fn, Ft, Qn, Qt, br, dW0);
+    side_all<T, DIM>(r, t, gam, D, iD, WR, ld, 1, cn, ct, prfix, Fn, Ft, qw, qn, qt, br, dW0);
   }
   {
     MxT<T> t;
     mx_tables<T, DIM>(z, t);
-    g0_dir<T, DIM, 0>(z, t, gam, D, iD, W0, dW0, cn, ct, prfix, Fn, Ft, Qn, Qt, b0);
-    g0_dir<T, DIM, 1>(z, t, gam, D, iD, W0, dW0 + NV, cn, ct, prfix, Fn, Ft, Qn, Qt, b0);
-    if constexpr (DIM == 3) g0_dir<T, DIM, 2>(z, t, gam, D, iD, W0, dW0 + 2 * NV, cn, ct, prfix, Fn, Ft, Qn, Qt, b0);
+    g0_dir<T, DIM, 0>(z, t, gam, D, iD, W0, dW0, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
+    g0_dir<T, DIM, 1>(z, t, gam, D, iD, W0, dW0 + NV, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
+    if constexpr (DIM == 3) g0_dir<T, DIM, 2>(z, t, gam, D, iD, W0, dW0 + 2 * NV, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
   }
   /* part 2: rho0 <A0 u psi> = (dF_x/dW)(rho0 b0), psi-moment rho0 b0 */
 #pragma unroll
@@ -1034,27 +1057,16 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
     Fn[i] += cn[2] * t1[i];
     Ft[i] += ct[2] * t1[i];
   }
-  if (prfix) { /* heat-flux correction F_E += (1/Pr - 1) q about the interface velocity */
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      Qn[i] += cn[2] * t2[i];
-      Qt[i] += ct[2] * t2[i];
-    }
+  if (prfix) { /* heat-flux correction F_E += (1/Pr - 1) q about the interface velocity:
+                  q = qw . F - U_x qw . Q */
+    const T q2 = qdot<T, DIM>(qw, t2);
+    qn += cn[2] * q2;
+    qt += ct[2] * q2;
     const T f = T(1) / ph_pr<T>(ph) - T(1);
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-      T* F = pass == 0 ? Fn : Ft;
-      T* Q = pass == 0 ? Qn : Qt;
-      T uf = T(0), uq = T(0), u2 = T(0);
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        uf += z.U[i] * F[1 + i];
-        uq += z.U[i] * Q[1 + i];
-        u2 += z.U[i] * z.U[i];
-      }
-      T q = (F[DIM + 1] - uf + T(0.5) * u2 * F[0]) - z.U[0] * (Q[DIM + 1] - uq + T(0.5) * u2 * Q[0]);
-      F[DIM + 1] += f * q;
-    }
+    const T hn = qdot<T, DIM>(qw, Fn) - z.U[0] * qn;
+    const T ht = qdot<T, DIM>(qw, Ft) - z.U[0] * qt;
+    Fn[DIM + 1] += f * hn;
+    Ft[DIM + 1] += f * ht;
   }
   /* interface values for the derivative update (temporal discretisation section) */
   const T tau0 = T(5) * jump * dt;
