@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(128, min_blocks<T, DIM>())
 /* interface flux: tiles of blockDim.x = 128 face-point items (flux_item),
    each point's Gauss-point states staged in shared memory */
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128, min_blocks<T, DIM>())
+__global__ void __launch_bounds__(128, flux_min_blocks<T, DIM, false>())
     kb_flux(const BatchCase* __restrict__ cases, TileList L, BatchArrays<T> A) {
   __shared__ BatchCase sc;
   __shared__ TileRef sr;

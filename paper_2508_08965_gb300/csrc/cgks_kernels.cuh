@@ -32,15 +32,16 @@ CGKS_HD void set_dt(DtState& d, double dt) {
    gains from the extra warps); the FP64 ones keep 2 (they are bound by the
    FP64 pipe, and spill more when capped) */
 template <typename T, int DIM = 3> constexpr int min_blocks() { return sizeof(T) == 4 ? (DIM == 2 ? 4 : 3) : 2; }
-/* the single-case Cartesian kernels: FP32 fits 4 blocks in 3-D as well (128
-   registers: the flux spills 8 B since its Maxwellian moments are
-   factorised, the reconstruction 196 B and still gains 4% from the extra
-   warps); the curvilinear ones, which spill more, keep 3 */
+/* the Cartesian kernels: FP32 fits 4 blocks in 3-D as well (128 registers:
+   the flux spills 8 B since its Maxwellian moments are factorised, the
+   reconstruction 196 B and still gains 4% from the extra warps) and the 2-D
+   flux 5 (96 registers, no spill); the curvilinear ones, which spill more,
+   keep 3 */
 template <typename T, int DIM, bool CURVI> constexpr int recon_min_blocks() {
   return sizeof(T) == 4 && DIM == 3 && !CURVI ? 4 : min_blocks<T, DIM>();
 }
 template <typename T, int DIM, bool CURVI> constexpr int flux_min_blocks() {
-  return sizeof(T) == 4 && !CURVI ? 4 : min_blocks<T, DIM>();
+  return sizeof(T) == 4 && !CURVI ? (DIM == 2 ? 5 : 4) : min_blocks<T, DIM>();
 }
 
 /* first order: every face Gauss-point state of cell c is its cell average
