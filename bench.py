@@ -39,23 +39,23 @@ WORKLOADS = {
 # instructions they execute).  recon: per cell; flux: per face Gauss point.
 FLOPS_PER_UNIT = {
     ("recon", 3): 1.249e4,
-    ("flux", 3): 3.729e3,
+    ("flux", 3): 3.616e3,
 }
 # DRAM bytes per unit of the same capture (read + write), for `traffic`
 DRAM_BYTES_PER_UNIT = {
-    ("recon", 3): (0.3029e9 + 1.0170e9) / 262144,
-    ("flux", 3): (1.0080e9 + 0.7137e9) / (262144 * 12),
+    ("recon", 3): (0.3039e9 + 1.0170e9) / 262144,
+    ("flux", 3): (1.0110e9 + 0.7142e9) / (262144 * 12),
 }
 # the same for the FP32 form (flops = 2 FFMA + FADD + FMUL; ncu, TGV 64^3);
 # update: per (cell, variable)
 FLOPS_PER_UNIT_FP32 = {
-    ("recon", 3): 1.236e4,
-    ("flux", 3): 3.424e3,
+    ("recon", 3): 1.235e4,
+    ("flux", 3): 3.395e3,
     ("update", 3): 158.0,
 }
 DRAM_BYTES_PER_UNIT_FP32 = {
-    ("recon", 3): (130.8e6 + 463.3e6) / 262144,
-    ("flux", 3): (503.5e6 + 337.2e6) / (262144 * 12),
+    ("recon", 3): (157.8e6 + 492.7e6) / 262144,
+    ("flux", 3): (503.4e6 + 337.0e6) / (262144 * 12),
     ("update", 3): (388.5e6 + 159.3e6) / (262144 * 5),
 }
 
