@@ -129,46 +129,56 @@ CGKS_HD void gen_coeffs_2d(const Ld& ld, T* __restrict__ a) {
     const T nppQ = ld.avg(1, 1, 0);
     T nppG[2];
     ld.grefv(1, 1, 0, nppG);
-    { const T f = nmmQ +npmQ +nmpQ +nppQ;
+    const T o1x0 = nmmQ, o1x1 = npmQ, o1x2 = nmpQ, o1x3 = nppQ;
+    const T o1ap = o1x0 + o1x1;
+    const T o1am = o1x0 - o1x1;
+    const T o1bp = o1x2 + o1x3;
+    const T o1bm = o1x2 - o1x3;
+    { const T f = o1ap + o1bp;
       a[0] = cg_fma(T(0.03289473684210526), f, a[0]);
       a[1] = cg_fma(T(0.03289473684210526), f, a[1]);
       a[2] = cg_fma(T(-0.3157894736842105), f, a[2]);
       a[3] = cg_fma(T(0.15789473684210525), f, a[3]);
       a[4] = cg_fma(T(-0.3157894736842105), f, a[4]);
     }
-    { const T f = nmmQ +npmQ -nmpQ -nppQ;
+    { const T f = o1ap - o1bp;
       a[5] = cg_fma(T(0.0002545824847250509), f, a[5]);
       a[6] = cg_fma(T(-0.06720977596741344), f, a[6]);
       a[7] = cg_fma(T(0.012219959266802444), f, a[7]);
     }
-    { const T f = nmmQ -npmQ +nmpQ -nppQ;
+    { const T f = o1am + o1bm;
       a[8] = cg_fma(T(0.0002545824847250509), f, a[8]);
       a[9] = cg_fma(T(0.012219959266802444), f, a[9]);
       a[10] = cg_fma(T(-0.06720977596741344), f, a[10]);
     }
-    { const T f = nmmQ -npmQ -nmpQ +nppQ;
+    { const T f = o1am - o1bm;
       a[11] = cg_fma(T(0.024349211970958032), f, a[11]);
       a[12] = cg_fma(T(0.02071896582256065), f, a[12]);
       a[13] = cg_fma(T(0.02071896582256065), f, a[13]);
     }
-    { const T f = (-nmmG[0] -nmmG[1]) +(npmG[0] -npmG[1]) +(-nmpG[0] +nmpG[1]) +(nppG[0] +nppG[1]);
+    const T o2x0 = (-nmmG[0] -nmmG[1]), o2x1 = (npmG[0] -npmG[1]), o2x2 = (-nmpG[0] +nmpG[1]), o2x3 = (nppG[0] +nppG[1]);
+    const T o2ap = o2x0 + o2x1;
+    const T o2am = o2x0 - o2x1;
+    const T o2bp = o2x2 + o2x3;
+    const T o2bm = o2x2 - o2x3;
+    { const T f = o2ap + o2bp;
       a[0] = cg_fma(T(-0.01864035087719298), f, a[0]);
       a[1] = cg_fma(T(-0.01864035087719298), f, a[1]);
       a[2] = cg_fma(T(0.07894736842105263), f, a[2]);
       a[3] = cg_fma(T(0.21052631578947367), f, a[3]);
       a[4] = cg_fma(T(0.07894736842105263), f, a[4]);
     }
-    { const T f = (-nmmG[0] -nmmG[1]) +(npmG[0] -npmG[1]) -(-nmpG[0] +nmpG[1]) -(nppG[0] +nppG[1]);
+    { const T f = o2ap - o2bp;
       a[5] = cg_fma(T(0.019305838424983027), f, a[5]);
       a[6] = cg_fma(T(-0.09674134419551934), f, a[6]);
       a[7] = cg_fma(T(-0.07331975560081466), f, a[7]);
     }
-    { const T f = (-nmmG[0] -nmmG[1]) -(npmG[0] -npmG[1]) +(-nmpG[0] +nmpG[1]) -(nppG[0] +nppG[1]);
+    { const T f = o2am + o2bm;
       a[8] = cg_fma(T(0.019305838424983027), f, a[8]);
       a[9] = cg_fma(T(-0.07331975560081466), f, a[9]);
       a[10] = cg_fma(T(-0.09674134419551934), f, a[10]);
     }
-    { const T f = (-nmmG[0] -nmmG[1]) -(npmG[0] -npmG[1]) -(-nmpG[0] +nmpG[1]) +(nppG[0] +nppG[1]);
+    { const T f = o2am - o2bm;
       a[11] = cg_fma(T(-0.05108907384451922), f, a[11]);
       a[12] = cg_fma(T(0.21834602443775455), f, a[12]);
       a[13] = cg_fma(T(0.21834602443775455), f, a[13]);
@@ -468,61 +478,76 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
 #pragma unroll
   for (int b = 0; b < 34; ++b) a[b] = T(0);
   {
-    { const T f = ld.line(0) +ld.line(1) +ld.line(2) +ld.line(3);
+    const T o1x0 = ld.line(0), o1x1 = ld.line(1), o1x2 = ld.line(2), o1x3 = ld.line(3);
+    const T o1ap = o1x0 + o1x1;
+    const T o1am = o1x0 - o1x1;
+    const T o1bp = o1x2 + o1x3;
+    const T o1bm = o1x2 - o1x3;
+    { const T f = o1ap + o1bp;
       a[21] = cg_fma(T(0.10817307692307693), f, a[21]);
       a[22] = cg_fma(T(-0.5192307692307693), f, a[22]);
     }
-    { const T f = ld.line(0) +ld.line(1) -ld.line(2) -ld.line(3);
+    { const T f = o1ap - o1bp;
       a[25] = cg_fma(T(-0.22401937772088515), f, a[25]);
       a[26] = cg_fma(T(0.28317079043922294), f, a[26]);
       a[27] = cg_fma(T(0.23326159319779152), f, a[27]);
       a[28] = cg_fma(T(0.4981839941374284), f, a[28]);
     }
-    { const T f = ld.line(0) -ld.line(1) +ld.line(2) -ld.line(3);
+    { const T f = o1am + o1bm;
       a[29] = cg_fma(T(-0.22401937772088515), f, a[29]);
       a[30] = cg_fma(T(0.28317079043922294), f, a[30]);
       a[31] = cg_fma(T(0.4981839941374284), f, a[31]);
       a[32] = cg_fma(T(0.23326159319779152), f, a[32]);
     }
-    { const T f = ld.line(0) -ld.line(1) -ld.line(2) +ld.line(3);
+    { const T f = o1am - o1bm;
       a[33] = cg_fma(T(0.058823529411764705), f, a[33]);
     }
-    { const T f = ld.line(4) +ld.line(5) +ld.line(6) +ld.line(7);
+    const T o2x0 = ld.line(4), o2x1 = ld.line(5), o2x2 = ld.line(6), o2x3 = ld.line(7);
+    const T o2ap = o2x0 + o2x1;
+    const T o2am = o2x0 - o2x1;
+    const T o2bp = o2x2 + o2x3;
+    const T o2bm = o2x2 - o2x3;
+    { const T f = o2ap + o2bp;
       a[13] = cg_fma(T(0.10817307692307693), f, a[13]);
       a[15] = cg_fma(T(-0.5192307692307693), f, a[15]);
     }
-    { const T f = ld.line(4) +ld.line(5) -ld.line(6) -ld.line(7);
+    { const T f = o2ap - o2bp;
       a[17] = cg_fma(T(-0.22401937772088515), f, a[17]);
       a[18] = cg_fma(T(0.23326159319779152), f, a[18]);
       a[19] = cg_fma(T(0.28317079043922294), f, a[19]);
       a[20] = cg_fma(T(0.4981839941374284), f, a[20]);
     }
-    { const T f = ld.line(4) -ld.line(5) +ld.line(6) -ld.line(7);
+    { const T f = o2am + o2bm;
       a[29] = cg_fma(T(-0.22401937772088515), f, a[29]);
       a[30] = cg_fma(T(0.4981839941374284), f, a[30]);
       a[31] = cg_fma(T(0.28317079043922294), f, a[31]);
       a[32] = cg_fma(T(0.23326159319779152), f, a[32]);
     }
-    { const T f = ld.line(4) -ld.line(5) -ld.line(6) +ld.line(7);
+    { const T f = o2am - o2bm;
       a[33] = cg_fma(T(0.058823529411764705), f, a[33]);
     }
-    { const T f = ld.line(8) +ld.line(9) +ld.line(10) +ld.line(11);
+    const T o3x0 = ld.line(8), o3x1 = ld.line(9), o3x2 = ld.line(10), o3x3 = ld.line(11);
+    const T o3ap = o3x0 + o3x1;
+    const T o3am = o3x0 - o3x1;
+    const T o3bp = o3x2 + o3x3;
+    const T o3bm = o3x2 - o3x3;
+    { const T f = o3ap + o3bp;
       a[9] = cg_fma(T(0.10817307692307693), f, a[9]);
       a[12] = cg_fma(T(-0.5192307692307693), f, a[12]);
     }
-    { const T f = ld.line(8) +ld.line(9) -ld.line(10) -ld.line(11);
+    { const T f = o3ap - o3bp;
       a[17] = cg_fma(T(-0.22401937772088515), f, a[17]);
       a[18] = cg_fma(T(0.23326159319779152), f, a[18]);
       a[19] = cg_fma(T(0.4981839941374284), f, a[19]);
       a[20] = cg_fma(T(0.28317079043922294), f, a[20]);
     }
-    { const T f = ld.line(8) -ld.line(9) +ld.line(10) -ld.line(11);
+    { const T f = o3am + o3bm;
       a[25] = cg_fma(T(-0.22401937772088515), f, a[25]);
       a[26] = cg_fma(T(0.4981839941374284), f, a[26]);
       a[27] = cg_fma(T(0.23326159319779152), f, a[27]);
       a[28] = cg_fma(T(0.28317079043922294), f, a[28]);
     }
-    { const T f = ld.line(8) -ld.line(9) -ld.line(10) +ld.line(11);
+    { const T f = o3am - o3bm;
       a[33] = cg_fma(T(0.058823529411764705), f, a[33]);
     }
   }
@@ -731,7 +756,12 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T nzppQ = ld.avg(0, 1, 1);
     T nzppG[3];
     ld.grefv(0, 1, 1, nzppG);
-    { const T f = nzmmQ +nzpmQ +nzmpQ +nzppQ;
+    const T o1x0 = nzmmQ, o1x1 = nzpmQ, o1x2 = nzmpQ, o1x3 = nzppQ;
+    const T o1ap = o1x0 + o1x1;
+    const T o1am = o1x0 - o1x1;
+    const T o1bp = o1x2 + o1x3;
+    const T o1bm = o1x2 - o1x3;
+    { const T f = o1ap + o1bp;
       a[0] = cg_fma(T(-0.0038288288288288288), f, a[0]);
       a[1] = cg_fma(T(0.031081081081081083), f, a[1]);
       a[2] = cg_fma(T(0.031081081081081083), f, a[2]);
@@ -742,44 +772,54 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
       a[7] = cg_fma(T(0.15675675675675677), f, a[7]);
       a[8] = cg_fma(T(-0.3081081081081081), f, a[8]);
     }
-    { const T f = nzmmQ +nzpmQ -nzmpQ -nzppQ;
+    { const T f = o1ap - o1bp;
       a[9] = cg_fma(T(0.0021929824561403508), f, a[9]);
       a[10] = cg_fma(T(0.007017543859649123), f, a[10]);
       a[11] = cg_fma(T(-0.05964912280701754), f, a[11]);
     }
-    { const T f = nzmmQ -nzpmQ +nzmpQ -nzppQ;
+    { const T f = o1am + o1bm;
       a[13] = cg_fma(T(0.0021929824561403508), f, a[13]);
       a[14] = cg_fma(T(0.007017543859649123), f, a[14]);
       a[16] = cg_fma(T(-0.05964912280701754), f, a[16]);
     }
-    { const T f = nzmmQ -nzpmQ -nzmpQ +nzppQ;
+    { const T f = o1am - o1bm;
       a[17] = cg_fma(T(0.020213669328926834), f, a[17]);
       a[18] = cg_fma(T(-0.052189479482236296), f, a[18]);
       a[19] = cg_fma(T(0.03222252822913798), f, a[19]);
       a[20] = cg_fma(T(0.03222252822913798), f, a[20]);
     }
-    { const T f = nzmmG[0] +nzpmG[0] +nzmpG[0] +nzppG[0];
+    const T o2x0 = nzmmG[0], o2x1 = nzpmG[0], o2x2 = nzmpG[0], o2x3 = nzppG[0];
+    const T o2ap = o2x0 + o2x1;
+    const T o2am = o2x0 - o2x1;
+    const T o2bp = o2x2 + o2x3;
+    const T o2bm = o2x2 - o2x3;
+    { const T f = o2ap + o2bp;
       a[21] = cg_fma(T(0.0076332658569500675), f, a[21]);
       a[22] = cg_fma(T(-0.057692307692307696), f, a[22]);
       a[23] = cg_fma(T(0.05263157894736842), f, a[23]);
       a[24] = cg_fma(T(0.05263157894736842), f, a[24]);
     }
-    { const T f = nzmmG[0] +nzpmG[0] -nzmpG[0] -nzppG[0];
+    { const T f = o2ap - o2bp;
       a[25] = cg_fma(T(0.010416666666666666), f, a[25]);
       a[26] = cg_fma(T(0.2482758620689655), f, a[26]);
       a[27] = cg_fma(T(-0.25), f, a[27]);
       a[28] = cg_fma(T(-0.2482758620689655), f, a[28]);
     }
-    { const T f = nzmmG[0] -nzpmG[0] +nzmpG[0] -nzppG[0];
+    { const T f = o2am + o2bm;
       a[29] = cg_fma(T(0.010416666666666666), f, a[29]);
       a[30] = cg_fma(T(0.2482758620689655), f, a[30]);
       a[31] = cg_fma(T(-0.2482758620689655), f, a[31]);
       a[32] = cg_fma(T(-0.25), f, a[32]);
     }
-    { const T f = nzmmG[0] -nzpmG[0] -nzmpG[0] +nzppG[0];
+    { const T f = o2am - o2bm;
       a[33] = cg_fma(T(0.0784313725490196), f, a[33]);
     }
-    { const T f = (-nzmmG[1] -nzmmG[2]) +(nzpmG[1] -nzpmG[2]) +(-nzmpG[1] +nzmpG[2]) +(nzppG[1] +nzppG[2]);
+    const T o3x0 = (-nzmmG[1] -nzmmG[2]), o3x1 = (nzpmG[1] -nzpmG[2]), o3x2 = (-nzmpG[1] +nzmpG[2]), o3x3 = (nzppG[1] +nzppG[2]);
+    const T o3ap = o3x0 + o3x1;
+    const T o3am = o3x0 - o3x1;
+    const T o3bp = o3x2 + o3x3;
+    const T o3bm = o3x2 - o3x3;
+    { const T f = o3ap + o3bp;
       a[0] = cg_fma(T(0.0009572072072072072), f, a[0]);
       a[1] = cg_fma(T(-0.01818693693693694), f, a[1]);
       a[2] = cg_fma(T(-0.01818693693693694), f, a[2]);
@@ -790,19 +830,19 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
       a[7] = cg_fma(T(0.21081081081081082), f, a[7]);
       a[8] = cg_fma(T(0.07702702702702703), f, a[8]);
     }
-    { const T f = (-nzmmG[1] -nzmmG[2]) +(nzpmG[1] -nzpmG[2]) -(-nzmpG[1] +nzmpG[2]) -(nzppG[1] +nzppG[2]);
+    { const T f = o3ap - o3bp;
       a[9] = cg_fma(T(0.015308704453441296), f, a[9]);
       a[10] = cg_fma(T(0.010526315789473684), f, a[10]);
       a[11] = cg_fma(T(-0.08947368421052632), f, a[11]);
       a[12] = cg_fma(T(-0.057692307692307696), f, a[12]);
     }
-    { const T f = (-nzmmG[1] -nzmmG[2]) -(nzpmG[1] -nzpmG[2]) +(-nzmpG[1] +nzmpG[2]) -(nzppG[1] +nzppG[2]);
+    { const T f = o3am + o3bm;
       a[13] = cg_fma(T(0.015308704453441296), f, a[13]);
       a[14] = cg_fma(T(0.010526315789473684), f, a[14]);
       a[15] = cg_fma(T(-0.057692307692307696), f, a[15]);
       a[16] = cg_fma(T(-0.08947368421052632), f, a[16]);
     }
-    { const T f = (-nzmmG[1] -nzmmG[2]) -(nzpmG[1] -nzpmG[2]) -(-nzmpG[1] +nzmpG[2]) +(nzppG[1] +nzppG[2]);
+    { const T f = o3am - o3bm;
       a[17] = cg_fma(T(-0.040719957771045624), f, a[17]);
       a[18] = cg_fma(T(-0.017488295235472323), f, a[18]);
       a[19] = cg_fma(T(0.20077113742770586), f, a[19]);
@@ -822,7 +862,12 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T npzpQ = ld.avg(1, 0, 1);
     T npzpG[3];
     ld.grefv(1, 0, 1, npzpG);
-    { const T f = nmzmQ +npzmQ +nmzpQ +npzpQ;
+    const T o1x0 = nmzmQ, o1x1 = npzmQ, o1x2 = nmzpQ, o1x3 = npzpQ;
+    const T o1ap = o1x0 + o1x1;
+    const T o1am = o1x0 - o1x1;
+    const T o1bp = o1x2 + o1x3;
+    const T o1bm = o1x2 - o1x3;
+    { const T f = o1ap + o1bp;
       a[0] = cg_fma(T(0.031081081081081083), f, a[0]);
       a[1] = cg_fma(T(-0.0038288288288288288), f, a[1]);
       a[2] = cg_fma(T(0.031081081081081083), f, a[2]);
@@ -833,44 +878,54 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
       a[7] = cg_fma(T(0.021621621621621623), f, a[7]);
       a[8] = cg_fma(T(-0.3081081081081081), f, a[8]);
     }
-    { const T f = nmzmQ +npzmQ -nmzpQ -npzpQ;
+    { const T f = o1ap - o1bp;
       a[9] = cg_fma(T(0.0021929824561403508), f, a[9]);
       a[10] = cg_fma(T(-0.05964912280701754), f, a[10]);
       a[11] = cg_fma(T(0.007017543859649123), f, a[11]);
     }
-    { const T f = nmzmQ -npzmQ +nmzpQ -npzpQ;
+    { const T f = o1am + o1bm;
       a[21] = cg_fma(T(0.0021929824561403508), f, a[21]);
       a[23] = cg_fma(T(0.007017543859649123), f, a[23]);
       a[24] = cg_fma(T(-0.05964912280701754), f, a[24]);
     }
-    { const T f = nmzmQ -npzmQ -nmzpQ +npzpQ;
+    { const T f = o1am - o1bm;
       a[25] = cg_fma(T(0.020213669328926834), f, a[25]);
       a[26] = cg_fma(T(0.03222252822913798), f, a[26]);
       a[27] = cg_fma(T(-0.052189479482236296), f, a[27]);
       a[28] = cg_fma(T(0.03222252822913798), f, a[28]);
     }
-    { const T f = nmzmG[1] +npzmG[1] +nmzpG[1] +npzpG[1];
+    const T o2x0 = nmzmG[1], o2x1 = npzmG[1], o2x2 = nmzpG[1], o2x3 = npzpG[1];
+    const T o2ap = o2x0 + o2x1;
+    const T o2am = o2x0 - o2x1;
+    const T o2bp = o2x2 + o2x3;
+    const T o2bm = o2x2 - o2x3;
+    { const T f = o2ap + o2bp;
       a[13] = cg_fma(T(0.0076332658569500675), f, a[13]);
       a[14] = cg_fma(T(0.05263157894736842), f, a[14]);
       a[15] = cg_fma(T(-0.057692307692307696), f, a[15]);
       a[16] = cg_fma(T(0.05263157894736842), f, a[16]);
     }
-    { const T f = nmzmG[1] +npzmG[1] -nmzpG[1] -npzpG[1];
+    { const T f = o2ap - o2bp;
       a[17] = cg_fma(T(0.010416666666666666), f, a[17]);
       a[18] = cg_fma(T(-0.25), f, a[18]);
       a[19] = cg_fma(T(0.2482758620689655), f, a[19]);
       a[20] = cg_fma(T(-0.2482758620689655), f, a[20]);
     }
-    { const T f = nmzmG[1] -npzmG[1] +nmzpG[1] -npzpG[1];
+    { const T f = o2am + o2bm;
       a[29] = cg_fma(T(0.010416666666666666), f, a[29]);
       a[30] = cg_fma(T(-0.2482758620689655), f, a[30]);
       a[31] = cg_fma(T(0.2482758620689655), f, a[31]);
       a[32] = cg_fma(T(-0.25), f, a[32]);
     }
-    { const T f = nmzmG[1] -npzmG[1] -nmzpG[1] +npzpG[1];
+    { const T f = o2am - o2bm;
       a[33] = cg_fma(T(0.0784313725490196), f, a[33]);
     }
-    { const T f = (-nmzmG[0] -nmzmG[2]) +(npzmG[0] -npzmG[2]) +(-nmzpG[0] +nmzpG[2]) +(npzpG[0] +npzpG[2]);
+    const T o3x0 = (-nmzmG[0] -nmzmG[2]), o3x1 = (npzmG[0] -npzmG[2]), o3x2 = (-nmzpG[0] +nmzpG[2]), o3x3 = (npzpG[0] +npzpG[2]);
+    const T o3ap = o3x0 + o3x1;
+    const T o3am = o3x0 - o3x1;
+    const T o3bp = o3x2 + o3x3;
+    const T o3bm = o3x2 - o3x3;
+    { const T f = o3ap + o3bp;
       a[0] = cg_fma(T(-0.01818693693693694), f, a[0]);
       a[1] = cg_fma(T(0.0009572072072072072), f, a[1]);
       a[2] = cg_fma(T(-0.01818693693693694), f, a[2]);
@@ -881,19 +936,19 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
       a[7] = cg_fma(T(-0.005405405405405406), f, a[7]);
       a[8] = cg_fma(T(0.07702702702702703), f, a[8]);
     }
-    { const T f = (-nmzmG[0] -nmzmG[2]) +(npzmG[0] -npzmG[2]) -(-nmzpG[0] +nmzpG[2]) -(npzpG[0] +npzpG[2]);
+    { const T f = o3ap - o3bp;
       a[9] = cg_fma(T(0.015308704453441296), f, a[9]);
       a[10] = cg_fma(T(-0.08947368421052632), f, a[10]);
       a[11] = cg_fma(T(0.010526315789473684), f, a[11]);
       a[12] = cg_fma(T(-0.057692307692307696), f, a[12]);
     }
-    { const T f = (-nmzmG[0] -nmzmG[2]) -(npzmG[0] -npzmG[2]) +(-nmzpG[0] +nmzpG[2]) -(npzpG[0] +npzpG[2]);
+    { const T f = o3am + o3bm;
       a[21] = cg_fma(T(0.015308704453441296), f, a[21]);
       a[22] = cg_fma(T(-0.057692307692307696), f, a[22]);
       a[23] = cg_fma(T(0.010526315789473684), f, a[23]);
       a[24] = cg_fma(T(-0.08947368421052632), f, a[24]);
     }
-    { const T f = (-nmzmG[0] -nmzmG[2]) -(npzmG[0] -npzmG[2]) -(-nmzpG[0] +nmzpG[2]) +(npzpG[0] +npzpG[2]);
+    { const T f = o3am - o3bm;
       a[25] = cg_fma(T(-0.040719957771045624), f, a[25]);
       a[26] = cg_fma(T(0.20077113742770586), f, a[26]);
       a[27] = cg_fma(T(-0.017488295235472323), f, a[27]);
@@ -913,7 +968,12 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
     const T nppzQ = ld.avg(1, 1, 0);
     T nppzG[3];
     ld.grefv(1, 1, 0, nppzG);
-    { const T f = nmmzQ +npmzQ +nmpzQ +nppzQ;
+    const T o1x0 = nmmzQ, o1x1 = npmzQ, o1x2 = nmpzQ, o1x3 = nppzQ;
+    const T o1ap = o1x0 + o1x1;
+    const T o1am = o1x0 - o1x1;
+    const T o1bp = o1x2 + o1x3;
+    const T o1bm = o1x2 - o1x3;
+    { const T f = o1ap + o1bp;
       a[0] = cg_fma(T(0.031081081081081083), f, a[0]);
       a[1] = cg_fma(T(0.031081081081081083), f, a[1]);
       a[2] = cg_fma(T(-0.0038288288288288288), f, a[2]);
@@ -924,44 +984,54 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
       a[7] = cg_fma(T(0.021621621621621623), f, a[7]);
       a[8] = cg_fma(T(0.016216216216216217), f, a[8]);
     }
-    { const T f = nmmzQ +npmzQ -nmpzQ -nppzQ;
+    { const T f = o1ap - o1bp;
       a[13] = cg_fma(T(0.0021929824561403508), f, a[13]);
       a[14] = cg_fma(T(-0.05964912280701754), f, a[14]);
       a[16] = cg_fma(T(0.007017543859649123), f, a[16]);
     }
-    { const T f = nmmzQ -npmzQ +nmpzQ -nppzQ;
+    { const T f = o1am + o1bm;
       a[21] = cg_fma(T(0.0021929824561403508), f, a[21]);
       a[23] = cg_fma(T(-0.05964912280701754), f, a[23]);
       a[24] = cg_fma(T(0.007017543859649123), f, a[24]);
     }
-    { const T f = nmmzQ -npmzQ -nmpzQ +nppzQ;
+    { const T f = o1am - o1bm;
       a[29] = cg_fma(T(0.020213669328926834), f, a[29]);
       a[30] = cg_fma(T(0.03222252822913798), f, a[30]);
       a[31] = cg_fma(T(0.03222252822913798), f, a[31]);
       a[32] = cg_fma(T(-0.052189479482236296), f, a[32]);
     }
-    { const T f = nmmzG[2] +npmzG[2] +nmpzG[2] +nppzG[2];
+    const T o2x0 = nmmzG[2], o2x1 = npmzG[2], o2x2 = nmpzG[2], o2x3 = nppzG[2];
+    const T o2ap = o2x0 + o2x1;
+    const T o2am = o2x0 - o2x1;
+    const T o2bp = o2x2 + o2x3;
+    const T o2bm = o2x2 - o2x3;
+    { const T f = o2ap + o2bp;
       a[9] = cg_fma(T(0.0076332658569500675), f, a[9]);
       a[10] = cg_fma(T(0.05263157894736842), f, a[10]);
       a[11] = cg_fma(T(0.05263157894736842), f, a[11]);
       a[12] = cg_fma(T(-0.057692307692307696), f, a[12]);
     }
-    { const T f = nmmzG[2] +npmzG[2] -nmpzG[2] -nppzG[2];
+    { const T f = o2ap - o2bp;
       a[17] = cg_fma(T(0.010416666666666666), f, a[17]);
       a[18] = cg_fma(T(-0.25), f, a[18]);
       a[19] = cg_fma(T(-0.2482758620689655), f, a[19]);
       a[20] = cg_fma(T(0.2482758620689655), f, a[20]);
     }
-    { const T f = nmmzG[2] -npmzG[2] +nmpzG[2] -nppzG[2];
+    { const T f = o2am + o2bm;
       a[25] = cg_fma(T(0.010416666666666666), f, a[25]);
       a[26] = cg_fma(T(-0.2482758620689655), f, a[26]);
       a[27] = cg_fma(T(-0.25), f, a[27]);
       a[28] = cg_fma(T(0.2482758620689655), f, a[28]);
     }
-    { const T f = nmmzG[2] -npmzG[2] -nmpzG[2] +nppzG[2];
+    { const T f = o2am - o2bm;
       a[33] = cg_fma(T(0.0784313725490196), f, a[33]);
     }
-    { const T f = (-nmmzG[0] -nmmzG[1]) +(npmzG[0] -npmzG[1]) +(-nmpzG[0] +nmpzG[1]) +(nppzG[0] +nppzG[1]);
+    const T o3x0 = (-nmmzG[0] -nmmzG[1]), o3x1 = (npmzG[0] -npmzG[1]), o3x2 = (-nmpzG[0] +nmpzG[1]), o3x3 = (nppzG[0] +nppzG[1]);
+    const T o3ap = o3x0 + o3x1;
+    const T o3am = o3x0 - o3x1;
+    const T o3bp = o3x2 + o3x3;
+    const T o3bm = o3x2 - o3x3;
+    { const T f = o3ap + o3bp;
       a[0] = cg_fma(T(-0.01818693693693694), f, a[0]);
       a[1] = cg_fma(T(-0.01818693693693694), f, a[1]);
       a[2] = cg_fma(T(0.0009572072072072072), f, a[2]);
@@ -972,19 +1042,19 @@ CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
       a[7] = cg_fma(T(-0.005405405405405406), f, a[7]);
       a[8] = cg_fma(T(-0.004054054054054054), f, a[8]);
     }
-    { const T f = (-nmmzG[0] -nmmzG[1]) +(npmzG[0] -npmzG[1]) -(-nmpzG[0] +nmpzG[1]) -(nppzG[0] +nppzG[1]);
+    { const T f = o3ap - o3bp;
       a[13] = cg_fma(T(0.015308704453441296), f, a[13]);
       a[14] = cg_fma(T(-0.08947368421052632), f, a[14]);
       a[15] = cg_fma(T(-0.057692307692307696), f, a[15]);
       a[16] = cg_fma(T(0.010526315789473684), f, a[16]);
     }
-    { const T f = (-nmmzG[0] -nmmzG[1]) -(npmzG[0] -npmzG[1]) +(-nmpzG[0] +nmpzG[1]) -(nppzG[0] +nppzG[1]);
+    { const T f = o3am + o3bm;
       a[21] = cg_fma(T(0.015308704453441296), f, a[21]);
       a[22] = cg_fma(T(-0.057692307692307696), f, a[22]);
       a[23] = cg_fma(T(-0.08947368421052632), f, a[23]);
       a[24] = cg_fma(T(0.010526315789473684), f, a[24]);
     }
-    { const T f = (-nmmzG[0] -nmmzG[1]) -(npmzG[0] -npmzG[1]) -(-nmpzG[0] +nmpzG[1]) +(nppzG[0] +nppzG[1]);
+    { const T f = o3am - o3bm;
       a[29] = cg_fma(T(-0.040719957771045624), f, a[29]);
       a[30] = cg_fma(T(0.20077113742770586), f, a[30]);
       a[31] = cg_fma(T(0.20077113742770586), f, a[31]);

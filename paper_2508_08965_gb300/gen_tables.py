@@ -583,7 +583,66 @@ def emit_recon_code(path):
                 terms = ["%s%sG[%d]" % ("+" if o[a] > 0 else "-", nm, a) for a in range(dim) if o[a] != 0]
                 return "(%s)" % " ".join(terms).lstrip("+")
 
+            oi = [0]
+
+            def butterfly_plan(work):
+                """For an orbit whose features are +-g sums (g a power of two)
+                over the same four items: every feature is
+                g (+-(x_0 +- x_1) +- (x_2 +- x_3)), so the pair sums and
+                differences serve all features (at most 4 additions, plus one
+                per feature, instead of three per feature).  None otherwise."""
+                if len(work) < 3:
+                    return None
+                its = sorted(work[0][1], key=lambda it: pos[it])
+                if len(its) != 4 or any(sorted(cf, key=lambda it: pos[it]) != its for _, cf, _, _ in work):
+                    return None
+                mags = {abs(v) for _, cf, _, _ in work for v in cf.values()}
+                if len(mags) != 1:
+                    return None
+                g = mags.pop()
+                if g & (g - 1):
+                    return None
+                plan = []
+                for _, cf, _, _ in work:
+                    sg = [cf[its[q]] // g for q in range(4)]
+                    plan.append((sg[0], sg[0] * sg[1], sg[2], sg[2] * sg[3]))
+                return its, g, plan
+
             for rep, orb, stab, feats in orbs:
+                # features of this orbit that reach a coefficient
+                work = []
+                for c, coef in feats.items():
+                    if all(it[0] == "Q0" for it in coef):
+                        continue
+                    rows = [b for b in range(nb) if cls[b] == c and M[b][pos[rep]] != 0.0]
+                    if rows:
+                        work.append((c, coef, rows, None))
+                bp = butterfly_plan(work)
+                if bp is not None:
+                    its, g, plan = bp
+                    (i, j), (k, l) = (0, 1), (2, 3)
+                    oi[0] += 1
+                    nm = "o%d" % oi[0]
+                    fn.append("    const T %sx0 = %s, %sx1 = %s, %sx2 = %s, %sx3 = %s;" % (
+                        nm, item_expr(its[0]), nm, item_expr(its[1]), nm, item_expr(its[2]), nm, item_expr(its[3])))
+                    used = set()
+                    for _, pij, _, pkl in plan:
+                        used.add(("a", pij))
+                        used.add(("b", pkl))
+                    for side, (p, q) in (("a", (i, j)), ("b", (k, l))):
+                        for sg in (1, -1):
+                            if (side, sg) in used:
+                                fn.append("    const T %s%s%s = %sx%d %s %sx%d;" % (
+                                    nm, side, "p" if sg > 0 else "m", nm, p, "+" if sg > 0 else "-", nm, q))
+                    for (c, coef, rows, _), (si, pij, sk, pkl) in zip(work, plan):
+                        t1 = "%sa%s" % (nm, "p" if pij > 0 else "m")
+                        t2 = "%sb%s" % (nm, "p" if pkl > 0 else "m")
+                        expr = "%s%s %s %s" % ("" if si > 0 else "-", t1, "+" if si * sk > 0 else "-", t2)
+                        fn.append("    { const T f = %s;" % expr.strip())
+                        for b in rows:
+                            fn.append("      a[%d] = cg_fma(%s, f, a[%d]);" % (b, _lit(M[b][pos[rep]] / stab * g), b))
+                        fn.append("    }")
+                    continue
                 for c, coef in feats.items():
                     # the loader hands averages over relative to q0, so q0
                     # itself is zero: its terms add nothing
