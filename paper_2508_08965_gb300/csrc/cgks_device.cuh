@@ -431,6 +431,50 @@ template <typename T, int DIM, bool CURVI, bool WALL> struct ReconLd {
   }
 };
 
+/* FP64 path: whether the path function certainly saturates, chi = 1 to the
+   last bit, judged from the smoothness indicators evaluated in FP32 (64
+   times the FP64 rate on GB300) with a rigorous rounding margin, so that the
+   FP64 indicators are only formed where chi may be below 1.  With
+   r_L = IS^tau / (IS^L + eps) and r_H = IS^tau / (IS^H + eps) <= 1, the
+   blend parameter is alpha = 2 (1 + r_H^2) / (2 + r_H^2 + r_L^2) >=
+   2 / (3 + r_L^2); tanh(C alpha) rounds to exactly 1 = tanh(C) once
+   C alpha >= 25 (1 - tanh(25) < 1e-21), which holds when
+   r_L^2 <= 2 C / 25 - 3.  IS^tau = a^T (GH - GL) a and IS^L = a^T GL a are
+   bounded from their FP32 values with 2e-5 times the forms of the absolute
+   values (the FP32 error of these sums of at most ~100 terms is below 7e-6
+   of that, the FP64 one far below).  FP32 form: never (its indicators are
+   FP32 already). */
+template <typename T, int DIM> CGKS_HD bool geno_saturates_fp32(const T* a, double C) {
+  if constexpr (sizeof(T) == 4) {
+    return false;
+  } else {
+    const double r2 = 2.0 * C / 25.0 - 3.0 - 0.2;
+    if (!(r2 > 0.0)) return false;
+    typedef Sz<DIM> S;
+    float af[S::NB], aa[S::NB];
+#pragma unroll
+    for (int b = 0; b < S::NB; ++b) {
+      af[b] = (float)a[b];
+      aa[b] = fabsf(af[b]);
+    }
+    float ist, isl, ista, isla;
+    if constexpr (DIM == 3) {
+      ist = gen_ist_3d<float>(af);
+      isl = gen_isl_3d<float>(af);
+      ista = gen_ista_3d<float>(aa);
+      isla = gen_isla_3d<float>(aa);
+    } else {
+      ist = gen_ist_2d<float>(af);
+      isl = gen_isl_2d<float>(af);
+      ista = gen_ista_2d<float>(aa);
+      isla = gen_isla_2d<float>(aa);
+    }
+    const float ist_ub = fmaxf(ist + 2e-5f * ista, 0.f);
+    const float isl_lb = fmaxf(isl - 2e-5f * isla, 0.f) + 1e-15f;
+    return ist_ub <= sqrtf((float)r2) * isl_lb; /* false for inf / NaN */
+  }
+}
+
 /* Reconstruction of Eq. (compact-big-ref) on the reference cell: a = M d by the
    generated symmetry-reduced code, the linear sub-stencil gradients of
    Eq. (compact-sub-2) (closed form: the face-neighbour difference along the
@@ -472,6 +516,8 @@ CGKS_HD T recon_var(const double* __restrict__ avg, const float* __restrict__ av
   T chi;
   if (chi_force >= T(0)) {
     chi = chi_force;
+  } else if (geno_saturates_fp32<T, DIM>(a, ph_cchi<double>(ph))) {
+    chi = T(1); /* exactly what the FP64 evaluation below gives */
   } else {
     T ish, isl;
     if constexpr (DIM == 3) {

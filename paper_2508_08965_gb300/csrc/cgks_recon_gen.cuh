@@ -313,6 +313,171 @@ CGKS_HD T gen_isl_2d(const T* __restrict__ a) {
 }
 
 template <typename T>
+CGKS_HD T gen_ist_2d(const T* __restrict__ a) {
+  T s = T(0);
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[0], r);
+    r = cg_fma(T(0.08333333333333333), a[2], r);
+    r = cg_fma(T(0.08333333333333333), a[3], r);
+    s = cg_fma(a[0], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[1], r);
+    r = cg_fma(T(0.08333333333333333), a[3], r);
+    r = cg_fma(T(0.08333333333333333), a[4], r);
+    s = cg_fma(a[1], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[2], r);
+    r = cg_fma(T(0.003472222222222222), a[3], r);
+    s = cg_fma(a[2], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.179861111111111), a[3], r);
+    r = cg_fma(T(0.003472222222222222), a[4], r);
+    s = cg_fma(a[3], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[4], r);
+    s = cg_fma(a[4], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[6], r);
+    s = cg_fma(a[6], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[7], r);
+    s = cg_fma(a[7], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[9], r);
+    s = cg_fma(a[9], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[10], r);
+    s = cg_fma(a[10], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[11], r);
+    r = cg_fma(T(0.08333333333333333), a[12], r);
+    r = cg_fma(T(0.08333333333333333), a[13], r);
+    s = cg_fma(a[11], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[12], r);
+    r = cg_fma(T(0.003472222222222222), a[13], r);
+    s = cg_fma(a[12], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[13], r);
+    s = cg_fma(a[13], r, s); }
+  return s;
+}
+
+template <typename T>
+CGKS_HD T gen_ista_2d(const T* __restrict__ a) {
+  T s = T(0);
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[0], r);
+    r = cg_fma(T(0.08333333333333333), a[2], r);
+    r = cg_fma(T(0.08333333333333333), a[3], r);
+    s = cg_fma(a[0], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[1], r);
+    r = cg_fma(T(0.08333333333333333), a[3], r);
+    r = cg_fma(T(0.08333333333333333), a[4], r);
+    s = cg_fma(a[1], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[2], r);
+    r = cg_fma(T(0.003472222222222222), a[3], r);
+    s = cg_fma(a[2], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.179861111111111), a[3], r);
+    r = cg_fma(T(0.003472222222222222), a[4], r);
+    s = cg_fma(a[3], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[4], r);
+    s = cg_fma(a[4], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[6], r);
+    s = cg_fma(a[6], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[7], r);
+    s = cg_fma(a[7], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[9], r);
+    s = cg_fma(a[9], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[10], r);
+    s = cg_fma(a[10], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[11], r);
+    r = cg_fma(T(0.08333333333333333), a[12], r);
+    r = cg_fma(T(0.08333333333333333), a[13], r);
+    s = cg_fma(a[11], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[12], r);
+    r = cg_fma(T(0.003472222222222222), a[13], r);
+    s = cg_fma(a[12], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[13], r);
+    s = cg_fma(a[13], r, s); }
+  return s;
+}
+
+template <typename T>
+CGKS_HD T gen_isla_2d(const T* __restrict__ a) {
+  T s = T(0);
+  { T r = T(0);
+    r = cg_fma(T(0.08333333333333333), a[0], r);
+    r = cg_fma(T(0.004166666666666667), a[2], r);
+    r = cg_fma(T(0.006944444444444444), a[3], r);
+    s = cg_fma(a[0], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.08333333333333333), a[1], r);
+    r = cg_fma(T(0.006944444444444444), a[3], r);
+    r = cg_fma(T(0.004166666666666667), a[4], r);
+    s = cg_fma(a[1], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(6.200396825396825e-05), a[2], r);
+    r = cg_fma(T(0.00017361111111111112), a[3], r);
+    s = cg_fma(a[2], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0005208333333333333), a[3], r);
+    r = cg_fma(T(0.00017361111111111112), a[4], r);
+    s = cg_fma(a[3], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(6.200396825396825e-05), a[4], r);
+    s = cg_fma(a[4], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[5], r);
+    r = cg_fma(T(0.08333333333333333), a[6], r);
+    r = cg_fma(T(0.08333333333333333), a[7], r);
+    s = cg_fma(a[5], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.010069444444444445), a[6], r);
+    r = cg_fma(T(0.003472222222222222), a[7], r);
+    s = cg_fma(a[6], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.003125), a[7], r);
+    s = cg_fma(a[7], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[8], r);
+    r = cg_fma(T(0.08333333333333333), a[9], r);
+    r = cg_fma(T(0.08333333333333333), a[10], r);
+    s = cg_fma(a[8], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.003125), a[9], r);
+    r = cg_fma(T(0.003472222222222222), a[10], r);
+    s = cg_fma(a[9], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.010069444444444445), a[10], r);
+    s = cg_fma(a[10], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.16666666666666666), a[11], r);
+    r = cg_fma(T(0.011111111111111112), a[12], r);
+    r = cg_fma(T(0.011111111111111112), a[13], r);
+    s = cg_fma(a[11], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0003224206349206349), a[12], r);
+    r = cg_fma(T(0.00034722222222222224), a[13], r);
+    s = cg_fma(a[12], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0003224206349206349), a[13], r);
+    s = cg_fma(a[13], r, s); }
+  return s;
+}
+
+template <typename T>
 CGKS_HD T gen_mean_2d(const T* __restrict__ a) {
   T s = T(0);
   s = cg_fma(T(0.041666666666666664), a[0], s);
@@ -1227,6 +1392,438 @@ CGKS_HD T gen_ish_3d(const T* __restrict__ a) {
 
 template <typename T>
 CGKS_HD T gen_isl_3d(const T* __restrict__ a) {
+  T s = T(0);
+  { T r = T(0);
+    r = cg_fma(T(0.08333333333333333), a[0], r);
+    r = cg_fma(T(0.004166666666666667), a[3], r);
+    r = cg_fma(T(0.006944444444444444), a[4], r);
+    r = cg_fma(T(0.006944444444444444), a[5], r);
+    s = cg_fma(a[0], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.08333333333333333), a[1], r);
+    r = cg_fma(T(0.006944444444444444), a[4], r);
+    r = cg_fma(T(0.004166666666666667), a[6], r);
+    r = cg_fma(T(0.006944444444444444), a[7], r);
+    s = cg_fma(a[1], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.08333333333333333), a[2], r);
+    r = cg_fma(T(0.006944444444444444), a[5], r);
+    r = cg_fma(T(0.006944444444444444), a[7], r);
+    r = cg_fma(T(0.004166666666666667), a[8], r);
+    s = cg_fma(a[2], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(6.200396825396825e-05), a[3], r);
+    r = cg_fma(T(0.00017361111111111112), a[4], r);
+    r = cg_fma(T(0.00017361111111111112), a[5], r);
+    s = cg_fma(a[3], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0005208333333333333), a[4], r);
+    r = cg_fma(T(0.00028935185185185184), a[5], r);
+    r = cg_fma(T(0.00017361111111111112), a[6], r);
+    r = cg_fma(T(0.00028935185185185184), a[7], r);
+    s = cg_fma(a[4], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0005208333333333333), a[5], r);
+    r = cg_fma(T(0.00028935185185185184), a[7], r);
+    r = cg_fma(T(0.00017361111111111112), a[8], r);
+    s = cg_fma(a[5], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(6.200396825396825e-05), a[6], r);
+    r = cg_fma(T(0.00017361111111111112), a[7], r);
+    s = cg_fma(a[6], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0005208333333333333), a[7], r);
+    r = cg_fma(T(0.00017361111111111112), a[8], r);
+    s = cg_fma(a[7], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(6.200396825396825e-05), a[8], r);
+    s = cg_fma(a[8], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[9], r);
+    r = cg_fma(T(0.08333333333333333), a[10], r);
+    r = cg_fma(T(0.08333333333333333), a[11], r);
+    r = cg_fma(T(0.08333333333333333), a[12], r);
+    s = cg_fma(a[9], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.010069444444444445), a[10], r);
+    r = cg_fma(T(0.003472222222222222), a[11], r);
+    r = cg_fma(T(0.003472222222222222), a[12], r);
+    s = cg_fma(a[10], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.010069444444444445), a[11], r);
+    r = cg_fma(T(0.003472222222222222), a[12], r);
+    s = cg_fma(a[11], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.003125), a[12], r);
+    s = cg_fma(a[12], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[13], r);
+    r = cg_fma(T(0.08333333333333333), a[14], r);
+    r = cg_fma(T(0.08333333333333333), a[15], r);
+    r = cg_fma(T(0.08333333333333333), a[16], r);
+    s = cg_fma(a[13], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.010069444444444445), a[14], r);
+    r = cg_fma(T(0.003472222222222222), a[15], r);
+    r = cg_fma(T(0.003472222222222222), a[16], r);
+    s = cg_fma(a[14], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.003125), a[15], r);
+    r = cg_fma(T(0.003472222222222222), a[16], r);
+    s = cg_fma(a[15], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.010069444444444445), a[16], r);
+    s = cg_fma(a[16], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.16666666666666666), a[17], r);
+    r = cg_fma(T(0.013888888888888888), a[18], r);
+    r = cg_fma(T(0.011111111111111112), a[19], r);
+    r = cg_fma(T(0.011111111111111112), a[20], r);
+    s = cg_fma(a[17], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.001099537037037037), a[18], r);
+    r = cg_fma(T(0.000462962962962963), a[19], r);
+    r = cg_fma(T(0.000462962962962963), a[20], r);
+    s = cg_fma(a[18], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0003224206349206349), a[19], r);
+    r = cg_fma(T(0.00034722222222222224), a[20], r);
+    s = cg_fma(a[19], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0003224206349206349), a[20], r);
+    s = cg_fma(a[20], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[21], r);
+    r = cg_fma(T(0.08333333333333333), a[22], r);
+    r = cg_fma(T(0.08333333333333333), a[23], r);
+    r = cg_fma(T(0.08333333333333333), a[24], r);
+    s = cg_fma(a[21], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.003125), a[22], r);
+    r = cg_fma(T(0.003472222222222222), a[23], r);
+    r = cg_fma(T(0.003472222222222222), a[24], r);
+    s = cg_fma(a[22], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.010069444444444445), a[23], r);
+    r = cg_fma(T(0.003472222222222222), a[24], r);
+    s = cg_fma(a[23], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.010069444444444445), a[24], r);
+    s = cg_fma(a[24], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.16666666666666666), a[25], r);
+    r = cg_fma(T(0.011111111111111112), a[26], r);
+    r = cg_fma(T(0.013888888888888888), a[27], r);
+    r = cg_fma(T(0.011111111111111112), a[28], r);
+    s = cg_fma(a[25], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0003224206349206349), a[26], r);
+    r = cg_fma(T(0.000462962962962963), a[27], r);
+    r = cg_fma(T(0.00034722222222222224), a[28], r);
+    s = cg_fma(a[26], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.001099537037037037), a[27], r);
+    r = cg_fma(T(0.000462962962962963), a[28], r);
+    s = cg_fma(a[27], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0003224206349206349), a[28], r);
+    s = cg_fma(a[28], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.16666666666666666), a[29], r);
+    r = cg_fma(T(0.011111111111111112), a[30], r);
+    r = cg_fma(T(0.011111111111111112), a[31], r);
+    r = cg_fma(T(0.013888888888888888), a[32], r);
+    s = cg_fma(a[29], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0003224206349206349), a[30], r);
+    r = cg_fma(T(0.00034722222222222224), a[31], r);
+    r = cg_fma(T(0.000462962962962963), a[32], r);
+    s = cg_fma(a[30], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.0003224206349206349), a[31], r);
+    r = cg_fma(T(0.000462962962962963), a[32], r);
+    s = cg_fma(a[31], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.001099537037037037), a[32], r);
+    s = cg_fma(a[32], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(0.020833333333333332), a[33], r);
+    s = cg_fma(a[33], r, s); }
+  return s;
+}
+
+template <typename T>
+CGKS_HD T gen_ist_3d(const T* __restrict__ a) {
+  T s = T(0);
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[0], r);
+    r = cg_fma(T(0.08333333333333333), a[3], r);
+    r = cg_fma(T(0.08333333333333333), a[4], r);
+    r = cg_fma(T(0.08333333333333333), a[5], r);
+    s = cg_fma(a[0], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[1], r);
+    r = cg_fma(T(0.08333333333333333), a[4], r);
+    r = cg_fma(T(0.08333333333333333), a[6], r);
+    r = cg_fma(T(0.08333333333333333), a[7], r);
+    s = cg_fma(a[1], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[2], r);
+    r = cg_fma(T(0.08333333333333333), a[5], r);
+    r = cg_fma(T(0.08333333333333333), a[7], r);
+    r = cg_fma(T(0.08333333333333333), a[8], r);
+    s = cg_fma(a[2], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[3], r);
+    r = cg_fma(T(0.003472222222222222), a[4], r);
+    r = cg_fma(T(0.003472222222222222), a[5], r);
+    s = cg_fma(a[3], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.179861111111111), a[4], r);
+    r = cg_fma(T(0.003472222222222222), a[5], r);
+    r = cg_fma(T(0.003472222222222222), a[6], r);
+    r = cg_fma(T(0.003472222222222222), a[7], r);
+    s = cg_fma(a[4], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.179861111111111), a[5], r);
+    r = cg_fma(T(0.003472222222222222), a[7], r);
+    r = cg_fma(T(0.003472222222222222), a[8], r);
+    s = cg_fma(a[5], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[6], r);
+    r = cg_fma(T(0.003472222222222222), a[7], r);
+    s = cg_fma(a[6], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.179861111111111), a[7], r);
+    r = cg_fma(T(0.003472222222222222), a[8], r);
+    s = cg_fma(a[7], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[8], r);
+    s = cg_fma(a[8], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[10], r);
+    s = cg_fma(a[10], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[11], r);
+    s = cg_fma(a[11], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[12], r);
+    s = cg_fma(a[12], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[14], r);
+    s = cg_fma(a[14], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[15], r);
+    s = cg_fma(a[15], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[16], r);
+    s = cg_fma(a[16], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[17], r);
+    r = cg_fma(T(0.08333333333333333), a[18], r);
+    r = cg_fma(T(0.08333333333333333), a[19], r);
+    r = cg_fma(T(0.08333333333333333), a[20], r);
+    s = cg_fma(a[17], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.2739583333333333), a[18], r);
+    r = cg_fma(T(0.003472222222222222), a[19], r);
+    r = cg_fma(T(0.003472222222222222), a[20], r);
+    s = cg_fma(a[18], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[19], r);
+    r = cg_fma(T(0.003472222222222222), a[20], r);
+    s = cg_fma(a[19], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[20], r);
+    s = cg_fma(a[20], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[22], r);
+    s = cg_fma(a[22], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[23], r);
+    s = cg_fma(a[23], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[24], r);
+    s = cg_fma(a[24], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[25], r);
+    r = cg_fma(T(0.08333333333333333), a[26], r);
+    r = cg_fma(T(0.08333333333333333), a[27], r);
+    r = cg_fma(T(0.08333333333333333), a[28], r);
+    s = cg_fma(a[25], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[26], r);
+    r = cg_fma(T(0.003472222222222222), a[27], r);
+    r = cg_fma(T(0.003472222222222222), a[28], r);
+    s = cg_fma(a[26], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.2739583333333333), a[27], r);
+    r = cg_fma(T(0.003472222222222222), a[28], r);
+    s = cg_fma(a[27], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[28], r);
+    s = cg_fma(a[28], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[29], r);
+    r = cg_fma(T(0.08333333333333333), a[30], r);
+    r = cg_fma(T(0.08333333333333333), a[31], r);
+    r = cg_fma(T(0.08333333333333333), a[32], r);
+    s = cg_fma(a[29], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[30], r);
+    r = cg_fma(T(0.003472222222222222), a[31], r);
+    r = cg_fma(T(0.003472222222222222), a[32], r);
+    s = cg_fma(a[30], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[31], r);
+    r = cg_fma(T(0.003472222222222222), a[32], r);
+    s = cg_fma(a[31], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.2739583333333333), a[32], r);
+    s = cg_fma(a[32], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.25), a[33], r);
+    s = cg_fma(a[33], r, s); }
+  return s;
+}
+
+template <typename T>
+CGKS_HD T gen_ista_3d(const T* __restrict__ a) {
+  T s = T(0);
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[0], r);
+    r = cg_fma(T(0.08333333333333333), a[3], r);
+    r = cg_fma(T(0.08333333333333333), a[4], r);
+    r = cg_fma(T(0.08333333333333333), a[5], r);
+    s = cg_fma(a[0], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[1], r);
+    r = cg_fma(T(0.08333333333333333), a[4], r);
+    r = cg_fma(T(0.08333333333333333), a[6], r);
+    r = cg_fma(T(0.08333333333333333), a[7], r);
+    s = cg_fma(a[1], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[2], r);
+    r = cg_fma(T(0.08333333333333333), a[5], r);
+    r = cg_fma(T(0.08333333333333333), a[7], r);
+    r = cg_fma(T(0.08333333333333333), a[8], r);
+    s = cg_fma(a[2], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[3], r);
+    r = cg_fma(T(0.003472222222222222), a[4], r);
+    r = cg_fma(T(0.003472222222222222), a[5], r);
+    s = cg_fma(a[3], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.179861111111111), a[4], r);
+    r = cg_fma(T(0.003472222222222222), a[5], r);
+    r = cg_fma(T(0.003472222222222222), a[6], r);
+    r = cg_fma(T(0.003472222222222222), a[7], r);
+    s = cg_fma(a[4], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.179861111111111), a[5], r);
+    r = cg_fma(T(0.003472222222222222), a[7], r);
+    r = cg_fma(T(0.003472222222222222), a[8], r);
+    s = cg_fma(a[5], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[6], r);
+    r = cg_fma(T(0.003472222222222222), a[7], r);
+    s = cg_fma(a[6], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.179861111111111), a[7], r);
+    r = cg_fma(T(0.003472222222222222), a[8], r);
+    s = cg_fma(a[7], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0864583333333333), a[8], r);
+    s = cg_fma(a[8], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[10], r);
+    s = cg_fma(a[10], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[11], r);
+    s = cg_fma(a[11], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[12], r);
+    s = cg_fma(a[12], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[14], r);
+    s = cg_fma(a[14], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[15], r);
+    s = cg_fma(a[15], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[16], r);
+    s = cg_fma(a[16], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[17], r);
+    r = cg_fma(T(0.08333333333333333), a[18], r);
+    r = cg_fma(T(0.08333333333333333), a[19], r);
+    r = cg_fma(T(0.08333333333333333), a[20], r);
+    s = cg_fma(a[17], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.2739583333333333), a[18], r);
+    r = cg_fma(T(0.003472222222222222), a[19], r);
+    r = cg_fma(T(0.003472222222222222), a[20], r);
+    s = cg_fma(a[18], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[19], r);
+    r = cg_fma(T(0.003472222222222222), a[20], r);
+    s = cg_fma(a[19], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[20], r);
+    s = cg_fma(a[20], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0833333333333333), a[22], r);
+    s = cg_fma(a[22], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[23], r);
+    s = cg_fma(a[23], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1666666666666667), a[24], r);
+    s = cg_fma(a[24], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[25], r);
+    r = cg_fma(T(0.08333333333333333), a[26], r);
+    r = cg_fma(T(0.08333333333333333), a[27], r);
+    r = cg_fma(T(0.08333333333333333), a[28], r);
+    s = cg_fma(a[25], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[26], r);
+    r = cg_fma(T(0.003472222222222222), a[27], r);
+    r = cg_fma(T(0.003472222222222222), a[28], r);
+    s = cg_fma(a[26], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.2739583333333333), a[27], r);
+    r = cg_fma(T(0.003472222222222222), a[28], r);
+    s = cg_fma(a[27], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[28], r);
+    s = cg_fma(a[28], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.0), a[29], r);
+    r = cg_fma(T(0.08333333333333333), a[30], r);
+    r = cg_fma(T(0.08333333333333333), a[31], r);
+    r = cg_fma(T(0.08333333333333333), a[32], r);
+    s = cg_fma(a[29], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[30], r);
+    r = cg_fma(T(0.003472222222222222), a[31], r);
+    r = cg_fma(T(0.003472222222222222), a[32], r);
+    s = cg_fma(a[30], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.1767361111111112), a[31], r);
+    r = cg_fma(T(0.003472222222222222), a[32], r);
+    s = cg_fma(a[31], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.2739583333333333), a[32], r);
+    s = cg_fma(a[32], r, s); }
+  { T r = T(0);
+    r = cg_fma(T(1.25), a[33], r);
+    s = cg_fma(a[33], r, s); }
+  return s;
+}
+
+template <typename T>
+CGKS_HD T gen_isla_3d(const T* __restrict__ a) {
   T s = T(0);
   { T r = T(0);
     r = cg_fma(T(0.08333333333333333), a[0], r);

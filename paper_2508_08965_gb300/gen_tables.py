@@ -672,7 +672,12 @@ def emit_recon_code(path):
         # Gram quadratic forms (block diagonal by class)
         GH = [[float(x) for x in row] for row in t["GH"]]
         GL = [[float(x) for x in row] for row in t["GL"]]
-        for name, Gm in (("ish", GH), ("isl", GL)):
+        # the higher-derivative part GH - GL (exact in rational arithmetic) and
+        # the entrywise absolute values, for the FP32 screen of the FP64 path
+        GT = [[float(t["GH"][i][j] - t["GL"][i][j]) for j in range(nb)] for i in range(nb)]
+        GTA = [[abs(x) for x in row] for row in GT]
+        GLA = [[abs(x) for x in row] for row in GL]
+        for name, Gm in (("ish", GH), ("isl", GL), ("ist", GT), ("ista", GTA), ("isla", GLA)):
             fn.append("template <typename T>")
             fn.append("CGKS_HD T gen_%s_%dd(const T* __restrict__ a) {" % (name, dim))
             fn.append("  T s = T(0);")
