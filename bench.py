@@ -36,14 +36,14 @@ WORKLOADS = {
 # FP64 work per unit of the two compute kernels, from the executed FP64
 # instructions of an ncu capture (TGV 64^3, same kernels): flops = 2 DFMA +
 # DADD + DMUL (division, sqrt and the special functions enter through the
-# instructions they execute).  recon: per cell; flux: per face Gauss point.
+# instructions they execute); flux: per face Gauss point.  The FP64
+# reconstruction is not listed: since its FP32 screen of the smoothness
+# indicators, its FP64 work per cell depends on the data.
 FLOPS_PER_UNIT = {
-    ("recon", 3): 1.249e4,
     ("flux", 3): 3.616e3,
 }
 # DRAM bytes per unit of the same capture (read + write), for `traffic`
 DRAM_BYTES_PER_UNIT = {
-    ("recon", 3): (0.3039e9 + 1.0170e9) / 262144,
     ("flux", 3): (1.0110e9 + 0.7142e9) / (262144 * 12),
 }
 # the same for the FP32 form (flops = 2 FFMA + FADD + FMUL; ncu, TGV 64^3);

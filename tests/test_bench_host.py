@@ -1,0 +1,85 @@
+"""Host logic of bench.py, without a GPU: the reference arm (the CPU oracle)
+prints one JSON line with the keys the benchmark line carries and only rank 0
+prints it; the roofline arithmetic of the dominant kernel; the clock sample
+summary."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module")
+def bench():
+    import bench as b
+    return b
+
+
+def _run_reference(env_extra):
+    env = dict(os.environ, OMP_NUM_THREADS="4", **env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                           "--workload", "vortex64", "--steps", "2", "--warmup", "1"],
+                          capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+
+
+def test_reference_arm_line(orc):
+    r = _run_reference({})
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "cell-updates/s per S2O4 step"
+    assert d["unit"] == "cell-updates/s" and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["config"]["workload"] == "vortex64"
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == 4 and cb["sample"]
+    # value = cells x steps / time
+    assert abs(d["value"] * d["ms_per_step"] / 1e3 - 64 * 64) < 1e-6 * 64 * 64
+
+
+def test_reference_arm_other_ranks_print_nothing(orc):
+    r = _run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_roofline_dominant_kernel(bench):
+    n = 128 ** 3
+    prof = {"recon": (10, 259.0), "flux": (10, 1028.0), "update": (10, 30.8), "dt": (5, 0.35)}
+    r = bench.roofline(prof, bench.WORKLOADS["tgv128"], n, 0)
+    assert r["kernel"] == "flux" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    units = n * 3 * 4                       # 12 face Gauss points owned per cell in 3-D
+    assert r["flops_per_launch"] == pytest.approx(3.616e3 * units)
+    assert r["achieved"] == pytest.approx(3.616e3 * units / 0.1028 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] == pytest.approx((1.0110e9 + 0.7142e9) * 8)   # 64^3 capture scaled to 128^3
+
+
+def test_roofline_uncounted_kernel(bench):
+    """a dominant kernel without a counted flop figure reports no fraction"""
+    r = bench.roofline({"recon": (2, 100.0), "flux": (2, 50.0)}, bench.WORKLOADS["tgv128"], 128 ** 3, 0)
+    assert r["kernel"] == "recon" and r["achieved"] is None and r["frac"] is None and "note" in r
+
+
+def test_roofline_fp32_update_units(bench):
+    n = 64 * 64 * 64
+    r = bench.roofline({"update": (4, 4.0)}, bench.WORKLOADS["tgv64"], n, 1)
+    assert r["kernel"] == "update"
+    assert r["flops_per_launch"] == pytest.approx(158.0 * n * 5)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+
+
+def test_clock_summary(bench):
+    s = bench.ClockSampler(0)
+    s.rows = [["0", "2070", "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+              ["0", "1980", "2070", "1400", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+              ["0", "2070", "2070", "1100", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+              ["0", "[N/A]", "2070"]]
+    out = s.summary()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
