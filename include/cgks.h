@@ -125,6 +125,21 @@ cgks_status cgks_set_state(cgks_ctx* ctx, const double* src, int is_device, doub
 /* Copy the state out; *t (may be NULL) receives the time.  Synchronises. */
 cgks_status cgks_get_state(cgks_ctx* ctx, double* dst, int is_device, double* t);
 
+/* The same two copies, enqueued on the context's stream without waiting,
+   so that the copies of one context overlap the steps of another (each on
+   its own stream).  Stream order keeps them in sequence with this context's
+   steps.  The caller keeps src valid and unmodified, and does not read dst,
+   until cgks_sync returns (or a later synchronising call on this context:
+   cgks_step, cgks_get_state, cgks_set_state from host memory).  Host
+   buffers should be page-locked (cudaHostAlloc, cudaHostRegister); copies
+   from or to pageable memory are made synchronously by CUDA.  Sets the time
+   to t; cgks_get_state_async does not report it.  A copy error may only
+   show at the next synchronising call. */
+cgks_status cgks_set_state_async(cgks_ctx* ctx, const double* src, int is_device, double t);
+cgks_status cgks_get_state_async(cgks_ctx* ctx, double* dst, int is_device);
+/* Wait until everything enqueued on the context's stream has finished. */
+cgks_status cgks_sync(cgks_ctx* ctx);
+
 /* Advance nsteps S2O4 steps.  t_end > 0 shortens the last step so that the
    time does not pass t_end (and stops there).  t_out / dt_last may be NULL.
    Returns CGKS_ENONPHYS if a state became non-physical (the state is then

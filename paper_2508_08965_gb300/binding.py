@@ -82,7 +82,8 @@ class BatchTiles(C.Structure):
 
 
 EXPORTS = ["cgks_create_mesh", "cgks_destroy", "cgks_num_vars", "cgks_num_fields", "cgks_num_cells",
-           "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_compute_dt", "cgks_init_points_per_cell",
+           "cgks_set_state", "cgks_get_state", "cgks_set_state_async", "cgks_get_state_async", "cgks_sync",
+           "cgks_step", "cgks_compute_dt", "cgks_init_points_per_cell",
            "cgks_init_points", "cgks_init_from_prims", "cgks_get_chi", "cgks_profile_enable",
            "cgks_profile_read", "cgks_last_error", "cgks_compute_dt_noalloc", "cgks_batch_create",
            "cgks_batch_destroy", "cgks_batch_num_cases", "cgks_batch_num_cells", "cgks_batch_set_state",
@@ -115,6 +116,9 @@ def lib(build_if_missing=True):
     L.cgks_num_cells.restype = C.c_long
     L.cgks_set_state.argtypes = [vp, vp, C.c_int, C.c_double]
     L.cgks_get_state.argtypes = [vp, vp, C.c_int, dp]
+    L.cgks_set_state_async.argtypes = [vp, vp, C.c_int, C.c_double]
+    L.cgks_get_state_async.argtypes = [vp, vp, C.c_int]
+    L.cgks_sync.argtypes = [vp]
     L.cgks_step.argtypes = [vp, C.c_int, C.c_double, dp, dp]
     L.cgks_compute_dt.argtypes = [vp, dp]
     L.cgks_init_points_per_cell.argtypes = [vp]
@@ -207,6 +211,7 @@ class Mesh:
         d.stream = C.c_void_p(self.stream.cuda_stream)
         h = C.c_void_p()
         self._h = None
+        self._pending = []  # host or device buffers of enqueued copies, kept alive until a sync
         self._check(L.cgks_create_mesh(C.byref(d), C.byref(h)))
         self._h = h
         self.dim = dim
@@ -227,8 +232,11 @@ class Mesh:
 
     def close(self):
         if self._h:
+            if self._pending:
+                lib().cgks_sync(self._h)
             lib().cgks_destroy(self._h)
             self._h = None
+            self._pending = []
 
     def __del__(self):
         try:
@@ -259,14 +267,56 @@ class Mesh:
         t = C.c_double(0)
         if out is not None and isinstance(out, torch.Tensor) and out.is_cuda:
             self._check(lib().cgks_get_state(self._h, C.c_void_p(out.data_ptr()), 1, C.byref(t)))
+            self._pending = []
             return out, t.value
         a = np.empty(self.state_shape) if out is None else out
         self._check(lib().cgks_get_state(self._h, a.ctypes.data_as(C.c_void_p), 0, C.byref(t)))
+        self._pending = []
         return a, t.value
+
+    @staticmethod
+    def _buffer(a, writable):
+        """(pointer, is_device, keep-alive) of a torch tensor (CUDA, or CPU,
+        best page-locked) or a numpy array, in the public layout, float64"""
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise ValueError("state buffers are contiguous float64")
+            return a.data_ptr(), int(a.is_cuda), a
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise ValueError("state buffers are contiguous float64")
+        if writable and not a.flags.writeable:
+            raise ValueError("read-only output buffer")
+        return a.ctypes.data, 0, a
+
+    def set_state_async(self, s, t=0.0):
+        """Enqueue the copy of state s in (no wait); s must stay valid and
+        unchanged until sync() (or step(), get_state())."""
+        p, dev, keep = self._buffer(s, False)
+        n = keep.size if isinstance(keep, np.ndarray) else keep.numel()
+        if n != self.nf * self.nv * self.ncell:
+            raise ValueError("state of the wrong size")
+        self._check(lib().cgks_set_state_async(self._h, C.c_void_p(p), dev, float(t)))
+        self._pending.append(keep)
+
+    def get_state_async(self, out):
+        """Enqueue the copy of the state out into `out` (no wait); read it
+        after sync()."""
+        p, dev, keep = self._buffer(out, True)
+        n = keep.size if isinstance(keep, np.ndarray) else keep.numel()
+        if n != self.nf * self.nv * self.ncell:
+            raise ValueError("output buffer of the wrong size")
+        self._check(lib().cgks_get_state_async(self._h, C.c_void_p(p), dev))
+        self._pending.append(keep)
+
+    def sync(self):
+        self._check(lib().cgks_sync(self._h))
+        self._pending = []
 
     def step(self, nsteps=1, t_end=0.0):
         t, dt = C.c_double(0), C.c_double(0)
         self._check(lib().cgks_step(self._h, int(nsteps), float(t_end), C.byref(t), C.byref(dt)))
+        self._pending = []
         return t.value, dt.value
 
     def advance_to(self, t_end, max_steps=10 ** 7):

@@ -297,27 +297,55 @@ int cgks_num_vars(const cgks_ctx* ctx) { return ctx ? ctx->nv : -1; }
 int cgks_num_fields(const cgks_ctx* ctx) { return ctx ? ctx->nf : -1; }
 long cgks_num_cells(const cgks_ctx* ctx) { return ctx ? ctx->ncell : -1; }
 
-cgks_status cgks_set_state(cgks_ctx* ctx, const double* src, int is_device, double t) {
-  if (!ctx || !src) return CGKS_EINVAL;
+/* the copy in, the FP32 split and a fresh time-step record, enqueued on the
+   context's stream without waiting */
+static cgks_status enqueue_set(cgks_ctx* ctx, const double* src, int is_device, double t) {
   size_t sz = sizeof(double) * (size_t)ctx->nf * ctx->nv * ctx->ncell;
   CK(cudaMemcpyAsync(ctx->U, src, sz, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
   cgks_status r0 = split_in(ctx);
   if (r0 != CGKS_OK) return r0;
+  k_dt_init<<<1, 1, 0, ctx->stream>>>(ctx->dts, t, ctx->desc.dt_fixed);
+  CK(cudaGetLastError());
   ctx->t = t;
-  DtState init{};
-  init.t = t;
-  init.dt_fixed = ctx->desc.dt_fixed;
-  CK(cudaMemcpyAsync(ctx->dts, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+  return CGKS_OK;
+}
+/* the FP32 join and the copy out, enqueued without waiting */
+static cgks_status enqueue_get(cgks_ctx* ctx, double* dst, int is_device) {
+  size_t sz = sizeof(double) * (size_t)ctx->nf * ctx->nv * ctx->ncell;
+  cgks_status r0 = join_out(ctx);
+  if (r0 != CGKS_OK) return r0;
+  CK(cudaMemcpyAsync(dst, ctx->U, sz, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  return CGKS_OK;
+}
+
+cgks_status cgks_set_state(cgks_ctx* ctx, const double* src, int is_device, double t) {
+  if (!ctx || !src) return CGKS_EINVAL;
+  cgks_status r0 = enqueue_set(ctx, src, is_device, t);
+  if (r0 != CGKS_OK) return r0;
   if (!is_device) CK(cudaStreamSynchronize(ctx->stream));
+  return CGKS_OK;
+}
+
+cgks_status cgks_set_state_async(cgks_ctx* ctx, const double* src, int is_device, double t) {
+  if (!ctx || !src) return CGKS_EINVAL;
+  return enqueue_set(ctx, src, is_device, t);
+}
+
+cgks_status cgks_get_state_async(cgks_ctx* ctx, double* dst, int is_device) {
+  if (!ctx || !dst) return CGKS_EINVAL;
+  return enqueue_get(ctx, dst, is_device);
+}
+
+cgks_status cgks_sync(cgks_ctx* ctx) {
+  if (!ctx) return CGKS_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
   return CGKS_OK;
 }
 
 cgks_status cgks_get_state(cgks_ctx* ctx, double* dst, int is_device, double* t) {
   if (!ctx || !dst) return CGKS_EINVAL;
-  size_t sz = sizeof(double) * (size_t)ctx->nf * ctx->nv * ctx->ncell;
-  cgks_status r0 = join_out(ctx);
+  cgks_status r0 = enqueue_get(ctx, dst, is_device);
   if (r0 != CGKS_OK) return r0;
-  CK(cudaMemcpyAsync(dst, ctx->U, sz, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   DtState h;
   CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

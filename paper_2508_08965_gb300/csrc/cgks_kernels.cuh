@@ -403,6 +403,15 @@ static __global__ void k_dt_final(Phys ph, DtState* dts, int* st) {
 }
 
 static __global__ void k_time_advance(DtState* dts) { dts->t += dts->dt; }
+/* a fresh time-step record at time t (dt_fixed > 0: that step, else CFL);
+   a kernel rather than a copy from host memory, so that setting a state
+   never waits for the stream */
+static __global__ void k_dt_init(DtState* dts, double t, double dt_fixed) {
+  DtState d{};
+  d.t = t;
+  d.dt_fixed = dt_fixed;
+  *dts = d;
+}
 
 /* ------------------------------------------------------------------ */
 /* metrics from node coordinates (Sec. 4 J0, Appendix volume)           */
