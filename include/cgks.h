@@ -51,7 +51,7 @@ typedef enum {
   CGKS_ENONPHYS = -4,    /* non-positive density/pressure that even chi = 0 cannot cure */
   CGKS_ETIMEOUT = -5,    /* reserved: a bounded device wait gave up */
   CGKS_ESTATE = -6,      /* call made in the wrong state */
-  CGKS_EUNSUPPORTED = -7, /* option not available in this build */
+  CGKS_EUNSUPPORTED = -7, /* option the library does not support */
   CGKS_ETOOLARGE = -8     /* problem larger than a fixed-size buffer of the library */
 } cgks_status;
 
