@@ -209,10 +209,27 @@ def cpu_baseline(wl, sample_cells=None):
     orc.step(steps)
     el = time.perf_counter() - t0
     ncell = int(math.prod(n))
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": ncell * steps / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
-            "sample": "%s on %s (%d cells, same per-cell work), %d S2O4 steps, %.1f s" % (
-                spec["desc"].split(",")[0], "x".join(map(str, n)), ncell, steps, el)}
+    threads = o.set_threads(0)
+    out = {"value": ncell * steps / el, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+           "sample": "%s on %s (%d cells, same per-cell work), %d S2O4 steps, %.1f s" % (
+               spec["desc"].split(",")[0], "x".join(map(str, n)), ncell, steps, el)}
+    # the same on one core, on a smaller sample
+    n1 = (12, 12, 12) if dim == 3 else (32, 32)
+    o1 = o.Oracle(dim, n1, **kw)
+    o1.init(field_fn(wl))
+    o.set_threads(1)
+    try:
+        o1.step(1)
+        steps1 = 2 if dim == 3 else 10
+        t0 = time.perf_counter()
+        o1.step(steps1)
+        el1 = time.perf_counter() - t0
+    finally:
+        o.set_threads(threads)
+    nc1 = int(math.prod(n1))
+    out["single_core"] = {"value": nc1 * steps1 / el1, "unit": "cell-updates/s", "cores": 1,
+                          "sample": "%s cells, %d S2O4 steps, %.1f s" % ("x".join(map(str, n1)), steps1, el1)}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -237,7 +254,7 @@ def run_reference(args, rank, world):
     tot = sum(times)
     ncell = int(math.prod(n))
     val = ncell * args.steps / tot
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = o.set_threads(0)
     line = {
         "impl": "reference", "metric": "cell-updates/s per S2O4 step", "value": val, "unit": "cell-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,

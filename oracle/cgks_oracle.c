@@ -16,6 +16,9 @@
 #include <stdlib.h>
 #include <stdint.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define NB3 34 /* quartic zero-mean basis size in 3-D (Eq. base, 1 <= |d| <= 4) */
 #define ND3 73 /* data vector size in 3-D (Eq. stencil-5) */
@@ -1060,6 +1063,16 @@ int orc_get_metrics(const orc_ctx* c, double* vol, double* closure) {
     }
   }
   return 0;
+}
+
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */

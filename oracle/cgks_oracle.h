@@ -54,6 +54,9 @@ long orc_num_init_points(const orc_ctx* c);
 void orc_init_points(const orc_ctx* c, double* pts);          /* npts*dim */
 int orc_init_from_prims(orc_ctx* c, const double* prim);       /* npts*nv */
 double orc_compute_dt(orc_ctx* c);
+/* threads of the OpenMP loops from now on (n <= 0: unchanged); returns the
+   number in use.  Results do not depend on it. */
+int orc_set_threads(int n);
 int orc_step(orc_ctx* c, int nsteps, double* dt_last);
 /* one step with a given time step */
 int orc_step_dt(orc_ctx* c, double dt);

@@ -53,6 +53,7 @@ def lib():
         L.orc_num_init_points.argtypes = [C.c_void_p]
         L.orc_init_points.argtypes = [C.c_void_p, dp]
         L.orc_init_from_prims.argtypes = [C.c_void_p, dp]
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_compute_dt.restype = C.c_double
         L.orc_compute_dt.argtypes = [C.c_void_p]
         L.orc_step.argtypes = [C.c_void_p, C.c_int, dp]
@@ -83,6 +84,12 @@ def lib():
         L.orc_s2o4_stage2.argtypes = [C.c_double] * 5
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Threads of the oracle's OpenMP loops from now on (n <= 0: unchanged);
+    returns the number in use.  Results do not depend on it."""
+    return lib().orc_set_threads(int(n))
 
 
 def _p(a):

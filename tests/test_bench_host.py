@@ -83,3 +83,22 @@ def test_clock_summary(bench):
               ["0", "[N/A]", "2070"]]
     out = s.summary()
     assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_oracle_threads_do_not_change_results(orc):
+    """the single-core baseline times the same arithmetic: one thread and
+    all threads give the same state bit for bit"""
+    import numpy as np
+    import synth
+    full = orc.set_threads(0)
+    res = []
+    for th in (1, full):
+        orc.set_threads(th)
+        assert orc.set_threads(0) == th
+        o = orc.Oracle(3, (6, 5, 7), lo=(0, 0, 0), hi=(6.283185307179586,) * 3, mu=1 / 1600, prandtl=0.72,
+                       tau_mode=2)
+        o.init(lambda x, y, z: synth.taylor_green_3d(x, y, z))
+        o.step(2)
+        res.append(o.get_state())
+    orc.set_threads(full)
+    assert np.array_equal(res[0], res[1])
