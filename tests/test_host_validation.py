@@ -86,3 +86,25 @@ def test_batch_rejects_mixed_and_invalid_cases(cg):
     assert L.cgks_batch_create(None, 1, None, C.byref(h)) == EINVAL
     arr = (cg.MeshDesc * 1)(ok)
     assert L.cgks_batch_create(arr, 0, None, C.byref(h)) == EINVAL
+
+
+def test_async_copy_buffers(cg):
+    """the binding's checks on the buffers of the asynchronous copies"""
+    import numpy as np
+    import torch
+    buf = cg.Mesh._buffer
+    a = np.zeros((3, 4))
+    p, dev, keep = buf(a, True)
+    assert p == a.ctypes.data and dev == 0 and keep is a
+    t = torch.zeros(12, dtype=torch.float64)
+    p, dev, keep = buf(t, False)
+    assert p == t.data_ptr() and dev == 0 and keep is t
+    for bad in (np.zeros(4, dtype=np.float32), np.zeros((4, 4))[:, 1], torch.zeros(4, dtype=torch.float32),
+                torch.zeros((4, 4), dtype=torch.float64)[:, 1], [0.0] * 4):
+        with pytest.raises(ValueError):
+            buf(bad, False)
+    ro = np.zeros(4)
+    ro.flags.writeable = False
+    assert buf(ro, False)[2] is ro
+    with pytest.raises(ValueError):
+        buf(ro, True)
