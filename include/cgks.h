@@ -102,7 +102,12 @@ typedef struct {
   double c_chi;         /* GENO path-function constant C (<= 0: default 100) */
   int precision;        /* 0: FP64 throughout; 1: reconstruction, interface flux,
                            weights and derivative fields in FP32, cell averages
-                           (accumulated across the S2O4 stages) and metrics in FP64 */
+                           (accumulated across the S2O4 stages) and metrics in FP64;
+                           2: as 0, with the GKS solve of the interior face Gauss
+                           points in paired-FP32 arithmetic (hi + lo floats, about
+                           48 bits; exp, erfc, sqrt in FP64), uniform boxes only
+                           (nodes != NULL: CGKS_EUNSUPPORTED); other values:
+                           CGKS_EUNSUPPORTED.  Batches take 0 or 1. */
   void* stream;         /* cudaStream_t to queue work on; NULL = default stream */
 } cgks_mesh_desc;
 

@@ -123,7 +123,8 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   if (d->dim != 2 && d->dim != 3) return CGKS_EINVAL;
   for (int a = 0; a < d->dim; ++a)
     if (d->n[a] < 3) return CGKS_EINVAL;
-  if (d->precision != 0 && d->precision != 1) return CGKS_EUNSUPPORTED;
+  if (d->precision < 0 || d->precision > 2) return CGKS_EUNSUPPORTED;
+  if (d->precision == 2 && d->nodes) return CGKS_EUNSUPPORTED; /* the paired form is Cartesian only */
   for (int f = 0; f < 2 * d->dim; ++f) {
     if (d->bc[f] < CGKS_BC_PERIODIC || d->bc[f] > CGKS_BC_INFLOW) return CGKS_EINVAL;
     if ((d->bc[f] == CGKS_BC_PERIODIC) != (d->bc[f ^ 1] == CGKS_BC_PERIODIC)) return CGKS_EINVAL;
@@ -142,7 +143,8 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   ctx->n[2] = d->dim == 3 ? d->n[2] : 1;
   ctx->ncell = (long)ctx->n[0] * ctx->n[1] * ctx->n[2];
   ctx->stream = (cudaStream_t)d->stream;
-  ctx->prec = d->precision;
+  ctx->prec = d->precision == 1 ? 1 : 0;
+  ctx->pair_flux = d->precision == 2;
   ctx->ph.gamma = d->gamma;
   ctx->ph.mu = d->mu;
   ctx->ph.prandtl = d->prandtl > 0.0 ? d->prandtl : 1.0;

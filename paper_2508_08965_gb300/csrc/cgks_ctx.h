@@ -35,6 +35,7 @@ struct cgks_ctx {
   long ncell;
   int prec;                 /* 0: FP64; 1: FP32 bulk with FP64 averages */
   bool walls;               /* some face is a wall: reconstruction with mirror images */
+  bool pair_flux;           /* FP64 storage, interface flux solved in paired FP32 (precision 2) */
   cgks_mesh_desc desc;
   cudaStream_t stream;
   cgks::DevGeo geo;
@@ -118,5 +119,13 @@ void launch_stage(cgks_ctx* ctx, int stage);
   extern template void launch_stage<T, 3, true, false>(cgks_ctx*, int);
 CGKS_DECLARE_STAGES(float)
 CGKS_DECLARE_STAGES(double)
+
+/* the interface flux of the paired form: FP64 Gauss-point states in, the
+   GKS solve in paired-FP32 arithmetic, FP64 fluxes out; Cartesian meshes.
+   Instantiated in cgks_stage_pair.cu. */
+template <int DIM>
+void launch_flux_pair(cgks_ctx* ctx, const double* gpL, const double* gpR, double* flux);
+extern template void launch_flux_pair<2>(cgks_ctx*, const double*, const double*, double*);
+extern template void launch_flux_pair<3>(cgks_ctx*, const double*, const double*, double*);
 
 #endif

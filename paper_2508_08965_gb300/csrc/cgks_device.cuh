@@ -328,6 +328,7 @@ CGKS_HD double cg_fabs(double x) { return fabs(x); }
 CGKS_HD float cg_fabs(float x) { return fabsf(x); }
 CGKS_HD double cg_fma(double a, double b, double c) { return fma(a, b, c); }
 CGKS_HD float cg_fma(float a, float b, float c) { return fmaf(a, b, c); }
+#include "cgks_pair.cuh"
 CGKS_HD double cg_tanh(double x) { return tanh(x); }
 CGKS_HD float cg_tanh(float x) { return tanhf(x); }
 
@@ -1152,18 +1153,18 @@ CGKS_HD bool gks_point(const Phys& ph, T dt, const T* WL, const T* dWL, const T*
    [(base + q) * N + c]: the global face-major arrays (base of the face, N =
    cells, c = slot), or a thread's staged copy in shared memory (base 0, N =
    the block size, c = the thread) */
-template <typename T, int DIM> struct CartLd {
+template <typename T, int DIM, typename C = T> struct CartLd {
   const T* gl;
   const T* gr;
   long base, N, c;
   int p[3], s[3];
-  CGKS_HD void grad(int side, int j, T* o) const {
+  CGKS_HD void grad(int side, int j, C* o) const {
     const T* src = side == 0 ? gl : gr;
 #pragma unroll
     for (int v = 0; v < DIM + 2; ++v) {
       int vg = v, sv = 1;
       if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
-      o[v] = T(sv * s[j]) * src[(base + vg * (1 + DIM) + 1 + p[j]) * N + c];
+      o[v] = C(T(sv * s[j]) * src[(base + vg * (1 + DIM) + 1 + p[j]) * N + c]);
     }
   }
 };
@@ -1269,8 +1270,11 @@ CGKS_HD void to_global(const double R[3][3], T* F) {
    frames and general face frames.  Cartesian: with sm (this thread's slot of
    a [2][NV (1+DIM)][ns] shared array, ns = the block size) the point's two
    Gauss-point states are first copied there asynchronously, all 2 NV (1+DIM)
-   loads in flight at once, and the solve reads them from shared memory. */
-template <typename T, int DIM, bool CURVI>
+   loads in flight at once, and the solve reads them from shared memory.
+   C is the type the solve computes in: T, or fpair for the paired form
+   (Cartesian only), which converts the loaded states and rounds the
+   results back to T. */
+template <typename T, int DIM, bool CURVI, typename C = T>
 CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, long c,
                         const T* __restrict__ gpL, const T* __restrict__ gpR, T* __restrict__ flux,
                         T* sm = nullptr, int ns = 0) {
@@ -1278,12 +1282,12 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
   constexpr int NV = S::NV;
   const long N = g.ncell;
   const long base = (long)((ax * S::GPF + k) * NV) * (1 + DIM);
-  T WL[NV], WR[NV], out[6 * NV];
   if constexpr (!CURVI) {
     /* value and momentum: W_loc[1+i] = s_i m_{p_i}; derivative along local j:
        s_j d/dx_{p_j} of the local variable (loaded when its side needs it) */
     constexpr int NQ = NV * (1 + DIM);
-    CartLd<T, DIM> ld;
+    C WL[NV], WR[NV], out[6 * NV];
+    CartLd<T, DIM, C> ld;
     if (sm) {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
@@ -1311,10 +1315,10 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
       int vg = v, sv = 1;
       if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
       const long b = (ld.base + vg * (1 + DIM)) * ld.N + ld.c;
-      WL[v] = T(sv) * ld.gl[b];
-      WR[v] = T(sv) * ld.gr[b];
+      WL[v] = C(T(sv) * ld.gl[b]);
+      WR[v] = C(T(sv) * ld.gr[b]);
     }
-    bool ok = gks_point_ld<T, DIM>(ph, dt, WL, WR, ld, out);
+    bool ok = gks_point_ld<C, DIM>(ph, C(dt), WL, WR, ld, out);
     const long fb = (long)((ax * S::GPF + k) * 6) * NV;
 #pragma unroll
     for (int part = 0; part < 6; ++part) {
@@ -1322,11 +1326,13 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
       for (int v = 0; v < NV; ++v) {
         int vg = v, sv = 1;
         if (v >= 1 && v <= DIM) { vg = 1 + p[v - 1]; sv = s[v - 1]; }
-        flux[(fb + part * NV + vg) * N + c] = T(sv) * out[part * NV + v];
+        flux[(fb + part * NV + vg) * N + c] = T(sv) * to_storage<T>(out[part * NV + v]);
       }
     }
     return ok;
   } else {
+  static_assert(cg_same<C, T>::value, "the curvilinear path computes in its storage type");
+  T WL[NV], WR[NV], out[6 * NV];
   T dWL[DIM * NV], dWR[DIM * NV];
   T sl[NV * (1 + DIM)], sr[NV * (1 + DIM)];
   for (int q = 0; q < NV * (1 + DIM); ++q) {

@@ -173,7 +173,7 @@ __global__ void k_selector_features(const double* __restrict__ avg, const float*
 /* face-point item t = (ax * GPF + k) * N + c of a mesh: the face slot above
    cell c along ax at Gauss point k; slots on a non-periodic high boundary are
    left to the boundary items */
-template <typename T, int DIM, bool CURVI>
+template <typename T, int DIM, bool CURVI, typename C = T>
 __device__ __forceinline__ void flux_item(const DevGeo& g, const Phys& ph, double dt, long t, const T* __restrict__ gpL,
                                           const T* __restrict__ gpR, T* __restrict__ flux, int* __restrict__ st,
                                           T* sm = nullptr, int ns = 0) {
@@ -186,7 +186,7 @@ __device__ __forceinline__ void flux_item(const DevGeo& g, const Phys& ph, doubl
     cell_ijk(g, c, ijk[0], ijk[1], ijk[2]);
     if (ijk[ax] == g.n[ax] - 1) return;
   }
-  if (!flux_point<T, DIM, CURVI>(g, ph, T(dt), ax, k, c, gpL, gpR, flux, sm, ns)) atomicOr(&st[ST_FLUX], 1);
+  if (!flux_point<T, DIM, CURVI, C>(g, ph, T(dt), ax, k, c, gpL, gpR, flux, sm, ns)) atomicOr(&st[ST_FLUX], 1);
 }
 
 /* boundary face-point item t = ((side * DIM + ax) * GPF + k) * nplane + plane.
@@ -224,8 +224,9 @@ __device__ __forceinline__ void flux_bnd_item(const DevGeo& g, const Phys& ph, d
 }
 
 /* one thread per face slot and Gauss point (blocks of 128); the Cartesian
-   path stages each point's Gauss-point states in shared memory */
-template <typename T, int DIM, bool CURVI>
+   path stages each point's Gauss-point states in shared memory.  C: the
+   solve's compute type (fpair: the paired form, Cartesian FP64 storage) */
+template <typename T, int DIM, bool CURVI, typename C = T>
 __global__ void __launch_bounds__(128, flux_min_blocks<T, DIM, CURVI>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
                                               const T* __restrict__ gpL, const T* __restrict__ gpR,
                                               T* __restrict__ flux, int* __restrict__ st) {
@@ -236,9 +237,9 @@ __global__ void __launch_bounds__(128, flux_min_blocks<T, DIM, CURVI>()) k_flux(
   if (!(dt > 0.0)) return;
   if constexpr (!CURVI) {
     __shared__ T stage[2 * Sz<DIM>::NV * (1 + DIM) * 128];
-    flux_item<T, DIM, CURVI>(g, ph, dt, t, gpL, gpR, flux, st, stage + threadIdx.x, 128);
+    flux_item<T, DIM, CURVI, C>(g, ph, dt, t, gpL, gpR, flux, st, stage + threadIdx.x, 128);
   } else {
-    flux_item<T, DIM, CURVI>(g, ph, dt, t, gpL, gpR, flux, st);
+    flux_item<T, DIM, CURVI, C>(g, ph, dt, t, gpL, gpR, flux, st);
   }
 }
 

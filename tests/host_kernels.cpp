@@ -63,7 +63,7 @@ namespace {
 int g_bc[6] = {0, 0, 0, 0, 0, 0};
 double g_bcq[BCQ_DOUBLES] = {0};
 
-template <typename T, int DIM, bool CV>
+template <typename T, int DIM, bool CV, typename C = T>
 int run_stage(DevGeo& g, Phys& ph, double dt, int stage, double** avg, T** der, double* savg, T* sder,
               std::vector<T>& gpL, std::vector<T>& gpR, std::vector<T>& flux, float** avh, float** avl,
               std::vector<T>& fxb) {
@@ -82,7 +82,7 @@ int run_stage(DevGeo& g, Phys& ph, double dt, int stage, double** avg, T** der, 
   }
   for (long t = 0; t < (long)DIM * Sz<DIM>::GPF * N; ++t) {
     blockIdx.x = (unsigned)t;
-    k_flux<T, DIM, CV>(g, ph, &dts, gpL.data(), gpR.data(), flux.data(), st);
+    k_flux<T, DIM, CV, C>(g, ph, &dts, gpL.data(), gpR.data(), flux.data(), st);
   }
   for (long t = 0; t < 2L * DIM * Sz<DIM>::GPF * g.nplane; ++t) {
     blockIdx.x = (unsigned)t;
@@ -117,7 +117,7 @@ void geometry(DevGeo& g, const int* n, const double* lo, const double* hi) {
   }
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, typename C = T>
 int run(const int* n, const double* lo, const double* hi, const double* nodes, const double* phys, double* U,
         int nsteps, double* dt_out) {
   DevGeo g{};
@@ -159,11 +159,15 @@ int run(const int* n, const double* lo, const double* hi, const double* nodes, c
     }
     int bad = 0;
     if (g.curvi) {
-      bad |= run_stage<T, DIM, true>(g, ph, dt, 1, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
-      bad |= run_stage<T, DIM, true>(g, ph, dt, 2, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
+      if constexpr (cg_same<C, T>::value) {
+        bad |= run_stage<T, DIM, true>(g, ph, dt, 1, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
+        bad |= run_stage<T, DIM, true>(g, ph, dt, 2, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
+      } else {
+        return -7; /* the paired form is Cartesian only */
+      }
     } else {
-      bad |= run_stage<T, DIM, false>(g, ph, dt, 1, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
-      bad |= run_stage<T, DIM, false>(g, ph, dt, 2, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
+      bad |= run_stage<T, DIM, false, C>(g, ph, dt, 1, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
+      bad |= run_stage<T, DIM, false, C>(g, ph, dt, 2, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
     }
     if (bad) return -4;
     *dt_out = dt;
@@ -203,14 +207,19 @@ void host_set_bc(const int* bc, const double* states) {
   pack_bcq(st, g_bcq);
 }
 /* nsteps S2O4 steps of the public-layout state U (in place); precision 0:
-   FP64 kernels, 1: the FP32 form.  Returns 0, or -4 on a non-physical state */
+   FP64 kernels, 1: the FP32 form, 2: FP64 with the paired-FP32 interface
+   flux.  Returns 0, -4 on a non-physical state, -7 for the paired form on a
+   curvilinear mesh */
 int host_run(int dim, int precision, const int* n, const double* lo, const double* hi, const double* nodes,
              const double* phys, double* U, int nsteps, double* dt_out) {
-  if (dim == 3)
-    return precision ? run<float, 3>(n, lo, hi, nodes, phys, U, nsteps, dt_out)
-                     : run<double, 3>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
-  return precision ? run<float, 2>(n, lo, hi, nodes, phys, U, nsteps, dt_out)
-                   : run<double, 2>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
+  if (dim == 3) {
+    if (precision == 1) return run<float, 3>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
+    if (precision == 2) return run<double, 3, fpair>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
+    return run<double, 3>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
+  }
+  if (precision == 1) return run<float, 2>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
+  if (precision == 2) return run<double, 2, fpair>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
+  return run<double, 2>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
 }
 /* the learned selector's 16 features of every cell (uniform boxes) */
 void host_features(int dim, const int* n, const double* lo, const double* hi, const double* U, int precision,

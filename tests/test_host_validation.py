@@ -39,7 +39,8 @@ CASES = [
     ("negative viscosity", dict(dim=2, n=(8, 8), mu=-1e-3), EINVAL),
     ("zero CFL", dict(dim=2, n=(8, 8), cfl=0.0), EINVAL),
     ("collision-time mode 3", dict(dim=2, n=(8, 8), tau_mode=3), EINVAL),
-    ("precision 2", dict(dim=2, n=(8, 8), precision=2), EUNSUPPORTED),
+    ("precision 3", dict(dim=2, n=(8, 8), precision=3), EUNSUPPORTED),
+    ("negative precision", dict(dim=2, n=(8, 8), precision=-1), EUNSUPPORTED),
 ]
 
 
@@ -55,6 +56,12 @@ def test_create_mesh_rejects(cg, case):
 def test_walls_and_inflow_need_a_box(cg, bc):
     nodes = synth.perturbed_nodes_3d((6, 6, 6))
     st, h, _ = create(cg, dim=3, n=(6, 6, 6), nodes=nodes, bc=bc)
+    assert st == EUNSUPPORTED and not h.value
+
+
+def test_paired_form_needs_a_box(cg):
+    nodes = synth.perturbed_nodes_3d((6, 6, 6))
+    st, h, _ = create(cg, dim=3, n=(6, 6, 6), nodes=nodes, precision=2)
     assert st == EUNSUPPORTED and not h.value
 
 
@@ -74,6 +81,7 @@ def test_batch_rejects_mixed_and_invalid_cases(cg):
     ok, _ = cg.make_desc(dim=2, n=(8, 8))
     for bad, want in ((dict(dim=3, n=(8, 8, 8)), EINVAL),             # mixed dimensions
                       (dict(dim=2, n=(8, 8), precision=1), EINVAL),   # mixed precisions
+                      (dict(dim=2, n=(8, 8), precision=2), EINVAL),
                       (dict(dim=2, n=(8, 2)), EINVAL),
                       (dict(dim=2, n=(8, 8), bc=[2, 0, 0, 0]), EINVAL),
                       (dict(dim=2, n=(8, 8), nodes=synth.uniform_nodes((8, 8), (0, 0), (1, 1))), EUNSUPPORTED)):
@@ -82,7 +90,10 @@ def test_batch_rejects_mixed_and_invalid_cases(cg):
         h = C.c_void_p()
         assert L.cgks_batch_create(arr, 2, None, C.byref(h)) == want, bad
         assert not h.value
+    pd, _ = cg.make_desc(dim=2, n=(8, 8), precision=2)
+    arr = (cg.MeshDesc * 2)(pd, pd)
     h = C.c_void_p()
+    assert L.cgks_batch_create(arr, 2, None, C.byref(h)) == EUNSUPPORTED and not h.value   # paired form
     assert L.cgks_batch_create(None, 1, None, C.byref(h)) == EINVAL
     arr = (cg.MeshDesc * 1)(ok)
     assert L.cgks_batch_create(arr, 0, None, C.byref(h)) == EINVAL
