@@ -478,6 +478,8 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-selector", action="store_true")
+    ap.add_argument("--with-pair", action="store_true",
+                    help="also time precision 2 (interface flux in paired FP32)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -591,6 +593,23 @@ def main():
             "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in prof32.items()},
             "roofline": roofline(prof32, spec, ncell, 1),
             "clocks": clk32.summary(),
+        }
+
+    if args.with_pair:
+        # FP64 with the interface flux in paired FP32, same start and steps
+        mp, _, msp, profp, clkp = timed_form(2, s_init)
+        sp, _ = mp.get_state()
+        mp.close()
+        e = sp - s_fp64
+        forms["pair"] = {
+            "value": world * ncell * args.steps / (msp / 1e3), "unit": "cell-updates/s",
+            "ms_per_step": msp / args.steps, "speedup_vs_fp64": ms / msp,
+            "dtype": "f64 storage and arithmetic; interior interface flux in paired f32 (hi + lo)",
+            "difference_vs_fp64": {"steps": args.warmup + args.steps,
+                                   "density_linf": float(np.abs(e[0, 0]).max()),
+                                   "averages_linf_rel": float(np.abs(e[0]).max() / np.abs(s_fp64[0]).max())},
+            "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in profp.items()},
+            "clocks": clkp.summary(),
         }
 
     line = {
