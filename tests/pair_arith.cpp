@@ -1,0 +1,50 @@
+// Host build of the paired-FP32 type (paper_2508_08965_gb300/csrc/cgks_pair.cuh)
+// for its arithmetic tests: error-free sums, and the relative errors of
+// sums, products, quotients and conversions on random operands.
+#define CGKS_HD inline
+#include <cmath>
+#include <cstdint>
+#include <random>
+namespace cgks {
+inline double cg_erfc(double x) { return erfc(x); }
+inline double cg_exp(double x) { return exp(x); }
+inline double cg_expm1(double x) { return expm1(x); }
+inline double cg_sqrt(double x) { return sqrt(x); }
+inline double cg_rsqrt(double x) { return 1.0 / sqrt(x); }
+#include "../paper_2508_08965_gb300/csrc/cgks_pair.cuh"
+}  // namespace cgks
+using cgks::fpair;
+
+extern "C" {
+/* out: [0] two-sum failures, [1] fast-two-sum failures, [2] max rel error of
+   sums, [3] of differences of nearby values (relative to the operands), [4]
+   of products, [5] of quotients, [6] of conversions from double */
+void pair_stats(int n, unsigned seed, double* out) {
+  std::mt19937_64 rng(seed);
+  std::uniform_real_distribution<double> u(-1.0, 1.0), ex(-20.0, 20.0);
+  auto rnd = [&]() { return u(rng) * std::ldexp(1.0, (int)ex(rng)); };
+  for (int i = 0; i < 7; ++i) out[i] = 0;
+  for (int it = 0; it < n; ++it) {
+    const float a = (float)rnd(), b = (float)rnd();
+    float s, e;
+    cgks::fp_two_sum(a, b, s, e);
+    if ((long double)s + e != (long double)a + b) out[0] += 1;
+    const float big = std::fabs(a) >= std::fabs(b) ? a : b, small = big == a ? b : a;
+    cgks::fp_fast_two_sum(big, small, s, e);
+    if ((long double)s + e != (long double)big + small) out[1] += 1;
+    const double x = rnd(), y = rnd();
+    const fpair px(x), py(y);
+    const long double X = (long double)px.hi + px.lo, Y = (long double)py.hi + py.lo;
+    out[6] = std::fmax(out[6], (double)(fabsl(X - x) / fabsl((long double)x)));
+    const fpair ps = px + py, pm = px * py, pq = px / py;
+    const long double S = X + Y, M = X * Y, Q = X / Y;
+    out[2] = std::fmax(out[2], (double)(fabsl((long double)ps.hi + ps.lo - S) / (fabsl(X) + fabsl(Y))));
+    out[4] = std::fmax(out[4], (double)(fabsl((long double)pm.hi + pm.lo - M) / fabsl(M)));
+    out[5] = std::fmax(out[5], (double)(fabsl((long double)pq.hi + pq.lo - Q) / fabsl(Q)));
+    const fpair pz(x * (1.0 + 1e-9 * u(rng)));
+    const fpair pd = px - pz;
+    const long double Z = (long double)pz.hi + pz.lo;
+    out[3] = std::fmax(out[3], (double)(fabsl((long double)pd.hi + pd.lo - (X - Z)) / fabsl(X)));
+  }
+}
+}

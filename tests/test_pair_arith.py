@@ -1,0 +1,46 @@
+"""The paired-FP32 type of the paired flux form, built for the host: its
+two-sums are error-free, and sums, products, quotients and conversions
+from double keep about 48 bits (relative errors below 2^-44 ~ 5.7e-14)."""
+import ctypes as C
+import hashlib
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "pair_arith.cpp")
+HDR = os.path.join(os.path.dirname(HERE), "paper_2508_08965_gb300", "csrc", "cgks_pair.cuh")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no g++")
+    h = hashlib.sha1()
+    for p in (SRC, HDR):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    out = os.path.join(tempfile.gettempdir(), "cgks_pair_arith_%s.so" % h.hexdigest()[:16])
+    if not os.path.exists(out):
+        tmp = out + ".%d.tmp" % os.getpid()
+        subprocess.run([cxx, "-std=c++17", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, SRC],
+                       check=True, capture_output=True)
+        os.replace(tmp, out)
+    L = C.CDLL(out)
+    L.pair_stats.argtypes = [C.c_int, C.c_uint, C.POINTER(C.c_double)]
+    return L
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_pair_arithmetic(lib, seed):
+    out = (C.c_double * 7)()
+    lib.pair_stats(200000, seed, out)
+    two_sum_fail, fast_fail, e_sum, e_diff, e_mul, e_div, e_cvt = list(out)
+    assert two_sum_fail == 0 and fast_fail == 0
+    bound = 2.0 ** -44
+    assert e_cvt <= 2.0 ** -48
+    assert e_sum <= bound and e_diff <= bound and e_mul <= bound and e_div <= bound, list(out)
