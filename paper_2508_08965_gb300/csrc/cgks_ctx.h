@@ -35,7 +35,7 @@ struct cgks_ctx {
   long ncell;
   int prec;                 /* 0: FP64; 1: FP32 bulk with FP64 averages */
   bool walls;               /* some face is a wall: reconstruction with mirror images */
-  bool pair_flux;           /* FP64 storage, interface flux solved in paired FP32 (precision 2) */
+  bool pair_flux = false;   /* FP64 storage, interface flux solved in paired FP32 (precision 2) */
   cgks_mesh_desc desc;
   cudaStream_t stream;
   cgks::DevGeo geo;
