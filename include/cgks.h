@@ -105,8 +105,7 @@ typedef struct {
                            (accumulated across the S2O4 stages) and metrics in FP64;
                            2: as 0, with the GKS solve of the interior face Gauss
                            points in paired-FP32 arithmetic (hi + lo floats, about
-                           48 bits; exp, erfc, sqrt in FP64), uniform boxes only
-                           (nodes != NULL: CGKS_EUNSUPPORTED); other values:
+                           48 bits; exp, erfc, sqrt in FP64); other values:
                            CGKS_EUNSUPPORTED.  Batches take 0 or 1. */
   void* stream;         /* cudaStream_t to queue work on; NULL = default stream */
 } cgks_mesh_desc;

@@ -124,7 +124,6 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   for (int a = 0; a < d->dim; ++a)
     if (d->n[a] < 3) return CGKS_EINVAL;
   if (d->precision < 0 || d->precision > 2) return CGKS_EUNSUPPORTED;
-  if (d->precision == 2 && d->nodes) return CGKS_EUNSUPPORTED; /* the paired form is Cartesian only */
   for (int f = 0; f < 2 * d->dim; ++f) {
     if (d->bc[f] < CGKS_BC_PERIODIC || d->bc[f] > CGKS_BC_INFLOW) return CGKS_EINVAL;
     if ((d->bc[f] == CGKS_BC_PERIODIC) != (d->bc[f ^ 1] == CGKS_BC_PERIODIC)) return CGKS_EINVAL;

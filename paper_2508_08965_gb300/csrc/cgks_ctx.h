@@ -121,11 +121,13 @@ CGKS_DECLARE_STAGES(float)
 CGKS_DECLARE_STAGES(double)
 
 /* the interface flux of the paired form: FP64 Gauss-point states in, the
-   GKS solve in paired-FP32 arithmetic, FP64 fluxes out; Cartesian meshes.
-   Instantiated in cgks_stage_pair.cu. */
-template <int DIM>
+   GKS solve in paired-FP32 arithmetic, FP64 fluxes out.  Instantiated in
+   cgks_stage_pair.cu (Cartesian) and cgks_stage_pair_curvi.cu. */
+template <int DIM, bool CURVI>
 void launch_flux_pair(cgks_ctx* ctx, const double* gpL, const double* gpR, double* flux);
-extern template void launch_flux_pair<2>(cgks_ctx*, const double*, const double*, double*);
-extern template void launch_flux_pair<3>(cgks_ctx*, const double*, const double*, double*);
+extern template void launch_flux_pair<2, false>(cgks_ctx*, const double*, const double*, double*);
+extern template void launch_flux_pair<3, false>(cgks_ctx*, const double*, const double*, double*);
+extern template void launch_flux_pair<2, true>(cgks_ctx*, const double*, const double*, double*);
+extern template void launch_flux_pair<3, true>(cgks_ctx*, const double*, const double*, double*);
 
 #endif

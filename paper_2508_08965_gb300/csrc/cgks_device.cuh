@@ -1271,8 +1271,8 @@ CGKS_HD void to_global(const double R[3][3], T* F) {
    a [2][NV (1+DIM)][ns] shared array, ns = the block size) the point's two
    Gauss-point states are first copied there asynchronously, all 2 NV (1+DIM)
    loads in flight at once, and the solve reads them from shared memory.
-   C is the type the solve computes in: T, or fpair for the paired form
-   (Cartesian only), which converts the loaded states and rounds the
+   C is the type the solve computes in: T, or fpair for the paired form,
+   which converts the loaded (curvilinear: rotated) states and rounds the
    results back to T. */
 template <typename T, int DIM, bool CURVI, typename C = T>
 CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, long c,
@@ -1331,7 +1331,6 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
     }
     return ok;
   } else {
-  static_assert(cg_same<C, T>::value, "the curvilinear path computes in its storage type");
   T WL[NV], WR[NV], out[6 * NV];
   T dWL[DIM * NV], dWR[DIM * NV];
   T sl[NV * (1 + DIM)], sr[NV * (1 + DIM)];
@@ -1349,7 +1348,23 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
   face_frame<DIM>(A, Tt, R);
   to_local<T, DIM>(R, sl, WL, dWL);
   to_local<T, DIM>(R, sr, WR, dWR);
-  bool ok = gks_point<T, DIM>(ph, dt, WL, dWL, WR, dWR, out);
+  bool ok;
+  if constexpr (cg_same<C, T>::value) {
+    ok = gks_point<T, DIM>(ph, dt, WL, dWL, WR, dWR, out);
+  } else {
+    /* the rotation stays in the storage type; the solve computes in C */
+    C cWL[NV], cWR[NV], cdL[DIM * NV], cdR[DIM * NV], cout[6 * NV];
+    for (int i = 0; i < NV; ++i) {
+      cWL[i] = C(WL[i]);
+      cWR[i] = C(WR[i]);
+    }
+    for (int i = 0; i < DIM * NV; ++i) {
+      cdL[i] = C(dWL[i]);
+      cdR[i] = C(dWR[i]);
+    }
+    ok = gks_point<C, DIM>(ph, C(dt), cWL, cdL, cWR, cdR, cout);
+    for (int i = 0; i < 6 * NV; ++i) out[i] = to_storage<T>(cout[i]);
+  }
   for (int p = 0; p < 6; ++p) to_global<T, DIM>(R, out + p * NV);
   const long fb = (long)((ax * S::GPF + k) * 6) * NV;
   for (int q = 0; q < 6 * NV; ++q) flux[(fb + q) * N + c] = out[q];

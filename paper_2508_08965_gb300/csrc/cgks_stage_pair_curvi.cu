@@ -1,0 +1,18 @@
+/* Interface flux of the paired form (precision 2): FP64 Gauss-point states
+   in, the GKS solve of every face Gauss point in paired-FP32 arithmetic
+   (cgks_pair.cuh), FP64 fluxes out.  Curvilinear meshes (this unit; Cartesian ones in cgks_stage_pair.cu); the boundary faces and every
+   other kernel of the stage are the FP64 ones. */
+#include "cgks_ctx.h"
+
+using namespace cgks;
+using namespace cgks_host;
+
+template <int DIM, bool CURVI>
+void launch_flux_pair(cgks_ctx* ctx, const double* gpL, const double* gpR, double* flux) {
+  const long nf = (long)DIM * Sz<DIM>::GPF * ctx->ncell;
+  k_flux<double, DIM, CURVI, fpair><<<cdiv(nf, 128), 128, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, gpL, gpR,
+                                                                              flux, ctx->st);
+}
+
+template void launch_flux_pair<2, true>(cgks_ctx*, const double*, const double*, double*);
+template void launch_flux_pair<3, true>(cgks_ctx*, const double*, const double*, double*);

@@ -159,12 +159,8 @@ int run(const int* n, const double* lo, const double* hi, const double* nodes, c
     }
     int bad = 0;
     if (g.curvi) {
-      if constexpr (cg_same<C, T>::value) {
-        bad |= run_stage<T, DIM, true>(g, ph, dt, 1, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
-        bad |= run_stage<T, DIM, true>(g, ph, dt, 2, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
-      } else {
-        return -7; /* the paired form is Cartesian only */
-      }
+      bad |= run_stage<T, DIM, true, C>(g, ph, dt, 1, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
+      bad |= run_stage<T, DIM, true, C>(g, ph, dt, 2, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
     } else {
       bad |= run_stage<T, DIM, false, C>(g, ph, dt, 1, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
       bad |= run_stage<T, DIM, false, C>(g, ph, dt, 2, avg, der, SA.data(), SD.data(), gpL, gpR, fx, avh, avl, fxb);
@@ -208,8 +204,7 @@ void host_set_bc(const int* bc, const double* states) {
 }
 /* nsteps S2O4 steps of the public-layout state U (in place); precision 0:
    FP64 kernels, 1: the FP32 form, 2: FP64 with the paired-FP32 interface
-   flux.  Returns 0, -4 on a non-physical state, -7 for the paired form on a
-   curvilinear mesh */
+   flux.  Returns 0, or -4 on a non-physical state */
 int host_run(int dim, int precision, const int* n, const double* lo, const double* hi, const double* nodes,
              const double* phys, double* U, int nsteps, double* dt_out) {
   if (dim == 3) {

@@ -59,12 +59,6 @@ def test_walls_and_inflow_need_a_box(cg, bc):
     assert st == EUNSUPPORTED and not h.value
 
 
-def test_paired_form_needs_a_box(cg):
-    nodes = synth.perturbed_nodes_3d((6, 6, 6))
-    st, h, _ = create(cg, dim=3, n=(6, 6, 6), nodes=nodes, precision=2)
-    assert st == EUNSUPPORTED and not h.value
-
-
 def test_null_arguments(cg):
     L = cg.lib()
     h = C.c_void_p()
