@@ -76,8 +76,8 @@ def run_pair(orc, hk, dim, n, fn, steps, precision=0, lo=None, hi=None, nodes=No
                      kw.get("c_chi", 100.0), kw.get("tau_mode", 0), int(kw.get("linear", False)),
                      kw.get("dt_fixed", 0.0)])
     nn = (C.c_int * 3)(*(list(n) + [1] * (3 - dim)))
-    lo3 = np.array(list(lo) + [0.0] * (3 - dim))
-    hi3 = np.array(list(hi) + [1.0] * (3 - dim))
+    lo3 = np.array(list(lo) + [0.0] * (3 - dim), dtype=np.float64)
+    hi3 = np.array(list(hi) + [1.0] * (3 - dim), dtype=np.float64)
     nd = None if nodes is None else _dp(np.ascontiguousarray(nodes, dtype=np.float64))
     dt = C.c_double(0)
     rc = hk.host_run(dim, precision, nn, _dp(lo3), _dp(hi3), nd, _dp(phys), _dp(U), steps, C.byref(dt))
