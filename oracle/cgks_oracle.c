@@ -674,27 +674,40 @@ static int gks_point(int dim, double gamma, double mu, double prandtl, int tau_m
   }
   double* Fn = out;
   double* Ft = out + nv;
-  double Qn[MAXV], Qt[MAXV];
   for (int i = 0; i < nv; ++i) {
-    double sn = 0, st = 0, qn = 0, qt = 0;
+    double sn = 0, st = 0;
     for (int p = 0; p < 6; ++p) {
       sn += cn[p] * Fp[p][i];
       st += ct[p] * Fp[p][i];
-      qn += cn[p] * Qp[p][i];
-      qt += ct[p] * Qp[p][i];
     }
-    Fn[i] = sn; Ft[i] = st; Qn[i] = qn; Qt[i] = qt;
+    Fn[i] = sn; Ft[i] = st;
   }
   /* Prandtl-number fix for viscous flow: F_E += (1/Pr - 1) q, q the heat flux
-     about the interface velocity */
+     about the interface velocity of the non-equilibrium part f - g, where
+     g = g0 (1 + A0 t) is the equilibrium at the interface.  g contributes its
+     part 0 (g0) to f^n and its part 2 (A0 g0) to f_t^n with weight one, so q
+     is taken from the part sums with those weights lowered by one.  (The
+     heat flux of g0 about its own velocity vanishes; that of A0 g0 about the
+     fixed interface velocity does not: it is the work (E + p) dU/dt of the
+     equilibrium's own evolution.) */
   if (mu > 0.0 && prandtl > 0.0 && prandtl != 1.0) {
     for (int pass = 0; pass < 2; ++pass) {
-      double* F = pass == 0 ? Fn : Ft;
-      double* Q = pass == 0 ? Qn : Qt;
+      const double* cw = pass == 0 ? cn : ct;
+      const int peq = pass == 0 ? 0 : 2;
+      double F[MAXV], Q[MAXV]; /* u psi- and psi-moments of the non-equilibrium part */
+      for (int i = 0; i < nv; ++i) {
+        double sf = 0, sq = 0;
+        for (int p = 0; p < 6; ++p) {
+          const double c = p == peq ? cw[p] - 1.0 : cw[p];
+          sf += c * Fp[p][i];
+          sq += c * Qp[p][i];
+        }
+        F[i] = sf; Q[i] = sq;
+      }
       double uf = 0, uq = 0, u2 = 0;
       for (int i = 0; i < dim; ++i) { uf += g0.U[i] * F[1 + i]; uq += g0.U[i] * Q[1 + i]; u2 += g0.U[i] * g0.U[i]; }
       double q = (F[dim + 1] - uf + 0.5 * u2 * F[0]) - g0.U[0] * (Q[dim + 1] - uq + 0.5 * u2 * Q[0]);
-      F[dim + 1] += (1.0 / prandtl - 1.0) * q;
+      (pass == 0 ? Fn : Ft)[dim + 1] += (1.0 / prandtl - 1.0) * q;
     }
   }
   /* interface values: Q^e = W0 + t (dQ/dt)_0, Q_0^{l,r} = W_{l,r} + t (dQ/dt)_{l,r},
@@ -1724,7 +1737,8 @@ int orc_recon_matrix(int dim, double* M, int* exps) {
 int orc_recon_reference(int dim, const double* data, int linear, double c_chi, double* out, double* chi) {
   const ref_t* R = get_ref(dim);
   if (!R) return -1;
-  recon_var(R, data, linear ? 1.0 : -1.0, c_chi > 0 ? c_chi : 100.0, out, chi);
+  const double chi_force = linear == 1 ? 1.0 : (linear == 2 ? 0.0 : -1.0);
+  recon_var(R, data, chi_force, c_chi > 0 ? c_chi : 100.0, out, chi);
   return 0;
 }
 

@@ -82,7 +82,9 @@ int orc_data_size(int dim);
 /* reconstruction matrix M (nb x nd, row-major) and basis exponents (nb x 3) */
 int orc_recon_matrix(int dim, double* M, int* exps);
 /* one cell in reference space: data (nd) -> values and reference gradients at
-   all face Gauss points (ngp x (1+dim)), plus chi; linear: 1 forces chi = 1 */
+   all face Gauss points (ngp x (1+dim)), plus chi; linear: 0 takes chi from
+   the GENO path function, 1 forces chi = 1 (the fifth-order polynomial),
+   2 forces chi = 0 (the weighted linear sub-stencil polynomials alone) */
 int orc_recon_reference(int dim, const double* data, int linear, double c_chi,
                         double* out, double* chi);
 /* the P4 polynomial coefficients for a data vector */

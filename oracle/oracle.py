@@ -243,13 +243,17 @@ def recon_matrix(dim):
     return M, ex
 
 
-def recon_reference(dim, data, linear=False, c_chi=100.0):
+def recon_reference(dim, data, linear=False, c_chi=100.0, low_order=False):
+    """values and reference gradients at the face Gauss points of one cell;
+    linear: chi = 1 (fifth order), low_order: chi = 0 (the weighted linear
+    sub-stencils alone), neither: chi from the GENO path function"""
     L = lib()
     data = np.ascontiguousarray(data, dtype=np.float64)
     ngp = 2 * dim * (4 if dim == 3 else 2)
     out = np.empty((ngp, 1 + dim))
     chi = C.c_double(0)
-    L.orc_recon_reference(dim, _p(data), int(linear), c_chi, _p(out), C.byref(chi))
+    mode = 2 if low_order else (1 if linear else 0)
+    L.orc_recon_reference(dim, _p(data), mode, c_chi, _p(out), C.byref(chi))
     return out, chi.value
 
 

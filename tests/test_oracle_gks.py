@@ -185,3 +185,156 @@ def test_s2o4_is_fourth_order_taylor(orc):
         _, qn = orc.s2o4(Q, dt, lam * Q, lam * lam * Q, lam * lam * qs)
         z = lam * dt
         assert abs(qn - Q * (1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24)) < 1e-14 * abs(Q)
+
+
+# --- pins of the collision state (reading C3), the two-sided interface
+# values (reading C4) and the heat-flux fix of F_t (reading C16) ---------------
+
+def _prim(W, dim, gamma=1.4):
+    rho = W[0]
+    u = W[1:1 + dim] / rho
+    p = (gamma - 1.0) * (W[dim + 1] - 0.5 * rho * np.dot(u, u))
+    return rho, u, p
+
+
+def _half_space_closed(W, dim, side, gamma=1.4):
+    """Conservative moments of the half Maxwellian of W over u > 0 (side 0) or
+    u < 0 (side 1): the normal-velocity integrals by erfc, the transverse
+    velocity and internal energy full-space.  Works on complex W (complex
+    step)."""
+    from scipy.special import erfc
+    rho = W[0]
+    u = [W[1 + i] / rho for i in range(dim)]
+    ke = sum(W[1 + i] * u[i] for i in range(dim))
+    p = (gamma - 1.0) * (W[dim + 1] - 0.5 * ke)
+    lam = rho / (2.0 * p)
+    K = (5 - 3 * gamma) / (gamma - 1) if dim == 3 else (4 - 2 * gamma) / (gamma - 1)
+    s = 1.0 if side == 0 else -1.0
+    sl = np.sqrt(lam)
+    m0 = 0.5 * erfc(-s * sl * u[0])
+    e = np.exp(-lam * u[0] ** 2) / (2.0 * np.sqrt(np.pi * lam))
+    m1 = u[0] * m0 + s * e
+    m2 = u[0] * m1 + m0 / (2.0 * lam)
+    ut2 = sum(u[i] ** 2 for i in range(1, dim))
+    out = [rho * m0, rho * m1] + [rho * u[i] * m0 for i in range(1, dim)]
+    out.append(0.5 * rho * (m2 + (ut2 + (dim - 1 + K) / (2.0 * lam)) * m0))
+    return np.array(out)
+
+
+def _half_space_quad(W, dim, side, gamma=1.4):
+    """The same moments by adaptive quadrature over the half line of normal
+    velocities (independent of the erfc recurrences)."""
+    rho, u, p = _prim(W, dim, gamma)
+    lam = rho / (2.0 * p)
+    K = (5 - 3 * gamma) / (gamma - 1) if dim == 3 else (4 - 2 * gamma) / (gamma - 1)
+    g = lambda x: math.sqrt(lam / math.pi) * math.exp(-lam * (x - u[0]) ** 2)
+    lo, hi = (0.0, np.inf) if side == 0 else (-np.inf, 0.0)
+    mn = [integrate.quad(lambda x, n=n: x ** n * g(x), lo, hi, epsabs=1e-15, epsrel=1e-14)[0] for n in range(3)]
+    ut2 = float(np.dot(u[1:], u[1:]))
+    out = [rho * mn[0], rho * mn[1]] + [rho * u[i] * mn[0] for i in range(1, dim)]
+    out.append(0.5 * rho * (mn[2] + (ut2 + (dim - 1 + K) / (2.0 * lam)) * mn[0]))
+    return np.array(out)
+
+
+def _half_space_jvp(W, dW, dim, side):
+    """d/de of the half-space moments of W + e dW (complex step): the moments
+    of the half Maxwellian's spatial derivative g (a . psi)"""
+    return np.imag(_half_space_closed(W.astype(complex) + 1e-30j * dW, dim, side)) / 1e-30
+
+
+def _euler_dt(W, dW, dim, gamma=1.4):
+    """Q_t = -sum_j (dF_j/dW) dW_j (Euler Jacobians by complex step)"""
+    Qt = np.zeros(dim + 2)
+    for j in range(dim):
+        Aj = jac(lambda w, j=j: euler_flux_dir(w, dim, gamma, j), W)
+        Qt -= Aj @ dW[j]
+    return Qt
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_half_space_moments_closed_form_vs_quadrature(dim):
+    # the test's own closed form (used below) against quadrature
+    for W in (cons(dim, 1.2, [0.4, -0.3, 0.2][:dim], 0.8), cons(dim, 0.3, [-1.1, 0.5, 0.0][:dim], 0.2)):
+        for side in (0, 1):
+            a, b = _half_space_closed(W, dim, side), _half_space_quad(W, dim, side)
+            assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+STATES = [  # (rho, u, p) left | right, pressure jumps giving blend weights far from 1/2
+    ((1.0, [0.2, 0.1, -0.3], 1.0), (0.4, [-0.1, 0.3, 0.2], 0.1)),
+    ((0.9, [0.5, -0.2, 0.1], 0.8), (1.1, [0.3, 0.0, -0.1], 1.0)),
+    ((0.2, [-0.6, 0.4, 0.3], 0.15), (1.3, [-0.2, -0.1, 0.5], 1.4)),
+]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("k", range(len(STATES)))
+def test_collision_state_and_euler_limit_with_unequal_sides(orc, dim, k):
+    """tau = 0 (smooth-flow mode) with different left and right states and
+    slopes: the interface distribution is g0 (1 + A t) only, so F^n is the
+    Euler flux of the collision state W0 = int psi (g_l H(u) + g_r (1 - H(u)))
+    and F_t^n = A_x(W0) (dQ/dt)_0, with (dQ/dt)_0 = -sum_j A_j(W0) dW0_j and
+    dW0_j the same half-space combination of the two sides' slopes (C3)."""
+    (rl, ul, pl), (rr, ur, pr) = STATES[k]
+    WL, WR = cons(dim, rl, ul[:dim], pl), cons(dim, rr, ur[:dim], pr)
+    rng = np.random.default_rng(100 + 10 * dim + k)
+    dWL = rng.standard_normal((dim, dim + 2)) * 0.2
+    dWR = rng.standard_normal((dim, dim + 2)) * 0.2
+    out = orc.gks_point(dim, WL, dWL, WR, dWR, 0.01, tau_mode=0)
+    W0 = _half_space_quad(WL, dim, 0) + _half_space_quad(WR, dim, 1)
+    dW0 = np.array([_half_space_jvp(WL, dWL[j], dim, 0) + _half_space_jvp(WR, dWR[j], dim, 1) for j in range(dim)])
+    Qt0 = _euler_dt(W0, dW0, dim)
+    Ax = jac(lambda w: euler_flux(w, dim, 1.4), W0)
+    sc = np.abs(euler_flux(W0, dim, 1.4)).max()
+    assert np.abs(out[0] - euler_flux(W0, dim, 1.4)).max() <= 1e-12 * sc
+    assert np.abs(out[1] - Ax @ Qt0).max() <= 1e-11 * max(1.0, np.abs(Ax @ Qt0).max())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("k", range(len(STATES)))
+def test_two_sided_interface_values(orc, dim, mode, k):
+    """The interface values of the derivative update (C4): with
+    tau0 = 5 |pl - pr| / (pl + pr) dt and w = exp(-dt / tau0), each side gets
+    (1 - w) Q^e + w Q_0^side, where Q^e = W0 + t (dQ/dt)_0 is the collision
+    state's and Q_0^side = W_side + t (dQ/dt)_side the side's own Euler
+    evolution; the weight does not depend on the flux's tau mode."""
+    (rl, ul, pl), (rr, ur, pr) = STATES[k]
+    WL, WR = cons(dim, rl, ul[:dim], pl), cons(dim, rr, ur[:dim], pr)
+    rng = np.random.default_rng(200 + 10 * dim + k)
+    dWL = rng.standard_normal((dim, dim + 2)) * 0.2
+    dWR = rng.standard_normal((dim, dim + 2)) * 0.2
+    dt = 0.01
+    out = orc.gks_point(dim, WL, dWL, WR, dWR, dt, mu=1e-3 if mode == 2 else 0.0, prandtl=0.72, tau_mode=mode)
+    W0 = _half_space_quad(WL, dim, 0) + _half_space_quad(WR, dim, 1)
+    dW0 = np.array([_half_space_jvp(WL, dWL[j], dim, 0) + _half_space_jvp(WR, dWR[j], dim, 1) for j in range(dim)])
+    Qt0 = _euler_dt(W0, dW0, dim)
+    w = math.exp(-(pl + pr) / (5.0 * abs(pl - pr)))
+    assert 0.05 < w < 0.95 and abs(w - 0.5) > 0.1
+    for part, W, dW in ((2, WL, dWL), (4, WR, dWR)):
+        exp0 = (1 - w) * W0 + w * W
+        expt = (1 - w) * Qt0 + w * _euler_dt(W, dW, dim)
+        assert np.abs(out[part] - exp0).max() <= 1e-12 * np.abs(exp0).max()
+        assert np.abs(out[part + 1] - expt).max() <= 1e-11 * max(1.0, np.abs(expt).max())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("pr", [1.0, 0.72])
+def test_viscous_smooth_time_derivative_is_euler(orc, dim, pr):
+    """Identical smooth sides, viscous tau = mu/p: the interface distribution
+    is f(t) = g0 - tau (a.u + A) g0 + t A g0 exactly, so its time derivative is
+    the equilibrium's, A g0, whose flux is the Euler one, A_x Q_t, whatever mu
+    and Pr.  The heat-flux fix (C16) acts on the non-equilibrium part of f,
+    which does not change in time here, so it must leave F_t alone; a fix that
+    took the heat flux of all of f_t would count the work of the pressure
+    gradient at the interface velocity, (E + p) dU/dt, as heat."""
+    rng = np.random.default_rng(300 + dim)
+    for trial in range(3):
+        u = rng.uniform(-0.5, 0.5, dim) if trial else np.zeros(dim)
+        W = cons(dim, rng.uniform(0.6, 1.5), u, rng.uniform(0.6, 1.5))
+        dW = rng.standard_normal((dim, dim + 2)) * 0.3
+        out = orc.gks_point(dim, W, dW, W, dW, 1e-3, mu=2e-3, prandtl=pr, tau_mode=2)
+        Qt = _euler_dt(W, dW, dim)
+        Ft = jac(lambda w: euler_flux(w, dim, 1.4), W) @ Qt
+        assert np.abs(out[1] - Ft).max() <= 1e-10 * max(1.0, np.abs(Ft).max()), (trial, out[1], Ft)
+        assert np.allclose(out[3], Qt, rtol=1e-11, atol=1e-11) and np.allclose(out[5], Qt, rtol=1e-11, atol=1e-11)

@@ -5,6 +5,8 @@ reproduces every polynomial of degree <= 4 exactly (values and gradients at all
 face Gauss points).  P2: the linear sub-stencil polynomials of
 Eq. (compact-sub-2) reproduce linear data.  P14: GENO path function sanity.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -130,3 +132,95 @@ def test_geno_step_function_is_troubled(orc, dim):
     d = rg.data_vector(dim, f, grad)
     _, chi = orc.recon_reference(dim, d, linear=False)
     assert chi < 0.1
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_geno_low_order_weights(orc, dim):
+    """chi = 0 leaves the weighted linear sub-stencil polynomials of
+    Eq. (weno-new): sum_m w_m P_m^1 with w_m proportional to
+    d_m / (IS_m + eps)^5, d_m = 1 / (2 dim), IS_m = |grad P_m^1|^2 on the unit
+    cell (reading C5).  Data: a linear field whose face-neighbour averages are
+    moved so that each sub-stencil sees its own slope along its axis
+    (P_m^1 matches Q_{1,m} exactly and fits the perpendicular lines, which
+    stay those of the linear field), so every P_m^1 is known in closed form."""
+    g = np.array([0.3, -0.2, 0.1])[:dim]
+    q0 = 0.7
+    f = lambda x: q0 + float(np.dot(g, x))
+    d = rg.data_vector(dim, f, lambda x: g)
+    beta = [0.45, 0.8, -0.3, 0.35, 0.6, -0.25][:2 * dim]  # slope of P_m^1 along its axis
+    slopes = []
+    for m, o in enumerate(rg.face_offsets(dim)):
+        a, s = m // 2, o[m // 2]
+        d[1 + m] = q0 + s * beta[m]
+        b = g.copy()
+        b[a] = beta[m]
+        slopes.append(b)
+        assert np.allclose(orc.linear_sub(dim, m, d), b, atol=1e-14)
+    w = np.array([(1.0 / (2 * dim)) / (float(b @ b) + 1e-15) ** 5 for b in slopes])
+    w /= w.sum()
+    assert w.max() < 0.9 and np.sort(w)[-2] > 1e-3  # several sub-stencils matter
+    out, chi = orc.recon_reference(dim, d, low_order=True)
+    assert chi == 0.0
+    for gi, x in enumerate(rg.all_gps(dim)):
+        val = sum(w[m] * (q0 + slopes[m] @ x) for m in range(2 * dim))
+        grad = sum(w[m] * slopes[m] for m in range(2 * dim))
+        assert abs(out[gi, 0] - val) <= 1e-14
+        assert np.abs(out[gi, 1:] - grad).max() <= 1e-14
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_geno_chi_from_integrated_indicators(orc, dim):
+    """chi of the GENO path function (reading C5) on quartic data, with the
+    indicators integrated here from the polynomial itself: IS^H = sum over
+    multi-indices 1 <= |l| <= 4 (each once) of the integral over the unit cell
+    of (D^l P)^2, IS^L its |l| = 1 part, IS^tau = IS^H - IS^L, then
+    alpha = 2 a_H / (a_H + a_L) with a = 1 + (IS^tau / (IS + eps))^2 and
+    chi = tanh(C alpha) / tanh(C).  The reconstruction reproduces quartics
+    (P1), so P is the data's polynomial; a wrong Gram entry, a missing order
+    or a cross term counted twice changes chi."""
+    import itertools
+    import sympy as sp
+    X = sp.symbols("x0:%d" % dim)
+    t = sp.Symbol("t")
+    rng = np.random.default_rng(77 + dim)
+    c_chi = 0.3
+    exps = [e for e in itertools.product(range(5), repeat=dim) if 1 <= sum(e) <= 4]
+    coef = rng.standard_normal(len(exps))
+    # P = linear part + t (orders 2-4): the indicators are quadratics in t
+    P = sum(sp.Float(c, 30) * (1 if sum(e) == 1 else t) * sp.prod([X[a] ** e[a] for a in range(dim)])
+            for c, e in zip(coef, exps))
+    dom = [(X[a], -sp.Rational(1, 2), sp.Rational(1, 2)) for a in range(dim)]
+    ish = isl = sp.Integer(0)
+    for l in itertools.product(range(5), repeat=dim):
+        if not 1 <= sum(l) <= 4:
+            continue
+        D = P
+        for a in range(dim):
+            D = sp.diff(D, X[a], l[a])
+        v = sp.integrate(sp.expand(D * D), *dom)
+        ish += v
+        if sum(l) == 1:
+            isl += v
+    ishf, islf = sp.lambdify(t, ish), sp.lambdify(t, isl)
+    for target in (0.5, 1.0, 2.0):  # IS^tau / IS^L, set by t (bisection)
+        lo_t, hi_t = 0.0, 10.0
+        for _ in range(80):
+            tm = 0.5 * (lo_t + hi_t)
+            if (ishf(tm) - islf(tm)) / islf(tm) < target:
+                lo_t = tm
+            else:
+                hi_t = tm
+        tv = 0.5 * (lo_t + hi_t)
+        Pt = P.subs(t, tv)
+        fn = sp.lambdify(X, Pt, "math")
+        gr = [sp.lambdify(X, sp.diff(Pt, X[a]), "math") for a in range(dim)]
+        d = rg.data_vector(dim, lambda x: fn(*x), lambda x: np.array([gk(*x) for gk in gr]))
+        _, chi = orc.recon_reference(dim, d, c_chi=c_chi)
+        eps = 1e-15
+        vh, vl = float(ishf(tv)), float(islf(tv))
+        ist = max(vh - vl, 0.0)
+        ah = 1 + (ist / (vh + eps)) ** 2
+        al = 1 + (ist / (vl + eps)) ** 2
+        expect = math.tanh(c_chi * 2 * ah / (ah + al)) / math.tanh(c_chi)
+        assert 0.05 < expect < 0.95  # chi away from its bounds, where a wrong indicator shows
+        assert abs(chi - expect) <= 1e-11, (target, chi, expect)
