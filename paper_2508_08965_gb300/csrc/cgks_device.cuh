@@ -1104,14 +1104,16 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
     Fn[i] += cn[2] * t1[i];
     Ft[i] += ct[2] * t1[i];
   }
-  if (prfix) { /* heat-flux correction F_E += (1/Pr - 1) q about the interface velocity:
-                  q = qw . F - U_x qw . Q */
+  if (prfix) { /* heat-flux correction F_E += (1/Pr - 1) q about the interface velocity,
+                  q = qw . F - U_x qw . Q of the non-equilibrium part f - g0 (1 + A0 t):
+                  g0 adds no heat flux to f^n; A0 g0 (part 2, weight one in f_t^n)
+                  is taken out of the time derivative's */
     const T q2 = qdot<T, DIM>(qw, t2);
     qn += cn[2] * q2;
     qt += ct[2] * q2;
     const T f = T(1) / ph_pr<T>(ph) - T(1);
     const T hn = qdot<T, DIM>(qw, Fn) - z.U[0] * qn;
-    const T ht = qdot<T, DIM>(qw, Ft) - z.U[0] * qt;
+    const T ht = qdot<T, DIM>(qw, Ft) - z.U[0] * qt - (qdot<T, DIM>(qw, t1) - z.U[0] * q2);
     Fn[DIM + 1] += f * hn;
     Ft[DIM + 1] += f * ht;
   }
