@@ -182,14 +182,19 @@ int cgks_profile_read(cgks_ctx* ctx, const char** names, long* launches, double*
    must not pay for allocation, which can synchronise the device.
    desc: a uniform box (nodes must be NULL, else CGKS_EUNSUPPORTED) with dim,
    n, lo, hi, gamma, mu, cfl, dt_fixed and stream as for cgks_create_mesh;
-   dev_state: device pointer to a state in the public layout; *dt_out (host)
-   receives the same dt as cgks_compute_dt would for that state.  At most
-   CGKS_DT_NOALLOC_MAX_CELLS cells, else CGKS_ETOOLARGE.  The work space is a
-   fixed array of (CGKS_DT_NOALLOC_MAX_CELLS/256 + 1) 8-byte words that every
-   GPU loading the library holds until the process exits; the first call on a
-   device also looks up that array's device address.  All calls share the
-   array: calls whose kernels overlap on the GPU race.  Synchronises the
-   stream. */
+   dev_state: pointer to a state in the public layout in memory of the
+   current device (else CGKS_EINVAL); only its averages are read; *dt_out
+   (host) receives the same dt as cgks_compute_dt would for that state, or
+   dt_fixed when that is positive.  A cell whose rate is not finite and
+   positive (e.g. negative pressure) gives CGKS_ENONPHYS.  At most
+   CGKS_DT_NOALLOC_MAX_CELLS cells, else CGKS_ETOOLARGE before any CUDA call.
+   The work space is a fixed array of (CGKS_DT_NOALLOC_MAX_CELLS/256 + 1)
+   8-byte words that every GPU loading the library holds until the process
+   exits; the first call on a device also looks up that array's device
+   address (cudaGetSymbolAddress), so make it before any stream capture.
+   Every call overwrites the words it reads, so none has to start at zero.
+   All calls share the array: calls whose kernels overlap on the GPU race.
+   Synchronises the stream. */
 #define CGKS_DT_NOALLOC_MAX_CELLS 16777216
 cgks_status cgks_compute_dt_noalloc(const cgks_mesh_desc* desc, const double* dev_state, double* dt_out);
 

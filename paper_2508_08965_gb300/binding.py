@@ -37,11 +37,27 @@ BC_PERIODIC, BC_OUTFLOW, BC_SLIP_WALL, BC_NOSLIP_WALL, BC_INFLOW = 0, 1, 2, 3, 4
 SEL_NFEAT, SEL_NPARAM = 16, 2689
 
 
+def _f32(t, n, what):
+    """device pointer of a contiguous float32 CUDA tensor of n values on the
+    current device (the library reads or writes exactly n)"""
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous float32 CUDA tensor" % what)
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("%s is on another device than the current one" % what)
+    check_size(t.numel(), n, what)
+    return C.c_void_p(t.data_ptr())
+
+
 def mlp_loss_grad(params, X, y, w, grad, stream=None):
     """Weighted BCE loss of the selector network and its gradient (into
     `grad`), all torch CUDA float32 tensors; returns the loss."""
     torch = _torch()
     st = stream if stream is not None else torch.cuda.current_stream()
+    N = int(X.shape[0])
+    for t, n, what in ((params, SEL_NPARAM, "params"), (X, N * SEL_NFEAT, "X"), (y, N, "y"), (w, N, "w"),
+                       (grad, SEL_NPARAM, "grad")):
+        _f32(t, n, what)
     loss = C.c_float(0)
     status = lib().cgks_mlp_loss_grad(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()),
                                       C.c_void_p(y.data_ptr()), C.c_void_p(w.data_ptr()), int(X.shape[0]),
@@ -56,6 +72,9 @@ def mlp_logits(params, X, out=None, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream()
     if out is None:
         out = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    N = int(X.shape[0])
+    for t, n, what in ((params, SEL_NPARAM, "params"), (X, N * SEL_NFEAT, "X"), (out, N, "out")):
+        _f32(t, n, what)
     status = lib().cgks_mlp_logits(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()), int(X.shape[0]),
                                    C.c_void_p(out.data_ptr()), C.c_void_p(st.cuda_stream))
     if status:
@@ -66,6 +85,8 @@ def mlp_logits(params, X, out=None, stream=None):
 def mlp_adam(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     torch = _torch()
     st = stream if stream is not None else torch.cuda.current_stream()
+    for t, what in ((params, "params"), (grad, "grad"), (m, "m"), (v, "v")):
+        _f32(t, SEL_NPARAM, what)
     status = lib().cgks_mlp_adam(C.c_void_p(params.data_ptr()), C.c_void_p(grad.data_ptr()), C.c_void_p(m.data_ptr()),
                                  C.c_void_p(v.data_ptr()), int(step), float(lr), float(beta1), float(beta2),
                                  float(eps), C.c_void_p(st.cuda_stream))
@@ -189,6 +210,11 @@ def make_desc(dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=
     return d, keep
 
 
+def check_size(n, want, what):
+    if n != want:
+        raise ValueError("%s holds %d values, the library reads or writes %d" % (what, n, want))
+
+
 class Mesh:
     """One library context: a mesh, its device state and metrics.
 
@@ -252,37 +278,44 @@ class Mesh:
     def set_state(self, s, t=0.0):
         """s: numpy array (host) or torch CUDA tensor of state_shape, float64."""
         torch = _torch()
+        size = self.nf * self.nv * self.ncell
         if isinstance(s, torch.Tensor) and s.is_cuda:
+            if s.dtype != torch.float64:
+                raise ValueError("state must be float64")
             s = s.contiguous()
-            assert s.dtype == torch.float64 and s.numel() == self.nf * self.nv * self.ncell
+            check_size(s.numel(), size, "state")
             self._check(lib().cgks_set_state(self._h, C.c_void_p(s.data_ptr()), 1, float(t)))
             self._keep = s
         else:
             a = np.ascontiguousarray(s, dtype=np.float64)
-            assert a.size == self.nf * self.nv * self.ncell
+            check_size(a.size, size, "state")
             self._check(lib().cgks_set_state(self._h, a.ctypes.data_as(C.c_void_p), 0, float(t)))
 
     def get_state(self, out=None):
-        """Host numpy copy (or into a torch CUDA tensor `out`); returns (state, t)."""
+        """Host numpy copy (or into `out`: a contiguous float64 torch CUDA
+        tensor or writable numpy array of the state's size); returns (state, t)."""
         torch = _torch()
         t = C.c_double(0)
-        if out is not None and isinstance(out, torch.Tensor) and out.is_cuda:
-            self._check(lib().cgks_get_state(self._h, C.c_void_p(out.data_ptr()), 1, C.byref(t)))
-            self._pending = []
-            return out, t.value
-        a = np.empty(self.state_shape) if out is None else out
-        self._check(lib().cgks_get_state(self._h, a.ctypes.data_as(C.c_void_p), 0, C.byref(t)))
+        size = self.nf * self.nv * self.ncell
+        if out is None:
+            out = np.empty(self.state_shape)
+        p, dev, keep = self._buffer(out, True)
+        check_size(keep.numel() if isinstance(keep, torch.Tensor) else keep.size, size, "output buffer")
+        self._check(lib().cgks_get_state(self._h, C.c_void_p(p), dev, C.byref(t)))
         self._pending = []
-        return a, t.value
+        return out, t.value
 
     @staticmethod
     def _buffer(a, writable):
-        """(pointer, is_device, keep-alive) of a torch tensor (CUDA, or CPU,
-        best page-locked) or a numpy array, in the public layout, float64"""
+        """(pointer, is_device, keep-alive) of a torch tensor (CUDA on the
+        current device, or CPU, best page-locked) or a numpy array, in the
+        public layout, float64"""
         torch = _torch()
         if isinstance(a, torch.Tensor):
             if a.dtype != torch.float64 or not a.is_contiguous():
                 raise ValueError("state buffers are contiguous float64")
+            if a.is_cuda and a.device.index != torch.cuda.current_device():
+                raise ValueError("device buffer on another device than the current one")
             return a.data_ptr(), int(a.is_cuda), a
         if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
             raise ValueError("state buffers are contiguous float64")
@@ -333,7 +366,12 @@ class Mesh:
         """GENO weights of stage 1 of the last step, [v][cell] (host numpy, or
         into a torch CUDA float64 tensor `out`)."""
         if out is not None:
-            self._check(lib().cgks_get_chi(self._h, C.c_void_p(out.data_ptr()), 1))
+            torch = _torch()
+            if not (isinstance(out, torch.Tensor) and out.is_cuda):
+                raise ValueError("out must be a torch CUDA tensor")
+            p, _, keep = self._buffer(out, True)
+            check_size(keep.numel(), self.nv * self.ncell, "output buffer")
+            self._check(lib().cgks_get_chi(self._h, C.c_void_p(p), 1))
             return out
         a = np.empty((self.nv,) + tuple(reversed(self.n)))
         self._check(lib().cgks_get_chi(self._h, a.ctypes.data_as(C.c_void_p), 0))
@@ -365,7 +403,7 @@ class Mesh:
         torch = _torch()
         if out is None:
             out = torch.empty((self.ncell, SEL_NFEAT), dtype=torch.float32, device="cuda")
-        self._check(lib().cgks_selector_features(self._h, C.c_void_p(out.data_ptr())))
+        self._check(lib().cgks_selector_features(self._h, _f32(out, self.ncell * SEL_NFEAT, "out")))
         return out
 
     def init(self, field_fn, chunk_cells=1 << 18):
@@ -396,12 +434,28 @@ class Mesh:
 
 
 def compute_dt_noalloc(state, dim, n, lo, hi, gamma=1.4, mu=0.0, cfl=0.5, dt_fixed=0.0, stream=None):
-    """dt of a device state (torch CUDA float64 tensor, public layout) on a
-    uniform box, without any device allocation by the library (for callers
-    that cannot allocate: see cgks_compute_dt_noalloc in include/cgks.h).
-    Returns (status, dt); status 0 is CGKS_OK."""
+    """dt of a device state (contiguous torch CUDA float64 tensor, public
+    layout, at least its averages) on a uniform box, without any device
+    allocation by the library (for callers that cannot allocate: see
+    cgks_compute_dt_noalloc in include/cgks.h).  The call runs on the state's
+    device, on `stream` or that device's current stream.  Returns
+    (status, dt); status 0 is CGKS_OK."""
     torch = _torch()
-    assert isinstance(state, torch.Tensor) and state.is_cuda and state.dtype == torch.float64
+    if not (isinstance(state, torch.Tensor) and state.is_cuda and state.dtype == torch.float64
+            and state.is_contiguous()):
+        raise ValueError("state must be a contiguous float64 CUDA tensor")
+    ncell = 1
+    for a in range(dim):
+        ncell *= int(n[a])
+    if state.numel() < (dim + 2) * ncell:
+        raise ValueError("state holds %d values; the averages of %d cells need %d"
+                         % (state.numel(), ncell, (dim + 2) * ncell))
+    with torch.cuda.device(state.device):
+        return _compute_dt_noalloc(state, dim, n, lo, hi, gamma, mu, cfl, dt_fixed, stream)
+
+
+def _compute_dt_noalloc(state, dim, n, lo, hi, gamma, mu, cfl, dt_fixed, stream):
+    torch = _torch()
     d = MeshDesc()
     d.dim = dim
     nn = list(n) + [1] * (3 - len(n))
@@ -473,12 +527,20 @@ class Batch:
     def set_state(self, k, s, t=0.0):
         """State of case k: numpy (host) or torch CUDA float64, that case's layout."""
         torch = _torch()
+        if not 0 <= int(k) < self.ncase:
+            raise IndexError("case %d of %d" % (k, self.ncase))
+        size = int(np.prod(self.state_shape(k)))
         if isinstance(s, torch.Tensor) and s.is_cuda:
+            if s.dtype != torch.float64:
+                raise ValueError("state must be float64")
+            if s.device.index != torch.cuda.current_device():
+                raise ValueError("device buffer on another device than the current one")
             s = s.contiguous()
+            check_size(s.numel(), size, "state")
             self._check(lib().cgks_batch_set_state(self._h, int(k), C.c_void_p(s.data_ptr()), 1, float(t)))
         else:
             a = np.ascontiguousarray(s, dtype=np.float64)
-            assert a.shape == self.state_shape(k) or a.size == int(np.prod(self.state_shape(k)))
+            check_size(a.size, size, "state")
             self._check(lib().cgks_batch_set_state(self._h, int(k), a.ctypes.data_as(C.c_void_p), 0, float(t)))
 
     def get_state(self, k):

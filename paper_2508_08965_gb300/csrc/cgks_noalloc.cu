@@ -108,6 +108,15 @@ extern "C" cgks_status cgks_compute_dt_noalloc(const cgks_mesh_desc* d, const do
     if (ncell > CGKS_DT_NOALLOC_MAX_CELLS) return CGKS_ETOOLARGE;
   }
   if (!(d->gamma > 1.0) || d->mu < 0.0 || !(d->cfl > 0.0)) return CGKS_EINVAL;
+  /* the state must be device memory of the current device */
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return CGKS_ECUDA;
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, dev_state) != cudaSuccess) {
+    cudaGetLastError();
+    return CGKS_EINVAL;
+  }
+  if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != cur) return CGKS_EINVAL;
   unsigned long long* scratch = nullptr;
   cgks_status s = scratch_for_current_device(&scratch);
   if (s != CGKS_OK) return s;

@@ -1,7 +1,8 @@
-/* Interface flux of the paired form (precision 2): FP64 Gauss-point states
-   in, the GKS solve of every face Gauss point in paired-FP32 arithmetic
-   (cgks_pair.cuh), FP64 fluxes out.  Cartesian meshes (this unit; curvilinear ones in cgks_stage_pair_curvi.cu); the boundary faces and every
-   other kernel of the stage are the FP64 ones. */
+/* Interface flux of the paired form (precision 2) on Cartesian meshes
+   (cgks_stage_pair_curvi.cu holds the other kind): FP64 Gauss-point states in, the
+   GKS solve of every interior face Gauss point in paired-FP32 arithmetic
+   (cgks_pair.cuh), FP64 fluxes out.  Boundary faces and the other kernels
+   of the stage are the FP64 ones. */
 #include "cgks_ctx.h"
 
 using namespace cgks;

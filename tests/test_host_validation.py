@@ -113,3 +113,37 @@ def test_async_copy_buffers(cg):
     assert buf(ro, False)[2] is ro
     with pytest.raises(ValueError):
         buf(ro, True)
+
+
+def test_state_copies_refuse_bad_buffers(cg):
+    """The binding checks every buffer the library would read or write
+    before the call: size, dtype, contiguity, writability, device.  (Objects
+    built without a context: each refusal happens before any library call.)"""
+    import numpy as np
+    import torch
+    m = object.__new__(cg.Mesh)
+    m._h, m._pending = None, []
+    m.dim, m.n, m.nf, m.nv, m.ncell = 2, (4, 3), 7, 4, 12
+    size = 7 * 4 * 12
+    for bad in (np.zeros(size - 1), np.zeros(size, dtype=np.float32), np.zeros(2 * size)[::2],
+                torch.zeros(size, dtype=torch.float32), torch.zeros(size + 1, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            m.get_state(out=bad)
+    ro = np.zeros(size)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        m.get_state(out=ro)
+    for bad in (np.zeros(size - 1), np.zeros(size + 7)):
+        with pytest.raises(ValueError):
+            m.set_state(bad)
+    b = object.__new__(cg.Batch)
+    b._h, b.ncase, b.dims = None, 2, [(2, (4, 3)), (2, (8, 8))]
+    with pytest.raises(ValueError):
+        b.set_state(1, np.zeros(size))  # case 0's size given for case 1
+    with pytest.raises(IndexError):
+        b.set_state(2, np.zeros(size))
+    # the allocation-free time step and the network kernels take CUDA tensors only
+    with pytest.raises(ValueError):
+        cg.compute_dt_noalloc(torch.zeros(4 * 12, dtype=torch.float64), 2, (4, 3), (0, 0), (1, 1))
+    with pytest.raises(ValueError):
+        cg._f32(torch.zeros(16, dtype=torch.float32), 16, "X")
