@@ -146,8 +146,14 @@ cgks_status cgks_sync(cgks_ctx* ctx);
 
 /* Advance nsteps S2O4 steps.  t_end > 0 shortens the last step so that the
    time does not pass t_end (and stops there).  t_out / dt_last may be NULL.
-   Returns CGKS_ENONPHYS if a state became non-physical (the state is then
-   undefined; restore it with cgks_set_state). Synchronises once. */
+   Returns CGKS_ENONPHYS if a state became non-physical: a Gauss-point or
+   interface state that the positivity fallbacks (first order) cannot make
+   physical, or a cell average with rho <= 0, p <= 0 or a NaN.  The state and
+   time are then those of the last good step of this call: the input of the
+   step whose reconstruction or flux failed, or the input of the step whose
+   output the next time step found non-physical; the steps after it do no
+   work.  A state that is non-physical when the call starts is left as it
+   is.  Synchronises once. */
 cgks_status cgks_step(cgks_ctx* ctx, int nsteps, double t_end, double* t_out, double* dt_last);
 
 /* The CFL time step of the current state (dt = CFL / max over cells of

@@ -5,6 +5,8 @@
  */
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
@@ -69,7 +71,7 @@ static cgks_status run_stage(cgks_ctx* ctx, int stage) {
 }
 
 template <int DIM>
-static cgks_status run_dt(cgks_ctx* ctx, const double* avg, const float* avh) {
+static cgks_status run_dt(cgks_ctx* ctx, const double* avg, const float* avh, int in_step) {
   prof_begin(ctx, KID_DT);
   const long nb = cdiv(ctx->ncell, 256);
   k_dt_reset<<<1, 1, 0, ctx->stream>>>(ctx->dts);
@@ -80,20 +82,34 @@ static cgks_status run_dt(cgks_ctx* ctx, const double* avg, const float* avh) {
     k_dt_screen<DIM, double><<<nb, 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, avg, ctx->dts);
     k_dt_rate<DIM, double><<<nb, 256, 0, ctx->stream>>>(ctx->geo, ctx->ph, avg, avg, ctx->dts);
   }
-  k_dt_final<<<1, 1, 0, ctx->stream>>>(ctx->ph, ctx->dts, ctx->st);
+  k_dt_final<<<1, 1, 0, ctx->stream>>>(ctx->ph, ctx->dts, ctx->st, in_step);
   prof_end(ctx);
   CK(cudaGetLastError());
   return CGKS_OK;
 }
 
+/* The state arrays of index 0 hold the current state; both stages write
+   into those of index 1 (stage 2 reads only the stash, so it can overwrite
+   U*), and the two sets swap roles after every step.  A step thus never
+   overwrites its own input, which is what lets a failed call return the
+   last good state (cgks_step). */
+static void swap_state(cgks_ctx* ctx) {
+  std::swap(ctx->avg[0], ctx->avg[1]);
+  std::swap(ctx->der[0], ctx->der[1]);
+  std::swap(ctx->avh[0], ctx->avh[1]);
+  std::swap(ctx->avl[0], ctx->avl[1]);
+  if (ctx->prec == 0) std::swap(ctx->U, ctx->Us); /* the public-layout state is avg[0], der[0] */
+}
+
 template <int DIM>
 static cgks_status run_step(cgks_ctx* ctx) {
   cgks_status s;
-  if ((s = run_dt<DIM>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr)) != CGKS_OK) return s;
+  if ((s = run_dt<DIM>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr, 1)) != CGKS_OK) return s;
   if ((s = run_stage<DIM>(ctx, 1)) != CGKS_OK) return s;
   if ((s = run_stage<DIM>(ctx, 2)) != CGKS_OK) return s;
-  k_time_advance<<<1, 1, 0, ctx->stream>>>(ctx->dts);
+  k_time_advance<<<1, 1, 0, ctx->stream>>>(ctx->dts, ctx->st);
   CK(cudaGetLastError());
+  swap_state(ctx);
   return CGKS_OK;
 }
 
@@ -375,7 +391,10 @@ cgks_status cgks_step(cgks_ctx* ctx, int nsteps, double t_end, double* t_out, do
   CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   h.t_end = t_end > 0.0 ? t_end : 0.0;
+  h.nok = 0;
+  h.t_prev = h.t;
   CK(cudaMemcpyAsync(ctx->dts, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
+  int nrun = 0;
   for (int s = 0; s < nsteps; ++s) {
     if (t_end > 0.0) {
       CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
@@ -384,11 +403,15 @@ cgks_status cgks_step(cgks_ctx* ctx, int nsteps, double t_end, double* t_out, do
     }
     cgks_status r = ctx->dim == 3 ? run_step<3>(ctx) : run_step<2>(ctx);
     if (r != CGKS_OK) return r;
+    ++nrun;
   }
   if (ctx->prof.on) prof_fold(ctx);
   cgks_status r = check_status(ctx);
   CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  /* after a failure the last good state is the input of step nok of the
+     call: no later step wrote into it, and each step swapped the two sets */
+  if (r == CGKS_ENONPHYS && ((nrun - h.nok) & 1)) swap_state(ctx);
   ctx->t = h.t;
   if (t_out) *t_out = h.t;
   if (dt_last) *dt_last = h.dt;
@@ -403,8 +426,8 @@ cgks_status cgks_compute_dt(cgks_ctx* ctx, double* dt) {
   double keep_end = h.t_end;
   h.t_end = 0.0;
   CK(cudaMemcpyAsync(ctx->dts, &h, sizeof h, cudaMemcpyHostToDevice, ctx->stream));
-  cgks_status r = ctx->dim == 3 ? run_dt<3>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr)
-                                 : run_dt<2>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr);
+  cgks_status r = ctx->dim == 3 ? run_dt<3>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr, 0)
+                                 : run_dt<2>(ctx, ctx->avg[0], ctx->prec ? ctx->avh[0] : nullptr, 0);
   if (r != CGKS_OK) return r;
   CK(cudaMemcpyAsync(&h, ctx->dts, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

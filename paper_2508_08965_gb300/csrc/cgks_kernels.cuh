@@ -21,7 +21,14 @@ struct DtState {
   unsigned int pad;
   double dt, t, t_end, dt_fixed;
   StageCoef k; /* stage_coef(dt), set with dt */
+  /* within one cgks_step call: the steps whose output is not known to be
+     non-physical, and the time before the last of them (the time to go
+     back to when the next step's time step finds that output non-physical) */
+  double t_prev;
+  int nok, pad2;
 };
+/* a stage or time-step kernel has flagged a non-physical state */
+CGKS_HD bool st_failed(const int* st) { return st[ST_NONPHYS] || st[ST_FLUX] || st[ST_DT]; }
 CGKS_HD void set_dt(DtState& d, double dt) {
   d.dt = dt;
   d.k = stage_coef(dt);
@@ -225,7 +232,8 @@ __device__ __forceinline__ void flux_bnd_item(const DevGeo& g, const Phys& ph, d
 
 /* one thread per face slot and Gauss point (blocks of 128); the Cartesian
    path stages each point's Gauss-point states in shared memory.  C: the
-   solve's compute type (fpair: the paired form, Cartesian FP64 storage) */
+   solve's compute type (fpair: the paired form, FP64 storage, Cartesian or
+   curvilinear with the face-frame rotation in FP64) */
 template <typename T, int DIM, bool CURVI, typename C = T>
 __global__ void __launch_bounds__(128, flux_min_blocks<T, DIM, CURVI>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
                                               const T* __restrict__ gpL, const T* __restrict__ gpR,
@@ -390,12 +398,26 @@ static __global__ void k_dt_reset(DtState* dts) {
 }
 
 /* dt = CFL / max rate, or the fixed step; shortened to reach t_end */
-static __global__ void k_dt_final(Phys ph, DtState* dts, int* st) {
+/* in_step: the time step of a step of cgks_step.  Once a kernel has flagged
+   a non-physical state the step gets dt = 0, so that its updates (and those
+   of every later step of the call) write nothing; when this step's input,
+   the previous step's output, is the non-physical one, that step is
+   uncounted and the time goes back to before it. */
+static __global__ void k_dt_final(Phys ph, DtState* dts, int* st, int in_step) {
+  const bool prior = st_failed(st);
   double rate = __longlong_as_double((long long)dts->rate_bits);
+  const bool bad = !(rate > 0.0 && rate < 1e299);
   double dt;
   if (dts->dt_fixed > 0.0) dt = dts->dt_fixed;
-  else dt = (rate > 0.0 && rate < 1e299) ? ph.cfl / rate : 0.0;
-  if (rate >= 1e299) atomicOr(&st[ST_DT], 1);
+  else dt = bad ? 0.0 : ph.cfl / rate;
+  if (bad) atomicOr(&st[ST_DT], 1);
+  if (in_step) {
+    if (bad && !prior && dts->nok > 0) {
+      dts->nok -= 1;
+      dts->t = dts->t_prev;
+    }
+    if (prior || bad) dt = 0.0;
+  }
   if (dts->t_end > 0.0) {
     double rem = dts->t_end - dts->t;
     if (rem < dt) dt = rem > 0.0 ? rem : 0.0;
@@ -403,7 +425,14 @@ static __global__ void k_dt_final(Phys ph, DtState* dts, int* st) {
   set_dt(*dts, dt);
 }
 
-static __global__ void k_time_advance(DtState* dts) { dts->t += dts->dt; }
+/* the end of a step: counted, and the time advanced, unless a kernel of the
+   step flagged a non-physical state */
+static __global__ void k_time_advance(DtState* dts, const int* st) {
+  if (st_failed(st)) return;
+  dts->t_prev = dts->t;
+  dts->t += dts->dt;
+  dts->nok += 1;
+}
 /* a fresh time-step record at time t (dt_fixed > 0: that step, else CFL);
    a kernel rather than a copy from host memory, so that setting a state
    never waits for the stream */
