@@ -61,6 +61,12 @@ def test_paired_one_step(orc, cg, case):
     assert d <= 1e-12
 
 
-def test_paired_hundred_steps(orc, cg):
-    case = ("vortex-100", 2, (24, 24), (0, 0), (10, 10), lambda x, y: synth.isentropic_vortex_2d(x, y), None, {})
-    assert _run(orc, cg, case, 100) <= 1e-9
+@pytest.mark.parametrize("case", [
+    ("vortex-100", 2, (24, 24), (0, 0), (10, 10), lambda x, y: synth.isentropic_vortex_2d(x, y), None, {}),
+    ("tgv12", 3, (12, 12, 12), (0, 0, 0), (2 * math.pi,) * 3, lambda x, y, z: synth.taylor_green_3d(x, y, z),
+     None, TGV),
+    CASES[3]], ids=["vortex24", "tgv12", "tgv-curvilinear"])
+def test_paired_hundred_steps(orc, cg, case):
+    d = _run(orc, cg, case, 100)
+    print("%s 100 steps: %.2e" % (case[0], d))
+    assert d <= 1e-9

@@ -76,7 +76,11 @@ def test_one_step(orc, cg, case):
     m.step(1)
     sg, tg = m.get_state()
     assert abs(tg - o.time()) <= 1e-14 * o.time()
-    assert class_scaled_diff(sg, o.get_state(), hmin(n, lo, hi, nodes)) <= 1e-12
+    d = class_scaled_diff(sg, o.get_state(), hmin(n, lo, hi, nodes))
+    # the plain norm (derivative fields by their own size) is reported beside
+    # the bar's: its rounding floor is measured in tests/test_parity_norm.py
+    print("%s one step: class-scaled %.2e, plain %.2e" % (name, d, class_scaled_diff(sg, o.get_state())))
+    assert d <= 1e-12
     m.close()
 
 
@@ -85,12 +89,14 @@ def test_many_steps(orc, cg, case):
     name, dim, n, lo, hi, fn, nodes, kw = case
     if nodes == "perturbed":
         nodes = synth.perturbed_nodes_3d(n)
-    steps = 100 if dim == 2 else 20
+    steps = 100
     o, m = pair(orc, cg, dim, n, lo, hi, fn, nodes=nodes, **kw)
     o.step(steps)
     m.step(steps)
     sg, _ = m.get_state()
-    assert class_scaled_diff(sg, o.get_state(), hmin(n, lo, hi, nodes)) <= 1e-9
+    d = class_scaled_diff(sg, o.get_state(), hmin(n, lo, hi, nodes))
+    print("%s 100 steps: class-scaled %.2e, plain %.2e" % (name, d, class_scaled_diff(sg, o.get_state())))
+    assert d <= 1e-9
     m.close()
 
 
