@@ -33,22 +33,35 @@ WORKLOADS = {
     "vortex64": dict(dim=2, n=(64, 64), desc="2-D isentropic vortex 64^2 over [0,10]^2, eps 5"),
 }
 
-# FP64 work per unit of the two compute kernels, from the executed FP64
-# instructions of an ncu capture (TGV 64^3, same kernels): flops = 2 DFMA +
-# DADD + DMUL (division, sqrt and the special functions enter through the
-# instructions they execute); flux: per face Gauss point.  The FP64
-# reconstruction is not listed: since its FP32 screen of the smoothness
-# indicators, its FP64 work per cell depends on the data.
-FLOPS_PER_UNIT = {
+# Algorithmic FP64 (or FP32) flops per unit of work, recounted from the
+# kernels' source by tests/flop_count.cpp (the device routines built for the
+# host with a value-numbering compute type: shared subexpressions once,
+# products with exact 0 or +-1 and sums with exact 0 not at all, only what
+# a stored result depends on; +, -, * and / one flop, FMA two; special
+# functions not counted) and pinned by tests/test_flop_count.py.  Flux: per
+# face Gauss point, keyed by (kernel, dim, viscous); the viscous form adds
+# the collision-time and Prandtl-fix terms.  The same algorithm runs in the
+# FP64, FP32 and paired forms.
+ALG_FLOPS_PER_UNIT = {
+    ("flux", 3, True): 2911.0,
+    ("flux", 2, True): 1664.0,
+    ("flux", 2, False): 760.0,
+}
+# Executed work per unit from ncu instruction counts (TGV 64^3, same
+# kernels): 2 DFMA + DADD + DMUL (FP64) or 2 FFMA + FADD + FMUL (FP32),
+# which includes the instruction sequences of divisions and special
+# functions and whatever the compiler recomputes.  The FP64 reconstruction
+# is not listed: since its FP32 screen of the smoothness indicators its FP64
+# work per cell depends on the data.
+EXEC_FLOPS_PER_UNIT = {
     ("flux", 3): 3.616e3,
 }
 # DRAM bytes per unit of the same capture (read + write), for `traffic`
 DRAM_BYTES_PER_UNIT = {
     ("flux", 3): (1.0110e9 + 0.7142e9) / (262144 * 12),
 }
-# the same for the FP32 form (flops = 2 FFMA + FADD + FMUL; ncu, TGV 64^3);
-# update: per (cell, variable)
-FLOPS_PER_UNIT_FP32 = {
+# the same for the FP32 form (update: per (cell, variable))
+EXEC_FLOPS_PER_UNIT_FP32 = {
     ("recon", 3): 1.235e4,
     ("flux", 3): 3.395e3,
     ("update", 3): 158.0,
@@ -151,10 +164,11 @@ def fp32_alu_peak_tflops(sm_count=152, sm_mhz=2070.0):
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def roofline(prof, spec, ncell, precision):
-    """Roofline of the dominant kernel of a timed form: its executed flops per
-    unit (ncu counts) times the units of one launch, over its average
-    CUDA-event launch time, against the ALU pipe peak of its precision."""
+def roofline(prof, spec, ncell, precision, viscous):
+    """Roofline of the dominant kernel of a timed form: its algorithmic flops
+    per unit (ALG_FLOPS_PER_UNIT) times the units of one launch, over its
+    average CUDA-event launch time, against the ALU pipe peak of its
+    precision; the executed (ncu) count gives frac_executed beside it."""
     name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
     avg_ms = tot_ms / max(launches, 1)
     dim = spec["dim"]
@@ -164,27 +178,35 @@ def roofline(prof, spec, ncell, precision):
         units = ncell
     else:
         units = ncell * dim * (4 if dim == 3 else 2)
-    table = FLOPS_PER_UNIT if precision == 0 else FLOPS_PER_UNIT_FP32
-    dram = DRAM_BYTES_PER_UNIT if precision == 0 else DRAM_BYTES_PER_UNIT_FP32
-    fpu = table.get((name, dim))
-    if precision == 0:
-        peak = fp64_alu_peak_tflops()
-        src = ("FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz, derived (an FMA-chain probe measured "
-               "1.19-1.20 TFLOP/s)")
-    else:
+    exe = (EXEC_FLOPS_PER_UNIT if precision != 1 else EXEC_FLOPS_PER_UNIT_FP32).get((name, dim))
+    dram = (DRAM_BYTES_PER_UNIT if precision == 0 else DRAM_BYTES_PER_UNIT_FP32 if precision == 1 else {})
+    alg = ALG_FLOPS_PER_UNIT.get((name, dim, viscous))
+    if precision == 1:
         peak = fp32_alu_peak_tflops()
         src = ("FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz, derived (an FMA-chain probe measured "
                "72.9-73.3 TFLOP/s)")
-    out = {"bound": "alu", "kernel": name, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
-           "traffic": None, "avg_launch_ms": avg_ms, "peak_source": src}
-    if fpu:
-        achieved = fpu * units / (avg_ms / 1e3) / 1e12
-        dbu = dram.get((name, dim))
-        out.update({"achieved": achieved, "frac": achieved / peak, "flops_per_launch": fpu * units,
-                    "traffic": dbu * units if dbu else None,
-                    "traffic_source": "ncu dram__bytes_read+write of a 64^3 capture, scaled by units"})
     else:
-        out["note"] = "flops per unit not yet counted for this kernel"
+        peak = fp64_alu_peak_tflops()
+        src = ("FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz, derived (an FMA-chain probe measured "
+               "1.19-1.20 TFLOP/s)")
+        if precision == 2:
+            src += "; the paired form's flux runs its FP64-equivalent work on the FP32 pipe"
+    sec = avg_ms / 1e3
+    out = {"bound": "alu", "kernel": name, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+           "traffic": None, "avg_launch_ms": avg_ms, "units_per_launch": units, "peak_source": src}
+    if alg:
+        achieved = alg * units / sec / 1e12
+        out.update({"achieved": achieved, "frac": achieved / peak, "flops_per_unit": alg,
+                    "flops_per_launch": alg * units,
+                    "flops_source": "algorithmic count of the kernel's source (tests/flop_count.cpp)"})
+    if exe and precision != 2:
+        out.update({"flops_per_unit_executed": exe, "frac_executed": exe * units / sec / 1e12 / peak})
+    dbu = dram.get((name, dim))
+    if dbu and precision != 2:
+        out.update({"traffic": dbu * units,
+                    "traffic_source": "ncu dram__bytes_read+write of a 64^3 capture, scaled by units"})
+    if not alg:
+        out["note"] = "flops per unit not counted for this kernel"
     return out
 
 
@@ -504,6 +526,7 @@ def main():
 
     wl = args.workload
     spec = WORKLOADS[wl]
+    viscous = mesh_kwargs(wl).get("mu", 0.0) > 0.0
     stream = torch.cuda.Stream()
     peaks = measured_peaks()
 
@@ -591,7 +614,7 @@ def main():
                               "density_linf": float(np.abs(e).max()),
                               "kinetic_energy_rel": abs(ke(s32) - ke(s_fp64)) / ke(s_fp64)},
             "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in prof32.items()},
-            "roofline": roofline(prof32, spec, ncell, 1),
+            "roofline": roofline(prof32, spec, ncell, 1, viscous),
             "clocks": clk32.summary(),
         }
 
@@ -629,7 +652,7 @@ def main():
                            "method": "one context; cgks_set_state, cgks_step, cgks_get_state, each waiting"}},
         "gpu_launches": args.steps * KERNELS_PER_STEP,
         "kernels": kernels,
-        "roofline": roofline(prof, spec, ncell, 0),
+        "roofline": roofline(prof, spec, ncell, 0, viscous),
         "clocks": clk.summary(),
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
         "forms": forms,

@@ -51,54 +51,28 @@ def test_reference_arm_other_ranks_print_nothing(orc):
 def test_roofline_dominant_kernel(bench):
     n = 128 ** 3
     prof = {"recon": (10, 259.0), "flux": (10, 1028.0), "update": (10, 30.8), "dt": (5, 0.35)}
-    r = bench.roofline(prof, bench.WORKLOADS["tgv128"], n, 0)
+    r = bench.roofline(prof, bench.WORKLOADS["tgv128"], n, 0, True)
     assert r["kernel"] == "flux" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     units = n * 3 * 4                       # 12 face Gauss points owned per cell in 3-D
-    assert r["flops_per_launch"] == pytest.approx(3.616e3 * units)
-    assert r["achieved"] == pytest.approx(3.616e3 * units / 0.1028 / 1e12)
+    assert r["units_per_launch"] == units
+    assert r["flops_per_launch"] == pytest.approx(2911.0 * units)  # algorithmic count
+    assert r["achieved"] == pytest.approx(2911.0 * units / 0.1028 / 1e12)
     assert r["peak"] == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["frac_executed"] == pytest.approx(3.616e3 * units / 0.1028 / 1e12 / r["peak"])
     assert r["traffic"] == pytest.approx((1.0110e9 + 0.7142e9) * 8)   # 64^3 capture scaled to 128^3
 
 
 def test_roofline_uncounted_kernel(bench):
     """a dominant kernel without a counted flop figure reports no fraction"""
-    r = bench.roofline({"recon": (2, 100.0), "flux": (2, 50.0)}, bench.WORKLOADS["tgv128"], 128 ** 3, 0)
+    r = bench.roofline({"recon": (2, 100.0), "flux": (2, 50.0)}, bench.WORKLOADS["tgv128"], 128 ** 3, 0, True)
     assert r["kernel"] == "recon" and r["achieved"] is None and r["frac"] is None and "note" in r
 
 
-def test_roofline_fp32_update_units(bench):
+def test_roofline_fp32_flux(bench):
     n = 64 * 64 * 64
-    r = bench.roofline({"update": (4, 4.0)}, bench.WORKLOADS["tgv64"], n, 1)
-    assert r["kernel"] == "update"
-    assert r["flops_per_launch"] == pytest.approx(158.0 * n * 5)
+    r = bench.roofline({"flux": (4, 4.0), "update": (4, 1.0)}, bench.WORKLOADS["tgv64"], n, 1, True)
+    assert r["kernel"] == "flux"
+    assert r["flops_per_launch"] == pytest.approx(2911.0 * n * 12)
     assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
-
-
-def test_clock_summary(bench):
-    s = bench.ClockSampler(0)
-    s.rows = [["0", "2070", "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
-              ["0", "1980", "2070", "1400", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
-              ["0", "2070", "2070", "1100", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
-              ["0", "[N/A]", "2070"]]
-    out = s.summary()
-    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
-
-
-def test_oracle_threads_do_not_change_results(orc):
-    """the single-core baseline times the same arithmetic: one thread and
-    all threads give the same state bit for bit"""
-    import numpy as np
-    import synth
-    full = orc.set_threads(0)
-    res = []
-    for th in (1, full):
-        orc.set_threads(th)
-        assert orc.set_threads(0) == th
-        o = orc.Oracle(3, (6, 5, 7), lo=(0, 0, 0), hi=(6.283185307179586,) * 3, mu=1 / 1600, prandtl=0.72,
-                       tau_mode=2)
-        o.init(lambda x, y, z: synth.taylor_green_3d(x, y, z))
-        o.step(2)
-        res.append(o.get_state())
-    orc.set_threads(full)
-    assert np.array_equal(res[0], res[1])
+    assert r["frac_executed"] == pytest.approx(3.395e3 * n * 12 / 1e-3 / 1e12 / r["peak"])
