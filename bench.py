@@ -2,9 +2,13 @@
 
 Metric: cell-updates/s per S2O4 step (cells x steps / time) on the 3-D
 Taylor-Green vortex (Ma 0.1, Re 1600, Pr 0.72, gamma 1.4) on a periodic
-uniform [0, 2 pi]^3 mesh, 128^3 by default, plain FP64.
+uniform [0, 2 pi]^3 mesh, 128^3 by default, in the fastest form that keeps
+parity with the FP64 oracle at the FP64 bars: FP64 storage and arithmetic
+with the interior interface flux in paired FP32 (--form pair, the default);
+plain FP64 throughout (--form fp64) is timed beside it from the same state,
+and so are the FP32 form, the learned selector and the batched ensemble.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv128|tgv256|tgv64|vortex64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv128|tgv256|tgv64|vortex64] [--form pair|fp64]
   python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 A step is one full S2O4 step (time-step reduction, two stages of
@@ -55,6 +59,12 @@ ALG_FLOPS_PER_UNIT = {
 # work per cell depends on the data.
 EXEC_FLOPS_PER_UNIT = {
     ("flux", 3): 3.616e3,
+}
+# the paired form's flux (ncu, TGV 64^3): FP32 flops it executes per face
+# Gauss point for its FP64-equivalent work (2 FFMA + FADD + FMUL; plus 446
+# FP64 flops of conversions and special functions)
+EXEC_FP32_FLOPS_PER_UNIT_PAIR = {
+    ("flux", 3): 33761.0,
 }
 # DRAM bytes per unit of the same capture (read + write), for `traffic`
 DRAM_BYTES_PER_UNIT = {
@@ -201,6 +211,10 @@ def roofline(prof, spec, ncell, precision, viscous):
                     "flops_source": "algorithmic count of the kernel's source (tests/flop_count.cpp)"})
     if exe and precision != 2:
         out.update({"flops_per_unit_executed": exe, "frac_executed": exe * units / sec / 1e12 / peak})
+    pair32 = EXEC_FP32_FLOPS_PER_UNIT_PAIR.get((name, dim)) if precision == 2 and name == "flux" else None
+    if pair32:
+        p32 = fp32_alu_peak_tflops()
+        out.update({"fp32_flops_per_unit_executed": pair32, "frac_fp32_pipe": pair32 * units / sec / 1e12 / p32})
     dbu = dram.get((name, dim))
     if dbu and precision != 2:
         out.update({"traffic": dbu * units,
@@ -500,8 +514,9 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-selector", action="store_true")
-    ap.add_argument("--with-pair", action="store_true",
-                    help="also time precision 2 (interface flux in paired FP32)")
+    ap.add_argument("--form", default="pair", choices=["pair", "fp64"],
+                    help="the headline FP64-parity form: pair (FP64 with the interior interface flux in paired "
+                         "FP32, the default) or fp64 (FP64 throughout); the other is timed beside it")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -558,7 +573,8 @@ def main():
         mesh.profile(False)
         return mesh, s0, replicas.job_time_ms(ms, device="cuda"), prof, clk
 
-    mesh, s_init, ms, prof, clk = timed_form(0)
+    head = 2 if args.form == "pair" else 0
+    mesh, s_init, ms, prof, clk = timed_form(head)
     ncell = mesh.ncell
     value = replicas.whole_job_rate(ncell, args.steps, ms, world)
 
@@ -570,7 +586,7 @@ def main():
     h_in = torch.empty(shape, dtype=torch.float64, pin_memory=True)
     h_out = torch.empty(shape, dtype=torch.float64, pin_memory=True)
     mesh.get_state(h_in.numpy())
-    s_fp64 = h_in.numpy().copy()  # FP64 state after the warm-up and timed steps
+    s_head = h_in.numpy().copy()  # the headline form's state after the warm-up and timed steps
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -584,17 +600,42 @@ def main():
     mesh.close()
     outs = [torch.empty(shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
     barrier()
-    ov_s = e2e_overlapped(lambda st: Mesh(spec["dim"], spec["n"], stream=st, precision=0, **mesh_kwargs(wl)),
+    ov_s = e2e_overlapped(lambda st: Mesh(spec["dim"], spec["n"], stream=st, precision=head, **mesh_kwargs(wl)),
                           h_in, outs, args.e2e_steps)
     ov_s = replicas.job_time_ms(1e3 * ov_s, device="cuda") / 1e3
     lanes_match = all(np.array_equal(o.numpy(), h_out.numpy()) for o in outs)
     kernels = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)}
                for k, v in prof.items()}
 
-    # the FP32 form from the same initial state and the same number of steps;
-    # its error is stated against the FP64 form (itself parity-checked against
-    # the FP64 oracle)
+    # the other FP64-parity form from the same initial state and steps: the
+    # plain FP64 state is the reference of every difference below (itself
+    # parity-checked against the FP64 oracle)
     forms = {}
+    other = 0 if head == 2 else 2
+    mo, _, mso, profo, clko = timed_form(other, s_init)
+    s_other, _ = mo.get_state()
+    mo.close()
+    s_fp64 = s_other if head == 2 else s_head
+    s_pair = s_head if head == 2 else s_other
+    ms_fp64 = mso if head == 2 else ms
+    ms_pair = ms if head == 2 else mso
+    e = s_pair - s_fp64
+    forms["fp64"] = {
+        "value": world * ncell * args.steps / (ms_fp64 / 1e3), "unit": "cell-updates/s",
+        "ms_per_step": ms_fp64 / args.steps, "dtype": "f64",
+        "note": "plain FP64 throughout",
+    }
+    forms["pair"] = {
+        "value": world * ncell * args.steps / (ms_pair / 1e3), "unit": "cell-updates/s",
+        "ms_per_step": ms_pair / args.steps, "speedup_vs_fp64": ms_fp64 / ms_pair,
+        "dtype": "f64 storage and arithmetic; interior interface flux in paired f32 (hi + lo)",
+        "difference_vs_fp64": {"steps": args.warmup + args.steps,
+                               "density_linf": float(np.abs(e[0, 0]).max()),
+                               "averages_linf_rel": float(np.abs(e[0]).max() / np.abs(s_fp64[0]).max())},
+    }
+    forms["fp64" if other == 0 else "pair"].update({
+        "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in profo.items()},
+        "roofline": roofline(profo, spec, ncell, other, viscous), "clocks": clko.summary()})
     if not args.no_fp32:
         m32, _, ms32, prof32, clk32 = timed_form(1, s_init)
         s32, _ = m32.get_state()
@@ -607,7 +648,7 @@ def main():
 
         forms["fp32"] = {
             "value": world * ncell * args.steps / (ms32 / 1e3), "unit": "cell-updates/s",
-            "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": ms / ms32,
+            "ms_per_step": ms32 / args.steps, "speedup_vs_fp64": ms_fp64 / ms32,
             "dtype": "f32 reconstruction/flux/weights/derivative fields; f64 averages, accumulation, metrics",
             "error_vs_fp64": {"steps": args.warmup + args.steps,
                               "density_l2": float(np.sqrt(np.mean(e * e))),
@@ -618,28 +659,15 @@ def main():
             "clocks": clk32.summary(),
         }
 
-    if args.with_pair:
-        # FP64 with the interface flux in paired FP32, same start and steps
-        mp, _, msp, profp, clkp = timed_form(2, s_init)
-        sp, _ = mp.get_state()
-        mp.close()
-        e = sp - s_fp64
-        forms["pair"] = {
-            "value": world * ncell * args.steps / (msp / 1e3), "unit": "cell-updates/s",
-            "ms_per_step": msp / args.steps, "speedup_vs_fp64": ms / msp,
-            "dtype": "f64 storage and arithmetic; interior interface flux in paired f32 (hi + lo)",
-            "difference_vs_fp64": {"steps": args.warmup + args.steps,
-                                   "density_linf": float(np.abs(e[0, 0]).max()),
-                                   "averages_linf_rel": float(np.abs(e[0]).max() / np.abs(s_fp64[0]).max())},
-            "kernels": {k: {"launches": v[0], "ms_total": v[1]} for k, v in profp.items()},
-            "clocks": clkp.summary(),
-        }
-
     line = {
         "metric": "cell-updates/s per S2O4 step", "value": value, "unit": "cell-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32x2" if head == 2 else "f64", "data": "synthetic",
         "config": {"workload": wl, "description": spec["desc"], "cells": ncell,
+                   "form": ("FP64 storage and arithmetic, interior interface flux in paired FP32 (hi + lo, about "
+                            "48 bits); parity with the FP64 oracle at the FP64 bars" if head == 2 else
+                            "FP64 throughout"),
                    "l2": "state (%.2f GB) larger than L2; no flush" % (state_bytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": world * ncell * args.e2e_steps / ov_s, "unit": "cell-updates/s",
@@ -652,7 +680,7 @@ def main():
                            "method": "one context; cgks_set_state, cgks_step, cgks_get_state, each waiting"}},
         "gpu_launches": args.steps * KERNELS_PER_STEP,
         "kernels": kernels,
-        "roofline": roofline(prof, spec, ncell, 0, viscous),
+        "roofline": roofline(prof, spec, ncell, head, viscous),
         "clocks": clk.summary(),
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
         "forms": forms,
@@ -664,7 +692,7 @@ def main():
         if tg and "fp32" in forms:
             forms["fp32_learned"] = {"value": tg[0]["value"], "unit": "cell-updates/s",
                                      "ms_per_step": tg[0]["ms_per_step"]["selector"],
-                                     "speedup_vs_fp64": (ms / args.steps) / tg[0]["ms_per_step"]["selector"],
+                                     "speedup_vs_fp64": (ms_fp64 / args.steps) / tg[0]["ms_per_step"]["selector"],
                                      "density_l2_vs_fp64": tg[0].get("density_l2_vs_fp64"),
                                      "skip_rate": tg[0]["skip_rate"]}
     if not args.no_ensemble:
