@@ -366,13 +366,15 @@ def ensemble_bench(args, stream, ncase=256):
             break
     kws = [synth.spec_mesh(sp) for sp in specs]
     b = Batch(kws, precision=1, stream=stream)
-    meshes = []
+    meshes, init_states = [], {}
     for k, sp in enumerate(specs):
         m = Mesh(precision=1, stream=stream, **kws[k])
         m.init(synth.spec_field(sp))
         st = torch.empty(b.state_shape(k), dtype=torch.float64, device="cuda")
         m.get_state(out=st)
         b.set_state(k, st)
+        if k % max(1, ncase // 16) == 0:
+            init_states[k] = st.cpu().numpy()
         meshes.append(m)
     t0 = time.perf_counter()
     tiles, tune_ms = b.tune(reps=3)
@@ -400,10 +402,24 @@ def ensemble_bench(args, stream, ncase=256):
     torch.cuda.synchronize()
     ms_s = e0.elapsed_time(e1)
     worst = 0.0
-    for k in range(0, ncase, max(1, ncase // 16)):
+    sampled = list(range(0, ncase, max(1, ncase // 16)))
+    for k in sampled:
         sb, _ = b.get_state(k)
         ss, _ = meshes[k].get_state()
         worst = max(worst, float(np.abs(sb - ss).max() / max(np.abs(ss).max(), 1e-300)))
+    # how far rounding alone carries these problems: the same single-case
+    # runs from initial states moved by one unit in the last place
+    rng = np.random.default_rng(7)
+    sens = 0.0
+    for k in sampled:
+        s0 = init_states[k]
+        m = Mesh(precision=1, stream=stream, **kws[k])
+        m.set_state(s0 * (1 + rng.choice([-1.0, 1.0], size=s0.shape) * 2.0 ** -53), 0.0)
+        m.step(args.warmup + 2 * args.steps)
+        sp, _ = m.get_state()
+        m.close()
+        ss, _ = meshes[k].get_state()
+        sens = max(sens, float(np.abs(sp - ss).max() / max(np.abs(ss).max(), 1e-300)))
     ncell = int(b.ncell)
     for m in meshes:
         m.close()
@@ -419,6 +435,8 @@ def ensemble_bench(args, stream, ncase=256):
                        "ms_per_step": ms_s / args.steps, "launch": "one cgks_step call per case"},
         "speedup": ms_s / ms_b,
         "max_rel_diff_batched_vs_sequential": worst,
+        "max_rel_diff_sequential_one_ulp_input": sens,
+        "sampled_cases": len(sampled),
         "clocks": clk.summary(),
     }
 
