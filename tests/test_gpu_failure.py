@@ -119,8 +119,9 @@ def test_midrun_failure_returns_last_good_step(orc, cg, precision):
     o = orc.Oracle(**RIEMANN)
     o.init(_riemann_field())
     o.step(j)
-    tol = 1e-5 if precision == 1 else 1e-10  # the FP32 form's time steps follow its FP32-rounded states
-    assert abs(o.time() - tg) <= 1e-3 * tol * tg
+    # the FP32 form's time steps follow its FP32-rounded states
+    tol, tol_t = (1e-5, 1e-6) if precision == 1 else (1e-10, 1e-13)
+    assert abs(o.time() - tg) <= tol_t * tg
     assert class_scaled_diff(sg, o.get_state(), 1 / 32) <= tol
 
 
