@@ -11,10 +11,13 @@
  *   product  the FMA residual of hi*hi plus the two cross terms;
  *   quotient a reciprocal estimate and two remainder corrections.
  *
+ * exp, expm1, erfc (|x| < 3/4) and 1/sqrt are series and Newton steps in
+ * pair arithmetic (below); erfc beyond 3/4 is the FP64 function rounded to
+ * a pair.
+ *
  * Every operation goes through the round-to-nearest intrinsics (fp_add
  * ...), which the compiler never contracts into multiply-adds, so the
- * error-free steps stay exact.  exp, erfc, expm1, sqrt and 1/sqrt are taken in FP64 and rounded to
- * a pair (a few per Gauss point).  Conversions from double round twice
+ * error-free steps stay exact.  Conversions from double round twice
  * (hi, then the remainder), exactly for constants, which fold at compile
  * time.  Included by cgks_device.cuh after its math wrappers.
  */
@@ -126,11 +129,110 @@ CGKS_HD bool operator>=(fpair a, fpair b) { return !(a < b); }
 CGKS_HD bool operator==(fpair a, fpair b) { return a.hi == b.hi && a.lo == b.lo; }
 CGKS_HD bool operator!=(fpair a, fpair b) { return !(a == b); }
 
-CGKS_HD fpair cg_erfc(fpair x) { return fpair(cg_erfc((double)x)); }
-CGKS_HD fpair cg_exp(fpair x) { return fpair(cg_exp((double)x)); }
-CGKS_HD fpair cg_expm1(fpair x) { return fpair(cg_expm1((double)x)); }
-CGKS_HD fpair cg_sqrt(fpair x) { return fpair(cg_sqrt((double)x)); }
-CGKS_HD fpair cg_rsqrt(fpair x) { return fpair(cg_rsqrt((double)x)); }
+/* ---- special functions in pair arithmetic, on the FP32 pipe ----
+   (GB300's FP64 pipe runs at 1/64 of the FP32 rate, so the FP64 library
+   functions cost more than these series.) */
+
+/* 2^k as a float, -126 <= k <= 127 */
+CGKS_HD float fp_pow2(int k) {
+#if defined(__CUDA_ARCH__)
+  return __int_as_float((k + 127) << 23);
+#else
+  return std::ldexp(1.0f, k);
+#endif
+}
+CGKS_HD float fp_rint(float a) {
+#if defined(__CUDA_ARCH__)
+  return rintf(a);
+#else
+  return std::rint(a);
+#endif
+}
+CGKS_HD float fp_rsqrt_est(float a) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(a);
+#else
+  return 1.0f / std::sqrt(a);
+#endif
+}
+/* a * s for s a power of two: exact unless it underflows */
+CGKS_HD fpair fp_scale(fpair a, float s) { return fp_make(fp_mul(a.hi, s), fp_mul(a.lo, s)); }
+
+/* exp(r) - 1 = sum_{n=1..13} r^n / n! for |r| <= ln2/2 (truncation below
+   2e-16 of exp(r)), Horner's rule in pairs */
+CGKS_HD fpair fp_expm1_small(fpair r) {
+  fpair p(1.0 / 6227020800.0);
+  p = p * r + fpair(1.0 / 479001600.0);
+  p = p * r + fpair(1.0 / 39916800.0);
+  p = p * r + fpair(1.0 / 3628800.0);
+  p = p * r + fpair(1.0 / 362880.0);
+  p = p * r + fpair(1.0 / 40320.0);
+  p = p * r + fpair(1.0 / 5040.0);
+  p = p * r + fpair(1.0 / 720.0);
+  p = p * r + fpair(1.0 / 120.0);
+  p = p * r + fpair(1.0 / 24.0);
+  p = p * r + fpair(1.0 / 6.0);
+  p = p * r + fpair(0.5f);
+  p = p * r + fpair(1.0f);
+  return p * r;
+}
+
+/* exp(x) = 2^k exp(r), x = k ln2 + r, |r| <= ln2/2.  ln2 is split Cody-Waite
+   style into a 16-bit float (k * its part is exact for |k| < 256), a float
+   and a float remainder.  Below -87 the result is under the float range and
+   is returned as 0 (the flux only adds such values to O(1) ones). */
+CGKS_HD fpair cg_exp(fpair x) {
+  if (x.hi < -87.0f) return fpair(0.0f);
+  const float kf = fp_rint(fp_mul(x.hi, 1.44269504088896341f));
+  const float L1 = 0.693145751953125f;        /* 16 significant bits */
+  const float L2 = 1.42860676533018705e-06f; /* ln2 - L1 rounded to a float */
+  const float L3 = 5.49792314810410715e-14f; /* ln2 - L1 - L2 rounded (residual 1.3e-21) */
+  fpair r = x - fpair(fp_mul(kf, L1));
+  float p2 = fp_mul(kf, L2);
+  r = r - fp_make(p2, fp_fma(kf, L2, -p2));
+  r = r - fpair(fp_mul(kf, L3));
+  return fp_scale(fp_expm1_small(r) + fpair(1.0f), fp_pow2((int)kf));
+}
+
+CGKS_HD fpair cg_expm1(fpair x) {
+  if (x.hi > -0.34657359f && x.hi < 0.34657359f) return fp_expm1_small(x);
+  return cg_exp(x) - fpair(1.0f);
+}
+
+/* erfc(x) = 1 - (2/sqrt(pi)) x sum_{n>=0} (-x^2)^n / (n! (2n+1)) for |x| < 3/4
+   (terms n <= 15; truncation below 5e-18); beyond, the FP64 library
+   function rounded to a pair */
+CGKS_HD fpair cg_erfc(fpair x) {
+  if (!(x.hi > -0.75f && x.hi < 0.75f)) return fpair(cg_erfc((double)x));
+  const fpair t = x * x;
+  fpair p(-1.0 / (1307674368000.0 * 31.0));
+  p = p * t + fpair(1.0 / (87178291200.0 * 29.0));
+  p = p * t + fpair(-1.0 / (6227020800.0 * 27.0));
+  p = p * t + fpair(1.0 / (479001600.0 * 25.0));
+  p = p * t + fpair(-1.0 / (39916800.0 * 23.0));
+  p = p * t + fpair(1.0 / (3628800.0 * 21.0));
+  p = p * t + fpair(-1.0 / (362880.0 * 19.0));
+  p = p * t + fpair(1.0 / (40320.0 * 17.0));
+  p = p * t + fpair(-1.0 / (5040.0 * 15.0));
+  p = p * t + fpair(1.0 / (720.0 * 13.0));
+  p = p * t + fpair(-1.0 / (120.0 * 11.0));
+  p = p * t + fpair(1.0 / (24.0 * 9.0));
+  p = p * t + fpair(-1.0 / (6.0 * 7.0));
+  p = p * t + fpair(1.0 / (2.0 * 5.0));
+  p = p * t + fpair(-1.0 / 3.0);
+  p = p * t + fpair(1.0f);
+  return fpair(1.0f) - fpair(1.12837916709551257390) * (x * p); /* 2/sqrt(pi) */
+}
+
+/* 1/sqrt(x), x > 0: the FP32 estimate and two Newton steps
+   y <- y + y (1 - x y^2) / 2 in pairs */
+CGKS_HD fpair cg_rsqrt(fpair x) {
+  fpair y(fp_rsqrt_est(x.hi));
+  y = y + fp_scale(y * (fpair(1.0f) - x * (y * y)), 0.5f);
+  y = y + fp_scale(y * (fpair(1.0f) - x * (y * y)), 0.5f);
+  return y;
+}
+CGKS_HD fpair cg_sqrt(fpair x) { return x.hi > 0.f ? x * cg_rsqrt(x) : fpair(0.0f); }
 CGKS_HD fpair cg_fabs(fpair x) { return x.hi < 0.f ? -x : x; }
 CGKS_HD fpair cg_fma(fpair a, fpair b, fpair c) { return a * b + c; }
 

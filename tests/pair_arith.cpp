@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <random>
+#include <cmath>
 namespace cgks {
 inline double cg_erfc(double x) { return erfc(x); }
 inline double cg_exp(double x) { return exp(x); }
@@ -45,6 +46,40 @@ void pair_stats(int n, unsigned seed, double* out) {
     const fpair pd = px - pz;
     const long double Z = (long double)pz.hi + pz.lo;
     out[3] = std::fmax(out[3], (double)(fabsl((long double)pd.hi + pd.lo - (X - Z)) / fabsl(X)));
+  }
+}
+}
+
+extern "C" {
+/* largest relative errors of the pair special functions against long double
+   references on random arguments: out[0] exp on [-40, 2], [1] expm1 on
+   [-2, 2], [2] erfc on [-3, 3] (the series below |x| = 3/4), [3] 1/sqrt on
+   [1e-8, 1e8]; out[4] exp on [-1, 1] relative to the result */
+void pair_func_stats(int n, unsigned seed, double* out) {
+  std::mt19937_64 rng(seed);
+  std::uniform_real_distribution<double> u(0.0, 1.0);
+  for (int i = 0; i < 5; ++i) out[i] = 0;
+  auto val = [](const fpair& p) { return (long double)p.hi + p.lo; };
+  for (int it = 0; it < n; ++it) {
+    const double a = -40.0 + 42.0 * u(rng);
+    const fpair pa(a);
+    const long double A = val(pa);
+    out[0] = std::fmax(out[0], (double)fabsl(val(cgks::cg_exp(pa)) / expl(A) - 1.0L));
+    const double b = -2.0 + 4.0 * u(rng);
+    const fpair pb(b);
+    const long double B = val(pb);
+    out[1] = std::fmax(out[1], (double)fabsl(val(cgks::cg_expm1(pb)) / expm1l(B) - 1.0L));
+    const double c = -3.0 + 6.0 * u(rng);
+    const fpair pc(c);
+    const long double Cc = val(pc);
+    out[2] = std::fmax(out[2], (double)fabsl(val(cgks::cg_erfc(pc)) / erfcl(Cc) - 1.0L));
+    const double d = std::pow(10.0, -8.0 + 16.0 * u(rng));
+    const fpair pd(d);
+    const long double D = val(pd);
+    out[3] = std::fmax(out[3], (double)fabsl(val(cgks::cg_rsqrt(pd)) * sqrtl(D) - 1.0L));
+    const double e = -1.0 + 2.0 * u(rng);
+    const fpair pe(e);
+    out[4] = std::fmax(out[4], (double)fabsl(val(cgks::cg_exp(pe)) / expl(val(pe)) - 1.0L));
   }
 }
 }

@@ -44,3 +44,16 @@ def test_pair_arithmetic(lib, seed):
     bound = 2.0 ** -44
     assert e_cvt <= 2.0 ** -48
     assert e_sum <= bound and e_diff <= bound and e_mul <= bound and e_div <= bound, list(out)
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_pair_special_functions(lib, seed):
+    """exp, expm1, erfc and 1/sqrt of the paired form in pair arithmetic,
+    against long double references: within a few units of 2^-48."""
+    lib.pair_func_stats.argtypes = [C.c_int, C.c_uint, C.POINTER(C.c_double)]
+    out = (C.c_double * 5)()
+    lib.pair_func_stats(100000, seed, out)
+    e_exp, e_expm1, e_erfc, e_rsqrt, e_exp1 = list(out)
+    print("exp %.2e expm1 %.2e erfc %.2e rsqrt %.2e exp[-1,1] %.2e" % tuple(out))
+    assert e_exp1 <= 2.0 ** -46 and e_exp <= 2.0 ** -44
+    assert e_expm1 <= 2.0 ** -45 and e_erfc <= 2.0 ** -45 and e_rsqrt <= 2.0 ** -46
