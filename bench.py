@@ -456,8 +456,8 @@ def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
     params, thr, lo = selector.load()
     out = {"thr_skip": thr, "thr_lo": lo, "cases": []}
 
-    def run(kw, fn, s0, steps, on, precision):
-        m = Mesh(precision=precision, stream=stream, **kw)
+    def run(kw, fn, s0, steps, on, precision, linear=False):
+        m = Mesh(precision=precision, stream=stream, linear=linear, **kw)
         if s0 is None:
             m.init(fn)
         else:
@@ -502,12 +502,17 @@ def selector_bench(args, stream, s_tgv_init=None, s_tgv_fp64=None):
         except CgksError as ex:
             out["cases"].append({"case": name, "error": str(ex)})
             continue
+        try:  # the ceiling of any selector: every cell skips, for free (chi = 1, no features, no inference)
+            _, msl, rcl, _ = run(kw, fn, s0, args.steps, False, precision, linear=True)
+        except CgksError:
+            msl = rcl = None
         ncell = int(np.prod(kw["n"]))
         recons = 2 * (args.warmup + args.steps) * ncell
         e = s_sel[0, 0] - s_plain[0, 0]
         rec = {"case": name, "form": "fp32" if precision == 1 else "fp64",
-               "ms_per_step": {"plain": ms0, "selector": ms1}, "speedup": ms0 / ms1,
-               "recon_ms": {"plain": rc0, "selector": rc1},
+               "ms_per_step": {"plain": ms0, "selector": ms1, "skip_all_free": msl}, "speedup": ms0 / ms1,
+               "speedup_ceiling": ms0 / msl if msl else None,
+               "recon_ms": {"plain": rc0, "selector": rc1, "skip_all_free": rcl},
                "skip_rate": nskip / recons, "fallback_rate": 1.0 - nskip / recons,
                "low_confidence_rate": nuns / recons,
                "density_l2_vs_plain": float(np.sqrt(np.mean(e * e) / np.mean(s_plain[0, 0] ** 2))),
