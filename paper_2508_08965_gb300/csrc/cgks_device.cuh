@@ -328,6 +328,12 @@ CGKS_HD double cg_fabs(double x) { return fabs(x); }
 CGKS_HD float cg_fabs(float x) { return fabsf(x); }
 CGKS_HD double cg_fma(double a, double b, double c) { return fma(a, b, c); }
 CGKS_HD float cg_fma(float a, float b, float c) { return fmaf(a, b, c); }
+/* a b + c d and a b + c d + e f, evaluated left to right (the paired type
+   overloads them with compensated dot products) */
+CGKS_HD double cg_dot2(double a, double b, double c, double d) { return a * b + c * d; }
+CGKS_HD float cg_dot2(float a, float b, float c, float d) { return a * b + c * d; }
+CGKS_HD double cg_dot3(double a, double b, double c, double d, double e, double f) { return a * b + c * d + e * f; }
+CGKS_HD float cg_dot3(float a, float b, float c, float d, float e, float f) { return a * b + c * d + e * f; }
 #include "cgks_pair.cuh"
 CGKS_HD double cg_tanh(double x) { return tanh(x); }
 CGKS_HD float cg_tanh(float x) { return tanhf(x); }
@@ -772,7 +778,7 @@ template <typename T, int DIM> struct PolyMom {
     xi4 = s.xi4;
   }
   template <int R> CGKS_HD T S() const {
-    if constexpr (DIM == 3) return a0x * t.w[R] + a3 * t.w[R + 1] + ah * t.w[R + 2];
+    if constexpr (DIM == 3) return cg_dot3(a0x, t.w[R], a3, t.w[R + 1], ah, t.w[R + 2]);
     else return R == 0 ? a0x : T(0);
   }
   template <int R> CGKS_HD T W() const {
@@ -780,10 +786,10 @@ template <typename T, int DIM> struct PolyMom {
     else return R == 0 ? T(1) : T(0);
   }
   template <int Q, int R> CGKS_HD T Tq() const {
-    return t.v[Q] * S<R>() + (a2 * t.v[Q + 1] + ah * t.v[Q + 2]) * W<R>();
+    return cg_dot2(t.v[Q], S<R>(), cg_dot2(a2, t.v[Q + 1], ah, t.v[Q + 2]), W<R>());
   }
   template <int P, int Q, int R> CGKS_HD T G() const {
-    return t.u[P] * Tq<Q, R>() + (a1 * t.u[P + 1] + ah * t.u[P + 2]) * (t.v[Q] * W<R>());
+    return cg_dot2(t.u[P], Tq<Q, R>(), cg_dot2(a1, t.u[P + 1], ah, t.u[P + 2]), t.v[Q] * W<R>());
   }
   template <int A, int B, int C> CGKS_HD void out(T* o) const {
     const T g0 = G<A, B, C>();

@@ -129,6 +129,39 @@ CGKS_HD bool operator>=(fpair a, fpair b) { return !(a < b); }
 CGKS_HD bool operator==(fpair a, fpair b) { return a.hi == b.hi && a.lo == b.lo; }
 CGKS_HD bool operator!=(fpair a, fpair b) { return !(a == b); }
 
+/* a b + c d and a b + c d + e f with one renormalisation: the high-part
+   products and their FMA residuals, Knuth's two-sum of the products, the
+   residuals and sum errors gathered in the low part (a compensated dot
+   product in the manner of Ogita, Rump and Oishi's Dot2, on pairs) */
+CGKS_HD void fp_prod_parts(fpair a, fpair b, float& p, float& e) {
+  p = fp_mul(a.hi, b.hi);
+  e = fp_fma(a.hi, b.hi, -p);
+  e = fp_fma(a.hi, b.lo, e);
+  e = fp_fma(a.lo, b.hi, e);
+}
+CGKS_HD fpair fp_dot2(fpair a, fpair b, fpair c, fpair d) {
+  float p1, e1, p2, e2, s, t;
+  fp_prod_parts(a, b, p1, e1);
+  fp_prod_parts(c, d, p2, e2);
+  fp_two_sum(p1, p2, s, t);
+  t = fp_add(t, fp_add(e1, e2));
+  fp_fast_two_sum(s, t, s, t);
+  return fp_make(s, t);
+}
+CGKS_HD fpair fp_dot3(fpair a, fpair b, fpair c, fpair d, fpair e, fpair f) {
+  float p1, e1, p2, e2, p3, e3, s, t, u;
+  fp_prod_parts(a, b, p1, e1);
+  fp_prod_parts(c, d, p2, e2);
+  fp_prod_parts(e, f, p3, e3);
+  fp_two_sum(p1, p2, s, t);
+  fp_two_sum(s, p3, s, u);
+  t = fp_add(fp_add(t, u), fp_add(fp_add(e1, e2), e3));
+  fp_fast_two_sum(s, t, s, t);
+  return fp_make(s, t);
+}
+CGKS_HD fpair cg_dot2(fpair a, fpair b, fpair c, fpair d) { return fp_dot2(a, b, c, d); }
+CGKS_HD fpair cg_dot3(fpair a, fpair b, fpair c, fpair d, fpair e, fpair f) { return fp_dot3(a, b, c, d, e, f); }
+
 /* ---- special functions in pair arithmetic, on the FP32 pipe ----
    (GB300's FP64 pipe runs at 1/64 of the FP32 rate, so the FP64 library
    functions cost more than these series.) */

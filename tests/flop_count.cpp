@@ -135,6 +135,9 @@ inline fcount cg_fma(fcount a, fcount b, fcount c) {
   return fcount(std::fma(a.v, b.v, c.v), fc::G.op(fc::FMA, 0, a.id, b.id, c.id));
 }
 
+inline fcount cg_dot2(fcount a, fcount b, fcount c, fcount d) { return a * b + c * d; }
+inline fcount cg_dot3(fcount a, fcount b, fcount c, fcount d, fcount e, fcount f) { return a * b + c * d + e * f; }
+
 #include "host_kernels.cpp"
 
 namespace {
