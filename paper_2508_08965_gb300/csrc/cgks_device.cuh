@@ -334,6 +334,9 @@ CGKS_HD double cg_dot2(double a, double b, double c, double d) { return a * b + 
 CGKS_HD float cg_dot2(float a, float b, float c, float d) { return a * b + c * d; }
 CGKS_HD double cg_dot3(double a, double b, double c, double d, double e, double f) { return a * b + c * d + e * f; }
 CGKS_HD float cg_dot3(float a, float b, float c, float d, float e, float f) { return a * b + c * d + e * f; }
+/* a b + c (the paired type overloads it with one renormalisation) */
+CGKS_HD double cg_madd(double a, double b, double c) { return a * b + c; }
+CGKS_HD float cg_madd(float a, float b, float c) { return a * b + c; }
 #include "cgks_pair.cuh"
 CGKS_HD double cg_tanh(double x) { return tanh(x); }
 CGKS_HD float cg_tanh(float x) { return tanhf(x); }
@@ -748,9 +751,9 @@ CGKS_HD void mx_tables(const MxS<T, DIM>& m, MxT<T>& t) {
 #pragma unroll
   for (int n = 0; n < 5; ++n) {
     const T c = T(n + 1) * m.i2l;
-    t.u[n + 2] = m.U[0] * t.u[n + 1] + c * t.u[n];
-    t.v[n + 2] = m.U[1] * t.v[n + 1] + c * t.v[n];
-    t.w[n + 2] = DIM == 3 ? m.U[2] * t.w[n + 1] + c * t.w[n] : T(0);
+    t.u[n + 2] = cg_dot2(m.U[0], t.u[n + 1], c, t.u[n]);
+    t.v[n + 2] = cg_dot2(m.U[1], t.v[n + 1], c, t.v[n]);
+    t.w[n + 2] = DIM == 3 ? cg_dot2(m.U[2], t.w[n + 1], c, t.w[n]) : T(0);
   }
 }
 
@@ -873,8 +876,11 @@ CGKS_HD void euler_jvp(const MxS<T, DIM>& g, T gam, const T* W, int j, const T* 
   const T uj = g.U[j], dmj = dW[1 + j];
   out[0] = dmj;
 #pragma unroll
-  for (int i = 0; i < DIM; ++i) out[1 + i] = uj * dW[1 + i] + g.U[i] * dmj - uj * g.U[i] * dW[0] + (i == j ? dp : T(0));
-  out[DIM + 1] = uj * (dW[DIM + 1] + dp) + H * (dmj - uj * dW[0]);
+  for (int i = 0; i < DIM; ++i) {
+    const T o = cg_dot3(uj, dW[1 + i], g.U[i], dmj, -(uj * g.U[i]), dW[0]);
+    out[1 + i] = i == j ? o + dp : o;
+  }
+  out[DIM + 1] = cg_dot2(uj, dW[DIM + 1] + dp, H, dmj - uj * dW[0]);
 }
 
 /* time integrals over [0, dl] of the six coefficient functions of Eq. (flux),
@@ -899,7 +905,7 @@ CGKS_HD void tcoef(T tau, T dl, T em, T ex, T* c) {
 template <typename T, int DIM> CGKS_HD T qdot(const T* qw, const T* o) {
   T q = qw[DIM + 1] * o[DIM + 1];
 #pragma unroll
-  for (int i = 0; i <= DIM; ++i) q += qw[i] * o[i];
+  for (int i = 0; i <= DIM; ++i) q = cg_madd(qw[i], o[i], q);
   return q;
 }
 
@@ -919,21 +925,22 @@ CGKS_HD void side_dir(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, c
   slope_solve<T, DIM>(s, D, iD, b, a);
   mvec<T, DIM, 0, 0, 0>(s, t, a, t1);
 #pragma unroll
-  for (int i = 0; i < NV; ++i) dW0j[i] += s.rho * t1[i];
+  for (int i = 0; i < NV; ++i) dW0j[i] = cg_madd(s.rho, t1[i], dW0j[i]);
   euler_jvp<T, DIM>(s, gam, W, J, dWj, t1);
 #pragma unroll
-  for (int i = 0; i < NV; ++i) bs[i] -= t1[i] * s.irho;
+  for (int i = 0; i < NV; ++i) bs[i] = cg_madd(-t1[i], s.irho, bs[i]);
   mvec<T, DIM, 1 + E0, E1, E2>(s, t, a, t1);
+  const T crn = cn[4] * s.rho, crt = ct[4] * s.rho;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    Fn[i] += cn[4] * s.rho * t1[i];
-    Ft[i] += ct[4] * s.rho * t1[i];
+    Fn[i] = cg_madd(crn, t1[i], Fn[i]);
+    Ft[i] = cg_madd(crt, t1[i], Ft[i]);
   }
   if (prfix) {
     mvec<T, DIM, E0, E1, E2>(s, t, a, t1);
     const T q = qdot<T, DIM>(qw, t1);
-    qn += cn[4] * s.rho * q;
-    qt += ct[4] * s.rho * q;
+    qn = cg_madd(crn, q, qn);
+    qt = cg_madd(crt, q, qt);
   }
 }
 
@@ -956,16 +963,17 @@ CGKS_HD void side_all(const MxS<T, DIM>& s, const MxT<T>& t, T gam, T D, T iD, c
   T A[NV], t1[NV];
   slope_solve<T, DIM>(s, D, iD, bs, A);
   mvec<T, DIM, 1, 0, 0>(s, t, A, t1);
+  const T crn = cn[5] * s.rho, crt = ct[5] * s.rho;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    Fn[i] += cn[5] * s.rho * t1[i];
-    Ft[i] += ct[5] * s.rho * t1[i];
+    Fn[i] = cg_madd(crn, t1[i], Fn[i]);
+    Ft[i] = cg_madd(crt, t1[i], Ft[i]);
   }
   if (prfix) {
     mvec<T, DIM, 0, 0, 0>(s, t, A, t1);
     const T q = qdot<T, DIM>(qw, t1);
-    qn += cn[5] * s.rho * q;
-    qt += ct[5] * s.rho * q;
+    qn = cg_madd(crn, q, qn);
+    qt = cg_madd(crt, q, qt);
   }
 }
 
@@ -981,18 +989,19 @@ CGKS_HD void g0_dir(const MxS<T, DIM>& z, const MxT<T>& t, T gam, T D, T iD, con
   for (int i = 0; i < NV; ++i) b[i] = dW0j[i] * z.irho;
   slope_solve<T, DIM>(z, D, iD, b, a);
   mvec<T, DIM, 1 + E0, E1, E2>(z, t, a, t1);
+  const T crn = cn[1] * z.rho, crt = ct[1] * z.rho;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    Fn[i] += cn[1] * z.rho * t1[i];
-    Ft[i] += ct[1] * z.rho * t1[i];
+    Fn[i] = cg_madd(crn, t1[i], Fn[i]);
+    Ft[i] = cg_madd(crt, t1[i], Ft[i]);
   }
   euler_jvp<T, DIM>(z, gam, W0, J, dW0j, t1);
 #pragma unroll
-  for (int i = 0; i < NV; ++i) b0[i] -= t1[i] * z.irho;
+  for (int i = 0; i < NV; ++i) b0[i] = cg_madd(-t1[i], z.irho, b0[i]);
   if (prfix) {
     const T q = qdot<T, DIM>(qw, t1);
-    qn += cn[1] * q;
-    qt += ct[1] * q;
+    qn = cg_madd(cn[1], q, qn);
+    qt = cg_madd(ct[1], q, qt);
   }
 }
 
@@ -1075,8 +1084,8 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   euler_flux<T, DIM>(z, W0, 0, t1); /* part 0: rho0 <u psi> of g0 */
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    Fn[i] = cn[0] * t1[i] + cn[3] * H3[i];
-    Ft[i] = ct[0] * t1[i] + ct[3] * H3[i];
+    Fn[i] = cg_dot2(cn[0], t1[i], cn[3], H3[i]);
+    Ft[i] = cg_dot2(ct[0], t1[i], ct[3], H3[i]);
     b0[i] = T(0);
   }
   T qn = T(0), qt = T(0);
@@ -1107,8 +1116,8 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   euler_jvp<T, DIM>(z, gam, W0, 0, t2, t1);
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    Fn[i] += cn[2] * t1[i];
-    Ft[i] += ct[2] * t1[i];
+    Fn[i] = cg_madd(cn[2], t1[i], Fn[i]);
+    Ft[i] = cg_madd(ct[2], t1[i], Ft[i]);
   }
   if (prfix) { /* heat-flux correction F_E += (1/Pr - 1) q about the interface velocity,
                   q = qw . F - U_x qw . Q of the non-equilibrium part f - g0 (1 + A0 t):
@@ -1131,10 +1140,10 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
     out[i] = Fn[i];
     out[NV + i] = Ft[i];
     const T dq0 = z.rho * b0[i];
-    out[2 * NV + i] = (T(1) - w) * W0[i] + w * WL[i];
-    out[3 * NV + i] = (T(1) - w) * dq0 + w * l.rho * bl[i];
-    out[4 * NV + i] = (T(1) - w) * W0[i] + w * WR[i];
-    out[5 * NV + i] = (T(1) - w) * dq0 + w * r.rho * br[i];
+    out[2 * NV + i] = cg_dot2(T(1) - w, W0[i], w, WL[i]);
+    out[3 * NV + i] = cg_dot2(T(1) - w, dq0, w * l.rho, bl[i]);
+    out[4 * NV + i] = cg_dot2(T(1) - w, W0[i], w, WR[i]);
+    out[5 * NV + i] = cg_dot2(T(1) - w, dq0, w * r.rho, br[i]);
   }
   return true;
 }

@@ -159,6 +159,16 @@ CGKS_HD fpair fp_dot3(fpair a, fpair b, fpair c, fpair d, fpair e, fpair f) {
   fp_fast_two_sum(s, t, s, t);
   return fp_make(s, t);
 }
+/* a b + c with one renormalisation */
+CGKS_HD fpair fp_madd(fpair a, fpair b, fpair c) {
+  float p, e, s, t;
+  fp_prod_parts(a, b, p, e);
+  fp_two_sum(p, c.hi, s, t);
+  t = fp_add(t, fp_add(e, c.lo));
+  fp_fast_two_sum(s, t, s, t);
+  return fp_make(s, t);
+}
+CGKS_HD fpair cg_madd(fpair a, fpair b, fpair c) { return fp_madd(a, b, c); }
 CGKS_HD fpair cg_dot2(fpair a, fpair b, fpair c, fpair d) { return fp_dot2(a, b, c, d); }
 CGKS_HD fpair cg_dot3(fpair a, fpair b, fpair c, fpair d, fpair e, fpair f) { return fp_dot3(a, b, c, d, e, f); }
 
