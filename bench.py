@@ -47,9 +47,9 @@ WORKLOADS = {
 # the collision-time and Prandtl-fix terms.  The same algorithm runs in the
 # FP64, FP32 and paired forms.
 ALG_FLOPS_PER_UNIT = {
-    ("flux", 3, True): 2920.0,
-    ("flux", 2, True): 1670.0,
-    ("flux", 2, False): 764.0,
+    ("flux", 3, True): 2919.0,
+    ("flux", 2, True): 1672.0,
+    ("flux", 2, False): 766.0,
 }
 # Executed work per unit from ncu instruction counts (TGV 64^3, same
 # kernels): 2 DFMA + DADD + DMUL (FP64) or 2 FFMA + FADD + FMUL (FP32),

@@ -799,11 +799,12 @@ template <typename T, int DIM> struct PolyMom {
     o[0] = g0;
     o[1] = G<A + 1, B, C>();
     o[2] = G<A, B + 1, C>();
-    T e = G<A + 2, B, C>() + G<A, B + 2, C>() + xi2 * g0 + ah * (xi4 - xi2 * xi2) * (t.u[A] * t.v[B] * W<C>());
+    T gs = G<A + 2, B, C>() + G<A, B + 2, C>();
     if constexpr (DIM == 3) {
       o[3] = G<A, B, C + 1>();
-      e += G<A, B, C + 2>();
+      gs += G<A, B, C + 2>();
     }
+    const T e = cg_madd(ah * (xi4 - xi2 * xi2), t.u[A] * t.v[B] * W<C>(), cg_madd(xi2, g0, gs));
     o[DIM + 1] = T(0.5) * e;
   }
 };
@@ -819,12 +820,12 @@ CGKS_HD void mpsi_u(const MxS<T, DIM>& s, const MxT<T>& m, T* out) {
   out[0] = m.u[A];
   out[1] = m.u[A + 1];
   out[2] = m.u[A] * m.v[1];
-  T e = m.u[A + 2] + m.u[A] * m.v[2] + s.xi2 * m.u[A];
+  T c2 = m.v[2] + s.xi2;
   if constexpr (DIM == 3) {
     out[3] = m.u[A] * m.w[1];
-    e += m.u[A] * m.w[2];
+    c2 += m.w[2];
   }
-  out[DIM + 1] = T(0.5) * e;
+  out[DIM + 1] = T(0.5) * cg_madd(m.u[A], c2, m.u[A + 2]);
 }
 
 /* micro-slope: solve <a psi psi^T> = b in closed form (D = K + dim = 2/(gamma-1)) */
@@ -833,21 +834,22 @@ CGKS_HD void slope_solve(const MxS<T, DIM>& g, T D, T iD, const T* b, T* a) {
   T q2 = T(0), R[3], uR = T(0);
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
-    q2 += g.U[i] * g.U[i];
-    R[i] = b[1 + i] - g.U[i] * b[0];
-    uR += g.U[i] * R[i];
+    q2 = cg_madd(g.U[i], g.U[i], q2);
+    R[i] = cg_madd(-g.U[i], b[0], b[1 + i]);
+    uR = cg_madd(g.U[i], R[i], uR);
   }
-  const T th = q2 + D * g.i2l;
-  const T Re = T(2) * b[DIM + 1] - th * b[0];
+  const T th = cg_madd(D, g.i2l, q2);
+  const T Re = cg_madd(-th, b[0], T(2) * b[DIM + 1]);
   const T ae = T(4) * g.lam * g.lam * iD * (Re - T(2) * uR);
+  const T l2 = T(2) * g.lam;
   T s = T(0);
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
-    a[1 + i] = T(2) * g.lam * R[i] - g.U[i] * ae;
-    s += g.U[i] * a[1 + i];
+    a[1 + i] = cg_dot2(l2, R[i], -g.U[i], ae);
+    s = cg_madd(g.U[i], a[1 + i], s);
   }
   a[DIM + 1] = ae;
-  a[0] = b[0] - s - T(0.5) * ae * th;
+  a[0] = cg_madd(T(-0.5) * ae, th, b[0] - s);
 }
 
 /* Euler flux along local axis j of a Maxwellian state, and its Jacobian
