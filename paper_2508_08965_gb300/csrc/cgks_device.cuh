@@ -1098,7 +1098,26 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   }
 #pragma unroll
   for (int i = 0; i < DIM * NV; ++i) dW0[i] = T(0);
-  {
+  if constexpr (cg_same<T, fpair>::value) {
+    /* the paired solve: one copy of the per-side code, run for the left and
+       then the right side (its straight-line code is what the instruction
+       fetch of this kernel waits on); same order, same results */
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      const MxS<T, DIM> s = side ? r : l;
+      T W[NV], bs[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) W[i] = side ? WR[i] : WL[i];
+      MxT<T> t;
+      mx_tables<T, DIM>(s, t);
+      side_all<T, DIM>(s, t, gam, D, iD, W, ld, side, cn, ct, prfix, Fn, Ft, qw, qn, qt, bs, dW0);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        if (side) br[i] = bs[i];
+        else bl[i] = bs[i];
+      }
+    }
+  } else {
     MxT<T> t;
     mx_tables<T, DIM>(l, t);
     side_all<T, DIM>(l, t, gam, D, iD, WL, ld, 0, cn, ct, prfix, Fn, Ft, qw, qn, qt, bl, dW0);
