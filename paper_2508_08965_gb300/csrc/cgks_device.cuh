@@ -1022,12 +1022,38 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   const T iD = T(0.5) * (gam - T(1));
   const T K = D - T(DIM);
   MxS<T, DIM> l, r, z;
-  if (!mx_init<T, DIM>(WL, gam, K, REG_POS, l) || !mx_init<T, DIM>(WR, gam, K, REG_NEG, r)) return false;
   /* equilibrium state W0 and flux part 3 from the two half Maxwellians (the
      moment tables are rebuilt for the slope parts below: keeping both sides'
      tables live spills 250 B per thread in FP64 3-D and measured no faster) */
   T W0[NV], H3[NV], t1[NV], t2[NV];
-  {
+  if constexpr (cg_same<T, fpair>::value) {
+    /* the paired solve: one rolled copy for both sides (see the side loop) */
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      W0[i] = T(0);
+      H3[i] = T(0);
+    }
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      T W[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) W[i] = side ? WR[i] : WL[i];
+      MxS<T, DIM> m;
+      if (!mx_init<T, DIM>(W, gam, K, side ? REG_NEG : REG_POS, m)) return false;
+      MxT<T> t;
+      mx_tables<T, DIM>(m, t);
+      mpsi_u<T, DIM, 0>(m, t, t1);
+      mpsi_u<T, DIM, 1>(m, t, t2);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        W0[i] = cg_madd(m.rho, t1[i], W0[i]);
+        H3[i] = cg_madd(m.rho, t2[i], H3[i]);
+      }
+      if (side) r = m;
+      else l = m;
+    }
+  } else {
+    if (!mx_init<T, DIM>(WL, gam, K, REG_POS, l) || !mx_init<T, DIM>(WR, gam, K, REG_NEG, r)) return false;
     MxT<T> t;
     mx_tables<T, DIM>(l, t);
     mpsi_u<T, DIM, 0>(l, t, t1);
