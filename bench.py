@@ -61,10 +61,13 @@ EXEC_FLOPS_PER_UNIT = {
     ("flux", 3): 3.616e3,
 }
 # the paired form's flux (ncu, TGV 64^3): FP32 flops it executes per face
-# Gauss point for its FP64-equivalent work (2 FFMA + FADD + FMUL; plus 446
-# FP64 flops of conversions and special functions)
+# Gauss point for its FP64-equivalent work (2 FFMA + FADD + FMUL; plus 99
+# FP64 flops of conversions)
 EXEC_FP32_FLOPS_PER_UNIT_PAIR = {
-    ("flux", 3): 33761.0,
+    ("flux", 3): 31262.0,
+}
+DRAM_BYTES_PER_UNIT_PAIR = {
+    ("flux", 3): (1.007182e9 + 0.731100e9) / (262144 * 12),
 }
 # DRAM bytes per unit of the same capture (read + write), for `traffic`
 DRAM_BYTES_PER_UNIT = {
@@ -189,7 +192,8 @@ def roofline(prof, spec, ncell, precision, viscous):
     else:
         units = ncell * dim * (4 if dim == 3 else 2)
     exe = (EXEC_FLOPS_PER_UNIT if precision != 1 else EXEC_FLOPS_PER_UNIT_FP32).get((name, dim))
-    dram = (DRAM_BYTES_PER_UNIT if precision == 0 else DRAM_BYTES_PER_UNIT_FP32 if precision == 1 else {})
+    dram = (DRAM_BYTES_PER_UNIT if precision == 0 else DRAM_BYTES_PER_UNIT_FP32 if precision == 1
+            else DRAM_BYTES_PER_UNIT_PAIR)
     alg = ALG_FLOPS_PER_UNIT.get((name, dim, viscous))
     if precision == 1:
         peak = fp32_alu_peak_tflops()
@@ -214,9 +218,12 @@ def roofline(prof, spec, ncell, precision, viscous):
     pair32 = EXEC_FP32_FLOPS_PER_UNIT_PAIR.get((name, dim)) if precision == 2 and name == "flux" else None
     if pair32:
         p32 = fp32_alu_peak_tflops()
-        out.update({"fp32_flops_per_unit_executed": pair32, "frac_fp32_pipe": pair32 * units / sec / 1e12 / p32})
+        out.update({"fp32_flops_per_unit_executed": pair32, "frac_fp32_pipe": pair32 * units / sec / 1e12 / p32,
+                    "note": "FP64-equivalent work delivered through the FP32 pipe in paired arithmetic: frac is "
+                            "against the FP64 pipe it replaces and can exceed 1; frac_fp32_pipe is the FP32 "
+                            "pipe's own use"})
     dbu = dram.get((name, dim))
-    if dbu and precision != 2:
+    if dbu:
         out.update({"traffic": dbu * units,
                     "traffic_source": "ncu dram__bytes_read+write of a 64^3 capture, scaled by units"})
     if not alg:
