@@ -1153,9 +1153,42 @@ CGKS_HD bool gks_point_ld(const Phys& ph, T dt, const T* WL, const T* WR, const 
   {
     MxT<T> t;
     mx_tables<T, DIM>(z, t);
-    g0_dir<T, DIM, 0>(z, t, gam, D, iD, W0, dW0, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
-    g0_dir<T, DIM, 1>(z, t, gam, D, iD, W0, dW0 + NV, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
-    if constexpr (DIM == 3) g0_dir<T, DIM, 2>(z, t, gam, D, iD, W0, dW0 + 2 * NV, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
+    if constexpr (cg_same<T, fpair>::value) {
+      /* the paired solve: the three directions as one rolled loop (the
+         direction's slopes picked by selects, its flux moments by
+         warp-uniform branches); same order, same results */
+#pragma unroll 1
+      for (int j = 0; j < DIM; ++j) {
+        T dj[NV], b[NV], a[NV], t1[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          dj[i] = j == 0 ? dW0[i] : (j == 1 ? dW0[NV + i] : dW0[(DIM - 1) * NV + i]);
+          b[i] = dj[i] * z.irho;
+        }
+        slope_solve<T, DIM>(z, D, iD, b, a);
+        if (j == 0) mvec<T, DIM, 2, 0, 0>(z, t, a, t1);
+        else if (DIM == 2 || j == 1) mvec<T, DIM, 1, 1, 0>(z, t, a, t1);
+        else mvec<T, DIM, 1, 0, DIM == 3 ? 1 : 0>(z, t, a, t1);
+        const T crn = cn[1] * z.rho, crt = ct[1] * z.rho;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          Fn[i] = cg_madd(crn, t1[i], Fn[i]);
+          Ft[i] = cg_madd(crt, t1[i], Ft[i]);
+        }
+        euler_jvp<T, DIM>(z, gam, W0, j, dj, t1);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) b0[i] = cg_madd(-t1[i], z.irho, b0[i]);
+        if (prfix) {
+          const T q = qdot<T, DIM>(qw, t1);
+          qn = cg_madd(cn[1], q, qn);
+          qt = cg_madd(ct[1], q, qt);
+        }
+      }
+    } else {
+      g0_dir<T, DIM, 0>(z, t, gam, D, iD, W0, dW0, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
+      g0_dir<T, DIM, 1>(z, t, gam, D, iD, W0, dW0 + NV, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
+      if constexpr (DIM == 3) g0_dir<T, DIM, 2>(z, t, gam, D, iD, W0, dW0 + 2 * NV, cn, ct, prfix, Fn, Ft, qw, qn, qt, b0);
+    }
   }
   /* part 2: rho0 <A0 u psi> = (dF_x/dW)(rho0 b0), psi-moment rho0 b0 */
 #pragma unroll
