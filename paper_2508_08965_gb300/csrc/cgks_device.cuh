@@ -875,7 +875,10 @@ CGKS_HD void euler_jvp(const MxS<T, DIM>& g, T gam, const T* W, int j, const T* 
     um += g.U[i] * dW[1 + i];
   }
   const T dp = (gam - T(1)) * (dW[DIM + 1] - um + T(0.5) * q2 * dW[0]);
-  const T uj = g.U[j], dmj = dW[1 + j];
+  /* by selects: j may be a run-time loop index (an indexed register array
+     would go to local memory) */
+  const T uj = j == 0 ? g.U[0] : (j == 1 ? g.U[1] : g.U[DIM - 1]);
+  const T dmj = j == 0 ? dW[1] : (j == 1 ? dW[2] : dW[DIM]);
   out[0] = dmj;
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
