@@ -8,7 +8,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 # translation units, compiled in parallel and linked into one library
 SRCS = [os.path.join(CSRC, f) for f in ("cgks.cu", "cgks_stage_f64.cu", "cgks_stage_f32.cu", "cgks_stage_pair.cu",
-                                        "cgks_stage_pair_curvi.cu", "cgks_batch.cu", "cgks_mlp.cu", "cgks_noalloc.cu")]
+                                        "cgks_stage_pair_curvi.cu", "cgks_recon_pair.cu", "cgks_batch.cu", "cgks_mlp.cu", "cgks_noalloc.cu")]
 LIB = os.path.join(HERE, "libcgks.so")
 DEPS = SRCS + [os.path.join(CSRC, f) for f in ("cgks_device.cuh", "cgks_pair.cuh", "cgks_kernels.cuh", "cgks_ctx.h",
                                                "cgks_stage.inc",

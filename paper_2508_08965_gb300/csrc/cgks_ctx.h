@@ -130,4 +130,14 @@ extern template void launch_flux_pair<3, false>(cgks_ctx*, const double*, const 
 extern template void launch_flux_pair<2, true>(cgks_ctx*, const double*, const double*, double*);
 extern template void launch_flux_pair<3, true>(cgks_ctx*, const double*, const double*, double*);
 
+/* the reconstruction of the paired form on Cartesian meshes: FP64 averages
+   and derivatives in, the linear maps in paired FP32, FP64 Gauss-point
+   states out.  Instantiated in cgks_recon_pair.cu. */
+template <int DIM, bool WALL>
+void launch_recon_pair(cgks_ctx* ctx, int in, int record_chi);
+extern template void launch_recon_pair<2, false>(cgks_ctx*, int, int);
+extern template void launch_recon_pair<2, true>(cgks_ctx*, int, int);
+extern template void launch_recon_pair<3, false>(cgks_ctx*, int, int);
+extern template void launch_recon_pair<3, true>(cgks_ctx*, int, int);
+
 #endif

@@ -454,34 +454,103 @@ template <typename T, int DIM, bool CURVI, bool WALL> struct ReconLd {
    values (the FP32 error of these sums of at most ~100 terms is below 7e-6
    of that, the FP64 one far below).  FP32 form: never (its indicators are
    FP32 already). */
+template <int DIM> CGKS_HD bool geno_saturates_f32v(const float* af, double C) {
+  const double r2 = 2.0 * C / 25.0 - 3.0 - 0.2;
+  if (!(r2 > 0.0)) return false;
+  typedef Sz<DIM> S;
+  float aa[S::NB];
+#pragma unroll
+  for (int b = 0; b < S::NB; ++b) aa[b] = fabsf(af[b]);
+  float ist, isl, ista, isla;
+  if constexpr (DIM == 3) {
+    ist = gen_ist_3d<float>(af);
+    isl = gen_isl_3d<float>(af);
+    ista = gen_ista_3d<float>(aa);
+    isla = gen_isla_3d<float>(aa);
+  } else {
+    ist = gen_ist_2d<float>(af);
+    isl = gen_isl_2d<float>(af);
+    ista = gen_ista_2d<float>(aa);
+    isla = gen_isla_2d<float>(aa);
+  }
+  const float ist_ub = fmaxf(ist + 2e-5f * ista, 0.f);
+  const float isl_lb = fmaxf(isl - 2e-5f * isla, 0.f) + 1e-15f;
+  return ist_ub <= sqrtf((float)r2) * isl_lb; /* false for inf / NaN */
+}
 template <typename T, int DIM> CGKS_HD bool geno_saturates_fp32(const T* a, double C) {
   if constexpr (sizeof(T) == 4) {
     return false;
   } else {
-    const double r2 = 2.0 * C / 25.0 - 3.0 - 0.2;
-    if (!(r2 > 0.0)) return false;
     typedef Sz<DIM> S;
-    float af[S::NB], aa[S::NB];
+    float af[S::NB];
 #pragma unroll
-    for (int b = 0; b < S::NB; ++b) {
-      af[b] = (float)a[b];
-      aa[b] = fabsf(af[b]);
+    for (int b = 0; b < S::NB; ++b) af[b] = (float)a[b];
+    return geno_saturates_f32v<DIM>(af, C);
+  }
+}
+/* the GENO path function chi (Sec. 3.3) from the reconstruction's
+   coefficients a, evaluated in T */
+template <typename T, int DIM> CGKS_HD T geno_chi(const T* a, const Phys& ph) {
+  T ish, isl;
+  if constexpr (DIM == 3) {
+    ish = gen_ish_3d<T>(a);
+    isl = gen_isl_3d<T>(a);
+  } else {
+    ish = gen_ish_2d<T>(a);
+    isl = gen_isl_2d<T>(a);
+  }
+  const T eps = T(1e-15);
+  T ist = ish - isl;
+  if (ist < T(0)) ist = T(0);
+  const T rh = ist / (ish + eps), rl = ist / (isl + eps);
+  const T ah = T(1) + rh * rh, al = T(1) + rl * rl;
+  const T alpha = T(2) * ah / (ah + al);
+  return cg_tanh(ph_cchi<T>(ph) * alpha) / cg_tanh(ph_cchi<T>(ph));
+}
+
+/* the blended gradient bbar of the linear sub-stencil polynomials with their
+   WENO weights (d_m = 1/(2 dim)):
+   omega_m = (IS_m + eps)^-5 / sum_m' (IS_m' + eps)^-5, evaluated through the
+   ratios (IS_min + eps)/(IS_m + eps) <= 1, which stays finite in FP32. */
+template <typename T, int DIM, class Ld> CGKS_HD void substencil_bbar(const Ld& ld, T* bbar) {
+  typedef Sz<DIM> S;
+  T lsum[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < S::NL; ++s) lsum[s / S::GPF] += ld.line(s);
+  T bm[2 * DIM][3], tis[2 * DIM];
+#pragma unroll
+  for (int m = 0; m < 2 * DIM; ++m) {
+    const int ax = m / 2;
+    int o[3] = {0, 0, 0};
+    o[ax] = (m & 1) ? 1 : -1;
+    const T qf = ld.avg(o[0], o[1], o[2]);
+    const T sg = (m & 1) ? T(1) : T(-1);
+    T is = T(0);
+#pragma unroll
+    for (int kk = 0; kk < DIM; ++kk) {
+      const T bv = (kk == ax) ? sg * qf : lsum[kk] * (T(1) / T(S::GPF));
+      bm[m][kk] = bv;
+      is += bv * bv;
     }
-    float ist, isl, ista, isla;
-    if constexpr (DIM == 3) {
-      ist = gen_ist_3d<float>(af);
-      isl = gen_isl_3d<float>(af);
-      ista = gen_ista_3d<float>(aa);
-      isla = gen_isla_3d<float>(aa);
-    } else {
-      ist = gen_ist_2d<float>(af);
-      isl = gen_isl_2d<float>(af);
-      ista = gen_ista_2d<float>(aa);
-      isla = gen_isla_2d<float>(aa);
-    }
-    const float ist_ub = fmaxf(ist + 2e-5f * ista, 0.f);
-    const float isl_lb = fmaxf(isl - 2e-5f * isla, 0.f) + 1e-15f;
-    return ist_ub <= sqrtf((float)r2) * isl_lb; /* false for inf / NaN */
+    tis[m] = is + T(1e-15);
+  }
+  T tmin = tis[0];
+#pragma unroll
+  for (int m = 1; m < 2 * DIM; ++m) tmin = tis[m] < tmin ? tis[m] : tmin;
+  T wb[2 * DIM], ws = T(0);
+#pragma unroll
+  for (int m = 0; m < 2 * DIM; ++m) {
+    const T r = tmin / tis[m];
+    const T r2 = r * r;
+    wb[m] = r2 * r2 * r;
+    ws += wb[m];
+  }
+  const T iws = T(1) / ws;
+#pragma unroll
+  for (int m = 0; m < 2 * DIM; ++m) {
+    const T w = wb[m] * iws;
+#pragma unroll
+    for (int kk = 0; kk < DIM; ++kk) bbar[kk] += w * bm[m][kk];
   }
 }
 
@@ -529,70 +598,14 @@ CGKS_HD T recon_var(const double* __restrict__ avg, const float* __restrict__ av
   } else if (geno_saturates_fp32<T, DIM>(a, ph_cchi<double>(ph))) {
     chi = T(1); /* exactly what the FP64 evaluation below gives */
   } else {
-    T ish, isl;
-    if constexpr (DIM == 3) {
-      ish = gen_ish_3d<T>(a);
-      isl = gen_isl_3d<T>(a);
-    } else {
-      ish = gen_ish_2d<T>(a);
-      isl = gen_isl_2d<T>(a);
-    }
-    const T eps = T(1e-15);
-    T ist = ish - isl;
-    if (ist < T(0)) ist = T(0);
-    const T rh = ist / (ish + eps), rl = ist / (isl + eps);
-    const T ah = T(1) + rh * rh, al = T(1) + rl * rl;
-    const T alpha = T(2) * ah / (ah + al);
-    chi = cg_tanh(ph_cchi<T>(ph) * alpha) / cg_tanh(ph_cchi<T>(ph));
+    chi = geno_chi<T, DIM>(a, ph);
   }
   /* chi == 1 (forced, or the path function saturated in T): the blend is
      the fifth-order polynomial alone, bit for bit, and the sub-stencil
      polynomials are not needed */
   const bool lin = chi == T(1);
-  /* linear sub-stencil polynomials and their WENO weights (d_m = 1/(2 dim)).
-     omega_m = (IS_m + eps)^-5 / sum_m' (IS_m' + eps)^-5, evaluated through the
-     ratios (IS_min + eps)/(IS_m + eps) <= 1, which stays finite in FP32. */
   T bbar[3] = {T(0), T(0), T(0)};
-  if (!lin) {
-    T lsum[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int s = 0; s < S::NL; ++s) lsum[s / S::GPF] += ld.line(s);
-    T bm[2 * DIM][3], tis[2 * DIM];
-#pragma unroll
-    for (int m = 0; m < 2 * DIM; ++m) {
-      const int ax = m / 2;
-      int o[3] = {0, 0, 0};
-      o[ax] = (m & 1) ? 1 : -1;
-      const T qf = ld.avg(o[0], o[1], o[2]);
-      const T sg = (m & 1) ? T(1) : T(-1);
-      T is = T(0);
-#pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) {
-        const T bv = (kk == ax) ? sg * qf : lsum[kk] * (T(1) / T(S::GPF));
-        bm[m][kk] = bv;
-        is += bv * bv;
-      }
-      tis[m] = is + T(1e-15);
-    }
-    T tmin = tis[0];
-#pragma unroll
-    for (int m = 1; m < 2 * DIM; ++m) tmin = tis[m] < tmin ? tis[m] : tmin;
-    T wb[2 * DIM], ws = T(0);
-#pragma unroll
-    for (int m = 0; m < 2 * DIM; ++m) {
-      const T r = tmin / tis[m];
-      const T r2 = r * r;
-      wb[m] = r2 * r2 * r;
-      ws += wb[m];
-    }
-    const T iws = T(1) / ws;
-#pragma unroll
-    for (int m = 0; m < 2 * DIM; ++m) {
-      const T w = wb[m] * iws;
-#pragma unroll
-      for (int kk = 0; kk < DIM; ++kk) bbar[kk] += w * bm[m][kk];
-    }
-  }
+  if (!lin) substencil_bbar<T, DIM>(ld, bbar);
   T JiT[3][3];
   if constexpr (CURVI) {
 #pragma unroll
@@ -650,6 +663,115 @@ CGKS_HD T recon_var(const double* __restrict__ avg, const float* __restrict__ av
           sg = gref[kk] * geo_ih<T>(g, kk);
         }
         dst[b + (long)(1 + kk) * N] = sg;
+      }
+    }
+  }
+  return chi;
+}
+
+/* recon_var on Cartesian meshes in FP64 storage with its Gauss-point
+   transform on the FP32 pipe: a = M d in FP64 (in unnormalised pairs the
+   map's straight-line code outgrows the instruction cache and runs no
+   faster; nor does splitting its neighbour groups between the two
+   pipes), the coefficients converted to pairs (fpacc) on the integer pipe,
+   then the GENO screen (from their leading floats), the mean and the
+   Gauss-point values and gradients in pairs, rounded once to FP64 when
+   stored.  Where the screen cannot certify chi = 1, chi and the sub-stencil
+   gradient come from the FP64 code on the coefficients rounded back to
+   double, and the blend is FP64.  Same steps and readings as recon_var;
+   results agree with it to the pairs' rounding (relative 2^-47 per
+   coefficient). */
+template <int DIM, bool WALL>
+CGKS_HD double recon_var_pair(const double* __restrict__ avg, const double* __restrict__ der, const DevGeo& g,
+                              const Phys& ph, long c, int ci, int cj, int ck, int v, double chi_force,
+                              double* __restrict__ gpL, double* __restrict__ gpR) {
+  typedef Sz<DIM> S;
+  const long N = g.ncell;
+  constexpr int NV = S::NV;
+  ReconLd<double, DIM, false, WALL> ld;
+  ld.avgp = avg;
+  ld.avh = nullptr;
+  ld.avl = nullptr;
+  ld.der = der;
+  ld.g = g;
+  ld.c = c;
+  ld.ci = ci;
+  ld.cj = cj;
+  ld.ck = ck;
+  ld.v = v;
+  ld.nb.setup(g, ci, cj, ck);
+  ld.init_q0();
+  fpacc ap[S::NB];
+  {
+    double a[S::NB];
+    if constexpr (DIM == 3) gen_coeffs_3d<double>(ld, a);
+    else gen_coeffs_2d<double>(ld, a);
+#pragma unroll
+    for (int b = 0; b < S::NB; ++b) ap[b] = fpacc_from_double(a[b]);
+  }
+
+  double chi;
+  if (chi_force >= 0.0) {
+    chi = chi_force;
+  } else {
+    float af[S::NB];
+#pragma unroll
+    for (int b = 0; b < S::NB; ++b) {
+      ap[b] = fpacc_norm(ap[b]);
+      af[b] = ap[b].hi;
+    }
+    if (geno_saturates_f32v<DIM>(af, ph_cchi<double>(ph))) {
+      chi = 1.0;
+    } else {
+      double a[S::NB];
+#pragma unroll
+      for (int b = 0; b < S::NB; ++b) a[b] = fpacc_to_double(ap[b]);
+      chi = geno_chi<double, DIM>(a, ph);
+    }
+  }
+  const bool lin = chi == 1.0;
+  double bbar[3] = {0.0, 0.0, 0.0};
+  if (!lin) substencil_bbar<double, DIM>(ld, bbar);
+  fpacc mean4;
+  if constexpr (DIM == 3) mean4 = gen_mean_3d<fpacc>(ap);
+  else mean4 = gen_mean_2d<fpacc>(ap);
+  fpacc ih[3];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) ih[a] = fpacc_from_double(g.ih[a]);
+#pragma unroll 1
+  for (int ax = 0; ax < DIM; ++ax) {
+    fpacc pv[2 * S::GPF], pg[2 * S::GPF][DIM];
+    if constexpr (DIM == 3) {
+      if (ax == 0) gen_gp_3d_ax0<fpacc>(ap, pv, pg);
+      else if (ax == 1) gen_gp_3d_ax1<fpacc>(ap, pv, pg);
+      else gen_gp_3d_ax2<fpacc>(ap, pv, pg);
+    } else {
+      if (ax == 0) gen_gp_2d_ax0<fpacc>(ap, pv, pg);
+      else gen_gp_2d_ax1<fpacc>(ap, pv, pg);
+    }
+    int o[3] = {0, 0, 0};
+    o[ax] = -1;
+    const long clo = nbr(g, ci, cj, ck, o[0], o[1], o[2]);
+#pragma unroll
+    for (int i = 0; i < 2 * S::GPF; ++i) {
+      const int side = i / S::GPF, k = i % S::GPF;
+      const int gp = (2 * ax + side) * S::GPF + k;
+      double* dst = side ? gpL : gpR;
+      const long cell = side ? c : clo;
+      const long b = ((long)((ax * S::GPF + k) * NV + v) * (1 + DIM)) * N + cell;
+      const double rel = fpacc_to_double(pv[i] - mean4);
+      if (lin) {
+        dst[b] = ld.full(rel);
+#pragma unroll
+        for (int kk = 0; kk < DIM; ++kk) dst[b + (long)(1 + kk) * N] = fpacc_to_double(pg[i][kk] * ih[kk]);
+      } else {
+        double v1 = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < DIM; ++kk) v1 += bbar[kk] * gp_delta<DIM, double>(gp, kk);
+        dst[b] = ld.full(chi * rel + (1.0 - chi) * v1);
+#pragma unroll
+        for (int kk = 0; kk < DIM; ++kk)
+          dst[b + (long)(1 + kk) * N] = (chi * fpacc_to_double(pg[i][kk]) + (1.0 - chi) * bbar[kk]) * g.ih[kk];
       }
     }
   }

@@ -82,7 +82,20 @@ __device__ __noinline__ void first_order_states(const double* __restrict__ avg, 
    positivity fallbacks (shared by the single-case and batched kernels):
    chi = 0 if a face Gauss-point state has rho <= 0 or p <= 0, then first
    order if that is not enough either */
-template <typename T, int DIM, bool CURVI, bool WALL>
+/* one variable's reconstruction: PR selects the paired linear maps
+   (recon_var_pair; FP64 storage, Cartesian meshes) */
+template <typename T, int DIM, bool CURVI, bool WALL, bool PR>
+__device__ __forceinline__ T recon_var_any(const double* __restrict__ avg, const float* __restrict__ avh,
+                                           const float* __restrict__ avl, const T* __restrict__ der,
+                                           const DevGeo& g, const Phys& ph, long c, int i, int j, int k, int v,
+                                           T force, T* __restrict__ gpL, T* __restrict__ gpR) {
+  if constexpr (PR && !CURVI && sizeof(T) == 8)
+    return recon_var_pair<DIM, WALL>(avg, der, g, ph, c, i, j, k, v, force, gpL, gpR);
+  else
+    return recon_var<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, v, force, gpL, gpR);
+}
+
+template <typename T, int DIM, bool CURVI, bool WALL, bool PR = false>
 __device__ __forceinline__ void recon_cell(const double* __restrict__ avg, const float* __restrict__ avh,
                                            const float* __restrict__ avl, const T* __restrict__ der, const DevGeo& g,
                                            const Phys& ph, long c, int i, int j, int k, T* __restrict__ gpL,
@@ -93,11 +106,13 @@ __device__ __forceinline__ void recon_cell(const double* __restrict__ avg, const
   const T force = (ph.linear || skip) ? T(1) : T(-1);
   T cs[NV];
 #pragma unroll 1
-  for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, v, force, gpL, gpR);
+  for (int v = 0; v < NV; ++v)
+    cs[v] = recon_var_any<T, DIM, CURVI, WALL, PR>(avg, avh, avl, der, g, ph, c, i, j, k, v, force, gpL, gpR);
   if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) {
     atomicAdd(&st[ST_FALLBACK], 1);
 #pragma unroll 1
-    for (int v = 0; v < NV; ++v) cs[v] = recon_var<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, v, T(0), gpL, gpR);
+    for (int v = 0; v < NV; ++v)
+      cs[v] = recon_var_any<T, DIM, CURVI, WALL, PR>(avg, avh, avl, der, g, ph, c, i, j, k, v, T(0), gpL, gpR);
     if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) {
       first_order_states<T, DIM>(avg, avh, avl, g, c, i, j, k, gpL, gpR);
       if (!cell_states_physical<T, DIM>(g, ph, c, i, j, k, gpL, gpR)) atomicOr(&st[ST_NONPHYS], 1);
@@ -145,7 +160,7 @@ __device__ __forceinline__ bool selector_skip(const SelectorDev& sel, const doub
   return selector_decide(sel, f, active, stage[threadIdx.x >> 5]) == SEL_SKIP;
 }
 
-template <typename T, int DIM, bool CURVI, bool WALL>
+template <typename T, int DIM, bool CURVI, bool WALL, bool PR = false>
 __global__ void __launch_bounds__(128, recon_min_blocks<T, DIM, CURVI>())
     k_recon(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
             const T* __restrict__ der, DevGeo g, Phys ph, T* __restrict__ gpL, T* __restrict__ gpR,
@@ -158,8 +173,8 @@ __global__ void __launch_bounds__(128, recon_min_blocks<T, DIM, CURVI>())
   bool skip = false;
   if (sel.on && !ph.linear) skip = selector_skip<T, DIM, WALL>(sel, avg, avh, der, g, c, i, j, k, active, wall);
   if (!active) return;
-  if (wall) recon_cell<T, DIM, CURVI, WALL>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st, skip);
-  else recon_cell<T, DIM, CURVI, false>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st, skip);
+  if (wall) recon_cell<T, DIM, CURVI, WALL, PR>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st, skip);
+  else recon_cell<T, DIM, CURVI, false, PR>(avg, avh, avl, der, g, ph, c, i, j, k, gpL, gpR, chi, record_chi, st, skip);
 }
 
 /* features of every cell of a state, [cell][SEL_NF] (training samples) */

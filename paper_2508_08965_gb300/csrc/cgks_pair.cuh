@@ -279,6 +279,135 @@ CGKS_HD fpair cg_sqrt(fpair x) { return x.hi > 0.f ? x * cg_rsqrt(x) : fpair(0.0
 CGKS_HD fpair cg_fabs(fpair x) { return x.hi < 0.f ? -x : x; }
 CGKS_HD fpair cg_fma(fpair a, fpair b, fpair c) { return a * b + c; }
 
+/* ---- unnormalised pairs for the reconstruction's linear maps ----
+   fpacc holds hi + lo without the renormalisation after every operation: a
+   sum is Knuth's two-sum of the high parts with the low parts and the sum
+   error added into lo (8 operations), a multiply-add the exact product parts
+   two-summed into the accumulator (12), a product the product parts (4).
+   This is compensated summation in the manner of Ogita, Rump and Oishi's
+   Sum2 / Dot2: the result is as accurate as if the sums of products were
+   formed with about 48 bits and rounded once, which is what the
+   reconstruction's maps (sums of at most ~100 products of the data with
+   fixed rational coefficients) need.  Values are normalised only where a
+   float of them is read (fpacc_norm). */
+struct fpacc {
+  float hi, lo;
+  CGKS_HD fpacc() : hi(0.f), lo(0.f) {}
+  CGKS_HD fpacc(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  CGKS_HD fpacc(float x) : hi(x), lo(0.f) {}
+  CGKS_HD fpacc(int x) : fpacc((double)x) {}
+};
+CGKS_HD fpacc fpacc_make(float h, float l) {
+  fpacc r;
+  r.hi = h;
+  r.lo = l;
+  return r;
+}
+CGKS_HD fpacc operator+(fpacc a, fpacc b) {
+  float s, e;
+  fp_two_sum(a.hi, b.hi, s, e);
+  return fpacc_make(s, fp_add(fp_add(a.lo, b.lo), e));
+}
+CGKS_HD fpacc operator-(fpacc a) { return fpacc_make(-a.hi, -a.lo); }
+CGKS_HD fpacc operator-(fpacc a, fpacc b) { return a + (-b); }
+CGKS_HD fpacc operator*(fpacc a, fpacc b) {
+  const float p = fp_mul(a.hi, b.hi);
+  float e = fp_fma(a.hi, b.hi, -p);
+  e = fp_fma(a.hi, b.lo, e);
+  e = fp_fma(a.lo, b.hi, e);
+  return fpacc_make(p, e);
+}
+/* a b + c */
+CGKS_HD fpacc cg_fma(fpacc a, fpacc b, fpacc c) {
+  const float p = fp_mul(a.hi, b.hi);
+  float e = fp_fma(a.hi, b.hi, -p);
+  e = fp_fma(a.hi, b.lo, e);
+  e = fp_fma(a.lo, b.hi, e);
+  float s, t;
+  fp_two_sum(c.hi, p, s, t);
+  return fpacc_make(s, fp_add(c.lo, fp_add(e, t)));
+}
+/* hi + lo renormalised (two-sum: |lo| may exceed |hi| after cancellation) */
+CGKS_HD fpacc fpacc_norm(fpacc a) {
+  float s, e;
+  fp_two_sum(a.hi, a.lo, s, e);
+  return fpacc_make(s, e);
+}
+
+/* bit casts (host: the same bit logic through memcpy) */
+CGKS_HD unsigned fp_fbits(float f) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  __builtin_memcpy(&u, &f, sizeof u);
+  return u;
+#endif
+}
+CGKS_HD float fp_bitsf(unsigned u) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(u);
+#else
+  float f;
+  __builtin_memcpy(&f, &u, sizeof f);
+  return f;
+#endif
+}
+CGKS_HD unsigned long long fp_dbits(double d) {
+#if defined(__CUDA_ARCH__)
+  return (unsigned long long)__double_as_longlong(d);
+#else
+  unsigned long long u;
+  __builtin_memcpy(&u, &d, sizeof u);
+  return u;
+#endif
+}
+CGKS_HD double fp_bitsd(unsigned hi32, unsigned lo32) {
+#if defined(__CUDA_ARCH__)
+  return __hiloint2double((int)hi32, (int)lo32);
+#else
+  const unsigned long long u = ((unsigned long long)hi32 << 32) | lo32;
+  double d;
+  __builtin_memcpy(&d, &u, sizeof d);
+  return d;
+#endif
+}
+
+/* conversions on the integer pipe (GB300's FP64 pipe, which also converts
+   between double and float, runs at 1/64 of the FP32 rate).
+   double -> fpacc: hi = x truncated to its leading 24 bits, lo = the other
+   29 bits of the significand rounded to 23 (relative error at most 2^-47).
+   Magnitudes below 2^-103 are taken as (signed) 0; beyond the float range
+   (and inf, NaN) the conversion is the rounded one, so inf and NaN carry
+   through. */
+CGKS_HD fpacc fpacc_from_double(double x) {
+  const unsigned long long b = fp_dbits(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const int ef = (int)((h32 >> 20) & 0x7ffu) - 896; /* biased float exponent of hi */
+  if (ef > 254) return fpacc(x);
+  const unsigned sgn = h32 & 0x80000000u;
+  if (ef < 24) return fpacc_make(fp_bitsf(sgn), fp_bitsf(sgn));
+  const float hi = fp_bitsf(sgn | ((unsigned)ef << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29));
+  const unsigned el = (unsigned)(ef - 23) << 23;          /* 2^(E-23), E the exponent of x */
+  const unsigned r = ((l32 & 0x1fffffffu) + 32u) >> 6;   /* low 29 bits rounded to 23 (r <= 2^23) */
+  const float lo = fp_sub(fp_bitsf(el + r), fp_bitsf(el)); /* 2^(E-46) r, exact */
+  return fpacc_make(hi, fp_bitsf(fp_fbits(lo) | sgn));
+}
+/* float -> double, exact for normal floats; subnormal ones (below 2^-126,
+   which the reconstruction meets only in the low part of values below
+   about 2^-100) give a signed 0.  A branch to the rounded conversion for
+   them would cost a conversion on the FP64 pipe at every call (measured
+   +1.8 ms per TGV 128^3 reconstruction) */
+CGKS_HD double fp_f2d_bits(float f) {
+  const unsigned u = fp_fbits(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned e2 = e == 0u ? 0u : (e == 255u ? 2047u : e + 896u);
+  const unsigned m = e == 0u ? 0u : (u & 0x7fffffu);
+  return fp_bitsd((u & 0x80000000u) | (e2 << 20) | (m >> 3), m << 29);
+}
+/* hi + lo rounded once to double */
+CGKS_HD double fpacc_to_double(fpacc a) { return fp_f2d_bits(a.hi) + fp_f2d_bits(a.lo); }
+
 template <class A, class B> struct cg_same { static constexpr bool value = false; };
 template <class A> struct cg_same<A, A> { static constexpr bool value = true; };
 

@@ -83,3 +83,60 @@ void pair_func_stats(int n, unsigned seed, double* out) {
   }
 }
 }
+
+extern "C" {
+/* the integer-pipe conversions and unnormalised sums of the paired
+   reconstruction (fpacc).  out: [0] max relative error of double -> fpacc
+   on [2^-100, 2^100] (either sign), [1] conversions of x whose exact value
+   hi exceeds |x| in magnitude (hi is a truncation of x),
+   [2] float -> double mismatches against the plain conversion (subnormal
+   floats: signed 0) and hi + lo -> double mismatches against the exact sum
+   for |x| >= 2^-80, [3] special-value failures (zeros, values below 2^-103, beyond the
+   float range, inf, NaN), [4] max error of 80-term sums of products
+   (cg_fma chains with rounded-double constants) relative to the sum of the
+   products' magnitudes */
+void pair_conv_stats(int n, unsigned seed, double* out) {
+  using cgks::fpacc;
+  std::mt19937_64 rng(seed);
+  std::uniform_real_distribution<double> u(-1.0, 1.0), ex(-100.0, 100.0);
+  for (int i = 0; i < 5; ++i) out[i] = 0;
+  auto val = [](const fpacc& p) { return (long double)p.hi + p.lo; };
+  for (int it = 0; it < n; ++it) {
+    const double x = u(rng) * std::ldexp(1.0, (int)ex(rng));
+    if (std::fabs(x) < std::ldexp(1.0, -100)) continue; /* the flushed range is checked below */
+    const fpacc p = cgks::fpacc_from_double(x);
+    out[0] = std::fmax(out[0], (double)(fabsl(val(p) - x) / fabsl((long double)x)));
+    if (fabsl((long double)p.hi) > fabsl((long double)x)) out[1] += 1;
+    const float f = (float)(u(rng) * std::ldexp(1.0, (int)(ex(rng) * 1.2)));
+    if (cgks::fp_f2d_bits(f) != (std::fpclassify(f) == FP_SUBNORMAL ? std::copysign(0.0, f) : (double)f)) out[2] += 1;
+    if (std::fabs(x) >= std::ldexp(1.0, -80) && cgks::fpacc_to_double(p) != (double)((long double)p.hi + p.lo))
+      out[2] += 1;
+  }
+  const double specials[] = {0.0, -0.0, 1e-32, -3e-40, 1e300, -1e300, INFINITY, -INFINITY};
+  for (double x : specials) {
+    const fpacc p = cgks::fpacc_from_double(x);
+    const bool tiny = std::fabs(x) < std::ldexp(1.0, -103);
+    if (tiny && !(p.hi == 0.f && p.lo == 0.f && std::signbit(p.hi) == std::signbit(x))) out[3] += 1;
+    if (!tiny && std::fabs(x) > 1e200 && !(std::isinf(p.hi) && std::signbit(p.hi) == std::signbit(x))) out[3] += 1;
+  }
+  if (!std::isnan(cgks::fpacc_from_double(NAN).hi)) out[3] += 1;
+  if (!std::isnan(cgks::fp_f2d_bits(NAN)) || !std::isinf(cgks::fp_f2d_bits(INFINITY))) out[3] += 1;
+  if (cgks::fp_f2d_bits(1e-40f) != 0.0 || !std::signbit(cgks::fp_f2d_bits(-1e-40f)) ||
+      !std::signbit(cgks::fp_f2d_bits(-0.0f)))
+    out[3] += 1;
+  std::uniform_real_distribution<double> uc(-1.0, 1.0);
+  for (int it = 0; it < n / 100; ++it) {
+    fpacc acc(0.0f);
+    long double ref = 0.0L, mag = 0.0L;
+    for (int q = 0; q < 80; ++q) {
+      const double c = uc(rng), d = uc(rng) * std::ldexp(1.0, (int)(ex(rng) / 20));
+      const fpacc pc(c), pd = cgks::fpacc_from_double(d);
+      acc = cgks::cg_fma(pc, pd, acc);
+      ref += val(pc) * val(pd);
+      mag += fabsl(val(pc) * val(pd));
+    }
+    const fpacc nrm = cgks::fpacc_norm(acc);
+    out[4] = std::fmax(out[4], (double)(fabsl(val(nrm) - ref) / mag));
+  }
+}
+}

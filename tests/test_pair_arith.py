@@ -57,3 +57,22 @@ def test_pair_special_functions(lib, seed):
     print("exp %.2e expm1 %.2e erfc %.2e rsqrt %.2e exp[-1,1] %.2e" % tuple(out))
     assert e_exp1 <= 2.0 ** -46 and e_exp <= 2.0 ** -44
     assert e_expm1 <= 2.0 ** -45 and e_erfc <= 2.0 ** -45 and e_rsqrt <= 2.0 ** -46
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_pair_reconstruction_conversions(lib, seed):
+    """The unnormalised pairs of the paired reconstruction: the integer-pipe
+    split of a double keeps 47 bits (hi a truncation, never above |x|), the
+    float -> double rebuild is exact for normal floats (subnormal ones give
+    signed zeros), zeros and magnitudes below 2^-103 split to signed zeros, inf and NaN carry through, and 80-term sums of products
+    (compensated, Sum2/Dot2 style) stay within 2^-42 of the sum of the
+    products' magnitudes (measured about 14 units of 2^-48; the low part's
+    own FP32 rounding grows with the number of terms, and a plain FP64 sum
+    of 80 terms may err by up to 80 units of 2^-53)."""
+    lib.pair_conv_stats.argtypes = [C.c_int, C.c_uint, C.POINTER(C.c_double)]
+    out = (C.c_double * 5)()
+    lib.pair_conv_stats(200000, seed, out)
+    e_split, overshoot, f2d_bad, special_bad, e_dot = list(out)
+    print("split %.2e dot %.2e" % (e_split, e_dot))
+    assert e_split <= 2.0 ** -47 * (1 + 2.0 ** -20) and overshoot == 0 and f2d_bad == 0 and special_bad == 0
+    assert e_dot <= 2.0 ** -42
