@@ -337,6 +337,10 @@ CGKS_HD float cg_dot3(float a, float b, float c, float d, float e, float f) { re
 /* a b + c (the paired type overloads it with one renormalisation) */
 CGKS_HD double cg_madd(double a, double b, double c) { return a * b + c; }
 CGKS_HD float cg_madd(float a, float b, float c) { return a * b + c; }
+/* a value renormalised before its sign is read (the paired type overloads
+   it; plain types are their own normal form) */
+CGKS_HD double cg_norm(double x) { return x; }
+CGKS_HD float cg_norm(float x) { return x; }
 #include "cgks_pair.cuh"
 CGKS_HD double cg_tanh(double x) { return tanh(x); }
 CGKS_HD float cg_tanh(float x) { return tanhf(x); }
@@ -837,7 +841,7 @@ CGKS_HD bool mx_init(const T* W, T gam, T K, int region, MxS<T, DIM>& m) {
     m.U[i] = W[1 + i] * m.irho;
     ke += m.U[i] * W[1 + i];
   }
-  m.p = (gam - T(1)) * (W[DIM + 1] - T(0.5) * ke);
+  m.p = cg_norm((gam - T(1)) * (W[DIM + 1] - T(0.5) * ke));
   if (!(m.rho > T(0)) || !(m.p > T(0))) return false;
   m.i2l = m.p * m.irho; /* 1/(2 lambda) = p/rho */
   m.lam = T(0.5) / m.i2l;

@@ -1,15 +1,22 @@
 /*
  * Paired-FP32 arithmetic: the compute type of the interface flux in the
  * paired form (precision 2).  A value is the unevaluated sum hi + lo of two
- * floats, |lo| <= ulp(hi)/2: about 48 significant bits, on the FP32 pipe.
+ * floats: about 48 significant bits, on the FP32 pipe.
  *
  *   sum      Knuth's error-free two-sum of the high parts, plus the sum of
- *            the low parts, one renormalisation (11 operations; the form
- *            with a second two-sum for the low parts, 20 operations, is
- *            tighter when the sum cancels but measured no more accurate on
- *            whole steps of the flux against the FP64 oracle);
- *   product  the FMA residual of hi*hi plus the two cross terms;
- *   quotient a reciprocal estimate and two remainder corrections.
+ *            the low parts (8 operations);
+ *   product  hi*hi, and its FMA residual plus the two cross terms (4);
+ *   a b + c d, a b + c d + e f, a b + c: compensated dot products (Dot2);
+ *   quotient operands renormalised, a reciprocal estimate and two
+ *            remainder corrections.
+ * None of these renormalises its result (|lo| <= ulp(hi)/2 is not kept):
+ * the instruction fetch of the flux kernel is its bound, and the three
+ * operations of a final fast two-sum on every result cost 13% of the
+ * kernel's time (TGV 128^3), while whole steps stay within the FP64 parity
+ * bars with a margin of 4x or more.  Where a sign or a float of the value is
+ * read (the quotient, square roots, special functions, the pressure's
+ * positivity test), the value is renormalised first (fp_norm); the
+ * renormalised sum and product (fp_addn, fp_muln) serve those steps.
  *
  * exp, expm1, erfc (|x| < 3/4) and 1/sqrt are series and Newton steps in
  * pair arithmetic (below); erfc beyond 3/4 is the FP64 function rounded to
@@ -89,16 +96,20 @@ CGKS_HD void fp_fast_two_sum(float a, float b, float& s, float& e) {
   e = fp_sub(b, fp_sub(s, a));
 }
 
-CGKS_HD fpair operator+(fpair a, fpair b) {
+/* renormalised forms: hi the rounded value, |lo| <= ulp(hi)/2 */
+CGKS_HD fpair fp_norm(fpair a) { /* two-sum: after a cancellation |lo| may exceed |hi| */
+  float s, e;
+  fp_two_sum(a.hi, a.lo, s, e);
+  return fp_make(s, e);
+}
+CGKS_HD fpair fp_addn(fpair a, fpair b) {
   float s, e;
   fp_two_sum(a.hi, b.hi, s, e);
   e = fp_add(e, fp_add(a.lo, b.lo));
   fp_fast_two_sum(s, e, s, e);
   return fp_make(s, e);
 }
-CGKS_HD fpair operator-(fpair a) { return fp_make(-a.hi, -a.lo); }
-CGKS_HD fpair operator-(fpair a, fpair b) { return a + (-b); }
-CGKS_HD fpair operator*(fpair a, fpair b) {
+CGKS_HD fpair fp_muln(fpair a, fpair b) {
   const float p = fp_mul(a.hi, b.hi);
   float e = fp_fma(a.hi, b.hi, -p);
   e = fp_fma(a.hi, b.lo, e);
@@ -107,16 +118,39 @@ CGKS_HD fpair operator*(fpair a, fpair b) {
   fp_fast_two_sum(p, e, s, e);
   return fp_make(s, e);
 }
+/* the operators leave the last renormalisation out (the sum keeps the
+   two-sum of the high parts and gathers the errors in lo, the product is
+   its exact high product and the error terms): compensated arithmetic in
+   the manner of Sum2/Dot2, as accurate as the renormalised forms except
+   that after a cancellation lo may hold more than half an ulp of hi, or
+   the whole value.  Quotients, square roots, the special functions and
+   sign tests renormalise their operands first (fp_norm). */
+CGKS_HD fpair operator+(fpair a, fpair b) {
+  float s, e;
+  fp_two_sum(a.hi, b.hi, s, e);
+  return fp_make(s, fp_add(e, fp_add(a.lo, b.lo)));
+}
+CGKS_HD fpair operator-(fpair a) { return fp_make(-a.hi, -a.lo); }
+CGKS_HD fpair operator-(fpair a, fpair b) { return a + (-b); }
+CGKS_HD fpair operator*(fpair a, fpair b) {
+  const float p = fp_mul(a.hi, b.hi);
+  float e = fp_fma(a.hi, b.hi, -p);
+  e = fp_fma(a.hi, b.lo, e);
+  e = fp_fma(a.lo, b.hi, e);
+  return fp_make(p, e);
+}
 CGKS_HD fpair operator/(fpair a, fpair b) {
+  a = fp_norm(a);
+  b = fp_norm(b);
   const float r = fp_rcp(b.hi);
   const float q1 = fp_mul(a.hi, r);
-  fpair rem = a - b * fpair(q1);
+  fpair rem = fp_addn(a, -fp_muln(b, fpair(q1)));
   const float q2 = fp_mul(rem.hi, r);
-  rem = rem - b * fpair(q2);
+  rem = fp_addn(rem, -fp_muln(b, fpair(q2)));
   const float q3 = fp_mul(rem.hi, r);
   float s, e;
   fp_fast_two_sum(q1, q2, s, e);
-  return fp_make(s, e) + fpair(q3);
+  return fp_addn(fp_make(s, e), fpair(q3));
 }
 CGKS_HD fpair& operator+=(fpair& a, fpair b) { return a = a + b; }
 CGKS_HD fpair& operator-=(fpair& a, fpair b) { return a = a - b; }
@@ -129,10 +163,11 @@ CGKS_HD bool operator>=(fpair a, fpair b) { return !(a < b); }
 CGKS_HD bool operator==(fpair a, fpair b) { return a.hi == b.hi && a.lo == b.lo; }
 CGKS_HD bool operator!=(fpair a, fpair b) { return !(a == b); }
 
-/* a b + c d and a b + c d + e f with one renormalisation: the high-part
-   products and their FMA residuals, Knuth's two-sum of the products, the
-   residuals and sum errors gathered in the low part (a compensated dot
-   product in the manner of Ogita, Rump and Oishi's Dot2, on pairs) */
+/* a b + c d and a b + c d + e f: the high-part products and their FMA
+   residuals, Knuth's two-sum of the products, the residuals and sum errors
+   gathered in the low part (a compensated dot product in the manner of
+   Ogita, Rump and Oishi's Dot2, on pairs), left unrenormalised like the
+   operators */
 CGKS_HD void fp_prod_parts(fpair a, fpair b, float& p, float& e) {
   p = fp_mul(a.hi, b.hi);
   e = fp_fma(a.hi, b.hi, -p);
@@ -145,7 +180,6 @@ CGKS_HD fpair fp_dot2(fpair a, fpair b, fpair c, fpair d) {
   fp_prod_parts(c, d, p2, e2);
   fp_two_sum(p1, p2, s, t);
   t = fp_add(t, fp_add(e1, e2));
-  fp_fast_two_sum(s, t, s, t);
   return fp_make(s, t);
 }
 CGKS_HD fpair fp_dot3(fpair a, fpair b, fpair c, fpair d, fpair e, fpair f) {
@@ -156,16 +190,14 @@ CGKS_HD fpair fp_dot3(fpair a, fpair b, fpair c, fpair d, fpair e, fpair f) {
   fp_two_sum(p1, p2, s, t);
   fp_two_sum(s, p3, s, u);
   t = fp_add(fp_add(t, u), fp_add(fp_add(e1, e2), e3));
-  fp_fast_two_sum(s, t, s, t);
   return fp_make(s, t);
 }
-/* a b + c with one renormalisation */
+/* a b + c (unrenormalised) */
 CGKS_HD fpair fp_madd(fpair a, fpair b, fpair c) {
   float p, e, s, t;
   fp_prod_parts(a, b, p, e);
   fp_two_sum(p, c.hi, s, t);
   t = fp_add(t, fp_add(e, c.lo));
-  fp_fast_two_sum(s, t, s, t);
   return fp_make(s, t);
 }
 CGKS_HD fpair cg_madd(fpair a, fpair b, fpair c) { return fp_madd(a, b, c); }
@@ -202,22 +234,23 @@ CGKS_HD float fp_rsqrt_est(float a) {
 CGKS_HD fpair fp_scale(fpair a, float s) { return fp_make(fp_mul(a.hi, s), fp_mul(a.lo, s)); }
 
 /* exp(r) - 1 = sum_{n=1..13} r^n / n! for |r| <= ln2/2 (truncation below
-   2e-16 of exp(r)), Horner's rule in pairs */
+   2e-16 of exp(r)), Horner's rule in renormalised pairs (r renormalised) */
+CGKS_HD fpair fp_horner_step(fpair p, fpair r, double c) { return fp_addn(fp_muln(p, r), fpair(c)); }
 CGKS_HD fpair fp_expm1_small(fpair r) {
   fpair p(1.0 / 6227020800.0);
-  p = p * r + fpair(1.0 / 479001600.0);
-  p = p * r + fpair(1.0 / 39916800.0);
-  p = p * r + fpair(1.0 / 3628800.0);
-  p = p * r + fpair(1.0 / 362880.0);
-  p = p * r + fpair(1.0 / 40320.0);
-  p = p * r + fpair(1.0 / 5040.0);
-  p = p * r + fpair(1.0 / 720.0);
-  p = p * r + fpair(1.0 / 120.0);
-  p = p * r + fpair(1.0 / 24.0);
-  p = p * r + fpair(1.0 / 6.0);
-  p = p * r + fpair(0.5f);
-  p = p * r + fpair(1.0f);
-  return p * r;
+  p = fp_horner_step(p, r, 1.0 / 479001600.0);
+  p = fp_horner_step(p, r, 1.0 / 39916800.0);
+  p = fp_horner_step(p, r, 1.0 / 3628800.0);
+  p = fp_horner_step(p, r, 1.0 / 362880.0);
+  p = fp_horner_step(p, r, 1.0 / 40320.0);
+  p = fp_horner_step(p, r, 1.0 / 5040.0);
+  p = fp_horner_step(p, r, 1.0 / 720.0);
+  p = fp_horner_step(p, r, 1.0 / 120.0);
+  p = fp_horner_step(p, r, 1.0 / 24.0);
+  p = fp_horner_step(p, r, 1.0 / 6.0);
+  p = fp_horner_step(p, r, 0.5);
+  p = fp_horner_step(p, r, 1.0);
+  return fp_muln(p, r);
 }
 
 /* exp(x) = 2^k exp(r), x = k ln2 + r, |r| <= ln2/2.  ln2 is split Cody-Waite
@@ -225,58 +258,69 @@ CGKS_HD fpair fp_expm1_small(fpair r) {
    and a float remainder.  Below -87 the result is under the float range and
    is returned as 0 (the flux only adds such values to O(1) ones). */
 CGKS_HD fpair cg_exp(fpair x) {
+  x = fp_norm(x);
   if (x.hi < -87.0f) return fpair(0.0f);
   const float kf = fp_rint(fp_mul(x.hi, 1.44269504088896341f));
   const float L1 = 0.693145751953125f;        /* 16 significant bits */
   const float L2 = 1.42860676533018705e-06f; /* ln2 - L1 rounded to a float */
   const float L3 = 5.49792314810410715e-14f; /* ln2 - L1 - L2 rounded (residual 1.3e-21) */
-  fpair r = x - fpair(fp_mul(kf, L1));
+  fpair r = fp_addn(x, -fpair(fp_mul(kf, L1)));
   float p2 = fp_mul(kf, L2);
-  r = r - fp_make(p2, fp_fma(kf, L2, -p2));
-  r = r - fpair(fp_mul(kf, L3));
-  return fp_scale(fp_expm1_small(r) + fpair(1.0f), fp_pow2((int)kf));
+  r = fp_addn(r, -fp_make(p2, fp_fma(kf, L2, -p2)));
+  r = fp_addn(r, -fpair(fp_mul(kf, L3)));
+  return fp_scale(fp_addn(fp_expm1_small(r), fpair(1.0f)), fp_pow2((int)kf));
 }
 
 CGKS_HD fpair cg_expm1(fpair x) {
+  x = fp_norm(x);
   if (x.hi > -0.34657359f && x.hi < 0.34657359f) return fp_expm1_small(x);
-  return cg_exp(x) - fpair(1.0f);
+  return fp_addn(cg_exp(x), fpair(-1.0f));
 }
 
 /* erfc(x) = 1 - (2/sqrt(pi)) x sum_{n>=0} (-x^2)^n / (n! (2n+1)) for |x| < 3/4
    (terms n <= 15; truncation below 5e-18); beyond, the FP64 library
    function rounded to a pair */
 CGKS_HD fpair cg_erfc(fpair x) {
+  x = fp_norm(x);
   if (!(x.hi > -0.75f && x.hi < 0.75f)) return fpair(cg_erfc((double)x));
-  const fpair t = x * x;
+  const fpair t = fp_muln(x, x);
   fpair p(-1.0 / (1307674368000.0 * 31.0));
-  p = p * t + fpair(1.0 / (87178291200.0 * 29.0));
-  p = p * t + fpair(-1.0 / (6227020800.0 * 27.0));
-  p = p * t + fpair(1.0 / (479001600.0 * 25.0));
-  p = p * t + fpair(-1.0 / (39916800.0 * 23.0));
-  p = p * t + fpair(1.0 / (3628800.0 * 21.0));
-  p = p * t + fpair(-1.0 / (362880.0 * 19.0));
-  p = p * t + fpair(1.0 / (40320.0 * 17.0));
-  p = p * t + fpair(-1.0 / (5040.0 * 15.0));
-  p = p * t + fpair(1.0 / (720.0 * 13.0));
-  p = p * t + fpair(-1.0 / (120.0 * 11.0));
-  p = p * t + fpair(1.0 / (24.0 * 9.0));
-  p = p * t + fpair(-1.0 / (6.0 * 7.0));
-  p = p * t + fpair(1.0 / (2.0 * 5.0));
-  p = p * t + fpair(-1.0 / 3.0);
-  p = p * t + fpair(1.0f);
-  return fpair(1.0f) - fpair(1.12837916709551257390) * (x * p); /* 2/sqrt(pi) */
+  p = fp_horner_step(p, t, 1.0 / (87178291200.0 * 29.0));
+  p = fp_horner_step(p, t, -1.0 / (6227020800.0 * 27.0));
+  p = fp_horner_step(p, t, 1.0 / (479001600.0 * 25.0));
+  p = fp_horner_step(p, t, -1.0 / (39916800.0 * 23.0));
+  p = fp_horner_step(p, t, 1.0 / (3628800.0 * 21.0));
+  p = fp_horner_step(p, t, -1.0 / (362880.0 * 19.0));
+  p = fp_horner_step(p, t, 1.0 / (40320.0 * 17.0));
+  p = fp_horner_step(p, t, -1.0 / (5040.0 * 15.0));
+  p = fp_horner_step(p, t, 1.0 / (720.0 * 13.0));
+  p = fp_horner_step(p, t, -1.0 / (120.0 * 11.0));
+  p = fp_horner_step(p, t, 1.0 / (24.0 * 9.0));
+  p = fp_horner_step(p, t, -1.0 / (6.0 * 7.0));
+  p = fp_horner_step(p, t, 1.0 / (2.0 * 5.0));
+  p = fp_horner_step(p, t, -1.0 / 3.0);
+  p = fp_horner_step(p, t, 1.0);
+  return fp_addn(fpair(1.0f), -fp_muln(fpair(1.12837916709551257390), fp_muln(x, p))); /* 2/sqrt(pi) */
 }
 
 /* 1/sqrt(x), x > 0: the FP32 estimate and two Newton steps
-   y <- y + y (1 - x y^2) / 2 in pairs */
+   y <- y + y (1 - x y^2) / 2 in renormalised pairs */
 CGKS_HD fpair cg_rsqrt(fpair x) {
+  x = fp_norm(x);
   fpair y(fp_rsqrt_est(x.hi));
-  y = y + fp_scale(y * (fpair(1.0f) - x * (y * y)), 0.5f);
-  y = y + fp_scale(y * (fpair(1.0f) - x * (y * y)), 0.5f);
+  y = fp_addn(y, fp_scale(fp_muln(y, fp_addn(fpair(1.0f), -fp_muln(x, fp_muln(y, y)))), 0.5f));
+  y = fp_addn(y, fp_scale(fp_muln(y, fp_addn(fpair(1.0f), -fp_muln(x, fp_muln(y, y)))), 0.5f));
   return y;
 }
-CGKS_HD fpair cg_sqrt(fpair x) { return x.hi > 0.f ? x * cg_rsqrt(x) : fpair(0.0f); }
-CGKS_HD fpair cg_fabs(fpair x) { return x.hi < 0.f ? -x : x; }
+CGKS_HD fpair cg_sqrt(fpair x) {
+  x = fp_norm(x);
+  return x.hi > 0.f ? fp_muln(x, cg_rsqrt(x)) : fpair(0.0f);
+}
+CGKS_HD fpair cg_fabs(fpair x) {
+  x = fp_norm(x);
+  return x.hi < 0.f ? -x : x;
+}
+CGKS_HD fpair cg_norm(fpair x) { return fp_norm(x); }
 CGKS_HD fpair cg_fma(fpair a, fpair b, fpair c) { return a * b + c; }
 
 /* ---- unnormalised pairs for the reconstruction's linear maps ----

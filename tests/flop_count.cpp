@@ -137,6 +137,7 @@ inline fcount cg_fma(fcount a, fcount b, fcount c) {
 
 inline fcount cg_dot2(fcount a, fcount b, fcount c, fcount d) { return a * b + c * d; }
 inline fcount cg_madd(fcount a, fcount b, fcount c) { return a * b + c; }
+inline fcount cg_norm(fcount x) { return x; }
 inline fcount cg_dot3(fcount a, fcount b, fcount c, fcount d, fcount e, fcount f) { return a * b + c * d + e * f; }
 
 #include "host_kernels.cpp"
