@@ -742,16 +742,35 @@ CGKS_HD double recon_var_pair(const double* __restrict__ avg, const double* __re
   fpacc ih[3];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) ih[a] = fpacc_from_double(g.ih[a]);
+  /* every axis through one copy of the axis-0 transform: the coefficients
+     relabelled by pi (pi(0) = ax, the tangential axes in order; gen_perm),
+     the transform's derivative j being the physical derivative pi(j) (one
+     copy instead of three keeps the code the instruction cache must hold
+     to a third) */
 #pragma unroll 1
   for (int ax = 0; ax < DIM; ++ax) {
+    int pi[3];
+    pi[0] = ax;
+    pi[1] = ax == 0 ? 1 : 0;
+    pi[2] = ax == 2 ? 1 : 2;
+    fpacc ihc[DIM];
+    double ihd[DIM], bbc[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) { /* by selects: pi is a run-time relabelling */
+      ihc[j] = pi[j] == 0 ? ih[0] : (pi[j] == 1 ? ih[1] : ih[DIM - 1]);
+      ihd[j] = pi[j] == 0 ? g.ih[0] : (pi[j] == 1 ? g.ih[1] : g.ih[DIM - 1]);
+      bbc[j] = pi[j] == 0 ? bbar[0] : (pi[j] == 1 ? bbar[1] : bbar[DIM - 1]);
+    }
     fpacc pv[2 * S::GPF], pg[2 * S::GPF][DIM];
-    if constexpr (DIM == 3) {
-      if (ax == 0) gen_gp_3d_ax0<fpacc>(ap, pv, pg);
-      else if (ax == 1) gen_gp_3d_ax1<fpacc>(ap, pv, pg);
-      else gen_gp_3d_ax2<fpacc>(ap, pv, pg);
-    } else {
-      if (ax == 0) gen_gp_2d_ax0<fpacc>(ap, pv, pg);
-      else gen_gp_2d_ax1<fpacc>(ap, pv, pg);
+    {
+      fpacc ar[S::NB];
+      if constexpr (DIM == 3) {
+        gen_perm_3d<fpacc>(ap, ax, ar);
+        gen_gp_3d_ax0<fpacc>(ar, pv, pg);
+      } else {
+        gen_perm_2d<fpacc>(ap, ax, ar);
+        gen_gp_2d_ax0<fpacc>(ar, pv, pg);
+      }
     }
     int o[3] = {0, 0, 0};
     o[ax] = -1;
@@ -767,15 +786,15 @@ CGKS_HD double recon_var_pair(const double* __restrict__ avg, const double* __re
       if (lin) {
         dst[b] = ld.full(rel);
 #pragma unroll
-        for (int kk = 0; kk < DIM; ++kk) dst[b + (long)(1 + kk) * N] = fpacc_to_double(pg[i][kk] * ih[kk]);
+        for (int j = 0; j < DIM; ++j) dst[b + (long)(1 + pi[j]) * N] = fpacc_to_double(pg[i][j] * ihc[j]);
       } else {
         double v1 = 0.0;
 #pragma unroll
         for (int kk = 0; kk < DIM; ++kk) v1 += bbar[kk] * gp_delta<DIM, double>(gp, kk);
         dst[b] = ld.full(chi * rel + (1.0 - chi) * v1);
 #pragma unroll
-        for (int kk = 0; kk < DIM; ++kk)
-          dst[b + (long)(1 + kk) * N] = (chi * fpacc_to_double(pg[i][kk]) + (1.0 - chi) * bbar[kk]) * g.ih[kk];
+        for (int j = 0; j < DIM; ++j)
+          dst[b + (long)(1 + pi[j]) * N] = (chi * fpacc_to_double(pg[i][j]) + (1.0 - chi) * bbc[j]) * ihd[j];
       }
     }
   }

@@ -638,6 +638,26 @@ CGKS_HD void gen_gp_2d_ax1(const T* __restrict__ a, T* __restrict__ out_v, T (* 
   out_g[3][1] = wg1_1_0;
 }
 
+/* the coefficients a relabelled for the faces of axis ax: o[b'] = a[b] where
+   exponent(b)[pi(j)] = exponent(b')[j], pi(0) = ax, pi(1) < pi(2) */
+template <typename T>
+CGKS_HD void gen_perm_2d(const T* __restrict__ a, int ax, T* __restrict__ o) {
+  o[0] = ax == 0 ? a[0] : a[1];
+  o[1] = ax == 0 ? a[1] : a[0];
+  o[2] = ax == 0 ? a[2] : a[4];
+  o[3] = ax == 0 ? a[3] : a[3];
+  o[4] = ax == 0 ? a[4] : a[2];
+  o[5] = ax == 0 ? a[5] : a[8];
+  o[6] = ax == 0 ? a[6] : a[10];
+  o[7] = ax == 0 ? a[7] : a[9];
+  o[8] = ax == 0 ? a[8] : a[5];
+  o[9] = ax == 0 ? a[9] : a[7];
+  o[10] = ax == 0 ? a[10] : a[6];
+  o[11] = ax == 0 ? a[11] : a[11];
+  o[12] = ax == 0 ? a[12] : a[13];
+  o[13] = ax == 0 ? a[13] : a[12];
+}
+
 template <typename T, class Ld>
 CGKS_HD void gen_coeffs_3d(const Ld& ld, T* __restrict__ a) {
 #pragma unroll
@@ -2630,5 +2650,45 @@ CGKS_HD void gen_gp_3d_ax2(const T* __restrict__ a, T* __restrict__ out_v, T (* 
   out_g[7][0] = wg0_2_0;
   out_g[7][1] = wg1_2_0;
   out_g[7][2] = wg2_2_0;
+}
+
+/* the coefficients a relabelled for the faces of axis ax: o[b'] = a[b] where
+   exponent(b)[pi(j)] = exponent(b')[j], pi(0) = ax, pi(1) < pi(2) */
+template <typename T>
+CGKS_HD void gen_perm_3d(const T* __restrict__ a, int ax, T* __restrict__ o) {
+  o[0] = ax == 0 ? a[0] : (ax == 1 ? a[1] : a[2]);
+  o[1] = ax == 0 ? a[1] : (ax == 1 ? a[0] : a[0]);
+  o[2] = ax == 0 ? a[2] : (ax == 1 ? a[2] : a[1]);
+  o[3] = ax == 0 ? a[3] : (ax == 1 ? a[6] : a[8]);
+  o[4] = ax == 0 ? a[4] : (ax == 1 ? a[4] : a[5]);
+  o[5] = ax == 0 ? a[5] : (ax == 1 ? a[7] : a[7]);
+  o[6] = ax == 0 ? a[6] : (ax == 1 ? a[3] : a[3]);
+  o[7] = ax == 0 ? a[7] : (ax == 1 ? a[5] : a[4]);
+  o[8] = ax == 0 ? a[8] : (ax == 1 ? a[8] : a[6]);
+  o[9] = ax == 0 ? a[9] : (ax == 1 ? a[9] : a[13]);
+  o[10] = ax == 0 ? a[10] : (ax == 1 ? a[11] : a[16]);
+  o[11] = ax == 0 ? a[11] : (ax == 1 ? a[10] : a[14]);
+  o[12] = ax == 0 ? a[12] : (ax == 1 ? a[12] : a[15]);
+  o[13] = ax == 0 ? a[13] : (ax == 1 ? a[21] : a[21]);
+  o[14] = ax == 0 ? a[14] : (ax == 1 ? a[23] : a[24]);
+  o[15] = ax == 0 ? a[15] : (ax == 1 ? a[22] : a[22]);
+  o[16] = ax == 0 ? a[16] : (ax == 1 ? a[24] : a[23]);
+  o[17] = ax == 0 ? a[17] : (ax == 1 ? a[25] : a[29]);
+  o[18] = ax == 0 ? a[18] : (ax == 1 ? a[27] : a[32]);
+  o[19] = ax == 0 ? a[19] : (ax == 1 ? a[26] : a[30]);
+  o[20] = ax == 0 ? a[20] : (ax == 1 ? a[28] : a[31]);
+  o[21] = ax == 0 ? a[21] : (ax == 1 ? a[13] : a[9]);
+  o[22] = ax == 0 ? a[22] : (ax == 1 ? a[15] : a[12]);
+  o[23] = ax == 0 ? a[23] : (ax == 1 ? a[14] : a[10]);
+  o[24] = ax == 0 ? a[24] : (ax == 1 ? a[16] : a[11]);
+  o[25] = ax == 0 ? a[25] : (ax == 1 ? a[17] : a[17]);
+  o[26] = ax == 0 ? a[26] : (ax == 1 ? a[19] : a[20]);
+  o[27] = ax == 0 ? a[27] : (ax == 1 ? a[18] : a[18]);
+  o[28] = ax == 0 ? a[28] : (ax == 1 ? a[20] : a[19]);
+  o[29] = ax == 0 ? a[29] : (ax == 1 ? a[29] : a[25]);
+  o[30] = ax == 0 ? a[30] : (ax == 1 ? a[31] : a[28]);
+  o[31] = ax == 0 ? a[31] : (ax == 1 ? a[30] : a[26]);
+  o[32] = ax == 0 ? a[32] : (ax == 1 ? a[32] : a[27]);
+  o[33] = ax == 0 ? a[33] : (ax == 1 ? a[33] : a[33]);
 }
 

@@ -792,6 +792,29 @@ def emit_recon_code(path):
                         fn.append("  out_g[%d][%d] = %s%s;" % (i, kk, "-" if kk in S else "", yg[kk][m]))
             fn.append("}")
             fn.append("")
+        # the coefficients in the frame of axis ax: the coordinates relabelled
+        # by pi (pi(0) = ax, the tangential axes in increasing order), so that
+        # the axis-0 Gauss-point code evaluates the faces of axis ax; the
+        # code's derivative j is the physical derivative pi(j)
+        fn.append("/* the coefficients a relabelled for the faces of axis ax: o[b'] = a[b] where")
+        fn.append("   exponent(b)[pi(j)] = exponent(b')[j], pi(0) = ax, pi(1) < pi(2) */")
+        fn.append("template <typename T>")
+        fn.append("CGKS_HD void gen_perm_%dd(const T* __restrict__ a, int ax, T* __restrict__ o) {" % dim)
+        index = {e: b for b, e in enumerate(ex)}
+        for b2, e2 in enumerate(ex):
+            srcs = []
+            for ax in range(dim):
+                pi = [ax] + [x for x in range(dim) if x != ax]
+                e = [0] * dim
+                for j in range(dim):
+                    e[pi[j]] = e2[j]
+                srcs.append(index[tuple(e)])
+            if dim == 3:
+                fn.append("  o[%d] = ax == 0 ? a[%d] : (ax == 1 ? a[%d] : a[%d]);" % (b2, srcs[0], srcs[1], srcs[2]))
+            else:
+                fn.append("  o[%d] = ax == 0 ? a[%d] : a[%d];" % (b2, srcs[0], srcs[1]))
+        fn.append("}")
+        fn.append("")
         out += fn
     with open(path, "w") as f:
         f.write("\n".join(out) + "\n")

@@ -77,8 +77,10 @@ int run_stage(DevGeo& g, Phys& ph, double dt, int stage, double** avg, T** der, 
   threadIdx.x = 0;
   for (long t = 0; t < N; ++t) {
     blockIdx.x = (unsigned)t;
-    k_recon<T, DIM, CV, true>(avg[in], avh[in], avl[in], der[in], g, ph, gpL.data(), gpR.data(), chi.data(), 0, st,
-                              SelectorDev{});
+    /* the paired form (C = fpair) also reconstructs with the paired
+       Gauss-point transform on Cartesian meshes, as the library does */
+    k_recon<T, DIM, CV, true, !CV && cg_same<C, fpair>::value>(avg[in], avh[in], avl[in], der[in], g, ph, gpL.data(),
+                                                                 gpR.data(), chi.data(), 0, st, SelectorDev{});
   }
   for (long t = 0; t < (long)DIM * Sz<DIM>::GPF * N; ++t) {
     blockIdx.x = (unsigned)t;
@@ -215,6 +217,56 @@ int host_run(int dim, int precision, const int* n, const double* lo, const doubl
   if (precision == 1) return run<float, 2>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
   if (precision == 2) return run<double, 2, fpair>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
   return run<double, 2>(n, lo, hi, nodes, phys, U, nsteps, dt_out);
+}
+/* the face Gauss-point transforms of the generated code: for random
+   coefficients, the largest relative difference between axis ax's own
+   transform and the axis-0 transform of the relabelled coefficients
+   (gen_perm), with the derivative j of the latter read as the physical
+   derivative pi(j) */
+double host_gp_perm_check(int dim, unsigned seed) {
+  unsigned long long x = 0x9e3779b97f4a7c15ull ^ seed;
+  auto rnd = [&]() {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  };
+  double worst = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    double a[34], o[34], v0[8], g0[8][3], v1[8], g1[8][3];
+    const int nb = dim == 3 ? 34 : 14, np = dim == 3 ? 8 : 4;
+    for (int b = 0; b < nb; ++b) a[b] = rnd();
+    for (int ax = 0; ax < dim; ++ax) {
+      if (dim == 3) {
+        if (ax == 0) gen_gp_3d_ax0<double>(a, v0, g0);
+        else if (ax == 1) gen_gp_3d_ax1<double>(a, v0, g0);
+        else gen_gp_3d_ax2<double>(a, v0, g0);
+        gen_perm_3d<double>(a, ax, o);
+        gen_gp_3d_ax0<double>(o, v1, g1);
+      } else {
+        double g02[4][2], g12[4][2];
+        if (ax == 0) gen_gp_2d_ax0<double>(a, v0, g02);
+        else gen_gp_2d_ax1<double>(a, v0, g02);
+        gen_perm_2d<double>(a, ax, o);
+        gen_gp_2d_ax0<double>(o, v1, g12);
+        for (int i = 0; i < np; ++i)
+          for (int k = 0; k < 2; ++k) {
+            g0[i][k] = g02[i][k];
+            g1[i][k] = g12[i][k];
+          }
+      }
+      int pi[3] = {ax, 0, 0};
+      for (int j = 1, q = 0; q < dim; ++q)
+        if (q != ax) pi[j++] = q;
+      double scale = 0.0;
+      for (int i = 0; i < np; ++i) scale = std::max(scale, std::fabs(v0[i]));
+      for (int i = 0; i < np; ++i) {
+        worst = std::max(worst, std::fabs(v1[i] - v0[i]) / scale);
+        for (int j = 0; j < dim; ++j) worst = std::max(worst, std::fabs(g1[i][j] - g0[i][pi[j]]) / scale);
+      }
+    }
+  }
+  return worst;
 }
 /* the learned selector's 16 features of every cell (uniform boxes) */
 void host_features(int dim, const int* n, const double* lo, const double* hi, const double* U, int precision,

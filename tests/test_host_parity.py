@@ -53,6 +53,8 @@ def hk():
     lib.host_set_bc.argtypes = [ip, dp]
     lib.host_run.argtypes = [C.c_int, C.c_int, ip, dp, dp, dp, dp, dp, C.c_int, dp]
     lib.host_features.argtypes = [C.c_int, ip, dp, dp, dp, C.c_int, fp]
+    lib.host_gp_perm_check.argtypes = [C.c_int, C.c_uint]
+    lib.host_gp_perm_check.restype = C.c_double
     return lib
 
 
@@ -172,3 +174,16 @@ def test_host_selector_features_bit_exact(orc, hk, precision):
     hk.host_features(2, (C.c_int * 3)(24, 20, 1), _dp(np.zeros(3)), _dp(np.ones(3)), _dp(U), precision,
                      out.ctypes.data_as(C.POINTER(C.c_float)))
     assert np.array_equal(out, fo)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gauss_point_transform_axis_symmetry(hk, dim):
+    """The face Gauss-point transform of axis ax equals the axis-0 transform
+    of the coefficients relabelled by the permutation pi of the coordinates
+    (pi(0) = ax, tangential axes in order; gen_perm), with the axis-0
+    derivative j read as the physical derivative pi(j): the reference cell
+    and the basis (all monomials of degree 1..4) are symmetric under
+    relabelling.  The paired reconstruction evaluates all three axes this
+    way through one copy of the axis-0 code."""
+    worst = max(hk.host_gp_perm_check(dim, seed) for seed in (1, 2, 3))
+    assert worst <= 1e-14, worst
