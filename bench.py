@@ -60,14 +60,14 @@ ALG_FLOPS_PER_UNIT = {
 EXEC_FLOPS_PER_UNIT = {
     ("flux", 3): 3.616e3,
 }
-# the paired form's flux (ncu, TGV 64^3): FP32 flops it executes per face
-# Gauss point for its FP64-equivalent work (2 FFMA + FADD + FMUL; plus 99
-# FP64 flops of conversions)
+# the paired form's flux (ncu, TGV 64^3, profiles/flux_pair_tgv64_full.md):
+# FP32 flops it executes per face Gauss point for its FP64-equivalent work
+# (2 FFMA + FADD + FMUL; plus 101 FP64 flops of conversions)
 EXEC_FP32_FLOPS_PER_UNIT_PAIR = {
-    ("flux", 3): 31262.0,
+    ("flux", 3): 26580.0,
 }
 DRAM_BYTES_PER_UNIT_PAIR = {
-    ("flux", 3): (1.007182e9 + 0.731100e9) / (262144 * 12),
+    ("flux", 3): (1.007367e9 + 0.735652e9) / (262144 * 12),
 }
 # DRAM bytes per unit of the same capture (read + write), for `traffic`
 DRAM_BYTES_PER_UNIT = {
