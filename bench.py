@@ -339,7 +339,8 @@ def e2e_overlapped(make_mesh, h_in, outs, nsteps):
         # overlapping the first lane's step, and so on
         lanes[0].set_state_async(h_in, 0.0)
         lanes[0].sync()
-        lanes[1].set_state_async(h_in, 0.0)
+        if nsteps > 1:
+            lanes[1].set_state_async(h_in, 0.0)
         for i in range(nsteps):
             m = lanes[i % 2]
             m.step(1)
@@ -648,7 +649,7 @@ def main():
     overlapped = ov_s is not None
     if overlapped:
         ov_s = replicas.job_time_ms(1e3 * ov_s, device="cuda") / 1e3
-        lanes_match = all(np.array_equal(o.numpy(), h_out.numpy()) for o in outs)
+        lanes_match = all(np.array_equal(o.numpy(), h_out.numpy()) for o in outs[:min(2, args.e2e_steps)])
     else:
         ov_s, lanes_match = e2e_s, None
     kernels = {k: {"launches": v[0], "ms_total": v[1], "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-30)}
