@@ -41,11 +41,15 @@ CGKS_HD void set_dt(DtState& d, double dt) {
 template <typename T, int DIM = 3> constexpr int min_blocks() { return sizeof(T) == 4 ? (DIM == 2 ? 4 : 3) : 2; }
 /* the Cartesian kernels: FP32 fits 4 blocks in 3-D as well (128 registers:
    the flux spills 8 B since its Maxwellian moments are factorised, the
-   reconstruction 196 B and still gains 4% from the extra warps) and the 2-D
-   flux 5 (96 registers, no spill); the curvilinear ones, which spill more,
-   keep 3 */
-template <typename T, int DIM, bool CURVI> constexpr int recon_min_blocks() {
-  return sizeof(T) == 4 && DIM == 3 && !CURVI ? 4 : min_blocks<T, DIM>();
+   reconstruction none since its Gauss-point transform runs one relabelled
+   copy for all axes; 5 blocks spill and run slower: reconstruction 1.57 ->
+   1.65 ms, flux 2.59 -> 3.29 ms at TGV 128^3) and the 2-D flux 5 (96
+   registers, no spill); the curvilinear ones, which spill more, keep 3.
+   PR: the paired form's 3-D reconstruction runs 3 (168 registers; its
+   812 B of spills cost less than the latency the extra warps hide: TGV
+   128^3 20.1 -> 19.4 ms per stage) */
+template <typename T, int DIM, bool CURVI, bool PR = false> constexpr int recon_min_blocks() {
+  return PR && DIM == 3 ? 3 : (sizeof(T) == 4 && DIM == 3 && !CURVI ? 4 : min_blocks<T, DIM>());
 }
 template <typename T, int DIM, bool CURVI> constexpr int flux_min_blocks() {
   return sizeof(T) == 4 && !CURVI ? (DIM == 2 ? 5 : 4) : min_blocks<T, DIM>();
@@ -161,7 +165,7 @@ __device__ __forceinline__ bool selector_skip(const SelectorDev& sel, const doub
 }
 
 template <typename T, int DIM, bool CURVI, bool WALL, bool PR = false>
-__global__ void __launch_bounds__(128, recon_min_blocks<T, DIM, CURVI>())
+__global__ void __launch_bounds__(128, recon_min_blocks<T, DIM, CURVI, PR>())
     k_recon(const double* __restrict__ avg, const float* __restrict__ avh, const float* __restrict__ avl,
             const T* __restrict__ der, DevGeo g, Phys ph, T* __restrict__ gpL, T* __restrict__ gpR,
             double* __restrict__ chi, int record_chi, int* __restrict__ st, SelectorDev sel) {
