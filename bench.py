@@ -75,12 +75,12 @@ DRAM_BYTES_PER_UNIT = {
 }
 # the same for the FP32 form (update: per (cell, variable))
 EXEC_FLOPS_PER_UNIT_FP32 = {
-    ("recon", 3): 1.235e4,
+    ("recon", 3): 1.262e4,
     ("flux", 3): 3.395e3,
     ("update", 3): 158.0,
 }
 DRAM_BYTES_PER_UNIT_FP32 = {
-    ("recon", 3): (157.8e6 + 492.7e6) / 262144,
+    ("recon", 3): (151.1e6 + 465.3e6) / 262144,
     ("flux", 3): (503.4e6 + 337.0e6) / (262144 * 12),
     ("update", 3): (388.5e6 + 159.3e6) / (262144 * 5),
 }
