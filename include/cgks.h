@@ -49,7 +49,7 @@ typedef enum {
   CGKS_ENOMEM = -2,      /* device allocation failed */
   CGKS_ECUDA = -3,       /* a CUDA runtime call failed */
   CGKS_ENONPHYS = -4,    /* non-positive density/pressure that even chi = 0 cannot cure */
-  CGKS_ETIMEOUT = -5,    /* reserved: a bounded device wait gave up */
+  CGKS_ETIMEOUT = -5,    /* a bounded device wait gave up (the flux kernel's TMA staging) */
   CGKS_ESTATE = -6,      /* call made in the wrong state */
   CGKS_EUNSUPPORTED = -7, /* option the library does not support */
   CGKS_ETOOLARGE = -8     /* problem larger than a fixed-size buffer of the library */
@@ -122,6 +122,17 @@ void cgks_destroy(cgks_ctx* ctx);
 int cgks_num_vars(const cgks_ctx* ctx);    /* nv */
 int cgks_num_fields(const cgks_ctx* ctx);  /* nf */
 long cgks_num_cells(const cgks_ctx* ctx);
+
+/* How the interface-flux kernel of this context stages each face point's
+   Gauss-point states in shared memory (no counterpart in the paper, which
+   states no kernel design): 1 = one tensor-memory-accelerator (TMA) tile per
+   block of 128 points (Cartesian meshes whose cell count is a multiple of
+   128), 0 = one cp.async per value and thread (every other mesh, or the
+   environment variable CGKS_FLUX_STAGING=cp.async at cgks_create_mesh).
+   Results are the same bit for bit.  A TMA tile that does not arrive within
+   its bounded wait (about a second) makes cgks_step return CGKS_ETIMEOUT;
+   -1 for a NULL context. */
+int cgks_flux_staging(const cgks_ctx* ctx);
 
 /* Copy a full state in (layout above), from host (is_device = 0) or device
    memory, and set the time. */

@@ -103,6 +103,7 @@ class BatchTiles(C.Structure):
 
 
 EXPORTS = ["cgks_create_mesh", "cgks_destroy", "cgks_num_vars", "cgks_num_fields", "cgks_num_cells",
+           "cgks_flux_staging",
            "cgks_set_state", "cgks_get_state", "cgks_set_state_async", "cgks_get_state_async", "cgks_sync",
            "cgks_step", "cgks_compute_dt", "cgks_init_points_per_cell",
            "cgks_init_points", "cgks_init_from_prims", "cgks_get_chi", "cgks_profile_enable",
@@ -135,6 +136,8 @@ def lib(build_if_missing=True):
     L.cgks_num_fields.argtypes = [vp]
     L.cgks_num_cells.argtypes = [vp]
     L.cgks_num_cells.restype = C.c_long
+    L.cgks_flux_staging.argtypes = [vp]
+    L.cgks_flux_staging.restype = C.c_int
     L.cgks_set_state.argtypes = [vp, vp, C.c_int, C.c_double]
     L.cgks_get_state.argtypes = [vp, vp, C.c_int, dp]
     L.cgks_set_state_async.argtypes = [vp, vp, C.c_int, C.c_double]
@@ -246,6 +249,7 @@ class Mesh:
         self.nv = L.cgks_num_vars(h)
         self.nf = L.cgks_num_fields(h)
         self.ncell = L.cgks_num_cells(h)
+        self.flux_staging = "tma" if L.cgks_flux_staging(h) == 1 else "cp.async"
         self.lo, self.hi = tuple(lo[:dim]), tuple(hi[:dim])
 
     def _check(self, st):

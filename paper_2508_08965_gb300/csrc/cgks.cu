@@ -4,12 +4,14 @@
  * scheme runs in the kernels of cgks_kernels.cuh.
  */
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <utility>
 
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -133,6 +135,36 @@ static cgks_status join_out(cgks_ctx* ctx) {
 
 extern "C" {
 
+/* The tensor map of a Gauss-point state array (gpL or gpR) for the flux
+   kernel's TMA tiles: a 2-D array [row][cell] of N cells per row and
+   dim * GPF * NV * (1 + dim) rows (row = (ax * GPF + k) * NQ + q), boxes of
+   NQ rows x 128 cells.  The encoder comes from the driver through the
+   runtime (no link against the driver library); false if it is not there
+   or refuses the map. */
+static bool encode_gp_map(const cgks_ctx* ctx, void* base, CUtensorMap* map) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }();
+  if (!encode) return false;
+  const int dim = ctx->dim, gpf = dim == 3 ? 4 : 2;
+  const cuuint32_t nq = (cuuint32_t)(ctx->nv * (1 + dim));
+  const size_t es = ctx->prec == 0 ? sizeof(double) : sizeof(float);
+  const cuuint64_t gdim[2] = {(cuuint64_t)ctx->ncell, (cuuint64_t)dim * gpf * nq};
+  const cuuint64_t gstride[1] = {(cuuint64_t)ctx->ncell * es};
+  const cuuint32_t box[2] = {128, nq};
+  const cuuint32_t estride[2] = {1, 1};
+  return encode(map, es == sizeof(float) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base,
+                gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   cgks_ctx* ctx = nullptr;
   if (!d || !out) return CGKS_EINVAL;
@@ -237,6 +269,15 @@ cgks_status cgks_create_mesh(const cgks_mesh_desc* d, cgks_ctx** out) {
   }
   ALLOC(ctx->gpL, gp_sz);
   ALLOC(ctx->gpR, gp_sz);
+  /* CGKS_FLUX_STAGING=cp.async in the environment keeps the per-thread
+     staging (the tests compare the two) */
+  const char* staging = getenv("CGKS_FLUX_STAGING");
+  if (!d->nodes && N % 128 == 0 && !(staging && !strcmp(staging, "cp.async")))
+    ctx->tma = encode_gp_map(ctx, ctx->gpL, &ctx->tmL) && encode_gp_map(ctx, ctx->gpR, &ctx->tmR);
+  /* test hook of the bounded staging wait: CGKS_TEST_STAGING_STALL=1 makes
+     every TMA barrier of this context wait for 16 bytes that never come */
+  const char* stall = getenv("CGKS_TEST_STAGING_STALL");
+  ctx->ph.stall_tx = (ctx->tma && stall && !strcmp(stall, "1")) ? 16 : 0;
   ALLOC(ctx->flux, fx_sz);
   if (g.nplane > 0) ALLOC(ctx->fxb, rsz * (size_t)dim * gpf * 6 * nv * g.nplane);
   g.bcq = nullptr;
@@ -313,6 +354,7 @@ void cgks_destroy(cgks_ctx* ctx) {
 int cgks_num_vars(const cgks_ctx* ctx) { return ctx ? ctx->nv : -1; }
 int cgks_num_fields(const cgks_ctx* ctx) { return ctx ? ctx->nf : -1; }
 long cgks_num_cells(const cgks_ctx* ctx) { return ctx ? ctx->ncell : -1; }
+int cgks_flux_staging(const cgks_ctx* ctx) { return ctx ? (ctx->tma ? 1 : 0) : -1; }
 
 /* the copy in, the FP32 split and a fresh time-step record, enqueued on the
    context's stream without waiting */
@@ -379,6 +421,8 @@ static cgks_status check_status(cgks_ctx* ctx) {
     int z[ST_N] = {0, st[ST_FALLBACK], 0, 0};
     CK(cudaMemcpyAsync(ctx->st, z, sizeof z, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (st[ST_FLUX] & 2) /* a flux block's TMA tile did not arrive within its bounded wait */
+      return fail(ctx, CGKS_ETIMEOUT, "a staging wait of the interface flux gave up");
     return fail(ctx, CGKS_ENONPHYS, "non-physical state (recon %d, interface %d, cell %d)", st[ST_NONPHYS],
                 st[ST_FLUX], st[ST_DT]);
   }

@@ -65,6 +65,12 @@ struct cgks_ctx {
   void* flux = nullptr;
   void* fxb = nullptr;      /* low-boundary faces of the non-periodic axes */
   double* chi = nullptr;
+  /* the flux kernel's TMA tiles: gpL and gpR as 2-D arrays [row][cell]
+     (boxes of one Gauss point's quantities x 128 cells); tma = false where
+     the mesh does not allow them (curvilinear, cell count not a multiple of
+     128) or the driver gave no encoder: the flux then stages by cp.async */
+  bool tma = false;
+  CUtensorMap tmL{}, tmR{};
   cgks::DtState* dts = nullptr;
   int* st = nullptr;
   double t = 0.0;

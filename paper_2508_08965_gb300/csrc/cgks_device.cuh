@@ -132,6 +132,9 @@ struct Phys {
   /* FP32 copies and the heat-flux-fix switch (mu > 0 and Pr != 1) */
   float gammaf, muf, prandtlf, c_chif;
   int prfix;
+  /* test hook: bytes added to what the flux's TMA barrier expects, so that
+     it never completes and the bounded wait runs out (0 in normal use) */
+  int stall_tx;
 };
 
 /* the physics constants in T */
@@ -1555,7 +1558,7 @@ CGKS_HD void to_global(const double R[3][3], T* F) {
 template <typename T, int DIM, bool CURVI, typename C = T>
 CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, long c,
                         const T* __restrict__ gpL, const T* __restrict__ gpR, T* __restrict__ flux,
-                        T* sm = nullptr, int ns = 0) {
+                        T* sm = nullptr, int ns = 0, bool staged = false) {
   typedef Sz<DIM> S;
   constexpr int NV = S::NV;
   const long N = g.ncell;
@@ -1567,12 +1570,14 @@ CGKS_HD bool flux_point(const DevGeo& g, const Phys& ph, T dt, int ax, int k, lo
     C WL[NV], WR[NV], out[6 * NV];
     CartLd<T, DIM, C> ld;
     if (sm) {
+      if (!staged) { /* else the block's tile is in shared memory already (TMA) */
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        async_copy(sm + (long)q * ns, gpL + (base + q) * N + c);
-        async_copy(sm + (long)(NQ + q) * ns, gpR + (base + q) * N + c);
+        for (int q = 0; q < NQ; ++q) {
+          async_copy(sm + (long)q * ns, gpL + (base + q) * N + c);
+          async_copy(sm + (long)(NQ + q) * ns, gpR + (base + q) * N + c);
+        }
+        async_wait_all();
       }
-      async_wait_all();
       ld.gl = sm;
       ld.gr = sm + (long)NQ * ns;
       ld.base = 0;

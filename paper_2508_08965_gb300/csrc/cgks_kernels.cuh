@@ -4,6 +4,8 @@
  * initial-data kernels and the time-step reduction.
  */
 #pragma once
+#include <cuda.h> /* CUtensorMap (a type only: maps are encoded through the runtime's driver entry point) */
+
 #include "cgks_device.cuh"
 #include "cgks_selector.cuh"
 
@@ -202,7 +204,7 @@ __global__ void k_selector_features(const double* __restrict__ avg, const float*
 template <typename T, int DIM, bool CURVI, typename C = T>
 __device__ __forceinline__ void flux_item(const DevGeo& g, const Phys& ph, double dt, long t, const T* __restrict__ gpL,
                                           const T* __restrict__ gpR, T* __restrict__ flux, int* __restrict__ st,
-                                          T* sm = nullptr, int ns = 0) {
+                                          T* sm = nullptr, int ns = 0, bool staged = false) {
   const long N = g.ncell;
   const long c = t % N;
   const int r = (int)(t / N);
@@ -212,7 +214,64 @@ __device__ __forceinline__ void flux_item(const DevGeo& g, const Phys& ph, doubl
     cell_ijk(g, c, ijk[0], ijk[1], ijk[2]);
     if (ijk[ax] == g.n[ax] - 1) return;
   }
-  if (!flux_point<T, DIM, CURVI, C>(g, ph, T(dt), ax, k, c, gpL, gpR, flux, sm, ns)) atomicOr(&st[ST_FLUX], 1);
+  if (!flux_point<T, DIM, CURVI, C>(g, ph, T(dt), ax, k, c, gpL, gpR, flux, sm, ns, staged))
+    atomicOr(&st[ST_FLUX], 1);
+}
+
+/* ---- TMA tiles ----------------------------------------------------------
+   The Gauss-point states of the 128 face points of a flux block are, per
+   stored quantity q, 128 consecutive values of one row of gpL (and of gpR)
+   viewed as a 2-D array [row][cell] (row = (ax * GPF + k) * NQ + q): one
+   box of NQ rows x 128 cells each, which one thread loads with the tensor
+   memory accelerator (cp.async.bulk.tensor) into the block's staging tile
+   and the block waits for on a shared-memory barrier.  Requires a Cartesian
+   mesh whose cell count is a multiple of 128 (a block's points then share
+   (ax, k), its first cell is 16-byte aligned in every row, and the row
+   pitch is a multiple of 16 bytes); other meshes stage by cp.async. */
+__device__ __forceinline__ void tma_bar_init(uint64_t* bar) {
+#if defined(__CUDA_ARCH__)
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(a) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void tma_expect(uint64_t* bar, unsigned bytes) {
+#if defined(__CUDA_ARCH__)
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+#endif
+}
+/* box at (x = first cell, y = first row) of the tensor map into dst */
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+#if defined(__CUDA_ARCH__)
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(d),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(b)
+      : "memory");
+#endif
+}
+/* wait for phase 0 of the barrier; false if it has not completed within
+   about a second (the caller then reports CGKS_ETIMEOUT) */
+__device__ __forceinline__ bool tma_wait(uint64_t* bar) {
+#if defined(__CUDA_ARCH__)
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000LL) return false;
+  }
+#else
+  return true;
+#endif
 }
 
 /* boundary face-point item t = ((side * DIM + ax) * GPF + k) * nplane + plane.
@@ -253,18 +312,49 @@ __device__ __forceinline__ void flux_bnd_item(const DevGeo& g, const Phys& ph, d
    path stages each point's Gauss-point states in shared memory.  C: the
    solve's compute type (fpair: the paired form, FP64 storage, Cartesian or
    curvilinear with the face-frame rotation in FP64) */
-template <typename T, int DIM, bool CURVI, typename C = T>
+template <typename T, int DIM, bool CURVI, typename C = T, bool TMA = false>
 __global__ void __launch_bounds__(128, flux_min_blocks<T, DIM, CURVI>()) k_flux(DevGeo g, Phys ph, const DtState* __restrict__ dts,
                                               const T* __restrict__ gpL, const T* __restrict__ gpR,
-                                              T* __restrict__ flux, int* __restrict__ st) {
+                                              T* __restrict__ flux, int* __restrict__ st,
+                                              const __grid_constant__ CUtensorMap tmL,
+                                              const __grid_constant__ CUtensorMap tmR) {
   long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long N = g.ncell;
   if (t >= (long)DIM * Sz<DIM>::GPF * N) return;
   const double dt = dts->dt;
   if (!(dt > 0.0)) return;
   if constexpr (!CURVI) {
-    __shared__ T stage[2 * Sz<DIM>::NV * (1 + DIM) * 128];
-    flux_item<T, DIM, CURVI, C>(g, ph, dt, t, gpL, gpR, flux, st, stage + threadIdx.x, 128);
+    constexpr int NQ = Sz<DIM>::NV * (1 + DIM);
+    __shared__ __align__(128) T stage[2 * NQ * 128];
+    if constexpr (TMA) { /* every thread of the block is here: 128 | N, 128 | the point count */
+      __shared__ __align__(8) uint64_t bar;
+      __shared__ int gave_up;
+      const long t0 = blockIdx.x * 128L;
+      const int r = (int)(t0 / N);
+      if (threadIdx.x == 0) {
+        /* once a block's wait has given up, later blocks skip theirs, so a
+           launch that stalls ends after one wave of waits */
+        gave_up = *(volatile int*)&st[ST_FLUX] & 2;
+        if (!gave_up) tma_bar_init(&bar);
+      }
+      __syncthreads();
+      if (gave_up) return;
+      if (threadIdx.x == 0) {
+        tma_expect(&bar, 2u * NQ * 128u * (unsigned)sizeof(T) + (unsigned)ph.stall_tx);
+        tma_load_2d(stage, &tmL, (int)(t0 - (long)r * N), r * NQ, &bar);
+        tma_load_2d(stage + NQ * 128, &tmR, (int)(t0 - (long)r * N), r * NQ, &bar);
+      }
+      /* the two copies have landed whether or not the barrier completes
+         (only the test hook's extra bytes can hold it back), so a block that
+         gives up leaves nothing in flight */
+      if (!tma_wait(&bar)) {
+        if (threadIdx.x == 0) atomicOr(&st[ST_FLUX], 2);
+        return;
+      }
+      flux_item<T, DIM, CURVI, C>(g, ph, dt, t, gpL, gpR, flux, st, stage + threadIdx.x, 128, true);
+    } else {
+      flux_item<T, DIM, CURVI, C>(g, ph, dt, t, gpL, gpR, flux, st, stage + threadIdx.x, 128);
+    }
   } else {
     flux_item<T, DIM, CURVI, C>(g, ph, dt, t, gpL, gpR, flux, st);
   }

@@ -11,8 +11,13 @@ using namespace cgks_host;
 template <int DIM, bool CURVI>
 void launch_flux_pair(cgks_ctx* ctx, const double* gpL, const double* gpR, double* flux) {
   const long nf = (long)DIM * Sz<DIM>::GPF * ctx->ncell;
-  k_flux<double, DIM, CURVI, fpair><<<cdiv(nf, 128), 128, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, gpL, gpR,
-                                                                              flux, ctx->st);
+  if (ctx->tma)
+    k_flux<double, DIM, CURVI, fpair, true><<<cdiv(nf, 128), 128, 0, ctx->stream>>>(
+        ctx->geo, ctx->ph, ctx->dts, gpL, gpR, flux, ctx->st, ctx->tmL, ctx->tmR);
+  else
+    k_flux<double, DIM, CURVI, fpair><<<cdiv(nf, 128), 128, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, gpL,
+                                                                                gpR, flux, ctx->st, ctx->tmL,
+                                                                                ctx->tmR);
 }
 
 template void launch_flux_pair<2, false>(cgks_ctx*, const double*, const double*, double*);

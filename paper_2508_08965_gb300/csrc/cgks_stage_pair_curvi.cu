@@ -12,7 +12,7 @@ template <int DIM, bool CURVI>
 void launch_flux_pair(cgks_ctx* ctx, const double* gpL, const double* gpR, double* flux) {
   const long nf = (long)DIM * Sz<DIM>::GPF * ctx->ncell;
   k_flux<double, DIM, CURVI, fpair><<<cdiv(nf, 128), 128, 0, ctx->stream>>>(ctx->geo, ctx->ph, ctx->dts, gpL, gpR,
-                                                                              flux, ctx->st);
+                                                                              flux, ctx->st, ctx->tmL, ctx->tmR);
 }
 
 template void launch_flux_pair<2, true>(cgks_ctx*, const double*, const double*, double*);

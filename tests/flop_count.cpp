@@ -248,7 +248,7 @@ int count_stage(const int* n, const double* lo, const double* hi, const double* 
     fresh(fx, &fxd);
     const size_t before = fc::G.nodes.size();
     blockIdx.x = (unsigned)t;
-    k_flux<T, DIM, false, T>(g, ph, &dts, gpL.data(), gpR.data(), fx.data(), st);
+    k_flux<T, DIM, false, T>(g, ph, &dts, gpL.data(), gpR.data(), fx.data(), st, CUtensorMap{}, CUtensorMap{});
     roots.clear();
     roots_of(fx, before, roots);
     count_live(roots, c[1]);

@@ -30,6 +30,7 @@ static HostDim blockIdx, blockDim, threadIdx, gridDim;
 #define __device__
 #endif
 #define __forceinline__ inline
+#define __grid_constant__
 static inline long long __double_as_longlong(double d) { long long r; memcpy(&r, &d, 8); return r; }
 static inline double __longlong_as_double(long long d) { double r; memcpy(&r, &d, 8); return r; }
 static inline unsigned __float_as_uint(float f) { unsigned r; memcpy(&r, &f, 4); return r; }
@@ -84,7 +85,7 @@ int run_stage(DevGeo& g, Phys& ph, double dt, int stage, double** avg, T** der, 
   }
   for (long t = 0; t < (long)DIM * Sz<DIM>::GPF * N; ++t) {
     blockIdx.x = (unsigned)t;
-    k_flux<T, DIM, CV, C>(g, ph, &dts, gpL.data(), gpR.data(), flux.data(), st);
+    k_flux<T, DIM, CV, C>(g, ph, &dts, gpL.data(), gpR.data(), flux.data(), st, CUtensorMap{}, CUtensorMap{});
   }
   for (long t = 0; t < 2L * DIM * Sz<DIM>::GPF * g.nplane; ++t) {
     blockIdx.x = (unsigned)t;
