@@ -1813,6 +1813,11 @@ CGKS_HD StageCoef stage_coef(double dt) {
   return k;
 }
 
+/* a stored value as double: floats exactly, on the integer pipe (the FP32
+   form's update is bound by its FP64 pipe, which would convert them) */
+CGKS_HD double to_f64(float x) { return fp_f2d_exact(x); }
+CGKS_HD double to_f64(double x) { return x; }
+
 template <typename T, int DIM, bool CURVI>
 CGKS_HD void update_var(const DevGeo& g, const StageCoef& kc, int stage, long c, int ci, int cj, int ck, int v,
                         const double* __restrict__ avg_in, const T* __restrict__ flux, const T* __restrict__ fxb,
@@ -1893,8 +1898,8 @@ CGKS_HD void update_var(const DevGeo& g, const StageCoef& kc, int stage, long c,
       }
     }
     const double w = CURVI ? 1.0 : g.ih[ax] * (1.0 / GPF);
-    L += w * (double(sl_f) - double(sh_f));
-    Lt += w * (double(stl_f) - double(sth_f));
+    L += w * (to_f64(sl_f) - to_f64(sh_f));
+    Lt += w * (to_f64(stl_f) - to_f64(sth_f));
   }
   if constexpr (CURVI) {
     const double iv = 1.0 / met_vol<DIM>(g, c);
@@ -1916,7 +1921,7 @@ CGKS_HD void update_var(const DevGeo& g, const StageCoef& kc, int stage, long c,
   if constexpr (sizeof(T) == 4) {
     const float h = float(out);
     avh_out[iavg] = h;
-    avl_out[iavg] = float(out - double(h));
+    avl_out[iavg] = float(out - fp_f2d_exact(h));
   }
   /* gradient: Gauss' theorem (Eq. derivative); on an axis-aligned cell the
      mean of the line derivatives */

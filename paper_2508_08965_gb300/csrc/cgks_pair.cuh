@@ -452,6 +452,29 @@ CGKS_HD double fp_f2d_bits(float f) {
 /* hi + lo rounded once to double */
 CGKS_HD double fpacc_to_double(fpacc a) { return fp_f2d_bits(a.hi) + fp_f2d_bits(a.lo); }
 
+/* float -> double on the integer pipe, exact for every float: subnormals
+   normalised by a count of leading zeros (a rare branch), infinities and
+   NaNs carried through; the same value as the hardware conversion, which
+   GB300 runs on its FP64 pipe */
+CGKS_HD double fp_f2d_exact(float f) {
+  const unsigned u = fp_fbits(f);
+  const unsigned sgn = u & 0x80000000u;
+  int e = (int)((u >> 23) & 0xffu);
+  unsigned m = u & 0x7fffffu;
+  if (e == 0) {
+    if (m == 0u) return fp_bitsd(sgn, 0u);
+#if defined(__CUDA_ARCH__)
+    const int sh = __clz(m) - 8;
+#else
+    const int sh = __builtin_clz(m) - 8;
+#endif
+    m = (m << sh) & 0x7fffffu; /* the leading one becomes the implicit bit */
+    e = 1 - sh;
+  }
+  const unsigned e2 = e == 255 ? 2047u : (unsigned)(e + 896);
+  return fp_bitsd(sgn | (e2 << 20) | (m >> 3), m << 29);
+}
+
 template <class A, class B> struct cg_same { static constexpr bool value = false; };
 template <class A> struct cg_same<A, A> { static constexpr bool value = true; };
 

@@ -4,6 +4,7 @@
 #define CGKS_HD inline
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <random>
 #include <cmath>
 namespace cgks {
@@ -138,5 +139,38 @@ void pair_conv_stats(int n, unsigned seed, double* out) {
     const fpacc nrm = cgks::fpacc_norm(acc);
     out[4] = std::fmax(out[4], (double)(fabsl(val(nrm) - ref) / mag));
   }
+}
+}
+
+extern "C" {
+/* fp_f2d_exact (float -> double on the integer pipe, used by the FP32
+   form's update) against the compiler's conversion, bit for bit: every
+   37th subnormal pattern of either sign, n random bit patterns (normal,
+   inf, NaN), and zeros, the extremes and the boundary of the normal
+   range.  Returns the mismatches (NaN: any NaN matches). */
+long f2d_exact_mismatches(int n, unsigned seed) {
+  long bad = 0;
+  auto chk = [&](float f) {
+    const double a = cgks::fp_f2d_exact(f), b = (double)f;
+    if (std::isnan(a) && std::isnan(b)) return;
+    if (std::memcmp(&a, &b, sizeof a) != 0) ++bad;
+  };
+  for (unsigned u = 0; u < 0x00800000u; u += 37) {
+    float f;
+    std::memcpy(&f, &u, 4);
+    chk(f);
+    chk(-f);
+  }
+  std::mt19937 rng(seed);
+  for (int i = 0; i < n; ++i) {
+    const unsigned u = rng();
+    float f;
+    std::memcpy(&f, &u, 4);
+    chk(f);
+  }
+  const float sp[] = {0.f, -0.f, INFINITY, -INFINITY, 1.f, -1.f, 1e-45f, -1e-45f, 3.4028235e38f, 1.17549435e-38f,
+                      1.1754942e-38f};
+  for (float f : sp) chk(f);
+  return bad;
 }
 }

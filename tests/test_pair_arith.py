@@ -76,3 +76,13 @@ def test_pair_reconstruction_conversions(lib, seed):
     print("split %.2e dot %.2e" % (e_split, e_dot))
     assert e_split <= 2.0 ** -47 * (1 + 2.0 ** -20) and overshoot == 0 and f2d_bad == 0 and special_bad == 0
     assert e_dot <= 2.0 ** -42
+
+
+def test_float_to_double_on_the_integer_pipe(lib):
+    """The FP32 form's update converts its FP32 face sums to FP64 by bit
+    operations (fp_f2d_exact) instead of the FP64 pipe's conversion: the
+    result is the same double, bit for bit, for every float kind (normal,
+    subnormal, zero, inf; NaN stays NaN)."""
+    lib.f2d_exact_mismatches.argtypes = [C.c_int, C.c_uint]
+    lib.f2d_exact_mismatches.restype = C.c_long
+    assert lib.f2d_exact_mismatches(2000000, 11) == 0
