@@ -1815,8 +1815,8 @@ CGKS_HD StageCoef stage_coef(double dt) {
 
 /* a stored value as double: floats exactly, on the integer pipe (the FP32
    form's update is bound by its FP64 pipe, which would convert them) */
+template <typename T> CGKS_HD double to_f64(const T& x) { return double(x); }
 CGKS_HD double to_f64(float x) { return fp_f2d_exact(x); }
-CGKS_HD double to_f64(double x) { return x; }
 
 template <typename T, int DIM, bool CURVI>
 CGKS_HD void update_var(const DevGeo& g, const StageCoef& kc, int stage, long c, int ci, int cj, int ck, int v,
