@@ -66,12 +66,15 @@ EXEC_FLOPS_PER_UNIT = {
 EXEC_FP32_FLOPS_PER_UNIT_PAIR = {
     ("flux", 3): 26580.0,
 }
+# DRAM bytes per face point of the three flux kernels as built (inputs
+# staged as TMA tiles), from one launch-level capture at TGV 64^3
+# (profiles/flux_dram_tgv64.md; read + write averaged over the launches)
 DRAM_BYTES_PER_UNIT_PAIR = {
-    ("flux", 3): (1.007367e9 + 0.735652e9) / (262144 * 12),
+    ("flux", 3): (1.0079e9 + 0.7331e9) / (262144 * 12),
 }
 # DRAM bytes per unit of the same capture (read + write), for `traffic`
 DRAM_BYTES_PER_UNIT = {
-    ("flux", 3): (1.0110e9 + 0.7142e9) / (262144 * 12),
+    ("flux", 3): (1.0084e9 + 0.7103e9) / (262144 * 12),
 }
 # the same for the FP32 form (update: per (cell, variable))
 EXEC_FLOPS_PER_UNIT_FP32 = {
@@ -81,7 +84,7 @@ EXEC_FLOPS_PER_UNIT_FP32 = {
 }
 DRAM_BYTES_PER_UNIT_FP32 = {
     ("recon", 3): (151.1e6 + 465.3e6) / 262144,
-    ("flux", 3): (503.4e6 + 337.0e6) / (262144 * 12),
+    ("flux", 3): (503.4e6 + 333.5e6) / (262144 * 12),
     ("update", 3): (388.5e6 + 159.3e6) / (262144 * 5),
 }
 
