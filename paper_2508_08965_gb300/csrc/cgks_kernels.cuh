@@ -222,9 +222,10 @@ __device__ __forceinline__ void flux_item(const DevGeo& g, const Phys& ph, doubl
    The Gauss-point states of the 128 face points of a flux block are, per
    stored quantity q, 128 consecutive values of one row of gpL (and of gpR)
    viewed as a 2-D array [row][cell] (row = (ax * GPF + k) * NQ + q): one
-   box of NQ rows x 128 cells each, which one thread loads with the tensor
-   memory accelerator (cp.async.bulk.tensor) into the block's staging tile
-   and the block waits for on a shared-memory barrier.  Requires a Cartesian
+   box of NQ rows x 128 cells each.  One thread loads both boxes with the
+   tensor memory accelerator (cp.async.bulk.tensor) into the block's
+   staging tile, and the block waits for them on a shared-memory barrier.
+   Requires a Cartesian
    mesh whose cell count is a multiple of 128 (a block's points then share
    (ax, k), its first cell is 16-byte aligned in every row, and the row
    pitch is a multiple of 16 bytes); other meshes stage by cp.async. */
