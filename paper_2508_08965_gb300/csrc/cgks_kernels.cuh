@@ -49,7 +49,7 @@ template <typename T, int DIM = 3> constexpr int min_blocks() { return sizeof(T)
    registers, no spill); the curvilinear ones, which spill more, keep 3.
    PR: the paired form's 3-D reconstruction runs 3 (168 registers; its
    812 B of spills cost less than the latency the extra warps hide: TGV
-   128^3 20.1 -> 19.4 ms per stage) */
+   128^3 20.1 -> 19.4 ms per stage; 4 blocks spill 2.2 KB: 20.1 ms) */
 template <typename T, int DIM, bool CURVI, bool PR = false> constexpr int recon_min_blocks() {
   return PR && DIM == 3 ? 3 : (sizeof(T) == 4 && DIM == 3 && !CURVI ? 4 : min_blocks<T, DIM>());
 }
