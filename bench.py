@@ -623,6 +623,8 @@ def main():
     head = 2 if args.form == "pair" else 0
     mesh, s_init, ms, prof, clk = timed_form(head)
     ncell = mesh.ncell
+    flux_staging = ("TMA tiles (cp.async.bulk.tensor)" if mesh.flux_staging == "tma" else
+                    "per-thread cp.async")
     value = replicas.whole_job_rate(ncell, args.steps, ms, world)
 
     # end to end through the C-ABI with host buffers: every step copies the
@@ -720,6 +722,7 @@ def main():
                             "48 bits); parity with the FP64 oracle at the FP64 bars" if head == 2 else
                             "FP64 throughout"),
                    "l2": "state (%.2f GB) larger than L2; no flush" % (state_bytes / 1e9),
+                   "flux_staging": flux_staging,
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": world * ncell * args.e2e_steps / ov_s, "unit": "cell-updates/s",
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes, "steps": args.e2e_steps,
