@@ -180,6 +180,20 @@ def fp32_alu_peak_tflops(sm_count=152, sm_mhz=2070.0):
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def step_hbm(ncell, dim, ms_per_step, peak_gbs):
+    """The step's share of HBM bandwidth on the algorithmic bytes of an S2O4
+    step: six state-sized transfers per cell (stage 1 reads U^n and writes
+    U* and the stash; stage 2 reads U* and the stash and writes U^{n+1}),
+    the FP64 state being (dim + 2) variables x (1 + dim + lines) fields.
+    A step-level figure: the sweep is bound by its arithmetic, so this is
+    small by design."""
+    nf = 1 + dim + (12 if dim == 3 else 4)
+    per_cell = 6 * 8 * (dim + 2) * nf
+    gbs = ncell * per_cell / (ms_per_step * 1e-3) / 1e9
+    return {"algorithmic_bytes_per_cell": per_cell, "achieved_gbs": gbs, "peak_gbs": peak_gbs,
+            "frac": (gbs / peak_gbs) if peak_gbs else None}
+
+
 def roofline(prof, spec, ncell, precision, viscous):
     """Roofline of the dominant kernel of a timed form: its algorithmic flops
     per unit (ALG_FLOPS_PER_UNIT) times the units of one launch, over its
@@ -739,6 +753,7 @@ def main():
         "roofline": roofline(prof, spec, ncell, head, viscous),
         "clocks": clk.summary(),
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
+        "hbm_step": step_hbm(ncell, spec["dim"], ms / args.steps, peaks.get("hbm_gbs")),
         "forms": forms,
     }
     if not args.no_selector:

@@ -76,3 +76,14 @@ def test_roofline_fp32_flux(bench):
     assert r["flops_per_launch"] == pytest.approx(2919.0 * n * 12)
     assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
     assert r["frac_executed"] == pytest.approx(3.395e3 * n * 12 / 1e-3 / 1e12 / r["peak"])
+
+
+def test_step_hbm_share(bench):
+    """the step-level HBM share counts six FP64 state transfers per cell
+    (SURVEY-style algorithmic bytes: 3.84 KB per 3-D cell, 1.34 KB in 2-D)"""
+    r = bench.step_hbm(2097152, 3, 135.0, 6691.1)
+    assert r["algorithmic_bytes_per_cell"] == 6 * 640
+    assert r["achieved_gbs"] == pytest.approx(2097152 * 3840 / 0.135 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved_gbs"] / 6691.1)
+    assert bench.step_hbm(4096, 2, 1.0, None)["algorithmic_bytes_per_cell"] == 6 * 224
+    assert bench.step_hbm(4096, 2, 1.0, None)["frac"] is None
