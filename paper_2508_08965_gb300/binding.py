@@ -225,7 +225,9 @@ class Mesh:
     None for torch's current stream at construction time).  precision 0 is
     FP64 throughout; 1 runs reconstruction, interface flux and weights in
     FP32 with FP64 cell averages and metrics; 2 is FP64 with the interface
-    flux solved in paired-FP32 arithmetic.
+    flux solved in paired-FP32 arithmetic.  ``flux_staging`` says how the
+    interface-flux kernel stages its inputs ("tma" or "cp.async";
+    cgks_flux_staging).
     """
 
     def __init__(self, dim, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nodes=None, gamma=1.4, mu=0.0,
