@@ -34,3 +34,19 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*|/\*.*?\*/", "", src, flags=re.S), f
+
+
+def test_header_is_plain_c():
+    """include/cgks.h compiles as C11 (plain pointers and sizes, no C++ in
+    the signatures) and as C++"""
+    import shutil
+    import subprocess
+    import pytest
+    hdr = os.path.join(ROOT, "include", "cgks.h")
+    gcc, gxx = shutil.which("gcc"), shutil.which("g++")
+    if gcc is None or gxx is None:
+        pytest.skip("no host compiler")
+    for cmd in ([gcc, "-fsyntax-only", "-std=c11", "-Wall", "-Werror", "-x", "c", hdr],
+                [gxx, "-fsyntax-only", "-std=c++17", "-Wall", "-Werror", "-x", "c++", hdr]):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
