@@ -68,6 +68,7 @@ def test_null_arguments(cg):
     assert L.cgks_set_state(None, None, 0, 0.0) == EINVAL
     assert L.cgks_get_state(None, None, 0, None) == EINVAL
     assert L.cgks_step(None, 1, 0.0, None, None) == EINVAL
+    assert L.cgks_flux_staging(None) == -1
 
 
 def test_batch_rejects_mixed_and_invalid_cases(cg):
